@@ -1,0 +1,540 @@
+"""FP64 CPU oracle of the fully implicit water/oil/polymer model.
+
+Test infrastructure only: ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module; the product path
+never does.
+
+Everything is written from the paper's equations (arXiv 1807.05298):
+
+  rock        phi(P) = phi_r + c_r (P - P_r)                       (Sec. 2.1)
+  closure     S_w + S_o = 1, P_c = P_o - P_w                       (Sec. 2.2)
+  Darcy       phase mass flux  k k_r rho / mu  grad(P - gamma Z)   (Sec. 2.2)
+  oil, water  d/dt(phi S rho) = div(...) + q                       (Sec. 2.2)
+  polymer     d/dt(phi S_w rho_w C + (1 - phi) A_d) = div(...) + q_w C  (Sec. 2.3)
+  R_k         1 + (RRF - 1) A_d / A_d,max                          (Sec. 2.3)
+  viscosity   Todd-Longstaff mu_p,e, mu_w,partial, mu_w,e; linear or
+              nonlinear mixing rule in beta = C / C_ref             (Sec. 2.3)
+  wells       Peaceman index, eq. (wi), (wi:re:k); perforation rate
+              eq. (ssw:Q); hydrostatic wellbore eq. (ssw:dp); BHP and
+              rate constraints                                      (Sec. 2.4)
+  time        backward Euler                                       (Sec. 3.1)
+  space       two-point transmissibility, harmonic k and geometry,
+              pore-volume weighted rho and mu, upstream k_r          (Sec. 3.2)
+  Newton      Algorithm 1 with forcing term eq. (fterm), third form (Sec. 3.3)
+
+Where the paper is silent the following readings are taken (the CUDA path
+takes the same ones):
+  * rho_a(P_a) = rho_a,ref (1 + c_a (P_a - P_ref)); formation volume factor 1.
+  * C is kg of polymer per m^3 of water at reference conditions, so polymer
+    mass per unit water volume is rho_w C / rho_w,ref; A_d is kg per m^3 of
+    rock; the polymer well source is q_w C / rho_w,ref.
+  * inaccessible pore volume: polymer sees the fraction (1 - IPV) of the
+    water-filled pore space in the accumulation term; the flux is unchanged.
+  * Todd-Longstaff alpha = clip(C / C_ref, 0, 1).
+  * face averages of rho and mu weight the two cells by their reference pore
+    volumes V phi_r; k_r, R_k and the polymer concentration of a face come
+    from the upstream cell of the water (or oil) potential; for the face
+    (L, H) with H the higher natural index, H is upstream iff
+    Phi_H - Phi_L >= 0, where Phi_H - Phi_L = (P_H - P_L) - rho_bar g (Z_H - Z_L)
+    and Z is depth (positive downward).
+  * Langmuir adsorption A_d = a C / (1 + b C), A_d,max = a / b.
+  * Corey k_rw = krw_max Sn^nw, k_ro = kro_max (1 - Sn)^no,
+    Sn = (S - Swc) / (1 - Swc - Sor), clipped to [0, 1] (derivative of the
+    interior formula on the closed interval, 0 outside);
+    P_c = pc_e (1 - Sn)^pc_n.
+  * injector perforations use the cell's total mobility and rho_w; producer
+    perforations use phase mobilities; water phase flow is driven by P_w.
+  * gamma_well is evaluated at the start of the step and frozen: rho_w(P_b) g
+    for an injector, the mobility-weighted perforation mixture density times
+    g for a producer.
+  * residuals are masses [kg]; a BHP well row is dt * W (P_b - target) with
+    W = sum(WI) rho_w,ref / mu_w; a rate row is dt (sum of signed phase mass
+    rates - rho_ref * target).
+  * Newton update: S change per cell chopped to +-ds_max, then S clipped to
+    [0, 1] and C to >= 0.
+"""
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import dual as D
+from .dual import Dual
+
+NPHASE = 3  # rows per cell: oil, water, polymer; columns P_o, S_w, C
+
+
+# ---------------------------------------------------------------------------
+# set-up: geometry, transmissibility and well index
+# ---------------------------------------------------------------------------
+
+def faces(nx, ny, nz):
+    """Interior faces per direction as (L, H) natural-index arrays, H = L + stride."""
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    out = {}
+    out["x"] = (idx[:, :, :-1].ravel(), idx[:, :, 1:].ravel())
+    out["y"] = (idx[:, :-1, :].ravel(), idx[:, 1:, :].ravel())
+    out["z"] = (idx[:-1, :, :].ravel(), idx[1:, :, :].ravel())
+    return out
+
+
+def transmissibility(sc):
+    """Geometric transmissibility per face: area over the harmonic sum of the
+    two half-cell resistances, A / (dd/(2 k_L) + dd/(2 k_H))  (Sec. 3.2)."""
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    dx, dy, dz = sc["dx"], sc["dy"], sc["dz"]
+    f = faces(nx, ny, nz)
+    geo = {"x": (dy * dz, dx, sc["kx"]), "y": (dx * dz, dy, sc["ky"]), "z": (dx * dy, dz, sc["kz"])}
+    T = {}
+    for d, (L, H) in f.items():
+        area, dd, k = geo[d]
+        T[d] = area / (dd / (2.0 * k[L]) + dd / (2.0 * k[H]))
+    return f, T
+
+
+def cell_depth(sc):
+    nz = sc["nz"]
+    zc = sc["top"] + (np.arange(nz) + 0.5) * sc["dz"]
+    return np.repeat(zc, sc["nx"] * sc["ny"])
+
+
+def peaceman_wi(kx, ky, kz, dx, dy, dz, direction, rw, skin, gf=0.249, f=1.0, fh=1.0):
+    """Well index, eq. (wi) with r_e and k_a from eq. (wi:re:k).
+
+    The printed form is for a well along x (perpendicular directions y, z);
+    a well along y or z uses the same expression with the two directions
+    perpendicular to it."""
+    if direction == "x":
+        k1, k2, h1, h2, h = ky, kz, dy, dz, dx
+    elif direction == "y":
+        k1, k2, h1, h2, h = kx, kz, dx, dz, dy
+    else:
+        k1, k2, h1, h2, h = kx, ky, dx, dy, dz
+    # eq. (wi:re:k) with (y, z) -> (1, 2)
+    re = (2.0 * gf / math.sqrt(math.pi)) * math.sqrt(math.sqrt(k2 / k1) * h1 ** 2 + math.sqrt(k1 / k2) * h2 ** 2) \
+        / ((k2 / k1) ** 0.25 + (k1 / k2) ** 0.25)
+    ka = math.sqrt(k1 * k2)
+    return 2.0 * math.pi * f * h * fh * ka / (math.log(re / rw) + skin)
+
+
+class Setup:
+    """Static per-scenario data derived from the scenario dict."""
+
+    def __init__(self, sc):
+        self.sc = sc
+        self.ph = sc["physics"]
+        self.nx, self.ny, self.nz = sc["nx"], sc["ny"], sc["nz"]
+        self.n = self.nx * self.ny * self.nz
+        self.V = sc["dx"] * sc["dy"] * sc["dz"]
+        self.phi_r = sc["phi"]
+        self.Z = cell_depth(sc)
+        self.faces, self.T = transmissibility(sc)
+        self.wells = []
+        for w in sc["wells"]:
+            cells = np.asarray(w["cells"], dtype=np.int64)
+            wi = np.array([peaceman_wi(sc["kx"][c], sc["ky"][c], sc["kz"][c], sc["dx"], sc["dy"], sc["dz"],
+                                       d, w["rw"], w["skin"], w["gf"], w["f"], w["fh"])
+                           for c, d in zip(cells, w["dirs"])])
+            self.wells.append(dict(kind=w["kind"], cells=cells, WI=wi, z=self.Z[cells],
+                                   zb=self.Z[cells[0]],
+                                   W=float(wi.sum()) * self.ph["rho_w"] / self.ph["mu_w"]))
+        self.nw = len(self.wells)
+        self.nunk = NPHASE * self.n + self.nw
+
+
+# ---------------------------------------------------------------------------
+# cell properties (Sec. 2.1 - 2.3), generic in float arrays or Dual
+# ---------------------------------------------------------------------------
+
+def _clip01_dual(x):
+    x = D.where(x.v < 0.0, 0.0, x)
+    return D.where(x.v > 1.0, 1.0, x)
+
+
+def cell_properties(ph, phi_r, P, S, C):
+    """All per-cell quantities as Duals in the cell's own (P, S, C)."""
+    phi = phi_r + ph["c_r"] * (P - ph["p_r"])                       # porosity law
+    rho_o = ph["rho_o"] * (1.0 + ph["c_o"] * (P - ph["p_ref"]))
+    sn = _clip01_dual((S - ph["swc"]) / (1.0 - ph["swc"] - ph["sor"]))
+    krw = ph["krw_max"] * (sn ** ph["nw"])
+    kro = ph["kro_max"] * ((1.0 - sn) ** ph["no"])
+    if ph["pc_e"] != 0.0:
+        pc = ph["pc_e"] * ((1.0 - sn) ** ph["pc_n"])
+    else:
+        pc = Dual.const(np.zeros_like(P.v), P.k)
+    Pw = P - pc                                                      # P_c = P_o - P_w
+    rho_w = ph["rho_w"] * (1.0 + ph["c_w"] * (Pw - ph["p_ref"]))
+    ads = ph["ads_a"] * C / (1.0 + ph["ads_b"] * C)                  # Langmuir A_d(C)
+    ads_max = ph["ads_a"] / ph["ads_b"]
+    if ads_max > 0.0:                                                # permeability reduction
+        Rk = 1.0 + (ph["rrf"] - 1.0) * ads / ads_max
+    else:                                                            # no adsorption: R_k = 1
+        Rk = Dual.const(np.ones_like(P.v), P.k)
+    beta = C / ph["c_ref"]
+    if ph["mixing"] == 0:                    # nonlinear rule mu_p0^beta mu_w^(1-beta)
+        mu_m = D.exp(beta * math.log(ph["mu_p0"]) + (1.0 - beta) * math.log(ph["mu_w"]))
+    else:                                                            # linear rule
+        mu_m = beta * ph["mu_p0"] + (1.0 - beta) * ph["mu_w"]
+    om = ph["omega"]
+    mu_pe = (mu_m ** om) * (ph["mu_p0"] ** (1.0 - om))                # Todd-Longstaff
+    mu_wp = (mu_m ** om) * (ph["mu_w"] ** (1.0 - om))
+    alpha = _clip01_dual(C / ph["c_ref"])
+    mu_we = 1.0 / (alpha / mu_pe + (1.0 - alpha) / mu_wp)
+    return dict(phi=phi, rho_o=rho_o, rho_w=rho_w, krw=krw, kro=kro, Pw=Pw, ads=ads, Rk=Rk,
+                mu_pe=mu_pe, mu_we=mu_we, S=S, C=C, P=P)
+
+
+def accumulation(st, ph, pr):
+    """Component masses per cell [kg]: oil, water, polymer (Sec. 2.2, 2.3)."""
+    V = st.V
+    Mo = V * pr["phi"] * pr["rho_o"] * (1.0 - pr["S"])
+    Mw = V * pr["phi"] * pr["rho_w"] * pr["S"]
+    Mp = V * (1.0 - ph["ipv"]) * pr["phi"] * pr["S"] * pr["rho_w"] * pr["C"] / ph["rho_w"] \
+        + V * (1.0 - pr["phi"]) * pr["ads"]
+    return Mo, Mw, Mp
+
+
+def _cell_duals(st, x):
+    P = Dual.variable(x[0::3][: st.n], 3, 0)
+    S = Dual.variable(x[1::3][: st.n], 3, 1)
+    C = Dual.variable(x[2::3][: st.n], 3, 2)
+    return P, S, C
+
+
+def unpack(st, x):
+    n = st.n
+    xc = x[: 3 * n]
+    return xc[0::3], xc[1::3], xc[2::3], x[3 * n:]
+
+
+# ---------------------------------------------------------------------------
+# face fluxes (Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def face_fluxes(st, pr, L, H, T, dZ):
+    """Mass fluxes from H into L for oil, water, polymer as Duals in
+    (x_L, x_H) (6 derivative columns)."""
+    ph = st.ph
+    g = ph["g"]
+    w_L = st.phi_r[L] / (st.phi_r[L] + st.phi_r[H])
+    w_H = 1.0 - w_L
+
+    def lift(q):
+        a = q.take(L).embed(6, 0)
+        b = q.take(H).embed(6, 3)
+        return a, b
+
+    def avg(q):
+        a, b = lift(q)
+        return a * w_L + b * w_H
+
+    def upstream(q, up_H):
+        a, b = lift(q)
+        return D.where(up_H, b, a)
+
+    rho_o = avg(pr["rho_o"])
+    rho_w = avg(pr["rho_w"])
+    mu_we = avg(pr["mu_we"])
+    mu_pe = avg(pr["mu_pe"])
+    PL, PH = lift(pr["P"])
+    PwL, PwH = lift(pr["Pw"])
+    dPhi_o = (PH - PL) - rho_o * (g * dZ)
+    dPhi_w = (PwH - PwL) - rho_w * (g * dZ)
+    up_o = dPhi_o.v >= 0.0
+    up_w = dPhi_w.v >= 0.0
+    kro = upstream(pr["kro"], up_o)
+    krw = upstream(pr["krw"], up_w)
+    Rk = upstream(pr["Rk"], up_w)
+    Cu = upstream(pr["C"], up_w)
+    Fo = T * (kro / ph["mu_o"]) * rho_o * dPhi_o
+    Fw = T * (krw / (Rk * mu_we)) * rho_w * dPhi_w
+    Fp = T * (krw / (Rk * mu_pe)) * rho_w * dPhi_w * Cu / ph["rho_w"]
+    return Fo, Fw, Fp
+
+
+# ---------------------------------------------------------------------------
+# wells (Sec. 2.4)
+# ---------------------------------------------------------------------------
+
+def well_gamma(st, x, controls):
+    """Wellbore fluid unit weight per well at the state x (frozen over a step)."""
+    ph = st.ph
+    P, S, C, Pb = unpack(st, x)
+    pr = cell_properties(ph, st.phi_r, *_cell_duals(st, x))
+    out = np.zeros(st.nw)
+    for w, (wl, ctl) in enumerate(zip(st.wells, controls)):
+        if wl["kind"] == "inj":
+            out[w] = ph["g"] * ph["rho_w"] * (1.0 + ph["c_w"] * (Pb[w] - ph["p_ref"]))
+        else:
+            c = wl["cells"]
+            lw = pr["krw"].v[c] / (pr["Rk"].v[c] * pr["mu_we"].v[c])
+            lo = pr["kro"].v[c] / ph["mu_o"]
+            lt = float(np.sum(lw + lo))
+            if lt > 0.0:
+                out[w] = ph["g"] * float(np.sum(lw * pr["rho_w"].v[c] + lo * pr["rho_o"].v[c])) / lt
+            else:
+                out[w] = ph["g"] * float(pr["rho_o"].v[c[0]])
+    return out
+
+
+RATE_COEF = {  # control, kind -> (s_w, s_o, reference density key)
+    ("wrate", "inj"): (1.0, 0.0, "rho_w"),
+    ("wrate", "prod"): (-1.0, 0.0, "rho_w"),
+    ("orate", "prod"): (0.0, -1.0, "rho_o"),
+    ("lrate", "prod"): (-1.0, None, "rho_w"),   # s_o = -rho_w,ref / rho_o,ref
+}
+
+
+def rate_coefficients(ph, ctrl, kind):
+    s_w, s_o, key = RATE_COEF[(ctrl, kind)]
+    if s_o is None:
+        s_o = -ph["rho_w"] / ph["rho_o"]
+    return s_w, s_o, ph[key]
+
+
+def perforation_rates(st, pr, w, Pb_w, gamma_w, c_inj):
+    """Phase mass rates (water, oil, polymer) into the perforated cells of
+    well w, eq. (ssw:Q) with eq. (ssw:dp); Duals in (x_cell, P_b): 4 columns."""
+    ph = st.ph
+    wl = st.wells[w]
+    c = wl["cells"]
+    m = len(c)
+
+    def cellq(q):
+        return q.take(c).embed(4, 0)
+
+    Pb = Dual(np.full(m, Pb_w), np.tile(np.array([0.0, 0.0, 0.0, 1.0]), (m, 1)))
+    Pbm = Pb + gamma_w * (wl["z"] - wl["zb"])
+    krw, kro, Rk, mu_we = cellq(pr["krw"]), cellq(pr["kro"]), cellq(pr["Rk"]), cellq(pr["mu_we"])
+    rho_w, rho_o, P, Pw, C = cellq(pr["rho_w"]), cellq(pr["rho_o"]), cellq(pr["P"]), cellq(pr["Pw"]), cellq(pr["C"])
+    lam_w = krw / (Rk * mu_we)
+    lam_o = kro / ph["mu_o"]
+    WI = wl["WI"]
+    if wl["kind"] == "inj":
+        qw = WI * (lam_w + lam_o) * rho_w * (Pbm - Pw)
+        qo = Dual.const(np.zeros(m), 4)
+        qp = qw * (c_inj / ph["rho_w"])
+    else:
+        qw = WI * lam_w * rho_w * (Pbm - Pw)
+        qo = WI * lam_o * rho_o * (Pbm - P)
+        qp = qw * C / ph["rho_w"]
+    return qw, qo, qp
+
+
+# ---------------------------------------------------------------------------
+# residual and Jacobian
+# ---------------------------------------------------------------------------
+
+def assemble(st, x, M_old, dt, controls, gamma, with_jacobian=True):
+    """Residual R (length 3N + W) and sparse Jacobian dR/dx at the state x.
+
+    Cell rows: R = M(x) - M^n - dt (sum of face inflows + well sources)
+    (backward Euler, Sec. 3.1).  Well rows: the active constraint."""
+    n, ph = st.n, st.ph
+    P, S, C = _cell_duals(st, x)
+    pr = cell_properties(ph, st.phi_r, P, S, C)
+    Mo, Mw, Mp = accumulation(st, ph, pr)
+    R = np.zeros(st.nunk)
+    R[0:3 * n:3] = Mo.v - M_old[0]
+    R[1:3 * n:3] = Mw.v - M_old[1]
+    R[2:3 * n:3] = Mp.v - M_old[2]
+    rows, cols, vals = [], [], []
+    cell = np.arange(n)
+
+    def add_block(rblk, cblk, blk):
+        # blk: (m, 3, 3) derivative blocks d R[3 rblk + a] / d x[3 cblk + b]
+        a = np.arange(3)
+        rows.append((3 * rblk[:, None, None] + a[None, :, None]).repeat(3, axis=2).ravel())
+        cols.append((3 * cblk[:, None, None] + a[None, None, :]).repeat(3, axis=1).ravel())
+        vals.append(blk.ravel())
+
+    if with_jacobian:
+        add_block(cell, cell, np.stack([Mo.d, Mw.d, Mp.d], axis=1))
+
+    for d, (L, H) in st.faces.items():
+        if L.size == 0:
+            continue
+        dZ = st.Z[H] - st.Z[L]
+        Fo, Fw, Fp = face_fluxes(st, pr, L, H, st.T[d], dZ)
+        F = np.stack([Fo.v, Fw.v, Fp.v], axis=1)      # (f, 3) H -> L
+        np.add.at(R, 3 * L[:, None] + np.arange(3), -dt * F)
+        np.add.at(R, 3 * H[:, None] + np.arange(3), dt * F)
+        if with_jacobian:
+            dF = np.stack([Fo.d, Fw.d, Fp.d], axis=1)  # (f, 3, 6)
+            dL, dH = dF[:, :, :3], dF[:, :, 3:]
+            add_block(L, L, -dt * dL)
+            add_block(L, H, -dt * dH)
+            add_block(H, L, dt * dL)
+            add_block(H, H, dt * dH)
+
+    Pb = x[3 * n:]
+    for w, wl in enumerate(st.wells):
+        ctl = controls[w]
+        qw, qo, qp = perforation_rates(st, pr, w, Pb[w], gamma[w], ctl["c_inj"])
+        c = wl["cells"]
+        q = np.stack([qo.v, qw.v, qp.v], axis=1)       # rows ordered oil, water, polymer
+        np.add.at(R, 3 * c[:, None] + np.arange(3), -dt * q)
+        wrow = 3 * n + w
+        if ctl["ctrl"] == "bhp":
+            R[wrow] = dt * wl["W"] * (Pb[w] - ctl["target"])
+        else:
+            s_w, s_o, rho_t = rate_coefficients(ph, ctl["ctrl"], wl["kind"])
+            R[wrow] = dt * (s_w * qw.v.sum() + s_o * qo.v.sum() - rho_t * ctl["target"])
+        if with_jacobian:
+            dq = np.stack([qo.d, qw.d, qp.d], axis=1)   # (m, 3, 4)
+            add_block(c, c, -dt * dq[:, :, :3])
+            for r in range(3):                         # d R_cell / d P_b
+                rows.append(3 * c + r)
+                cols.append(np.full(len(c), wrow))
+                vals.append(-dt * dq[:, r, 3])
+            if ctl["ctrl"] == "bhp":
+                rows.append(np.array([wrow])); cols.append(np.array([wrow]))
+                vals.append(np.array([dt * wl["W"]]))
+            else:
+                dsum = s_w * qw.d + s_o * qo.d             # (m, 4)
+                for b in range(3):
+                    rows.append(np.full(len(c), wrow)); cols.append(3 * c + b)
+                    vals.append(dt * dsum[:, b])
+                rows.append(np.array([wrow])); cols.append(np.array([wrow]))
+                vals.append(np.array([dt * dsum[:, 3].sum()]))
+    if not with_jacobian:
+        return R, None
+    J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(st.nunk, st.nunk)).tocsr()
+    J.sum_duplicates()
+    return R, J
+
+
+def masses(st, x):
+    P, S, C = _cell_duals(st, x)
+    pr = cell_properties(st.ph, st.phi_r, P, S, C)
+    Mo, Mw, Mp = accumulation(st, st.ph, pr)
+    return np.stack([Mo.v, Mw.v, Mp.v])
+
+
+def scaled_residual(st, R, dt, controls):
+    """Max-norm of the residual in dimensionless units: cell rows over
+    V phi_r rho_ref (polymer over V phi_r C_ref), rate rows over
+    dt rho_ref |target|, BHP rows over dt W * 1 bar."""
+    n, ph = st.n, st.ph
+    pv = st.V * st.phi_r
+    s = np.abs(R[0:3 * n:3]) / (pv * ph["rho_o"])
+    s = np.maximum(s, np.abs(R[1:3 * n:3]) / (pv * ph["rho_w"]))
+    s = np.maximum(s, np.abs(R[2:3 * n:3]) / (pv * ph["c_ref"]))
+    out = float(s.max()) if n else 0.0
+    for w, wl in enumerate(st.wells):
+        ctl = controls[w]
+        if ctl["ctrl"] == "bhp":
+            sc = dt * wl["W"] * 1.0e5
+        else:
+            _, _, rho_t = rate_coefficients(ph, ctl["ctrl"], wl["kind"])
+            sc = dt * rho_t * max(abs(ctl["target"]), 1e-30)
+        out = max(out, abs(R[3 * n + w]) / sc)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Newton (Algorithm 1) and the forcing term eq. (fterm)
+# ---------------------------------------------------------------------------
+
+GOLDEN = (math.sqrt(5.0) + 1.0) / 2.0
+
+
+def forcing_term(norm_b, norm_b_prev, gamma=0.5, beta=GOLDEN, lo=0.01, hi=0.1):
+    """Third choice of eq. (fterm), restricted to [0.01, 0.1]; the first
+    iteration (no previous norm) takes the upper bound."""
+    if norm_b_prev is None or norm_b_prev <= 0.0:
+        return hi
+    eta = gamma * (norm_b / norm_b_prev) ** beta
+    return min(max(eta, lo), hi)
+
+
+def update(st, x, dx, ds_max):
+    n = st.n
+    y = x.copy()
+    y[0:3 * n:3] += dx[0:3 * n:3]
+    ds = np.clip(dx[1:3 * n:3], -ds_max, ds_max)
+    y[1:3 * n:3] = np.clip(x[1:3 * n:3] + ds, 0.0, 1.0)
+    y[2:3 * n:3] = np.maximum(x[2:3 * n:3] + dx[2:3 * n:3], 0.0)
+    y[3 * n:] += dx[3 * n:]
+    return y
+
+
+def solve_linear(J, b):
+    """Direct sparse solve of J x = b (the plain definition of the Newton
+    correction); a library LU serves as the step."""
+    return spla.spsolve(J.tocsc(), b)
+
+
+def initial_state(st):
+    sc = st.sc
+    x = np.empty(st.nunk)
+    x[0:3 * st.n:3] = sc["P0"]
+    x[1:3 * st.n:3] = sc["S0"]
+    x[2:3 * st.n:3] = sc["C0"]
+    x[3 * st.n:] = [w["Pb0"] for w in sc["wells"]]
+    return x
+
+
+def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, record=None):
+    """One backward-Euler step by Newton's method (Algorithm 1).
+
+    Returns (x_new, converged, iterations)."""
+    M_old = masses(st, x_old)
+    gamma = well_gamma(st, x_old, controls)
+    x = x_old.copy()
+    for it in range(max_iter + 1):
+        R, J = assemble(st, x, M_old, dt, controls, gamma)
+        res = scaled_residual(st, R, dt, controls)
+        if record is not None:
+            record.append(res)
+        if res <= tol:
+            return x, True, it
+        if it == max_iter or not np.all(np.isfinite(R)):
+            break
+        dx = solve_linear(J, -R)
+        x = update(st, x, dx, ds_max)
+    return x_old, False, max_iter
+
+
+def controls_with_defaults(controls):
+    return [dict(c) for c in controls]
+
+
+def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, callback=None):
+    """Time loop over the scenario schedule with fixed steps; on a Newton
+    failure the step is cut in half and retried (Sec. 3, step 4(a))."""
+    st = Setup(sc)
+    x = initial_state(st)
+    t = 0.0
+    history = []
+    done = 0
+    for period in sc["schedule"]:
+        ctl = controls_with_defaults(period["controls"])
+        for _ in range(period["n_steps"]):
+            if n_steps is not None and done >= n_steps:
+                return st, x, history
+            dt_left = period["dt"]
+            dt = dt_left
+            cuts = 0
+            newton_total = 0
+            while dt_left > 0.0:
+                dt = min(dt, dt_left)
+                xn, ok, its = newton_step(st, x, dt, ctl, tol=tol, max_iter=max_iter, ds_max=ds_max)
+                newton_total += its
+                if ok:
+                    x = xn
+                    t += dt
+                    dt_left -= dt
+                else:
+                    cuts += 1
+                    if cuts > max_cuts:
+                        raise RuntimeError("time step cut limit reached")
+                    dt = 0.5 * dt
+            done += 1
+            history.append(dict(t=t, x=x.copy(), newton=newton_total, cuts=cuts))
+            if callback is not None:
+                callback(st, x, history[-1])
+    return st, x, history

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against closed forms, invariants and independent
+computations (no GPU).  Each test names the paper passage it pins.
+
+A plausible slip in the oracle -- a dropped term, a wrong sign or index, a
+transposed operand -- is meant to fail at least one of these.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from oracle.linalg import lu_solve_dense
+from scenarios import generate as G
+
+DAY, BAR, MD, CP = G.DAY, G.BAR, G.MD, G.CP
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def one_d(n, L=1000.0, area=100.0, phi=0.2, perm_md=100.0, physics=None, q_day=20.0,
+          c_inj=0.0, s0=None, c0=0.0, dt_days=1.0, n_steps=10, bhp=200.0 * BAR, perm=None):
+    side = math.sqrt(area)
+    dx = L / n
+    k = np.full(n, perm_md * MD) if perm is None else perm
+    wells = [dict(kind="inj", cells=[0]), dict(kind="prod", cells=[n - 1])]
+    ctl = [dict(ctrl="wrate", target=q_day / DAY, limit=None, c_inj=c_inj),
+           dict(ctrl="bhp", target=bhp, limit=None, c_inj=0.0)]
+    sched = [dict(n_steps=n_steps, dt=dt_days * DAY, controls=ctl)]
+    return G.make_scenario(n, 1, 1, dx, side, side, 1000.0, k, k, k, np.full(n, phi), physics,
+                           wells, sched, p_top=200.0 * BAR, s0=s0, c0=c0)
+
+
+def incompressible(**over):
+    base = dict(c_w=0.0, c_o=0.0, c_r=0.0, g=0.0, pc_e=0.0)
+    base.update(over)
+    return G.default_physics(**base)
+
+
+def field(st, x, comp):
+    return x[comp:3 * st.n:3]
+
+
+# ---------------------------------------------------------------------------
+# Buckley-Leverett waterflood (Sec. 2.2 flow equations, Sec. 3.2 upstream k_r)
+# ---------------------------------------------------------------------------
+
+def _fractional_flow(ph):
+    def f(S):
+        sn = np.clip((S - ph["swc"]) / (1.0 - ph["swc"] - ph["sor"]), 0.0, 1.0)
+        lw = sn ** ph["nw"] / ph["mu_w"]
+        lo = (1.0 - sn) ** ph["no"] / ph["mu_o"]
+        return lw / (lw + lo)
+
+    def df(S, h=1e-7):
+        return (f(S + h) - f(S - h)) / (2.0 * h)
+
+    return f, df
+
+
+def welge_profile(ph, x, t, u, phi):
+    """Self-similar Buckley-Leverett saturation with the Welge tangent front."""
+    f, df = _fractional_flow(ph)
+    si, smax = ph["swc"], 1.0 - ph["sor"]
+    lo, hi = si + 1e-6, smax - 1e-9
+    g = lambda s: df(s) * (s - si) - f(s)
+    for _ in range(200):                      # g > 0 below the tangent point
+        mid = 0.5 * (lo + hi)
+        if g(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    sf = 0.5 * (lo + hi)
+    xf = u * t * df(sf) / phi
+    out = np.full_like(x, si)
+    for i, xi in enumerate(x):
+        if xi < xf:
+            a, b = sf, smax                       # df decreasing on [sf, smax]
+            for _ in range(100):
+                mid = 0.5 * (a + b)
+                if u * t * df(mid) / phi > xi:
+                    a = mid
+                else:
+                    b = mid
+            out[i] = 0.5 * (a + b)
+    return out, sf, xf
+
+
+@pytest.mark.slow
+def test_buckley_leverett_front_and_refinement():
+    ph = incompressible(mu_w=1.0 * CP, mu_o=2.0 * CP, ads_a=0.0, rrf=1.0, ipv=0.0, mu_p0=1.0 * CP)
+    t_end = 150.0
+    errs, fronts = [], []
+    for n, dt in [(50, 2.0), (200, 0.5)]:
+        sc = one_d(n, physics=ph, dt_days=dt, n_steps=int(round(t_end / dt)))
+        st, x, hist = M.run(sc)
+        S = field(st, x, 1)
+        dx = 1000.0 / n
+        xc = (np.arange(n) + 0.5) * dx
+        u = 20.0 / DAY / 100.0
+        Sex, sf, xf = welge_profile(ph, xc, t_end * DAY, u, 0.2)
+        errs.append(np.sum(np.abs(S - Sex)) * dx / 1000.0)
+        mid = 0.5 * (sf + ph["swc"])
+        i = int(np.nonzero(S < mid)[0][0])
+        x_mid = xc[i - 1] + (S[i - 1] - mid) / (S[i - 1] - S[i]) * dx
+        fronts.append((x_mid, xf, dx))
+    assert errs[1] < 0.7 * errs[0], errs
+    for x_mid, xf, dx in fronts:
+        assert abs(x_mid - xf) < max(3.0 * dx, 0.03 * xf), (x_mid, xf, dx)
+
+
+# ---------------------------------------------------------------------------
+# polymer shock speed (Sec. 2.3 polymer equation, adsorption, IPV)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ads_a", [0.0, 0.05])
+def test_polymer_front_rankine_hugoniot(ads_a):
+    ph = incompressible(swc=0.0, sor=0.0, ads_a=ads_a, ads_b=10.0, ipv=0.1, rrf=1.5,
+                        mu_w=1.0 * CP, mu_p0=4.0 * CP, c_ref=2.0)
+    n, t_end, dt = 200, 150.0, 0.5
+    sc = one_d(n, physics=ph, q_day=20.0, c_inj=1.0, s0=1.0, c0=0.0, dt_days=dt,
+               n_steps=int(round(t_end / dt)))
+    st, x, hist = M.run(sc)
+    C = field(st, x, 2)
+    phi, u, cin = 0.2, 20.0 / DAY / 100.0, 1.0
+    ads = ads_a * cin / (1.0 + 10.0 * cin)
+    vs = u * cin / (phi * (1.0 - 0.1) * cin + (1.0 - phi) * ads)
+    xs = vs * t_end * DAY
+    dx = 1000.0 / n
+    xc = (np.arange(n) + 0.5) * dx
+    i = int(np.nonzero(C < 0.5 * cin)[0][0])
+    x_half = xc[i - 1] + (C[i - 1] - 0.5 * cin) / (C[i - 1] - C[i]) * dx
+    assert abs(x_half - xs) < 3.0 * dx, (x_half, xs)
+    assert np.allclose(field(st, x, 1), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Darcy series resistance (Darcy's law Sec. 2.2, harmonic averaging Sec. 3.2,
+# R_k and mixing rule Sec. 2.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mixing,omega", [(0, 1.0), (1, 1.0)])
+def test_darcy_pressure_drop_series(mixing, omega):
+    c_ref, mu_w, mu_p0, rrf = 2.0, 1.0 * CP, 9.0 * CP, 2.2
+    ph = incompressible(swc=0.0, sor=0.0, ads_a=0.3, ads_b=1.0, ipv=0.1, rrf=rrf, mu_w=mu_w,
+                        mu_p0=mu_p0, c_ref=c_ref, mixing=mixing, omega=omega)
+    n = 12
+    rng = np.random.default_rng(5)
+    perm = np.exp(rng.normal(math.log(100.0), 0.8, n)) * MD
+    C = 1.0                                    # beta = 1/2 and b C = 1
+    sc = one_d(n, physics=ph, q_day=30.0, c_inj=C, s0=1.0, c0=C, n_steps=1, perm=perm)
+    st, x, _ = M.run(sc)
+    P = field(st, x, 0)
+    mu = math.sqrt(mu_p0 * mu_w) if mixing == 0 else 0.5 * (mu_p0 + mu_w)
+    Rk = 1.0 + (rrf - 1.0) * 0.5               # A_d / A_d,max = bC / (1 + bC) = 1/2
+    q, A, dx = 30.0 / DAY, 100.0, 1000.0 / n
+    for i in range(n - 1):
+        expect = q * mu * Rk * (dx / (2.0 * perm[i]) + dx / (2.0 * perm[i + 1])) / A
+        assert P[i] - P[i + 1] == pytest.approx(expect, rel=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# gravity: hydrostatic rest and segregation (Sec. 2.2 gravity term)
+# ---------------------------------------------------------------------------
+
+def test_hydrostatic_rest_is_a_root():
+    ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=0.0)
+    nx, ny, nz = 3, 2, 6
+    n = nx * ny * nz
+    k = np.exp(np.random.default_rng(1).normal(math.log(50.0), 1.0, n)) * MD
+    phi = np.repeat(np.linspace(0.1, 0.3, nz), nx * ny)
+    sc = G.make_scenario(nx, ny, nz, 10.0, 10.0, 3.0, 1500.0, k, k, k, phi, ph, [], [
+        dict(n_steps=2, dt=10 * DAY, controls=[])])
+    st = M.Setup(sc)
+    x = M.initial_state(st)
+    R, _ = M.assemble(st, x, M.masses(st, x), 10 * DAY, [], np.zeros(0), with_jacobian=False)
+    assert M.scaled_residual(st, R, 10 * DAY, []) < 1e-12
+    st, x2, hist = M.run(sc)
+    assert np.allclose(x2, x, rtol=1e-12, atol=1e-9)
+    assert hist[0]["newton"] == 0
+
+
+def test_water_sinks_below_oil():
+    ph = G.default_physics()
+    nx, ny, nz = 1, 1, 4
+    k = np.full(4, 500.0 * MD)
+    sc = G.make_scenario(nx, ny, nz, 10.0, 10.0, 2.0, 1500.0, k, k, k, np.full(4, 0.25), ph, [],
+                         [dict(n_steps=1, dt=1 * DAY, controls=[])])
+    sc["S0"] = np.array([0.8, 0.8, 0.2, 0.2])
+    st, x, _ = M.run(sc)
+    S = field(st, x, 1)
+    assert S[0] < 0.8 and S[1] < 0.8 and S[3] > 0.2
+    # total water is conserved without wells (masses change only through compression)
+    assert abs(S.sum() - 2.0) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# conservation, symmetry and special cases
+# ---------------------------------------------------------------------------
+
+def _random_state(st, rng):
+    x = M.initial_state(st)
+    n = st.n
+    x[0:3 * n:3] += rng.normal(0.0, 2.0 * BAR, n)
+    x[1:3 * n:3] = rng.uniform(0.25, 0.75, n)
+    x[2:3 * n:3] = rng.uniform(0.1, 1.5, n)
+    return x
+
+
+def test_interior_fluxes_cancel_mass_balance():
+    sc = G.scenario_c1(nx=5, ny=4, nz=3)
+    st = M.Setup(sc)
+    rng = np.random.default_rng(7)
+    x_old = _random_state(st, rng)
+    x = _random_state(st, rng)
+    ctl = sc["schedule"][0]["controls"]
+    gam = M.well_gamma(st, x_old, ctl)
+    dt = 2.0 * DAY
+    M_old = M.masses(st, x_old)
+    R, _ = M.assemble(st, x, M_old, dt, ctl, gam, with_jacobian=False)
+    Mnew = M.masses(st, x)
+    pr = M.cell_properties(st.ph, st.phi_r, *M._cell_duals(st, x))
+    src = np.zeros(3)
+    for w in range(st.nw):
+        qw, qo, qp = M.perforation_rates(st, pr, w, x[3 * st.n + w], gam[w], ctl[w]["c_inj"])
+        src += [qo.v.sum(), qw.v.sum(), qp.v.sum()]
+    for a in range(3):
+        lhs = R[a:3 * st.n:3].sum()
+        rhs = Mnew[a].sum() - M_old[a].sum() - dt * src[a]
+        scale = Mnew[a].sum()
+        assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+def test_five_spot_symmetry():
+    ph = G.default_physics()
+    nx = ny = 7
+    n = nx * ny
+    k = np.full(n, 100.0 * MD)
+    corners = [(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1)]
+    wells = [dict(kind="inj", cells=[i + nx * j]) for (i, j) in corners]
+    wells.append(dict(kind="prod", cells=[nx // 2 + nx * (ny // 2)]))
+    ctl = [dict(ctrl="wrate", target=50.0 / DAY, limit=None, c_inj=1.0)] * 4 + \
+          [dict(ctrl="bhp", target=150.0 * BAR, limit=None, c_inj=0.0)]
+    sc = G.make_scenario(nx, ny, 1, 20.0, 20.0, 5.0, 2000.0, k, k, k, np.full(n, 0.2), ph, wells,
+                         [dict(n_steps=4, dt=5 * DAY, controls=ctl)])
+    st, x, _ = M.run(sc)
+    for comp in range(3):
+        f = field(st, x, comp).reshape(ny, nx)
+        scale = np.abs(f).max()
+        assert np.abs(f - f.T).max() <= 1e-8 * scale
+        assert np.abs(f - f[:, ::-1]).max() <= 1e-8 * scale
+        assert np.abs(f - f[::-1, :]).max() <= 1e-8 * scale
+
+
+def test_passive_tracer_special_case():
+    base = dict(rrf=1.0, ads_a=0.0, ipv=0.0, mu_p0=G.default_physics()["mu_w"])
+    runs = []
+    for c in (0.0, 0.7):
+        sc = G.scenario_c1(nx=5, ny=5, nz=2, n_steps=4)
+        sc["physics"] = G.default_physics(**base)
+        sc["C0"][:] = c
+        sc["schedule"][0]["controls"] = [dict(cc, c_inj=c) if cc["ctrl"] != "bhp" else dict(cc)
+                                         for cc in sc["schedule"][0]["controls"]]
+        st, x, _ = M.run(sc)
+        runs.append((st, x))
+    (st, x0), (_, x1) = runs
+    assert np.allclose(field(st, x1, 2), 0.7, rtol=1e-9)
+    for comp in (0, 1):
+        assert np.allclose(field(st, x1, comp), field(st, x0, comp), rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Jacobian: exact (dual numbers) versus central finite differences
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mixing,omega,pc", [(0, 0.6, 0.3 * BAR), (1, 1.0, 0.0)])
+def test_jacobian_matches_finite_differences(mixing, omega, pc):
+    sc = G.scenario_c1(nx=4, ny=3, nz=2)
+    sc["physics"] = G.default_physics(mixing=mixing, omega=omega, pc_e=pc)
+    ctl = [dict(ctrl="wrate", target=100.0 / DAY, limit=None, c_inj=1.2),
+           dict(ctrl="lrate", target=80.0 / DAY, limit=None, c_inj=0.0)]
+    st = M.Setup(sc)
+    rng = np.random.default_rng(3)
+    x_old = _random_state(st, rng)
+    x = _random_state(st, rng)
+    x[3 * st.n:] += [10.0 * BAR, -10.0 * BAR]
+    gam = M.well_gamma(st, x_old, ctl)
+    dt = 3.0 * DAY
+    M_old = M.masses(st, x_old)
+    R, J = M.assemble(st, x, M_old, dt, ctl, gam)
+    J = J.toarray()
+    for j in range(st.nunk):
+        h = 1e-7 * abs(x[j]) if (j >= 3 * st.n or j % 3 == 0) else 1e-7
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        Rp, _ = M.assemble(st, xp, M_old, dt, ctl, gam, with_jacobian=False)
+        Rm, _ = M.assemble(st, xm, M_old, dt, ctl, gam, with_jacobian=False)
+        col = (Rp - Rm) / (2.0 * h)
+        scale = max(np.abs(J[:, j]).max(), 1e-300)
+        assert np.abs(col - J[:, j]).max() <= 2e-6 * scale, j
+
+
+# ---------------------------------------------------------------------------
+# linear solve, forcing term, well index
+# ---------------------------------------------------------------------------
+
+def test_sparse_solve_matches_own_dense_lu():
+    sc = G.scenario_c1(nx=4, ny=4, nz=2)
+    st = M.Setup(sc)
+    x = _random_state(st, np.random.default_rng(11))
+    ctl = sc["schedule"][0]["controls"]
+    gam = M.well_gamma(st, x, ctl)
+    R, J = M.assemble(st, x, M.masses(st, x) * 0.999, DAY, ctl, gam)
+    d1 = M.solve_linear(J, -R)
+    d2 = lu_solve_dense(J.toarray(), -R)
+    assert np.allclose(d1, d2, rtol=1e-9, atol=0.0) or \
+        np.abs(d1 - d2).max() <= 1e-9 * np.abs(d2).max()
+    assert np.linalg.norm(J @ d2 + R) <= 1e-10 * np.linalg.norm(R)
+
+
+def test_forcing_term_third_choice():
+    beta = (math.sqrt(5.0) + 1.0) / 2.0
+    assert M.forcing_term(1.0, None) == 0.1
+    assert M.forcing_term(1.0, 1.0) == 0.1                  # 0.5 clipped to 0.1
+    assert M.forcing_term(0.1, 1.0) == pytest.approx(0.5 * 0.1 ** beta)
+    assert M.forcing_term(1e-4, 1.0) == 0.01
+    assert 0.5 * 0.1 ** beta == pytest.approx(0.0120486, rel=1e-5)
+
+
+def test_peaceman_equivalent_radius():
+    h, rw = 20.0, 0.1
+    k = 100.0 * MD
+    wi = M.peaceman_wi(k, k, k, h, h, 4.0, "z", rw, 0.0)
+    re = rw * math.exp(2.0 * math.pi * 4.0 * k / wi)
+    assert re / h == pytest.approx(0.198, rel=5e-3)          # Peaceman's square-cell value
+    kx, ky, hx, hy = 300.0 * MD, 30.0 * MD, 20.0, 10.0
+    wi = M.peaceman_wi(kx, ky, k, hx, hy, 4.0, "z", rw, 0.5)
+    re = rw * math.exp(2.0 * math.pi * 4.0 * math.sqrt(kx * ky) / wi - 0.5)
+    expect = 0.28 * math.sqrt(math.sqrt(ky / kx) * hx ** 2 + math.sqrt(kx / ky) * hy ** 2) / \
+        ((ky / kx) ** 0.25 + (kx / ky) ** 0.25)
+    assert re == pytest.approx(expect, rel=5e-3)             # Peaceman's anisotropic form
+    # a well along x sees (y, z): same value as a z-well with the axes rotated
+    a = M.peaceman_wi(k, 2 * k, 3 * k, 7.0, 11.0, 13.0, "x", rw, 0.0)
+    b = M.peaceman_wi(2 * k, 3 * k, k, 11.0, 13.0, 7.0, "z", rw, 0.0)
+    assert a == pytest.approx(b, rel=1e-14)
+
+
+def test_viscosity_special_cases():
+    from oracle.dual import Dual
+    ph = G.default_physics(mu_w=0.5 * CP, mu_p0=8.0 * CP, c_ref=2.0)
+
+    def props(C, **over):
+        p = dict(ph, **over)
+        n = len(C)
+        P = Dual.variable(np.full(n, 200 * BAR), 3, 0)
+        S = Dual.variable(np.full(n, 0.5), 3, 1)
+        Cd = Dual.variable(np.asarray(C, float), 3, 2)
+        return M.cell_properties(p, np.full(n, 0.2), P, S, Cd)
+
+    pr = props([0.0, 2.0, 1.0], omega=1.0)
+    assert pr["mu_we"].v[0] == pytest.approx(0.5 * CP)       # beta = 0: pure water
+    assert pr["mu_we"].v[1] == pytest.approx(8.0 * CP)       # beta = 1: mu_p0
+    assert pr["mu_we"].v[2] == pytest.approx(2.0 * CP)       # geometric mean at beta = 1/2
+    pr = props([1.0], omega=1.0, mixing=1)
+    assert pr["mu_we"].v[0] == pytest.approx(4.25 * CP)      # linear rule at beta = 1/2
+    pr = props([1.0, 0.0, 3.0], omega=0.0)                    # fully segregated
+    assert pr["mu_pe"].v[0] == pytest.approx(8.0 * CP)
+    assert pr["mu_we"].v[1] == pytest.approx(0.5 * CP)        # alpha = 0 -> water
+    assert pr["mu_we"].v[2] == pytest.approx(8.0 * CP)        # alpha = 1 -> polymer
+    # alpha = 1/2, omega = 0: harmonic mean of mu_w and mu_p0
+    assert pr["mu_we"].v[0] == pytest.approx(1.0 / (0.5 / (8.0 * CP) + 0.5 / (0.5 * CP)))
