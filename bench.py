@@ -1,0 +1,433 @@
+"""Benchmark of the polymer-flooding Newton step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c2|c3|c1] [--precision fp64|mixed] [--precond cpr|bjacobi]
+
+A step is one full Newton iteration of the fully implicit water/oil/polymer
+model (Alg. 1): property evaluation, residual and 3x3 block-Jacobian assembly
+with upstream fluxes and wells, convergence test, forcing term eq. (fterm),
+CPR preconditioner set-up and FGMRES solve (Alg. 2), update.  The timed
+iterations run inside the time loop (begin-step work, convergence checks and
+BHP-limit re-solves are inside the timed region).  The default workload is the
+100x100x10 grid (100,000 cells, seeded layered lognormal permeability, 5-spot,
+0.3 PV polymer slug) in FP64; the metric is cells x Newton iterations / s.
+
+Multi-GPU: the path does not shard (one scenario per GPU), so N ranks run N
+independent replicas; value is the total over ranks, time the max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from scenarios import generate as G  # noqa: E402
+
+FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate
+HBM_FALLBACK_GBS = 6800.0         # profiling recipe fallback when no measured peak exists
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload(name):
+    if name == "c1":
+        return G.scenario_c1(), "10x10x3 (300 cells), C1 physics, 30 daily steps"
+    if name == "c3":
+        return G.scenario_c3(), "600x450x100 (27,000,000 cells) channelised, 40 injectors / 80 producers"
+    return G.scenario_c2(), "100x100x10 (100,000 cells) layered lognormal, 5-spot, 0.3 PV slug"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+        except Exception:
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the run."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def spmv_algorithmic(sc, nwell_perf):
+    """Bytes and FP64 flops of one SpMV launch (structured 3x3 blocks)."""
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    n = nx * ny * nz
+    faces = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    blocks = n + 2 * faces
+    return blocks, n, faces
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1807_05298_gb300 import binding as B
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    sc, desc = workload(args.workload)
+    prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
+    pc = B.PF_PC_CPR if args.precond == "cpr" else B.PF_PC_BJACOBI
+    stream = torch.cuda.Stream()
+    opts = dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
+                gmres_max_iter=300)
+    with torch.cuda.stream(stream):
+        sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
+    n = sim.n
+    sched = sc["schedule"]
+    period = sched[0]
+    dt = period["dt"]
+    # start-up (untimed): past the initial transient with the library's own step loop
+    sim.run_schedule(n_steps=args.startup_steps)
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    state = dict(in_step=False, dt=dt, its=0)
+
+    def newton_iteration():
+        """One full Newton iteration (assemble -> solve -> update) inside the
+        time loop; begin/end-of-step work that falls on the way is included."""
+        while True:
+            if not state["in_step"]:
+                sim.begin_step(state["dt"])
+                state["in_step"] = True
+                state["its"] = 0
+            try:
+                r = sim.newton_iteration()
+            except B.PfError as e:        # diverged iterate: cut the step (Sec. 3, step 4(a))
+                if e.status != B.PF_ENOT_CONVERGED:
+                    raise
+                sim.abort_step()
+                state["in_step"] = False
+                state["dt"] *= 0.5
+                continue
+            if r.converged:
+                state["in_step"] = False
+                if sim.end_step():
+                    continue          # BHP-limit switch: re-solve the step
+                state["dt"] = dt
+                continue
+            state["its"] += 1
+            if state["its"] >= 25:    # cut the step (Sec. 3, step 4(a))
+                sim.abort_step()
+                state["in_step"] = False
+                state["dt"] *= 0.5
+            return r
+
+    for _ in range(args.warmup):
+        newton_iteration()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev)
+    if rank == 0:
+        clocks.start()
+    sim.kernel_timing_enable(True)
+    launches0 = sim.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    krylov = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))                  # evict L2 between timed iterations (same stream)
+        ev[k][0].record(stream)
+        r = newton_iteration()
+        ev[k][1].record(stream)
+        krylov += r.krylov_iters
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = sim.launch_count() - launches0
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kt = {name: sim.kernel_timing(name) for name in B.PF_KT}
+    sim.kernel_timing_enable(False)
+    clk = clocks.stop() if rank == 0 else None
+
+    # end-to-end through the C ABI with host buffers: state in from pinned host
+    # memory, one Newton iteration, state out to pinned host memory
+    nunk = sim.nunk
+    h_in = torch.empty(nunk, dtype=torch.float64, pin_memory=True)
+    h_out = torch.empty(nunk, dtype=torch.float64, pin_memory=True)
+    sim.get_x_ptr(h_in.data_ptr())
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        sim.set_x_ptr(h_in.data_ptr())
+        newton_iteration()
+        sim.get_x_ptr(h_out.data_ptr())
+        h_in.copy_(h_out)
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - t0
+
+    t_dev = dev_ms / 1000.0
+    times = torch.tensor([t_dev, e2e_wall, wall], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_dev, e2e_wall, wall = [float(v) for v in times.cpu()]
+    value = world * n * args.steps / t_dev
+    e2e_value = world * n * e2e_steps / e2e_wall
+
+    # roofline of the SpMV (the Krylov operator; the metric names SpMV GB/s)
+    blocks, ncell, faces = spmv_algorithmic(sc, sim.npf)
+    jbytes = 4 if prec == B.PF_PREC_MIXED else 8
+    spmv_bytes = blocks * 9 * jbytes + 2 * 3 * ncell * 8 + sim.npf * 3 * 2 * jbytes + sim.nw * jbytes
+    spmv_flops = blocks * 18 + sim.npf * 12 + sim.nw * 2
+    cnt, ms = kt["spmv"]
+    hbm_peak, hbm_kind = peaks()
+    roof = None
+    if cnt > 0:
+        avg_s = ms / cnt / 1000.0
+        gbs = spmv_bytes / avg_s / 1e9
+        tfl = spmv_flops / avg_s / 1e12
+        t_hbm = spmv_bytes / (hbm_peak * 1e9)
+        t_alu = spmv_flops / (FP64_PEAK_TFLOPS_NOMINAL * 1e12)
+        if t_alu > t_hbm:
+            roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "alu", "achieved": round(tfl, 4),
+                    "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s (FP64)",
+                    "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4), "traffic": None,
+                    "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 4 FP64 FMA/clk), measured 1.20",
+                    "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+                    "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
+                    "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
+                    "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
+        else:
+            roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "hbm", "achieved": round(gbs, 1),
+                    "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                    "peak_kind": hbm_kind, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
+                    "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
+    kernel_ms = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()}
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
+        out = {
+            "metric": "cells*Newton-iters/s",
+            "value": round(value, 1),
+            "unit": "cells*Newton-iters/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(1000.0 * t_dev / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if prec == B.PF_PREC_FP64 else "f64-residual/f32-jacobian",
+            "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
+            "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
+                       "precond": args.precond, "gmres_restart": 30, "forcing_term": "eq. (fterm) third form",
+                       "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
+                       "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
+            "krylov_iters_per_newton": round(krylov / args.steps, 2),
+            "wall_s": round(wall, 4),
+            "e2e": {"value": round(e2e_value, 1), "unit": "cells*Newton-iters/s",
+                    "h2d_bytes_per_step": nunk * 8, "d2h_bytes_per_step": nunk * 8,
+                    "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels_ms": kernel_ms,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+    sim.close()
+    return out
+
+
+def oracle_sample(args):
+    """A bounded sample of the workload for the CPU oracle: the full grid's
+    recipe on its top layers (same physics, wells and schedule)."""
+    if args.workload == "c1":
+        return G.scenario_c1(), "full 10x10x3 grid"
+    if args.workload == "c3":
+        sc = G.scenario_c3(nx=120, ny=90, nz=2)
+        return sc, "120x90x2 sample of the channelised recipe"
+    sc = G.scenario_c2(nz=1)
+    return sc, "100x100x1 slab (top layer) of the 100x100x10 recipe"
+
+
+class OracleRunner:
+    """Oracle Newton iterations (dual-number assembly + direct sparse solve +
+    update) inside its own time loop on a sample scenario; set-up is done once
+    outside the timed calls."""
+
+    def __init__(self, sc):
+        from oracle import model as M
+        self.M = M
+        self.st = M.Setup(sc)
+        self.x = M.initial_state(self.st)
+        self.ctl = sc["schedule"][0]["controls"]
+        self.dt = sc["schedule"][0]["dt"]
+        self.n = self.st.n
+        self.in_step = False
+
+    def iteration(self):
+        M, st = self.M, self.st
+        if not self.in_step:
+            self.M_old = M.masses(st, self.x)
+            self.gam = M.well_gamma(st, self.x, self.ctl)
+            self.x_old = self.x.copy()
+            self.its = 0
+            self.in_step = True
+        R, J = M.assemble(st, self.x, self.M_old, self.dt, self.ctl, self.gam)
+        if M.scaled_residual(st, R, self.dt, self.ctl) <= 1e-8 or self.its >= 12 or \
+                not np.all(np.isfinite(R)):
+            if not np.all(np.isfinite(R)):
+                self.x = self.x_old
+            self.in_step = False
+            R, J = M.assemble(st, self.x, M.masses(st, self.x), self.dt, self.ctl, self.gam)
+            self.M_old = M.masses(st, self.x)
+            self.in_step = True
+            self.its = 0
+        self.x = M.update(st, self.x, M.solve_linear(J, -R), 0.2)
+        self.its += 1
+
+
+def time_oracle(sc, budget_s, max_iters):
+    r = OracleRunner(sc)
+    its = 0
+    t0 = time.perf_counter()
+    while its < max_iters and time.perf_counter() - t0 < budget_s:
+        r.iteration()
+        its += 1
+    return its, time.perf_counter() - t0, r.n
+
+
+def cpu_baseline(args):
+    sc, sample = oracle_sample(args)
+    its, secs, n = time_oracle(sc, args.cpu_budget, 1000)
+    return {"value": round(n * its / secs, 1), "unit": "cells*Newton-iters/s", "cores": 1, "kind": "oracle",
+            "sample": "%s: %d Newton iterations (numpy dual-number assembly + scipy sparse LU, one thread) "
+                      "in %.1f s" % (sample, its, secs),
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    sc, sample = oracle_sample(args)
+    r = OracleRunner(sc)
+    for _ in range(args.warmup):
+        r.iteration()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.iteration()
+    secs = time.perf_counter() - t0
+    n = r.n
+    value = n * args.steps / secs
+    return {"impl": "reference", "metric": "cells*Newton-iters/s", "value": round(value, 1),
+            "unit": "cells*Newton-iters/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000.0 * secs / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": sample},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": round(value, 1),
+                             "unit": "cells*Newton-iters/s"},
+            "e2e": {"value": round(value, 1), "unit": "cells*Newton-iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="cpr", choices=["cpr", "bjacobi"])
+    ap.add_argument("--newton-tol", type=float, default=1e-8)
+    ap.add_argument("--startup-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_1807_05298_gb300 import build as bld
+    if rank == 0 or world == 1:
+        bld.build()
+    if dist:
+        dist.barrier()
+    out = run_ours(args, rank, world, dist)
+    if out is not None:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

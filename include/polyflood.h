@@ -1,0 +1,249 @@
+/*
+ * polyflood.h -- C ABI of the GB300 Newton step for fully implicit polymer
+ * flooding (water, oil and polymer mass conservation under Darcy's law,
+ * upstream-weighted two-point finite volumes, backward Euler), after
+ * H. Liu, Z. Chen et al., arXiv 1807.05298.
+ *
+ * Conventions shared by every call
+ *   - Units are SI: Pa, m, m^2, s, kg, Pa*s; concentrations kg/m^3.
+ *   - The grid is Cartesian, nx * ny * nz cells of dx * dy * dz; cell (i,j,k)
+ *     has the natural index i + nx*(j + ny*k) (Sec. 3 "natural ordering");
+ *     k grows with depth; `top` is the depth of the top face of layer 0.
+ *   - Unknowns are block-wise (Sec. 3.4): per cell (P_o, S_w, C), cells in
+ *     natural order, then one bottom-hole pressure per well.  Residual rows
+ *     are per cell (oil, water, polymer) masses [kg], then one row per well.
+ *   - Every call returns pf_status.  On failure pf_last_error() gives a
+ *     message (thread-local, owned by the library, valid until the next call
+ *     on the same thread).  No C++ exception crosses this boundary.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Host
+ *     arrays passed out are written by the library and must have the stated
+ *     length.  Calls that take or return host arrays synchronise the stream.
+ *   - A pf_sim is bound to the CUDA device current at pf_create and to the
+ *     stream given there (NULL = the legacy default stream).  Calls on one
+ *     pf_sim must not overlap from several threads.
+ *   - After PF_ECUDA the pf_sim is unusable except for pf_destroy.
+ */
+#ifndef POLYFLOOD_H
+#define POLYFLOOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pf_status;
+enum {
+  PF_OK = 0,
+  PF_EINVAL = 1,          /* invalid argument; nothing was changed or allocated */
+  PF_ENOMEM = 2,          /* device or host allocation failed */
+  PF_ENOT_CONVERGED = 3,  /* Newton or the Krylov solve hit its iteration cap */
+  PF_ETIMEOUT = 4,        /* a bounded device wait gave up */
+  PF_ECUDA = 5,           /* CUDA runtime error; the object is unusable */
+  PF_EBUSY = 6            /* request cannot be admitted (serving) */
+};
+
+enum { PF_WELL_INJECTOR = 0, PF_WELL_PRODUCER = 1 };
+enum { PF_DIR_X = 0, PF_DIR_Y = 1, PF_DIR_Z = 2 };
+/* Well constraints, Sec. 2.4: fixed bottom-hole pressure, fixed water rate,
+ * fixed oil rate, fixed liquid rate.  Rates are positive volume rates at
+ * reference conditions [m^3/s] (formation volume factor 1). */
+enum { PF_CTRL_BHP = 0, PF_CTRL_WRATE = 1, PF_CTRL_ORATE = 2, PF_CTRL_LRATE = 3 };
+enum { PF_PREC_FP64 = 0, PF_PREC_MIXED = 1 };
+enum { PF_PC_BJACOBI = 0, PF_PC_CPR = 1 };
+enum { PF_MIX_NONLINEAR = 0, PF_MIX_LINEAR = 1 };
+
+/* Rock, fluid, relative permeability and polymer constants (Sec. 2.1-2.3).
+ *   phi(P) = phi_r + c_r (P - p_r)                                  Sec. 2.1
+ *   rho_a(P_a) = rho_a (1 + c_a (P_a - p_ref))     (reading: linear law)
+ *   Corey: Sn = (S - swc)/(1 - swc - sor) clipped to [0,1],
+ *          k_rw = krw_max Sn^nw, k_ro = kro_max (1-Sn)^no,
+ *          P_c = P_o - P_w = pc_e (1-Sn)^pc_n                       Sec. 2.2
+ *   Langmuir A_d = ads_a C / (1 + ads_b C) [kg/m^3 rock], A_d,max = a/b;
+ *   R_k = 1 + (rrf - 1) A_d / A_d,max                               Sec. 2.3
+ *   beta = C / c_ref; mu_m linear or nonlinear mixing rule of mu_w, mu_p0;
+ *   Todd-Longstaff mu_p,e, mu_w,partial, mu_w,e with mixing parameter omega
+ *   and alpha = clip(C/c_ref, 0, 1)                                 Sec. 2.3
+ *   Inaccessible pore volume ipv scales the polymer's pore space.    Sec. 2.3 */
+typedef struct pf_physics {
+  double rho_w, rho_o;      /* reference densities [kg/m^3] */
+  double c_w, c_o;          /* fluid compressibilities [1/Pa] */
+  double p_ref;             /* reference pressure of the density law [Pa] */
+  double mu_w, mu_o;        /* water and oil viscosities [Pa s] */
+  double c_r, p_r;          /* rock compressibility [1/Pa], reference pressure [Pa] */
+  double swc, sor, nw, no, krw_max, kro_max;
+  double pc_e, pc_n;        /* capillary entry pressure [Pa] and exponent */
+  double ads_a, ads_b;      /* Langmuir constants */
+  double rrf, ipv;          /* residual resistance factor, inaccessible pore volume */
+  double omega, mu_p0, c_ref;
+  int mixing;               /* PF_MIX_NONLINEAR or PF_MIX_LINEAR */
+  double g;                 /* gravity [m/s^2] */
+} pf_physics;
+
+/* One well: perforated cells (natural indices, the first one is the datum of
+ * the hydrostatic wellbore eq. (ssw:dp)), the direction of each perforation
+ * for the Peaceman index eq. (wi)/(wi:re:k), and the index parameters.  A cell
+ * may carry at most one perforation over all wells. */
+typedef struct pf_well_desc {
+  int kind;                 /* PF_WELL_INJECTOR or PF_WELL_PRODUCER */
+  int n_perf;
+  const int64_t* cells;     /* host [n_perf] */
+  const int* dirs;          /* host [n_perf] PF_DIR_*, or NULL for all z */
+  double rw, skin, gf, f, fh;
+  double pb0;               /* initial bottom-hole pressure [Pa] */
+} pf_well_desc;
+
+typedef struct pf_model_desc {
+  int nx, ny, nz;
+  double dx, dy, dz, top;
+  const double *kx, *ky, *kz;   /* host [N] permeability [m^2] */
+  const double* phi;            /* host [N] reference porosity phi_r */
+  const double *p0, *s0, *c0;   /* host [N] initial P_o, S_w, C */
+  pf_physics phys;
+  int n_wells;
+  const pf_well_desc* wells;    /* host [n_wells] */
+} pf_model_desc;
+
+typedef struct pf_solver_opts {
+  int precision;        /* PF_PREC_FP64: all arithmetic FP64.  PF_PREC_MIXED:
+                           FP32 Jacobian storage and assembly derivatives,
+                           FP32 preconditioner; residual, norms, Krylov basis
+                           and orthogonalisation stay FP64. */
+  int precond;          /* PF_PC_BJACOBI or PF_PC_CPR (Alg. 2) */
+  int gmres_restart;    /* Krylov basis size m (default 30) */
+  int gmres_max_iter;   /* cap on Krylov iterations per linear solve (default 300) */
+  int newton_max_iter;  /* cap on Newton iterations per step (default 25) */
+  int use_forcing;      /* 1: linear tolerance eta from eq. (fterm), third form;
+                           0: fixed lin_rtol */
+  double lin_rtol;      /* fixed relative linear tolerance (default 1e-12) */
+  double newton_tol;    /* scaled residual tolerance (default 1e-10) */
+  double ds_max;        /* per-iteration saturation change limit (default 0.2) */
+  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 1, 1) */
+  int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 64) */
+  int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
+} pf_solver_opts;
+
+typedef struct pf_well_control {
+  int ctrl;             /* PF_CTRL_* */
+  double target;        /* Pa for BHP, else m^3/s at reference conditions */
+  double limit;         /* BHP limit [Pa] or 0 for none (not enforced inside a step) */
+  double c_inj;         /* injected polymer concentration [kg/m^3] */
+} pf_well_control;
+
+typedef struct pf_iter_report {
+  double res_scaled;    /* dimensionless max-norm of the residual before the update */
+  double res_norm2;     /* 2-norm of the residual [kg] */
+  double eta;           /* linear tolerance used */
+  double lin_rel_res;   /* achieved relative linear residual */
+  int krylov_iters;
+  int converged;        /* 1 if res_scaled <= newton_tol (no update was made) */
+} pf_iter_report;
+
+typedef struct pf_step_report {
+  int newton_iters, krylov_iters, converged;
+  double res_scaled;
+} pf_step_report;
+
+/* Library version string (static storage). */
+const char* pf_version(void);
+/* Message of the last failed call on this thread (static thread-local storage). */
+const char* pf_last_error(void);
+/* Fills o with the defaults stated in pf_solver_opts. */
+pf_status pf_default_opts(pf_solver_opts* o);
+
+typedef struct pf_sim pf_sim;
+
+/* Model loading, grid set-up and initialisation (Sec. 3, steps 1-3): copies
+ * the description, computes transmissibilities (Sec. 3.2, harmonic k and
+ * geometry) and Peaceman well indices (eq. (wi), (wi:re:k)) on the host,
+ * uploads everything to device memory owned by the returned object.
+ * stream: a cudaStream_t borrowed for the life of the object (NULL allowed).
+ * Errors: PF_EINVAL (sizes, NaN, doubly perforated cell), PF_ENOMEM, PF_ECUDA. */
+pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* stream, pf_sim** out);
+/* Frees all device and host memory of s; NULL is accepted. */
+pf_status pf_destroy(pf_sim* s);
+/* Well constraints for the next steps (Sec. 3, step 4(b): unchanged within a
+ * step).  c[nwells], nwells must equal the model's well count. */
+pf_status pf_set_controls(pf_sim* s, const pf_well_control* c, int nwells);
+
+/* Starts a backward-Euler step of length dt [s] from the current state: keeps
+ * x^n, evaluates the old masses M^n and the lagged wellbore unit weights. */
+pf_status pf_begin_step(pf_sim* s, double dt);
+/* One Newton iteration of Alg. 1 at the current iterate: property evaluation,
+ * residual and Jacobian assembly, convergence test, linear tolerance from
+ * eq. (fterm), preconditioner set-up, Krylov solve, update.  Requires
+ * pf_begin_step.  rep may be NULL. */
+pf_status pf_newton_iteration(pf_sim* s, pf_iter_report* rep);
+/* pf_begin_step + Newton iterations to convergence (Alg. 1), controls fixed
+ * within the step (Sec. 3 step 4(b)).  BHP limits of rate wells (the limit
+ * field of pf_well_control, Sec. 4.1.2 "constrained with its bottom hole
+ * pressure"): after convergence a rate well whose BHP crossed its limit
+ * (injector above, producer below) is moved onto BHP = limit and the step is
+ * re-solved from x^n; a switched well whose rate at the limit exceeds its
+ * target returns to rate control; at most two re-solves per step.  The
+ * switched state persists across steps until the well's constraint changes
+ * in pf_set_controls.  On PF_ENOT_CONVERGED the state is restored to x^n (the
+ * caller cuts dt, Sec. 3 step 4(a)). */
+pf_status pf_step(pf_sim* s, double dt, pf_step_report* rep);
+/* Step pieces for callers that drive Newton one iteration at a time:
+ * pf_end_step after pf_newton_iteration reported convergence applies the BHP
+ * limit check of pf_step; *resolve = 1 means a switch changed, the state was
+ * restored to x^n and the step must be solved again (pf_begin_step with the
+ * same dt).  pf_abort_step restores x^n after a failed step. */
+pf_status pf_end_step(pf_sim* s, int* resolve);
+pf_status pf_abort_step(pf_sim* s);
+/* Per-well mass rates into the reservoir (positive for injection) [kg/s] of
+ * water, oil and polymer, eq. (ssw:Q) at the current state with the wellbore
+ * weight of the current step, and the reference BHP [Pa]; host arrays of the
+ * well count, any may be NULL. */
+pf_status pf_well_rates(pf_sim* s, double* q_w, double* q_o, double* q_p, double* pb);
+/* switched[w] = 1 if rate well w currently runs on its BHP limit. */
+pf_status pf_well_switched(const pf_sim* s, int* switched);
+
+/* Test hooks.  pf_assemble evaluates R and J at the current iterate (after
+ * pf_begin_step).  pf_export_system copies them to the host:
+ *   R[3N + W];
+ *   Jc[7 * 9 * N]: block slot s (0 diagonal, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z,
+ *     6 +z), entry e = 3*row + col within the 3x3 block (rows oil, water,
+ *     polymer; cols P, S, C), cell i at Jc[(s*9 + e)*N + i]; slots that leave
+ *     the grid hold 0;
+ *   Jw_b[3 * Pf]: dR_cell/dP_b per perforation (perforations in well order);
+ *   Jw_c[3 * Pf]: dR_well/dx_cell per perforation;  Jw_d[W]: dR_well/dP_b.
+ * Any output pointer may be NULL to skip it. */
+pf_status pf_assemble(pf_sim* s);
+pf_status pf_export_system(pf_sim* s, double* R, double* Jc, double* Jw_b, double* Jw_c, double* Jw_d);
+/* y = J x with the assembled Jacobian (host x[3N+W], host y[3N+W]). */
+pf_status pf_apply_jacobian(pf_sim* s, const double* x, double* y);
+/* Solves J x = b with the configured preconditioned Krylov method to relative
+ * tolerance rtol (host b, x of length 3N+W).  *iters and *rel_res may be NULL. */
+pf_status pf_solve_linear(pf_sim* s, const double* b, double* x, double rtol, int* iters, double* rel_res);
+
+/* Host copies of the state (checkpoint / resume).  P, S, C [N]; Pb [W];
+ * any pointer may be NULL. */
+pf_status pf_get_state(pf_sim* s, double* P, double* S, double* C, double* Pb);
+pf_status pf_set_state(pf_sim* s, const double* P, const double* S, const double* C, const double* Pb);
+/* Number of cells, wells and perforations of s. */
+pf_status pf_sizes(const pf_sim* s, int64_t* n_cells, int* n_wells, int64_t* n_perf);
+/* Device-resident state pointers (valid for the life of s): x is the
+ * interleaved unknown vector [3N + W] (FP64). */
+pf_status pf_device_state(pf_sim* s, double** x_dev);
+/* Host copies of the whole interleaved unknown vector x[3N + W] (block-wise
+ * order), straight between the caller's buffer (pinned or pageable) and the
+ * device state. */
+pf_status pf_get_x(pf_sim* s, double* x);
+pf_status pf_set_x(pf_sim* s, const double* x);
+/* Opt-in CUDA-event timing of kernel classes on the sim's stream: enabling
+ * (or disabling) resets the counters; pf_kernel_timing returns the launches
+ * and summed device time [ms] of one class since then. */
+enum { PF_KT_SPMV = 0, PF_KT_PROPS, PF_KT_FACE, PF_KT_GATHER, PF_KT_WELLS, PF_KT_ORTHO, PF_KT_PRECOND,
+       PF_KT_COUNT };
+pf_status pf_kernel_timing_enable(pf_sim* s, int on);
+pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* total_ms);
+/* Kernel launches issued by s so far (monotone counter). */
+pf_status pf_launch_count(const pf_sim* s, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYFLOOD_H */

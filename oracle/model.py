@@ -503,16 +503,81 @@ def controls_with_defaults(controls):
     return [dict(c) for c in controls]
 
 
-def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, callback=None):
+def well_totals(st, x, controls, gamma):
+    """Per well: summed water and oil mass rates into the reservoir (positive
+    for injection) at the state x, eq. (ssw:Q), and the reference BHP."""
+    pr = cell_properties(st.ph, st.phi_r, *_cell_duals(st, x))
+    out = []
+    for w in range(st.nw):
+        qw, qo, _ = perforation_rates(st, pr, w, x[3 * st.n + w], gamma[w], controls[w]["c_inj"])
+        out.append((float(qw.v.sum()), float(qo.v.sum()), float(x[3 * st.n + w])))
+    return out
+
+
+def controlled_rate(ph, kind, ctrl, qw, qo):
+    """The volume rate a rate constraint refers to (Sec. 2.4), positive."""
+    if kind == "inj":
+        return qw / ph["rho_w"]
+    if ctrl == "wrate":
+        return -qw / ph["rho_w"]
+    if ctrl == "orate":
+        return -qo / ph["rho_o"]
+    return -(qw / ph["rho_w"] + qo / ph["rho_o"])
+
+
+def effective_controls(st, controls, switched):
+    """Rate wells switched onto their BHP limit run under BHP = limit."""
+    out = []
+    for w, c in enumerate(controls):
+        if switched[w]:
+            out.append(dict(c, ctrl="bhp", target=c["limit"]))
+        else:
+            out.append(dict(c))
+    return out
+
+
+def update_switches(st, controls, switched, totals):
+    """Limit check after a converged step.  A rate well whose BHP crosses its
+    limit (above it for an injector, below it for a producer) moves to BHP
+    control at the limit; a switched well whose rate at the limit exceeds its
+    target returns to rate control.  Returns True if anything changed."""
+    changed = False
+    for w, c in enumerate(controls):
+        if c["ctrl"] == "bhp" or not c.get("limit"):
+            continue
+        kind = st.wells[w]["kind"]
+        qw, qo, pb = totals[w]
+        if not switched[w]:
+            if (kind == "inj" and pb > c["limit"]) or (kind == "prod" and pb < c["limit"]):
+                switched[w] = True
+                changed = True
+        else:
+            if controlled_rate(st.ph, kind, c["ctrl"], qw, qo) > c["target"]:
+                switched[w] = False
+                changed = True
+    return changed
+
+
+def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_switch_solves=2,
+        callback=None):
     """Time loop over the scenario schedule with fixed steps; on a Newton
-    failure the step is cut in half and retried (Sec. 3, step 4(a))."""
+    failure the step is cut in half and retried (Sec. 3, step 4(a)); controls
+    stay fixed within a step (step 4(b)) and BHP limits are applied by
+    ``update_switches`` with up to ``max_switch_solves`` re-solves."""
     st = Setup(sc)
     x = initial_state(st)
     t = 0.0
     history = []
     done = 0
+    switched = [False] * st.nw
+    prev = None
     for period in sc["schedule"]:
         ctl = controls_with_defaults(period["controls"])
+        if prev is not None:   # a well keeps its switched state while its constraint is unchanged
+            for w in range(st.nw):
+                if any(ctl[w].get(k) != prev[w].get(k) for k in ("ctrl", "target", "limit")):
+                    switched[w] = False
+        prev = ctl
         for _ in range(period["n_steps"]):
             if n_steps is not None and done >= n_steps:
                 return st, x, history
@@ -522,8 +587,15 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, callba
             newton_total = 0
             while dt_left > 0.0:
                 dt = min(dt, dt_left)
-                xn, ok, its = newton_step(st, x, dt, ctl, tol=tol, max_iter=max_iter, ds_max=ds_max)
-                newton_total += its
+                for attempt in range(max_switch_solves + 1):
+                    eff = effective_controls(st, ctl, switched)
+                    xn, ok, its = newton_step(st, x, dt, eff, tol=tol, max_iter=max_iter, ds_max=ds_max)
+                    newton_total += its
+                    if not ok or attempt == max_switch_solves:
+                        break
+                    gam = well_gamma(st, x, eff)
+                    if not update_switches(st, ctl, switched, well_totals(st, xn, eff, gam)):
+                        break
                 if ok:
                     x = xn
                     t += dt
@@ -534,7 +606,7 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, callba
                         raise RuntimeError("time step cut limit reached")
                     dt = 0.5 * dt
             done += 1
-            history.append(dict(t=t, x=x.copy(), newton=newton_total, cuts=cuts))
+            history.append(dict(t=t, x=x.copy(), newton=newton_total, cuts=cuts, switched=list(switched)))
             if callback is not None:
                 callback(st, x, history[-1])
     return st, x, history

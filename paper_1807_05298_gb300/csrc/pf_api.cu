@@ -1,0 +1,1154 @@
+// C ABI of the polyflood library: model set-up, device arena, Newton driver
+// (Alg. 1 with the forcing term eq. (fterm)) and the restarted flexible GMRES
+// with a right preconditioner (block-Jacobi or CPR, Alg. 2).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pf_cpr.cuh"
+#include "pf_internal.cuh"
+
+using namespace pf;
+
+static thread_local std::string g_last_error;
+
+static pf_status fail(pf_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define PF_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      if (s) s->dead = true;                                                                \
+      return fail(PF_ECUDA, std::string("CUDA error in ") + #call + ": " + cudaGetErrorString(e_)); \
+    }                                                                                       \
+  } while (0)
+
+#define PF_LAUNCHED(k)                                                                      \
+  do {                                                                                      \
+    s->launches += (k);                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                    \
+    if (e_ != cudaSuccess) {                                                                \
+      s->dead = true;                                                                       \
+      return fail(PF_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e_)); \
+    }                                                                                       \
+  } while (0)
+
+struct pf_sim {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool dead = false;
+  bool mixed = false;
+  pf_solver_opts opts;
+  Grid g;
+  Phys ph;
+  int nw = 0;
+  long long npf = 0;
+  long long nunk = 0, ld = 0;
+  int nblocks = 0;
+  int64_t launches = 0;
+  // host copies
+  std::vector<int> h_kind, h_ptr;
+  std::vector<long long> h_cell;
+  std::vector<double> h_W;
+  std::vector<pf_well_control> h_ctl;   // user controls
+  std::vector<char> switched;           // rate well running on its BHP limit
+  bool have_controls = false;
+  // arena
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // device arrays
+  double *phi_r = nullptr, *T3 = nullptr, *x = nullptr, *x_old = nullptr, *Mold = nullptr, *R = nullptr;
+  double *pv = nullptr, *Fbuf = nullptr, *dx = nullptr, *b = nullptr, *r = nullptr, *tmp = nullptr;
+  void *pd = nullptr, *J = nullptr, *Bw = nullptr, *Cw = nullptr, *Dw = nullptr;
+  void *Dinv = nullptr, *Dwinv = nullptr;
+  int *w_ptr = nullptr, *w_kind = nullptr, *w_ctrl = nullptr;
+  long long* w_cell = nullptr;
+  double *w_wi = nullptr, *w_dzb = nullptr, *w_target = nullptr, *w_cinj = nullptr, *w_W = nullptr;
+  double *w_sw = nullptr, *w_so = nullptr, *w_scale = nullptr, *w_gamma = nullptr;
+  double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
+  double* wtot = nullptr;  // [3 nw] well totals
+  double* h_pinned = nullptr;
+  CprData cpr;
+  // opt-in CUDA-event timing of selected kernels
+  bool kt_on = false;
+  std::vector<cudaEvent_t> kt_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kt_pending;
+  int64_t kt_count[PF_KT_COUNT] = {0};
+  double kt_ms[PF_KT_COUNT] = {0.0};
+  int switch_attempt = 0;
+  // step state
+  double dt = 0.0;
+  bool in_step = false;
+  bool assembled = false;
+  double prev_norm = -1.0;
+  int iter_in_step = 0;
+};
+
+namespace {
+
+cudaEvent_t kt_event(pf_sim* s) {
+  if (!s->kt_pool.empty()) {
+    cudaEvent_t e = s->kt_pool.back();
+    s->kt_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch of kernel class `which` with events on the sim's stream.
+struct KtScope {
+  pf_sim* s;
+  int which;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KtScope(pf_sim* s_, int w) : s(s_), which(w) {
+    if (s->kt_on) {
+      a = kt_event(s);
+      b = kt_event(s);
+      cudaEventRecord(a, s->stream);
+    }
+  }
+  ~KtScope() {
+    if (a) {
+      cudaEventRecord(b, s->stream);
+      s->kt_pending.push_back({which, {a, b}});
+    }
+  }
+};
+
+void kt_collect(pf_sim* s) {
+  if (s->kt_pending.empty()) return;
+  cudaStreamSynchronize(s->stream);
+  for (auto& p : s->kt_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    s->kt_count[p.first] += 1;
+    s->kt_ms[p.first] += ms;
+    s->kt_pool.push_back(p.second.first);
+    s->kt_pool.push_back(p.second.second);
+  }
+  s->kt_pending.clear();
+}
+
+Wells wells_view(const pf_sim* s) {
+  Wells w;
+  w.nw = s->nw;
+  w.npf = s->npf;
+  w.ptr = s->w_ptr;
+  w.cell = s->w_cell;
+  w.wi = s->w_wi;
+  w.dzb = s->w_dzb;
+  w.kind = s->w_kind;
+  w.ctrl = s->w_ctrl;
+  w.target = s->w_target;
+  w.cinj = s->w_cinj;
+  w.W = s->w_W;
+  w.sw = s->w_sw;
+  w.so = s->w_so;
+  w.scale = s->w_scale;
+  w.gamma = s->w_gamma;
+  return w;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Peaceman well index, eq. (wi) with eq. (wi:re:k); the printed form is for a
+// well along x, whose perpendicular directions are y and z.
+double well_index(double kx, double ky, double kz, double dx, double dy, double dz, int dir, double rw, double skin,
+                  double gf, double f, double fh) {
+  double k1, k2, h1, h2, h;
+  if (dir == PF_DIR_X) { k1 = ky; k2 = kz; h1 = dy; h2 = dz; h = dx; }
+  else if (dir == PF_DIR_Y) { k1 = kx; k2 = kz; h1 = dx; h2 = dz; h = dy; }
+  else { k1 = kx; k2 = ky; h1 = dx; h2 = dy; h = dz; }
+  const double r21 = k2 / k1, r12 = k1 / k2;
+  const double re = 2.0 * gf / sqrt(M_PI) * sqrt(sqrt(r21) * h1 * h1 + sqrt(r12) * h2 * h2) /
+                    (pow(r21, 0.25) + pow(r12, 0.25));
+  const double ka = sqrt(k1 * k2);
+  return 2.0 * M_PI * f * h * fh * ka / (log(re / rw) + skin);
+}
+
+Phys derive_phys(const pf_physics& p) {
+  Phys ph;
+  ph.rho_w = p.rho_w; ph.rho_o = p.rho_o; ph.c_w = p.c_w; ph.c_o = p.c_o; ph.p_ref = p.p_ref;
+  ph.mu_w = p.mu_w; ph.mu_o = p.mu_o; ph.c_r = p.c_r; ph.p_r = p.p_r;
+  ph.swc = p.swc; ph.sor = p.sor; ph.nw = p.nw; ph.no = p.no; ph.krw_max = p.krw_max; ph.kro_max = p.kro_max;
+  ph.pc_e = p.pc_e; ph.pc_n = p.pc_n; ph.ads_a = p.ads_a; ph.ads_b = p.ads_b; ph.rrf = p.rrf; ph.ipv = p.ipv;
+  ph.omega = p.omega; ph.mu_p0 = p.mu_p0; ph.c_ref = p.c_ref; ph.g = p.g; ph.mixing = p.mixing;
+  ph.inv_den = 1.0 / (1.0 - p.swc - p.sor);
+  ph.ln_mu_w = log(p.mu_w);
+  ph.ln_mu_ratio = log(p.mu_p0) - log(p.mu_w);
+  const double ads_max = p.ads_b > 0.0 ? p.ads_a / p.ads_b : 0.0;
+  ph.rk_coef = ads_max > 0.0 ? (p.rrf - 1.0) / ads_max : 0.0;
+  ph.mu_p0_pow = pow(p.mu_p0, 1.0 - p.omega);
+  ph.mu_w_pow = pow(p.mu_w, 1.0 - p.omega);
+  ph.inv_c_ref = 1.0 / p.c_ref;
+  ph.inv_rho_w = 1.0 / p.rho_w;
+  return ph;
+}
+
+pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
+  if (!m) return fail(PF_EINVAL, "model description is NULL");
+  if (m->nx < 1 || m->ny < 1 || m->nz < 1) return fail(PF_EINVAL, "grid dimensions must be >= 1");
+  const long long n = (long long)m->nx * m->ny * m->nz;
+  if (n > (1LL << 31) / 4) return fail(PF_EINVAL, "grid too large (more than 2^29 cells)");
+  if (!finite_pos(m->dx) || !finite_pos(m->dy) || !finite_pos(m->dz) || !std::isfinite(m->top))
+    return fail(PF_EINVAL, "cell sizes must be finite and positive");
+  if (!m->kx || !m->ky || !m->kz || !m->phi || !m->p0 || !m->s0 || !m->c0)
+    return fail(PF_EINVAL, "per-cell host arrays must not be NULL");
+  for (long long i = 0; i < n; ++i) {
+    if (!finite_pos(m->kx[i]) || !finite_pos(m->ky[i]) || !finite_pos(m->kz[i]))
+      return fail(PF_EINVAL, "permeability must be finite and positive at cell " + std::to_string(i));
+    if (!finite_pos(m->phi[i]) || m->phi[i] > 1.0) return fail(PF_EINVAL, "porosity must lie in (0, 1]");
+    if (!std::isfinite(m->p0[i]) || !std::isfinite(m->s0[i]) || !std::isfinite(m->c0[i]))
+      return fail(PF_EINVAL, "initial state must be finite");
+  }
+  const pf_physics& p = m->phys;
+  if (!finite_pos(p.rho_w) || !finite_pos(p.rho_o) || !finite_pos(p.mu_w) || !finite_pos(p.mu_o) ||
+      !finite_pos(p.mu_p0) || !finite_pos(p.c_ref) || !(1.0 - p.swc - p.sor > 0.0) || !std::isfinite(p.g))
+    return fail(PF_EINVAL, "invalid fluid or polymer constants");
+  if (p.ads_a < 0.0 || p.ads_b < 0.0 || p.ipv < 0.0 || p.ipv >= 1.0 || p.rrf < 1.0 || p.nw < 1.0 || p.no < 1.0)
+    return fail(PF_EINVAL, "invalid adsorption, IPV, RRF or Corey exponent");
+  if (m->n_wells < 0 || (m->n_wells > 0 && !m->wells)) return fail(PF_EINVAL, "invalid well list");
+  std::vector<char> seen((size_t)n, 0);
+  for (int w = 0; w < m->n_wells; ++w) {
+    const pf_well_desc& d = m->wells[w];
+    if (d.n_perf < 1 || !d.cells) return fail(PF_EINVAL, "well without perforations");
+    if (d.kind != PF_WELL_INJECTOR && d.kind != PF_WELL_PRODUCER) return fail(PF_EINVAL, "invalid well kind");
+    if (!finite_pos(d.rw) || !std::isfinite(d.skin) || !finite_pos(d.gf) || !finite_pos(d.f) || !finite_pos(d.fh) ||
+        !std::isfinite(d.pb0))
+      return fail(PF_EINVAL, "invalid well index parameters");
+    for (int q = 0; q < d.n_perf; ++q) {
+      const int64_t c = d.cells[q];
+      if (c < 0 || c >= n) return fail(PF_EINVAL, "perforation outside the grid");
+      if (seen[(size_t)c]) return fail(PF_EINVAL, "a cell carries more than one perforation");
+      seen[(size_t)c] = 1;
+      if (d.dirs && (d.dirs[q] < 0 || d.dirs[q] > 2)) return fail(PF_EINVAL, "invalid perforation direction");
+    }
+  }
+  if (o) {
+    if (o->gmres_restart < 1 || o->gmres_restart > 64) return fail(PF_EINVAL, "gmres_restart must be in [1, 64]");
+    if (o->precision != PF_PREC_FP64 && o->precision != PF_PREC_MIXED) return fail(PF_EINVAL, "invalid precision");
+    if (o->precond != PF_PC_BJACOBI && o->precond != PF_PC_CPR) return fail(PF_EINVAL, "invalid preconditioner");
+    if (o->amg_cycle != 1 && o->amg_cycle != 2) return fail(PF_EINVAL, "amg_cycle must be 1 or 2");
+    if (o->amg_pre_sweeps < 0 || o->amg_post_sweeps < 0 || o->amg_coarse_size < 1)
+      return fail(PF_EINVAL, "invalid multigrid parameters");
+  }
+  return PF_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Lays out every device array in one arena; with base == nullptr only sizes it.
+size_t carve(pf_sim* s, char* base) {
+  Carver c;
+  c.base = base;
+  const long long n = s->g.n;
+  const size_t dts = s->mixed ? sizeof(float) : sizeof(double);
+  const int m = s->opts.gmres_restart;
+  s->phi_r = c.take<double>(n);
+  s->T3 = c.take<double>(3 * n);
+  s->x = c.take<double>(s->nunk);
+  s->x_old = c.take<double>(s->nunk);
+  s->Mold = c.take<double>(3 * n);
+  s->R = c.take<double>(s->nunk);
+  s->pv = c.take<double>((size_t)PV_COUNT * n);
+  s->pd = c.take<char>((size_t)PD_COUNT * n * dts);
+  s->Fbuf = c.take<double>(9 * (size_t)n);
+  s->J = c.take<char>((size_t)SL_COUNT * 9 * n * dts);
+  s->Bw = c.take<char>(3 * (size_t)std::max(1LL, s->npf) * dts);
+  s->Cw = c.take<char>(3 * (size_t)std::max(1LL, s->npf) * dts);
+  s->Dw = c.take<char>((size_t)std::max(1, s->nw) * dts);
+  s->Dinv = c.take<char>(9 * (size_t)n * dts);
+  s->Dwinv = c.take<char>((size_t)std::max(1, s->nw) * dts);
+  s->w_ptr = c.take<int>(s->nw + 1);
+  s->w_kind = c.take<int>(std::max(1, s->nw));
+  s->w_ctrl = c.take<int>(std::max(1, s->nw));
+  s->w_cell = c.take<long long>(std::max(1LL, s->npf));
+  s->w_wi = c.take<double>(std::max(1LL, s->npf));
+  s->w_dzb = c.take<double>(std::max(1LL, s->npf));
+  s->w_target = c.take<double>(std::max(1, s->nw));
+  s->w_cinj = c.take<double>(std::max(1, s->nw));
+  s->w_W = c.take<double>(std::max(1, s->nw));
+  s->w_sw = c.take<double>(std::max(1, s->nw));
+  s->w_so = c.take<double>(std::max(1, s->nw));
+  s->w_scale = c.take<double>(std::max(1, s->nw));
+  s->w_gamma = c.take<double>(std::max(1, s->nw));
+  s->dx = c.take<double>(s->nunk);
+  s->b = c.take<double>(s->nunk);
+  s->r = c.take<double>(s->nunk);
+  s->tmp = c.take<double>(s->nunk);
+  s->V = c.take<double>((size_t)(m + 1) * s->ld);
+  s->Z = c.take<double>((size_t)m * s->ld);
+  s->hbuf = c.take<double>(4 * 128);
+  s->partial = c.take<double>((size_t)s->nblocks * 70);
+  s->norms = c.take<double>(4);
+  s->ydev = c.take<double>(128);
+  s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
+  if (s->opts.precond == PF_PC_CPR) cpr_carve(s->cpr, s->g, s->mixed, c.off, base);
+  return align_up(c.off, 256);
+}
+
+template <typename DT>
+pf_status assemble_t(pf_sim* s) {
+  const Wells w = wells_view(s);
+  cudaStream_t st = s->stream;
+  {
+    KtScope t(s, PF_KT_PROPS);
+    launch_cell_props<DT>(s->g, s->ph, s->phi_r, s->x, s->pv, (DT*)s->pd, s->Mold, s->R, (DT*)s->J, nullptr, 0, st);
+  }
+  {
+    KtScope t(s, PF_KT_FACE);
+    launch_face_flux<DT>(s->g, s->ph, s->phi_r, s->T3, s->x, s->pv, (const DT*)s->pd, s->dt, (DT*)s->J, s->Fbuf, st);
+  }
+  {
+    KtScope t(s, PF_KT_GATHER);
+    launch_gather<DT>(s->g, s->Fbuf, s->dt, s->R, (DT*)s->J, st);
+  }
+  {
+    KtScope t(s, PF_KT_WELLS);
+    launch_wells<DT>(s->g, s->ph, w, s->x, s->pv, (const DT*)s->pd, s->dt, s->R, (DT*)s->J, (DT*)s->Bw, (DT*)s->Cw,
+                     (DT*)s->Dw, st);
+  }
+  PF_LAUNCHED(3 + (s->nw > 0));
+  return PF_OK;
+}
+
+pf_status assemble(pf_sim* s) {
+  pf_status rc = s->mixed ? assemble_t<float>(s) : assemble_t<double>(s);
+  if (rc == PF_OK) s->assembled = true;
+  return rc;
+}
+
+// y = J x on device vectors
+pf_status spmv(pf_sim* s, const double* xin, double* y) {
+  const Wells w = wells_view(s);
+  KtScope t(s, PF_KT_SPMV);
+  if (s->mixed)
+    launch_spmv<float>(s->g, w, (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw, (const float*)s->Dw, xin,
+                       y, s->stream);
+  else
+    launch_spmv<double>(s->g, w, (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
+                        (const double*)s->Dw, xin, y, s->stream);
+  PF_LAUNCHED(1 + (s->nw > 0));
+  return PF_OK;
+}
+
+pf_status precond_setup(pf_sim* s) {
+  const Wells w = wells_view(s);
+  if (s->mixed)
+    launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
+                                       (float*)s->Dwinv, s->stream);
+  else
+    launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
+                                         (double*)s->Dwinv, s->stream);
+  PF_LAUNCHED(1 + (s->nw > 0));
+  if (s->opts.precond == PF_PC_CPR) {
+    int k = 0;
+    cpr_setup(s->cpr, s->g, s->ph, s->phi_r, wells_view(s), s->mixed, s->J, s->Bw, s->Dw, s->stream, &k);
+    PF_LAUNCHED(k);
+  }
+  return PF_OK;
+}
+
+// z = M^{-1} v
+pf_status precond_apply(pf_sim* s, const double* v, double* z) {
+  if (s->opts.precond == PF_PC_CPR) {
+    int k = 0;
+    KtScope t(s, PF_KT_PRECOND);
+    cpr_apply(s->cpr, s->g, wells_view(s), s->mixed, s->J, s->Bw, s->Cw, s->Dw, s->Dinv, s->Dwinv, v, z, s->tmp,
+              s->stream, &k);
+    PF_LAUNCHED(k);
+    return PF_OK;
+  }
+  if (s->mixed) launch_bjacobi_apply<float>(s->g, s->nw, (const float*)s->Dinv, (const float*)s->Dwinv, v, z, s->stream);
+  else launch_bjacobi_apply<double>(s->g, s->nw, (const double*)s->Dinv, (const double*)s->Dwinv, v, z, s->stream);
+  PF_LAUNCHED(1);
+  return PF_OK;
+}
+
+pf_status dev_norm2(pf_sim* s, const double* a, double* out_host) {
+  launch_dot(s->nunk, a, a, s->partial, s->nblocks, s->norms, s->stream);
+  PF_LAUNCHED(2);
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->norms, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  *out_host = sqrt(s->h_pinned[0]);
+  return PF_OK;
+}
+
+void scale_vec(pf_sim* s, const double* a, double f, double* b) {
+  launch_fill(1, f, s->norms + 3, s->stream);
+  launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, b, s->stream);
+  s->launches += 2;
+}
+
+// Restarted flexible GMRES (right preconditioning) for J x = b, x0 = 0.
+// Arnoldi with classical Gram-Schmidt applied twice; the second projection
+// reuses the pass that applies the first (fused kernel), and the
+// Hessenberg column crosses to the host once per iteration for the Givens
+// rotations.
+pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int maxit, int* iters, double* relres) {
+  const long long n = s->nunk, ld = s->ld;
+  const int m = s->opts.gmres_restart;
+  cudaStream_t st = s->stream;
+  pf_status rc;
+  double bnorm;
+  if ((rc = dev_norm2(s, bvec, &bnorm)) != PF_OK) return rc;
+  launch_fill(n, 0.0, xout, st);
+  s->launches += 1;
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (!(bnorm > 0.0)) {
+    if (!std::isfinite(bnorm)) return fail(PF_ENOT_CONVERGED, "non-finite right-hand side");
+    return PF_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int total = 0;
+  double beta = bnorm;
+  double res = bnorm;
+  launch_copy(n, bvec, s->r, st);
+  s->launches += 1;
+  bool converged = false;
+  while (total < maxit && !converged) {
+    scale_vec(s, s->r, 1.0 / beta, s->V);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      double* vj = s->V + (size_t)j * ld;
+      double* zj = s->Z + (size_t)j * ld;
+      double* w = s->V + (size_t)(j + 1) * ld;
+      if ((rc = precond_apply(s, vj, zj)) != PF_OK) return rc;
+      if ((rc = spmv(s, zj, w)) != PF_OK) return rc;
+      const int k = j + 1;
+      {
+        KtScope t(s, PF_KT_ORTHO);
+        launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, st);
+        launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 128, st);
+        launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, st);
+      }
+      s->launches += 6;
+      PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, 3 * 128 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PF_CUDA(cudaStreamSynchronize(st));
+      const double* h1 = s->h_pinned;
+      const double* h2 = s->h_pinned + 128;
+      const double hn = sqrt(std::max(s->h_pinned[256 + k], 0.0));
+      double* col = &H[(size_t)j * (m + 1)];
+      for (int i = 0; i < k; ++i) col[i] = h1[i] + h2[i];
+      col[k] = hn;
+      if (hn > 0.0) scale_vec(s, w, 1.0 / hn, w);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = hypot(col[j], col[j + 1]);
+      cs[j] = den > 0.0 ? col[j] / den : 1.0;
+      sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      res = fabs(gv[j + 1]);
+      ++total;
+      jdone = j + 1;
+      if (!std::isfinite(res)) return fail(PF_ENOT_CONVERGED, "Krylov solve produced a non-finite residual");
+      if (res <= rtol * bnorm || hn == 0.0) { converged = true; break; }
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int l = i + 1; l < jdone; ++l) t -= H[(size_t)l * (m + 1) + i] * y[l];
+      y[i] = t / H[(size_t)i * (m + 1) + i];
+    }
+    memcpy(s->h_pinned, y.data(), jdone * sizeof(double));
+    PF_CUDA(cudaMemcpyAsync(s->ydev, s->h_pinned, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_multi_axpy_add(n, jdone, s->Z, ld, s->ydev, xout, st);
+    s->launches += 1;
+    if (!converged && total < maxit) {
+      if ((rc = spmv(s, xout, s->r)) != PF_OK) return rc;
+      launch_sub(n, bvec, s->r, s->r, st);
+      s->launches += 1;
+      if ((rc = dev_norm2(s, s->r, &beta)) != PF_OK) return rc;
+      res = beta;
+      if (beta <= rtol * bnorm) converged = true;
+    }
+  }
+  PF_CUDA(cudaStreamSynchronize(st));
+  if (iters) *iters = total;
+  if (relres) *relres = res / bnorm;
+  return PF_OK;
+}
+
+pf_status residual_norms(pf_sim* s, double* scaled, double* norm2) {
+  launch_residual_norms(s->g, s->ph, s->phi_r, wells_view(s), s->R, s->dt, s->partial, s->nblocks, s->norms,
+                        s->stream);
+  PF_LAUNCHED(2);
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  *scaled = s->h_pinned[0];
+  *norm2 = sqrt(s->h_pinned[1]);
+  return PF_OK;
+}
+
+pf_status check(pf_sim* s) {
+  if (!s) return fail(PF_EINVAL, "pf_sim is NULL");
+  if (s->dead) return fail(PF_ECUDA, "pf_sim is unusable after an earlier CUDA error");
+  PF_CUDA(cudaSetDevice(s->device));
+  return PF_OK;
+}
+
+double forcing_term(double nb, double nb_prev) {
+  // eq. (fterm), third choice: gamma (|b^l| / |b^{l-1}|)^beta, gamma = 0.5,
+  // beta = (sqrt(5) + 1) / 2, restricted to [0.01, 0.1]; first iteration 0.1
+  if (!(nb_prev > 0.0)) return 0.1;
+  const double eta = 0.5 * pow(nb / nb_prev, (sqrt(5.0) + 1.0) / 2.0);
+  return std::min(std::max(eta, 0.01), 0.1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pf_version(void) { return "polyflood-gb300 0.1 (sm_103a)"; }
+
+const char* pf_last_error(void) { return g_last_error.c_str(); }
+
+pf_status pf_default_opts(pf_solver_opts* o) {
+  if (!o) return fail(PF_EINVAL, "opts is NULL");
+  o->precision = PF_PREC_FP64;
+  o->precond = PF_PC_BJACOBI;
+  o->gmres_restart = 30;
+  o->gmres_max_iter = 300;
+  o->newton_max_iter = 25;
+  o->use_forcing = 0;
+  o->lin_rtol = 1e-12;
+  o->newton_tol = 1e-10;
+  o->ds_max = 0.2;
+  o->amg_pre_sweeps = 1;
+  o->amg_post_sweeps = 1;
+  o->amg_coarse_size = 64;
+  o->amg_cycle = 1;
+  return PF_OK;
+}
+
+pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* stream, pf_sim** out) {
+  if (!out) return fail(PF_EINVAL, "out is NULL");
+  *out = nullptr;
+  pf_solver_opts opts;
+  pf_default_opts(&opts);
+  if (o) opts = *o;
+  pf_status rc = validate(m, &opts);
+  if (rc != PF_OK) return rc;
+  pf_sim* s = new (std::nothrow) pf_sim();
+  if (!s) return fail(PF_ENOMEM, "host allocation failed");
+  s->opts = opts;
+  s->mixed = opts.precision == PF_PREC_MIXED;
+  s->stream = (cudaStream_t)stream;
+  {
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { delete s; return fail(PF_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
+  }
+  Grid& g = s->g;
+  g.nx = m->nx; g.ny = m->ny; g.nz = m->nz;
+  g.nxy = (long long)m->nx * m->ny;
+  g.n = g.nxy * m->nz;
+  g.dx = m->dx; g.dy = m->dy; g.dz = m->dz; g.top = m->top;
+  g.V = m->dx * m->dy * m->dz;
+  s->ph = derive_phys(m->phys);
+  s->nw = m->n_wells;
+  s->h_ptr.assign(s->nw + 1, 0);
+  for (int w = 0; w < s->nw; ++w) s->h_ptr[w + 1] = s->h_ptr[w] + m->wells[w].n_perf;
+  s->npf = s->h_ptr[s->nw];
+  s->nunk = 3 * g.n + s->nw;
+  s->ld = (long long)align_up((size_t)s->nunk, 64);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  s->nblocks = 2 * sms;
+  s->h_ctl.resize(s->nw);
+  s->switched.assign(s->nw, 0);
+  // host set-up: transmissibilities and well indices
+  const long long n = g.n;
+  std::vector<double> T3((size_t)3 * n, 0.0);
+  for (long long k = 0; k < g.nz; ++k)
+    for (long long j = 0; j < g.ny; ++j)
+      for (long long i = 0; i < g.nx; ++i) {
+        const long long c = i + g.nx * (j + g.ny * k);
+        if (i + 1 < g.nx) {  // harmonic sum of half-cell resistances, Sec. 3.2
+          const long long h = c + 1;
+          T3[c] = (g.dy * g.dz) / (g.dx / (2.0 * m->kx[c]) + g.dx / (2.0 * m->kx[h]));
+        }
+        if (j + 1 < g.ny) {
+          const long long h = c + g.nx;
+          T3[n + c] = (g.dx * g.dz) / (g.dy / (2.0 * m->ky[c]) + g.dy / (2.0 * m->ky[h]));
+        }
+        if (k + 1 < g.nz) {
+          const long long h = c + g.nxy;
+          T3[2 * n + c] = (g.dx * g.dy) / (g.dz / (2.0 * m->kz[c]) + g.dz / (2.0 * m->kz[h]));
+        }
+      }
+  std::vector<long long> cell(std::max(1LL, s->npf));
+  std::vector<double> wi(std::max(1LL, s->npf)), dzb(std::max(1LL, s->npf));
+  std::vector<int> kind(std::max(1, s->nw));
+  std::vector<double> Wsc(std::max(1, s->nw));
+  std::vector<double> pb0(std::max(1, s->nw));
+  for (int w = 0; w < s->nw; ++w) {
+    const pf_well_desc& d = m->wells[w];
+    kind[w] = d.kind;
+    pb0[w] = d.pb0;
+    double sum = 0.0;
+    const double zb = g.top + ((double)(d.cells[0] / g.nxy) + 0.5) * g.dz;
+    for (int q = 0; q < d.n_perf; ++q) {
+      const long long c = d.cells[q];
+      const int dir = d.dirs ? d.dirs[q] : PF_DIR_Z;
+      const long long t = s->h_ptr[w] + q;
+      cell[t] = c;
+      wi[t] = well_index(m->kx[c], m->ky[c], m->kz[c], g.dx, g.dy, g.dz, dir, d.rw, d.skin, d.gf, d.f, d.fh);
+      dzb[t] = g.top + ((double)(c / g.nxy) + 0.5) * g.dz - zb;
+      sum += wi[t];
+    }
+    Wsc[w] = sum * m->phys.rho_w / m->phys.mu_w;
+  }
+  s->h_kind.assign(kind.begin(), kind.begin() + s->nw);
+  s->h_cell.assign(cell.begin(), cell.begin() + s->npf);
+  s->h_W.assign(Wsc.begin(), Wsc.begin() + s->nw);
+  // device arena
+  s->cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
+  s->arena_bytes = carve(s, nullptr);
+  {
+    cudaError_t e = cudaMalloc((void**)&s->arena, s->arena_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return fail(PF_ENOMEM, "device arena of " + std::to_string(s->arena_bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    e = cudaMallocHost((void**)&s->h_pinned, 4 * 128 * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(s->arena);
+      delete s;
+      return fail(PF_ENOMEM, "pinned host buffer");
+    }
+  }
+  carve(s, s->arena);
+  // upload
+  std::vector<double> x0((size_t)s->nunk);
+  for (long long i = 0; i < n; ++i) {
+    x0[3 * i] = m->p0[i];
+    x0[3 * i + 1] = m->s0[i];
+    x0[3 * i + 2] = m->c0[i];
+  }
+  for (int w = 0; w < s->nw; ++w) x0[3 * n + w] = pb0[w];
+  cudaStream_t st = s->stream;
+  PF_CUDA(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st));
+  PF_CUDA(cudaMemcpyAsync(s->phi_r, m->phi, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->T3, T3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->x, x0.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->w_ptr, s->h_ptr.data(), (s->nw + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (s->nw > 0) {
+    PF_CUDA(cudaMemcpyAsync(s->w_kind, kind.data(), s->nw * sizeof(int), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_cell, cell.data(), s->npf * sizeof(long long), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_wi, wi.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_dzb, dzb.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_W, Wsc.data(), s->nw * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  if (s->opts.precond == PF_PC_CPR) {
+    pf_status r2 = cpr_init(s->cpr, s->g, s->mixed, s->opts, s->stream);
+    if (r2 != PF_OK) { pf_destroy(s); return fail(r2, "CPR set-up failed"); }
+  }
+  PF_CUDA(cudaStreamSynchronize(st));
+  *out = s;
+  return PF_OK;
+}
+
+pf_status pf_destroy(pf_sim* s) {
+  if (!s) return PF_OK;
+  cudaSetDevice(s->device);
+  if (s->arena) cudaFree(s->arena);
+  if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  for (auto& p : s->kt_pending) { s->kt_pool.push_back(p.second.first); s->kt_pool.push_back(p.second.second); }
+  for (cudaEvent_t e : s->kt_pool) cudaEventDestroy(e);
+  delete s;
+  return PF_OK;
+}
+
+static pf_status upload_controls(pf_sim* s, const pf_well_control* c, int nwells) {
+  std::vector<int> ctrl(std::max(1, nwells));
+  std::vector<double> target(std::max(1, nwells)), cinj(std::max(1, nwells)), sw(std::max(1, nwells)),
+      so(std::max(1, nwells)), scale(std::max(1, nwells));
+  const Phys& ph = s->ph;
+  for (int w = 0; w < nwells; ++w) {
+    const pf_well_control& k = c[w];
+    if (!std::isfinite(k.target) || !std::isfinite(k.c_inj) || k.c_inj < 0.0) return fail(PF_EINVAL, "invalid control");
+    const bool inj = s->h_kind[w] == PF_WELL_INJECTOR;
+    ctrl[w] = k.ctrl;
+    cinj[w] = k.c_inj;
+    sw[w] = so[w] = 0.0;
+    double rho_t = 1.0;
+    switch (k.ctrl) {
+      case PF_CTRL_BHP:
+        target[w] = k.target;
+        scale[w] = s->h_W[w] * 1.0e5;
+        break;
+      case PF_CTRL_WRATE:
+        sw[w] = inj ? 1.0 : -1.0;
+        rho_t = ph.rho_w;
+        break;
+      case PF_CTRL_ORATE:
+        if (inj) return fail(PF_EINVAL, "oil-rate control on an injector");
+        so[w] = -1.0;
+        rho_t = ph.rho_o;
+        break;
+      case PF_CTRL_LRATE:
+        if (inj) return fail(PF_EINVAL, "liquid-rate control on an injector");
+        sw[w] = -1.0;
+        so[w] = -ph.rho_w / ph.rho_o;
+        rho_t = ph.rho_w;
+        break;
+      default:
+        return fail(PF_EINVAL, "unknown control");
+    }
+    if (k.ctrl != PF_CTRL_BHP) {
+      if (!(k.target >= 0.0)) return fail(PF_EINVAL, "rate targets are non-negative volume rates");
+      target[w] = rho_t * k.target;
+      scale[w] = rho_t * std::max(fabs(k.target), 1e-30);
+    }
+  }
+  cudaStream_t st = s->stream;
+  if (nwells > 0) {
+    PF_CUDA(cudaMemcpyAsync(s->w_ctrl, ctrl.data(), nwells * sizeof(int), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_target, target.data(), nwells * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_cinj, cinj.data(), nwells * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_sw, sw.data(), nwells * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_so, so.data(), nwells * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(s->w_scale, scale.data(), nwells * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaStreamSynchronize(st));
+  }
+  return PF_OK;
+}
+
+pf_status pf_set_controls(pf_sim* s, const pf_well_control* c, int nwells) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (nwells != s->nw || (nwells > 0 && !c)) return fail(PF_EINVAL, "control count must equal the well count");
+  if ((rc = upload_controls(s, c, nwells)) != PF_OK) return rc;
+  for (int w = 0; w < nwells; ++w) {
+    // a well keeps its switched state only while its constraint is unchanged
+    if (c[w].ctrl != s->h_ctl[w].ctrl || c[w].target != s->h_ctl[w].target || c[w].limit != s->h_ctl[w].limit)
+      s->switched[w] = 0;
+    s->h_ctl[w] = c[w];
+  }
+  s->have_controls = true;
+  return PF_OK;
+}
+
+// Controls in force for the next solve: switched rate wells run on BHP = limit.
+static std::vector<pf_well_control> effective_controls(const pf_sim* s) {
+  std::vector<pf_well_control> e(s->h_ctl);
+  for (int w = 0; w < s->nw; ++w)
+    if (s->switched[w]) { e[w].ctrl = PF_CTRL_BHP; e[w].target = e[w].limit; }
+  return e;
+}
+
+pf_status pf_begin_step(pf_sim* s, double dt) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PF_EINVAL, "dt must be finite and positive");
+  if (!s->have_controls && s->nw > 0) return fail(PF_EINVAL, "pf_set_controls must precede the first step");
+  s->dt = dt;
+  if (s->nw > 0) {
+    std::vector<pf_well_control> eff = effective_controls(s);
+    if ((rc = upload_controls(s, eff.data(), s->nw)) != PF_OK) return rc;
+  }
+  cudaStream_t st = s->stream;
+  launch_copy(s->nunk, s->x, s->x_old, st);
+  if (s->mixed)
+    launch_cell_props<float>(s->g, s->ph, s->phi_r, s->x, s->pv, (float*)s->pd, nullptr, nullptr, nullptr, s->Mold, 1, st);
+  else
+    launch_cell_props<double>(s->g, s->ph, s->phi_r, s->x, s->pv, (double*)s->pd, nullptr, nullptr, nullptr, s->Mold, 1,
+                              st);
+  launch_well_gamma(s->g, s->ph, wells_view(s), s->x, s->pv, s->w_gamma, st);
+  PF_LAUNCHED(2 + (s->nw > 0));
+  s->in_step = true;
+  s->assembled = false;
+  s->prev_norm = -1.0;
+  s->iter_in_step = 0;
+  return PF_OK;
+}
+
+pf_status pf_assemble(pf_sim* s) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->in_step) return fail(PF_EINVAL, "pf_begin_step must precede pf_assemble");
+  rc = assemble(s);
+  if (rc != PF_OK) return rc;
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_update) {
+  pf_status rc;
+  if ((rc = assemble(s)) != PF_OK) return rc;
+  double scaled, nrm;
+  if ((rc = residual_norms(s, &scaled, &nrm)) != PF_OK) return rc;
+  pf_iter_report r{};
+  r.res_scaled = scaled;
+  r.res_norm2 = nrm;
+  if (!std::isfinite(scaled) || !std::isfinite(nrm)) {
+    if (rep) *rep = r;
+    return fail(PF_ENOT_CONVERGED, "non-finite residual");
+  }
+  if (scaled <= s->opts.newton_tol) {
+    r.converged = 1;
+    if (rep) *rep = r;
+    return PF_OK;
+  }
+  if (!allow_update) {
+    if (rep) *rep = r;
+    return fail(PF_ENOT_CONVERGED, "Newton iteration cap reached");
+  }
+  const double eta = s->opts.use_forcing ? forcing_term(nrm, s->prev_norm) : s->opts.lin_rtol;
+  r.eta = eta;
+  if ((rc = precond_setup(s)) != PF_OK) return rc;
+  // b = -R
+  launch_fill(1, -1.0, s->norms + 3, s->stream);
+  launch_scale_by_dev(s->nunk, s->R, s->norms + 3, 0, s->b, s->stream);
+  s->launches += 2;
+  int its = 0;
+  double rr = 0.0;
+  rc = gmres(s, s->b, s->dx, eta, s->opts.gmres_max_iter, &its, &rr);
+  r.krylov_iters = its;
+  r.lin_rel_res = rr;
+  if (rc != PF_OK) {
+    if (rep) *rep = r;
+    return rc;
+  }
+  launch_newton_update(s->g, s->nw, s->x, s->dx, s->opts.ds_max, s->stream);
+  PF_LAUNCHED(1);
+  s->prev_norm = nrm;
+  s->iter_in_step++;
+  if (rep) *rep = r;
+  return PF_OK;
+}
+
+pf_status pf_newton_iteration(pf_sim* s, pf_iter_report* rep) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->in_step) return fail(PF_EINVAL, "pf_begin_step must precede pf_newton_iteration");
+  return newton_iteration(s, rep, true);
+}
+
+// Per-well water, oil and polymer mass rates and reference BHP at the current
+// state into host arrays (any may be NULL).
+static pf_status well_totals(pf_sim* s, std::vector<double>& tot, std::vector<double>& pb) {
+  cudaStream_t st = s->stream;
+  if (s->mixed)
+    launch_cell_props<float>(s->g, s->ph, s->phi_r, s->x, s->pv, (float*)s->pd, nullptr, nullptr, nullptr, nullptr, 2, st);
+  else
+    launch_cell_props<double>(s->g, s->ph, s->phi_r, s->x, s->pv, (double*)s->pd, nullptr, nullptr, nullptr, nullptr, 2,
+                              st);
+  launch_well_totals(s->g, s->ph, wells_view(s), s->x, s->pv, s->wtot, st);
+  PF_LAUNCHED(1 + (s->nw > 0));
+  tot.assign(3 * (size_t)std::max(1, s->nw), 0.0);
+  pb.assign(std::max(1, s->nw), 0.0);
+  if (s->nw > 0) {
+    PF_CUDA(cudaMemcpyAsync(tot.data(), s->wtot, 3 * s->nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA(cudaMemcpyAsync(pb.data(), s->x + 3 * s->g.n, s->nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  PF_CUDA(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+// The volume rate a rate constraint refers to (Sec. 2.4), positive.
+static double controlled_rate(const Phys& ph, int kind, int ctrl, double qw, double qo) {
+  if (kind == PF_WELL_INJECTOR) return qw / ph.rho_w;
+  if (ctrl == PF_CTRL_WRATE) return -qw / ph.rho_w;
+  if (ctrl == PF_CTRL_ORATE) return -qo / ph.rho_o;
+  return -(qw / ph.rho_w + qo / ph.rho_o);
+}
+
+// Limit check after a converged step: a rate well whose BHP crosses its limit
+// (above for an injector, below for a producer) moves onto BHP = limit; a
+// switched well whose rate at the limit exceeds its target returns to rate
+// control.  Returns true if a switch changed.
+static bool update_switches(pf_sim* s, const std::vector<double>& tot, const std::vector<double>& pb) {
+  bool changed = false;
+  for (int w = 0; w < s->nw; ++w) {
+    const pf_well_control& c = s->h_ctl[w];
+    if (c.ctrl == PF_CTRL_BHP || c.limit == 0.0) continue;
+    const int kind = s->h_kind[w];
+    if (!s->switched[w]) {
+      if ((kind == PF_WELL_INJECTOR && pb[w] > c.limit) || (kind == PF_WELL_PRODUCER && pb[w] < c.limit)) {
+        s->switched[w] = 1;
+        changed = true;
+      }
+    } else if (controlled_rate(s->ph, kind, c.ctrl, tot[3 * w], tot[3 * w + 1]) > c.target) {
+      s->switched[w] = 0;
+      changed = true;
+    }
+  }
+  return changed;
+}
+
+static bool has_limits(const pf_sim* s) {
+  for (int w = 0; w < s->nw; ++w)
+    if (s->h_ctl[w].ctrl != PF_CTRL_BHP && s->h_ctl[w].limit != 0.0) return true;
+  return false;
+}
+
+pf_status pf_end_step(pf_sim* s, int* resolve) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!resolve) return fail(PF_EINVAL, "resolve is NULL");
+  *resolve = 0;
+  const int max_switch_solves = 2;
+  if (s->switch_attempt < max_switch_solves && has_limits(s)) {
+    std::vector<double> tot, pb;
+    if ((rc = well_totals(s, tot, pb)) != PF_OK) return rc;
+    if (update_switches(s, tot, pb)) {
+      launch_copy(s->nunk, s->x_old, s->x, s->stream);
+      s->launches += 1;
+      s->switch_attempt++;
+      *resolve = 1;
+      return PF_OK;
+    }
+  }
+  s->switch_attempt = 0;
+  s->in_step = false;
+  return PF_OK;
+}
+
+pf_status pf_abort_step(pf_sim* s) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->in_step) return fail(PF_EINVAL, "no step in progress");
+  launch_copy(s->nunk, s->x_old, s->x, s->stream);
+  s->launches += 1;
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  s->switch_attempt = 0;
+  s->in_step = false;
+  return PF_OK;
+}
+
+pf_status pf_step(pf_sim* s, double dt, pf_step_report* rep) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  pf_step_report out{};
+  for (;;) {
+    if ((rc = pf_begin_step(s, dt)) != PF_OK) return rc;
+    bool converged = false;
+    for (int it = 0; it <= s->opts.newton_max_iter; ++it) {
+      pf_iter_report ir{};
+      rc = newton_iteration(s, &ir, it < s->opts.newton_max_iter);
+      out.krylov_iters += ir.krylov_iters;
+      out.res_scaled = ir.res_scaled;
+      if (rc == PF_ECUDA) return rc;
+      if (rc == PF_OK && ir.converged) {
+        converged = true;
+        out.newton_iters += it;
+        break;
+      }
+      if (rc != PF_OK) break;
+    }
+    if (!converged) {
+      out.newton_iters += s->opts.newton_max_iter;
+      if (rep) *rep = out;
+      pf_abort_step(s);
+      return fail(PF_ENOT_CONVERGED, "Newton did not converge; state restored to the start of the step");
+    }
+    int resolve = 0;
+    if ((rc = pf_end_step(s, &resolve)) != PF_OK) return rc;
+    if (!resolve) break;
+  }
+  out.converged = 1;
+  if (rep) *rep = out;
+  return PF_OK;
+}
+
+pf_status pf_well_rates(pf_sim* s, double* q_w, double* q_o, double* q_p, double* pb) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  std::vector<double> tot, pbv;
+  if ((rc = well_totals(s, tot, pbv)) != PF_OK) return rc;
+  for (int w = 0; w < s->nw; ++w) {
+    if (q_w) q_w[w] = tot[3 * w];
+    if (q_o) q_o[w] = tot[3 * w + 1];
+    if (q_p) q_p[w] = tot[3 * w + 2];
+    if (pb) pb[w] = pbv[w];
+  }
+  return PF_OK;
+}
+
+pf_status pf_well_switched(const pf_sim* s, int* switched) {
+  if (!s || (!switched && s->nw > 0)) return fail(PF_EINVAL, "NULL argument");
+  for (int w = 0; w < s->nw; ++w) switched[w] = s->switched[w];
+  return PF_OK;
+}
+
+pf_status pf_export_system(pf_sim* s, double* R, double* Jc, double* Jw_b, double* Jw_c, double* Jw_d) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->assembled) return fail(PF_EINVAL, "nothing assembled");
+  cudaStream_t st = s->stream;
+  PF_CUDA(cudaStreamSynchronize(st));
+  const long long n = s->g.n;
+  auto fetch = [&](const void* src, double* dst, size_t count) -> pf_status {
+    if (!dst) return PF_OK;
+    if (!s->mixed) {
+      PF_CUDA(cudaMemcpy(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> tmp(count);
+      PF_CUDA(cudaMemcpy(tmp.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < count; ++i) dst[i] = tmp[i];
+    }
+    return PF_OK;
+  };
+  if (R) PF_CUDA(cudaMemcpy(R, s->R, s->nunk * sizeof(double), cudaMemcpyDeviceToHost));
+  if ((rc = fetch(s->J, Jc, (size_t)SL_COUNT * 9 * n)) != PF_OK) return rc;
+  if (s->npf > 0) {
+    if ((rc = fetch(s->Bw, Jw_b, 3 * (size_t)s->npf)) != PF_OK) return rc;
+    if ((rc = fetch(s->Cw, Jw_c, 3 * (size_t)s->npf)) != PF_OK) return rc;
+  }
+  if (s->nw > 0 && (rc = fetch(s->Dw, Jw_d, s->nw)) != PF_OK) return rc;
+  return PF_OK;
+}
+
+pf_status pf_apply_jacobian(pf_sim* s, const double* xh, double* yh) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->assembled) return fail(PF_EINVAL, "nothing assembled");
+  if (!xh || !yh) return fail(PF_EINVAL, "NULL vector");
+  PF_CUDA(cudaMemcpyAsync(s->tmp, xh, s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  if ((rc = spmv(s, s->tmp, s->r)) != PF_OK) return rc;
+  PF_CUDA(cudaMemcpyAsync(yh, s->r, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+pf_status pf_solve_linear(pf_sim* s, const double* bh, double* xh, double rtol, int* iters, double* rel_res) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->assembled) return fail(PF_EINVAL, "nothing assembled");
+  if (!bh || !xh || !(rtol > 0.0)) return fail(PF_EINVAL, "invalid arguments");
+  if ((rc = precond_setup(s)) != PF_OK) return rc;
+  PF_CUDA(cudaMemcpyAsync(s->b, bh, s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  if ((rc = gmres(s, s->b, s->dx, rtol, s->opts.gmres_max_iter, iters, rel_res)) != PF_OK) return rc;
+  PF_CUDA(cudaMemcpyAsync(xh, s->dx, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+pf_status pf_get_state(pf_sim* s, double* P, double* S, double* C, double* Pb) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  const long long n = s->g.n;
+  std::vector<double> xh((size_t)s->nunk);
+  PF_CUDA(cudaMemcpyAsync(xh.data(), s->x, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  for (long long i = 0; i < n; ++i) {
+    if (P) P[i] = xh[3 * i];
+    if (S) S[i] = xh[3 * i + 1];
+    if (C) C[i] = xh[3 * i + 2];
+  }
+  if (Pb) for (int w = 0; w < s->nw; ++w) Pb[w] = xh[3 * n + w];
+  return PF_OK;
+}
+
+pf_status pf_set_state(pf_sim* s, const double* P, const double* S, const double* C, const double* Pb) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  const long long n = s->g.n;
+  std::vector<double> xh((size_t)s->nunk);
+  PF_CUDA(cudaMemcpyAsync(xh.data(), s->x, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  for (long long i = 0; i < n; ++i) {
+    if (P) xh[3 * i] = P[i];
+    if (S) xh[3 * i + 1] = S[i];
+    if (C) xh[3 * i + 2] = C[i];
+  }
+  if (Pb) for (int w = 0; w < s->nw; ++w) xh[3 * n + w] = Pb[w];
+  for (long long i = 0; i < s->nunk; ++i)
+    if (!std::isfinite(xh[i])) return fail(PF_EINVAL, "state must be finite");
+  PF_CUDA(cudaMemcpyAsync(s->x, xh.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  s->assembled = false;
+  return PF_OK;
+}
+
+pf_status pf_sizes(const pf_sim* s, int64_t* n_cells, int* n_wells, int64_t* n_perf) {
+  if (!s) return fail(PF_EINVAL, "pf_sim is NULL");
+  if (n_cells) *n_cells = s->g.n;
+  if (n_wells) *n_wells = s->nw;
+  if (n_perf) *n_perf = s->npf;
+  return PF_OK;
+}
+
+pf_status pf_device_state(pf_sim* s, double** x_dev) {
+  if (!s || !x_dev) return fail(PF_EINVAL, "NULL argument");
+  *x_dev = s->x;
+  return PF_OK;
+}
+
+pf_status pf_get_x(pf_sim* s, double* x) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!x) return fail(PF_EINVAL, "x is NULL");
+  PF_CUDA(cudaMemcpyAsync(x, s->x, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+pf_status pf_set_x(pf_sim* s, const double* x) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!x) return fail(PF_EINVAL, "x is NULL");
+  PF_CUDA(cudaMemcpyAsync(s->x, x, s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  s->assembled = false;
+  return PF_OK;
+}
+
+pf_status pf_kernel_timing_enable(pf_sim* s, int on) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  kt_collect(s);
+  s->kt_on = on != 0;
+  for (int k = 0; k < PF_KT_COUNT; ++k) { s->kt_count[k] = 0; s->kt_ms[k] = 0.0; }
+  return PF_OK;
+}
+
+pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* total_ms) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (which < 0 || which >= PF_KT_COUNT) return fail(PF_EINVAL, "unknown kernel class");
+  kt_collect(s);
+  if (launches) *launches = s->kt_count[which];
+  if (total_ms) *total_ms = s->kt_ms[which];
+  return PF_OK;
+}
+
+pf_status pf_launch_count(const pf_sim* s, int64_t* count) {
+  if (!s || !count) return fail(PF_EINVAL, "NULL argument");
+  *count = s->launches;
+  return PF_OK;
+}
+
+}  // extern "C"

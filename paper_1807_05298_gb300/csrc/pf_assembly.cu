@@ -1,0 +1,725 @@
+// Residual and 3x3 block-Jacobian assembly of the water/oil/polymer model.
+//
+// Equations (arXiv 1807.05298): porosity law Sec. 2.1; phase mass
+// conservation with Darcy flux and gravity Sec. 2.2; polymer conservation,
+// permeability reduction R_k, equilibrium adsorption, Todd-Longstaff
+// viscosities and mixing rules, inaccessible pore volume Sec. 2.3; wells
+// eq. (ssw:Q), (ssw:dp) and the BHP / rate constraints Sec. 2.4; backward
+// Euler Sec. 3.1; two-point transmissibility with harmonic geometry and
+// permeability, pore-volume weighted rho and mu, upstream k_r Sec. 3.2.
+//
+// Kernel sequence per assembly (all deterministic, no atomics):
+//   cell_props  one thread per cell: properties and their derivatives into a
+//               scratch (values FP64, derivatives DT), accumulation masses into
+//               R and their derivatives into the diagonal block;
+//   face_flux   one thread per cell for its +x, +y, +z faces: phase potentials,
+//               upstream selection, fluxes into a face buffer, and the two
+//               off-diagonal blocks of the face written straight into J;
+//   gather      one thread per cell: residual flux sum in the fixed order
+//               -x, +x, -y, +y, -z, +z and the flux part of the diagonal block
+//               as minus the sum of the column's off-diagonal blocks (a flux
+//               depends only on its two cells, so dF/dx_L = J[H][L] / dt);
+//   wells       one warp per well: perforation rates, their derivatives into
+//               the perforated cell rows and the well border, the well row.
+#include <math.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// cell properties and accumulation
+// ---------------------------------------------------------------------------
+
+struct CellEval {
+  double phi, rho_o, rho_w, Pw, krw, kro, Rk, mu_we, mu_pe, ads;
+  double dphi, drho_o, drho_wP, drho_wS, dPw_S, dkrw, dkro, dRk, dmu_we, dmu_pe, dads;
+};
+
+__device__ __forceinline__ double powi_or_pow(double b, double e) {
+  if (e == 2.0) return b * b;
+  if (e == 1.0) return b;
+  return pow(b, e);
+}
+
+__device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P, double S, double C,
+                                          CellEval& c) {
+  c.phi = phi_r + ph.c_r * (P - ph.p_r);
+  c.dphi = ph.c_r;
+  c.rho_o = ph.rho_o * (1.0 + ph.c_o * (P - ph.p_ref));
+  c.drho_o = ph.rho_o * ph.c_o;
+  // normalised saturation, clipped; derivative of the interior formula on [0, 1]
+  double sn = (S - ph.swc) * ph.inv_den, dsn = ph.inv_den;
+  if (sn < 0.0) { sn = 0.0; dsn = 0.0; }
+  if (sn > 1.0) { sn = 1.0; dsn = 0.0; }
+  const double so = 1.0 - sn;
+  c.krw = ph.krw_max * powi_or_pow(sn, ph.nw);
+  c.dkrw = (sn == 0.0 && ph.nw > 1.0) ? 0.0 : ph.krw_max * ph.nw * powi_or_pow(sn, ph.nw - 1.0) * dsn;
+  c.kro = ph.kro_max * powi_or_pow(so, ph.no);
+  c.dkro = (so == 0.0 && ph.no > 1.0) ? 0.0 : -ph.kro_max * ph.no * powi_or_pow(so, ph.no - 1.0) * dsn;
+  double pc = 0.0, dpc = 0.0;
+  if (ph.pc_e != 0.0) {
+    pc = ph.pc_e * powi_or_pow(so, ph.pc_n);
+    dpc = (so == 0.0 && ph.pc_n > 1.0) ? 0.0 : -ph.pc_e * ph.pc_n * powi_or_pow(so, ph.pc_n - 1.0) * dsn;
+  }
+  c.Pw = P - pc;
+  c.dPw_S = -dpc;
+  c.rho_w = ph.rho_w * (1.0 + ph.c_w * (c.Pw - ph.p_ref));
+  c.drho_wP = ph.rho_w * ph.c_w;
+  c.drho_wS = ph.rho_w * ph.c_w * c.dPw_S;
+  // Langmuir adsorption and permeability reduction
+  const double den = 1.0 + ph.ads_b * C;
+  c.ads = ph.ads_a * C / den;
+  c.dads = ph.ads_a / (den * den);
+  c.Rk = 1.0 + ph.rk_coef * c.ads;
+  c.dRk = ph.rk_coef * c.dads;
+  // mixing rule
+  const double beta = C * ph.inv_c_ref;
+  double mu_m, dmu_m;
+  if (ph.mixing == PF_MIX_NONLINEAR) {
+    mu_m = exp(ph.ln_mu_w + beta * ph.ln_mu_ratio);
+    dmu_m = mu_m * ph.ln_mu_ratio * ph.inv_c_ref;
+  } else {
+    mu_m = ph.mu_w + beta * (ph.mu_p0 - ph.mu_w);
+    dmu_m = (ph.mu_p0 - ph.mu_w) * ph.inv_c_ref;
+  }
+  // Todd-Longstaff effective viscosities
+  double alpha = beta, dalpha = ph.inv_c_ref;
+  if (alpha < 0.0) { alpha = 0.0; dalpha = 0.0; }
+  if (alpha > 1.0) { alpha = 1.0; dalpha = 0.0; }
+  double mu_pe, dmu_pe, mu_wp, dmu_wp;
+  if (ph.omega == 1.0) {
+    mu_pe = mu_m; dmu_pe = dmu_m; mu_wp = mu_m; dmu_wp = dmu_m;
+  } else {
+    const double mo = pow(mu_m, ph.omega);
+    const double dmo = ph.omega * mo / mu_m * dmu_m;
+    mu_pe = mo * ph.mu_p0_pow; dmu_pe = dmo * ph.mu_p0_pow;
+    mu_wp = mo * ph.mu_w_pow; dmu_wp = dmo * ph.mu_w_pow;
+  }
+  const double inv = alpha / mu_pe + (1.0 - alpha) / mu_wp;
+  const double dinv = dalpha / mu_pe - alpha * dmu_pe / (mu_pe * mu_pe) - dalpha / mu_wp -
+                      (1.0 - alpha) * dmu_wp / (mu_wp * mu_wp);
+  c.mu_we = 1.0 / inv;
+  c.dmu_we = -dinv * c.mu_we * c.mu_we;
+  c.mu_pe = mu_pe;
+  c.dmu_pe = dmu_pe;
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const double* __restrict__ phi_r,
+                                                    const double* __restrict__ x, double* __restrict__ pv,
+                                                    DT* __restrict__ pd, const double* __restrict__ Mold,
+                                                    double* __restrict__ R, DT* __restrict__ J,
+                                                    double* __restrict__ Mold_out, int mode) {
+  const long long n = g.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double P = x[3 * i], S = x[3 * i + 1], C = x[3 * i + 2];
+    CellEval c;
+    eval_cell(ph, phi_r[i], P, S, C, c);
+    const double V = g.V;
+    // accumulation masses (oil, water, polymer)
+    const double Mo = V * c.phi * c.rho_o * (1.0 - S);
+    const double Mw = V * c.phi * c.rho_w * S;
+    const double k1 = V * (1.0 - ph.ipv) * ph.inv_rho_w;
+    const double Mp = k1 * c.phi * S * c.rho_w * C + V * (1.0 - c.phi) * c.ads;
+    if (mode == 2) {  // values only, for well totals
+      pv[PV_RHO_O * n + i] = c.rho_o;
+      pv[PV_RHO_W * n + i] = c.rho_w;
+      pv[PV_PW * n + i] = c.Pw;
+      pv[PV_KRW * n + i] = c.krw;
+      pv[PV_KRO * n + i] = c.kro;
+      pv[PV_RK * n + i] = c.Rk;
+      pv[PV_MUWE * n + i] = c.mu_we;
+      pv[PV_MUPE * n + i] = c.mu_pe;
+      continue;
+    }
+    if (mode == 1) {
+      Mold_out[3 * i] = Mo;
+      Mold_out[3 * i + 1] = Mw;
+      Mold_out[3 * i + 2] = Mp;
+      pv[PV_RHO_O * n + i] = c.rho_o;
+      pv[PV_RHO_W * n + i] = c.rho_w;
+      pv[PV_KRW * n + i] = c.krw;
+      pv[PV_KRO * n + i] = c.kro;
+      pv[PV_RK * n + i] = c.Rk;
+      pv[PV_MUWE * n + i] = c.mu_we;
+      continue;
+    }
+    pv[PV_RHO_O * n + i] = c.rho_o;
+    pv[PV_RHO_W * n + i] = c.rho_w;
+    pv[PV_PW * n + i] = c.Pw;
+    pv[PV_KRW * n + i] = c.krw;
+    pv[PV_KRO * n + i] = c.kro;
+    pv[PV_RK * n + i] = c.Rk;
+    pv[PV_MUWE * n + i] = c.mu_we;
+    pv[PV_MUPE * n + i] = c.mu_pe;
+    pd[PD_RHO_O * n + i] = (DT)c.drho_o;
+    pd[PD_RHO_WP * n + i] = (DT)c.drho_wP;
+    pd[PD_RHO_WS * n + i] = (DT)c.drho_wS;
+    pd[PD_PW_S * n + i] = (DT)c.dPw_S;
+    pd[PD_KRW * n + i] = (DT)c.dkrw;
+    pd[PD_KRO * n + i] = (DT)c.dkro;
+    pd[PD_RK * n + i] = (DT)c.dRk;
+    pd[PD_MUWE * n + i] = (DT)c.dmu_we;
+    pd[PD_MUPE * n + i] = (DT)c.dmu_pe;
+    R[3 * i] = Mo - Mold[3 * i];
+    R[3 * i + 1] = Mw - Mold[3 * i + 1];
+    R[3 * i + 2] = Mp - Mold[3 * i + 2];
+    // d(M)/d(P, S, C): rows oil, water, polymer
+    DT* Jd = J + (size_t)SL_D * 9 * n;
+    const double dMoP = V * (c.dphi * c.rho_o + c.phi * c.drho_o) * (1.0 - S);
+    const double dMoS = -V * c.phi * c.rho_o;
+    const double dMwP = V * (c.dphi * c.rho_w + c.phi * c.drho_wP) * S;
+    const double dMwS = V * c.phi * (c.drho_wS * S + c.rho_w);
+    const double dMpP = k1 * S * C * (c.dphi * c.rho_w + c.phi * c.drho_wP) - V * c.dphi * c.ads;
+    const double dMpS = k1 * C * c.phi * (c.rho_w + S * c.drho_wS);
+    const double dMpC = k1 * c.phi * S * c.rho_w + V * (1.0 - c.phi) * c.dads;
+    Jd[0 * n + i] = (DT)dMoP;
+    Jd[1 * n + i] = (DT)dMoS;
+    Jd[2 * n + i] = (DT)0.0;
+    Jd[3 * n + i] = (DT)dMwP;
+    Jd[4 * n + i] = (DT)dMwS;
+    Jd[5 * n + i] = (DT)0.0;
+    Jd[6 * n + i] = (DT)dMpP;
+    Jd[7 * n + i] = (DT)dMpS;
+    Jd[8 * n + i] = (DT)dMpC;
+  }
+}
+
+template <typename DT>
+void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x, double* pv,
+                       DT* pd, const double* Mold, double* R, DT* J, double* Mold_out, int mode,
+                       cudaStream_t st) {
+  k_cell_props<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
+}
+
+// ---------------------------------------------------------------------------
+// face fluxes with upstream weighting
+// ---------------------------------------------------------------------------
+
+struct SideV {
+  double P, C, rho_o, rho_w, Pw, krw, kro, Rk, mu_we, mu_pe;
+};
+template <typename DT>
+struct SideD {
+  DT drho_o, drho_wP, drho_wS, dPw_S, dkrw, dkro, dRk, dmu_we, dmu_pe;
+};
+
+template <typename DT>
+__device__ __forceinline__ void load_side(long long i, long long n, const double* __restrict__ x,
+                                          const double* __restrict__ pv, const DT* __restrict__ pd,
+                                          SideV& v, SideD<DT>& d) {
+  v.P = x[3 * i];
+  v.C = x[3 * i + 2];
+  v.rho_o = pv[PV_RHO_O * n + i];
+  v.rho_w = pv[PV_RHO_W * n + i];
+  v.Pw = pv[PV_PW * n + i];
+  v.krw = pv[PV_KRW * n + i];
+  v.kro = pv[PV_KRO * n + i];
+  v.Rk = pv[PV_RK * n + i];
+  v.mu_we = pv[PV_MUWE * n + i];
+  v.mu_pe = pv[PV_MUPE * n + i];
+  d.drho_o = pd[PD_RHO_O * n + i];
+  d.drho_wP = pd[PD_RHO_WP * n + i];
+  d.drho_wS = pd[PD_RHO_WS * n + i];
+  d.dPw_S = pd[PD_PW_S * n + i];
+  d.dkrw = pd[PD_KRW * n + i];
+  d.dkro = pd[PD_KRO * n + i];
+  d.dRk = pd[PD_RK * n + i];
+  d.dmu_we = pd[PD_MUWE * n + i];
+  d.dmu_pe = pd[PD_MUPE * n + i];
+}
+
+// Mass fluxes F (oil, water, polymer) from H into L across one face and their
+// derivatives dL = dF/d(P_L, S_L, C_L), dH = dF/d(P_H, S_H, C_H), row-major
+// 3x3 (rows oil, water, polymer).  gdz = g (Z_H - Z_L).
+template <typename DT>
+__device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, double wL,
+                                          const SideV& a, const SideD<DT>& da, const SideV& b,
+                                          const SideD<DT>& db, double F[3], DT dL[9], DT dH[9]) {
+  const double wH = 1.0 - wL;
+  // oil phase
+  const double rho_o = wL * a.rho_o + wH * b.rho_o;
+  const double dPo = (b.P - a.P) - rho_o * gdz;
+  const bool upHo = dPo >= 0.0;
+  const double kro = upHo ? b.kro : a.kro;
+  const DT dkro = upHo ? db.dkro : da.dkro;
+  const double To = T / ph.mu_o;
+  F[0] = To * kro * rho_o * dPo;
+  {
+    const DT Tk = (DT)(To * kro);
+    const DT ddPL = (DT)(-1.0) - (DT)gdz * (DT)wL * da.drho_o;
+    const DT ddPH = (DT)(1.0) - (DT)gdz * (DT)wH * db.drho_o;
+    dL[0] = Tk * ((DT)wL * da.drho_o * (DT)dPo + (DT)rho_o * ddPL);
+    dH[0] = Tk * ((DT)wH * db.drho_o * (DT)dPo + (DT)rho_o * ddPH);
+    const DT dS = (DT)To * dkro * (DT)(rho_o * dPo);
+    dL[1] = upHo ? (DT)0 : dS;
+    dH[1] = upHo ? dS : (DT)0;
+    dL[2] = (DT)0;
+    dH[2] = (DT)0;
+  }
+  // water phase (and polymer carried by it)
+  const double rho_w = wL * a.rho_w + wH * b.rho_w;
+  const double dPw = (b.Pw - a.Pw) - rho_w * gdz;
+  const bool upHw = dPw >= 0.0;
+  const double krw = upHw ? b.krw : a.krw;
+  const double Rk = upHw ? b.Rk : a.Rk;
+  const double Cu = upHw ? b.C : a.C;
+  const DT dkrw = upHw ? db.dkrw : da.dkrw;
+  const DT dRk = upHw ? db.dRk : da.dRk;
+  const double mu_we = wL * a.mu_we + wH * b.mu_we;
+  const double mu_pe = wL * a.mu_pe + wH * b.mu_pe;
+  const double A = rho_w * dPw;
+  const double mw = krw / (Rk * mu_we);
+  const double mp = krw / (Rk * mu_pe);
+  const double cf = Cu * ph.inv_rho_w;
+  F[1] = T * mw * A;
+  F[2] = T * mp * A * cf;
+  // dA/d(P_L, S_L, P_H, S_H)
+  const DT dA_PL = (DT)wL * da.drho_wP * (DT)dPw + (DT)rho_w * ((DT)(-1.0) - (DT)gdz * (DT)wL * da.drho_wP);
+  const DT dA_SL = (DT)wL * da.drho_wS * (DT)dPw + (DT)rho_w * (-da.dPw_S - (DT)gdz * (DT)wL * da.drho_wS);
+  const DT dA_PH = (DT)wH * db.drho_wP * (DT)dPw + (DT)rho_w * ((DT)(1.0) - (DT)gdz * (DT)wH * db.drho_wP);
+  const DT dA_SH = (DT)wH * db.drho_wS * (DT)dPw + (DT)rho_w * (db.dPw_S - (DT)gdz * (DT)wH * db.drho_wS);
+  const DT Tmw = (DT)(T * mw), Tmp = (DT)(T * mp * cf);
+  // pressure and saturation columns through A
+  dL[3] = Tmw * dA_PL;
+  dH[3] = Tmw * dA_PH;
+  dL[4] = Tmw * dA_SL;
+  dH[4] = Tmw * dA_SH;
+  dL[6] = Tmp * dA_PL;
+  dH[6] = Tmp * dA_PH;
+  dL[7] = Tmp * dA_SL;
+  dH[7] = Tmp * dA_SH;
+  // concentration columns through the averaged viscosities
+  const DT TA = (DT)(T * A);
+  dL[5] = -TA * (DT)mw * (DT)wL * da.dmu_we / (DT)mu_we;
+  dH[5] = -TA * (DT)mw * (DT)wH * db.dmu_we / (DT)mu_we;
+  dL[8] = -TA * (DT)(mp * cf) * (DT)wL * da.dmu_pe / (DT)mu_pe;
+  dH[8] = -TA * (DT)(mp * cf) * (DT)wH * db.dmu_pe / (DT)mu_pe;
+  // upstream cell: k_rw (saturation), R_k and the carried concentration
+  const DT dFw_S = TA * dkrw / (DT)(Rk * mu_we);
+  const DT dFp_S = TA * (DT)cf * dkrw / (DT)(Rk * mu_pe);
+  const DT dFw_C = -TA * (DT)mw * dRk / (DT)Rk;
+  const DT dFp_C = TA * ((DT)(mp * cf) * (-dRk / (DT)Rk) + (DT)(mp * ph.inv_rho_w));
+  if (upHw) {
+    dH[4] += dFw_S; dH[7] += dFp_S; dH[5] += dFw_C; dH[8] += dFp_C;
+  } else {
+    dL[4] += dFw_S; dL[7] += dFp_S; dL[5] += dFw_C; dL[8] += dFp_C;
+  }
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double* __restrict__ phi_r,
+                                                   const double* __restrict__ T3, const double* __restrict__ x,
+                                                   const double* __restrict__ pv, const DT* __restrict__ pd,
+                                                   double dt, DT* __restrict__ J, double* __restrict__ Fbuf) {
+  const long long n = g.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / g.nxy;
+    const long long rem = i - k * g.nxy;
+    const long long j = rem / g.nx;
+    const long long ii = rem - j * g.nx;
+    SideV a; SideD<DT> da;
+    load_side<DT>(i, n, x, pv, pd, a, da);
+    const double phL = phi_r[i];
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      bool has;
+      long long s;
+      double gdz = 0.0;
+      if (d == 0) { has = ii + 1 < g.nx; s = 1; }
+      else if (d == 1) { has = j + 1 < g.ny; s = g.nx; }
+      else { has = k + 1 < g.nz; s = g.nxy; gdz = ph.g * g.dz; }
+      double* Fd = Fbuf + (size_t)d * 3 * n;
+      if (!has) {
+        Fd[i] = 0.0; Fd[n + i] = 0.0; Fd[2 * n + i] = 0.0;
+        continue;
+      }
+      const long long h = i + s;
+      SideV b; SideD<DT> db;
+      load_side<DT>(h, n, x, pv, pd, b, db);
+      const double phH = phi_r[h];
+      const double wL = phL / (phL + phH);
+      double F[3]; DT dL[9], dH[9];
+      face_flux<DT>(ph, T3[(size_t)d * n + i], gdz, wL, a, da, b, db, F, dL, dH);
+      Fd[i] = F[0]; Fd[n + i] = F[1]; Fd[2 * n + i] = F[2];
+      // row L, column H: -dt dF/dx_H  (slot +d of row i)
+      DT* Jp = J + (size_t)(SL_XP + 2 * d) * 9 * n;
+      // row H, column L: +dt dF/dx_L  (slot -d of row h)
+      DT* Jm = J + (size_t)(SL_XM + 2 * d) * 9 * n;
+      const DT mdt = (DT)(-dt), pdt = (DT)dt;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        Jp[(size_t)e * n + i] = mdt * dH[e];
+        Jm[(size_t)e * n + h] = pdt * dL[e];
+      }
+    }
+    // slots that leave the grid on the minus side are zero
+    if (ii == 0) { DT* Jm = J + (size_t)SL_XM * 9 * n; for (int e = 0; e < 9; ++e) Jm[(size_t)e * n + i] = (DT)0; }
+    if (j == 0) { DT* Jm = J + (size_t)SL_YM * 9 * n; for (int e = 0; e < 9; ++e) Jm[(size_t)e * n + i] = (DT)0; }
+    if (k == 0) { DT* Jm = J + (size_t)SL_ZM * 9 * n; for (int e = 0; e < 9; ++e) Jm[(size_t)e * n + i] = (DT)0; }
+    if (ii + 1 == g.nx) { DT* Jp = J + (size_t)SL_XP * 9 * n; for (int e = 0; e < 9; ++e) Jp[(size_t)e * n + i] = (DT)0; }
+    if (j + 1 == g.ny) { DT* Jp = J + (size_t)SL_YP * 9 * n; for (int e = 0; e < 9; ++e) Jp[(size_t)e * n + i] = (DT)0; }
+    if (k + 1 == g.nz) { DT* Jp = J + (size_t)SL_ZP * 9 * n; for (int e = 0; e < 9; ++e) Jp[(size_t)e * n + i] = (DT)0; }
+  }
+}
+
+template <typename DT>
+void launch_face_flux(const Grid& g, const Phys& ph, const double* phi_r, const double* T3, const double* x,
+                      const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st) {
+  k_face_flux<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, phi_r, T3, x, pv, pd, dt, J, Fbuf);
+}
+
+// ---------------------------------------------------------------------------
+// gather: residual flux sums and the flux part of the diagonal block
+// ---------------------------------------------------------------------------
+
+template <typename DT>
+__global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict__ Fbuf, double dt,
+                                                double* __restrict__ R, DT* __restrict__ J) {
+  const long long n = g.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / g.nxy;
+    const long long rem = i - k * g.nxy;
+    const long long j = rem / g.nx;
+    const long long ii = rem - j * g.nx;
+    double fs[3] = {0.0, 0.0, 0.0};
+    DT dsum[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) dsum[e] = (DT)0;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      const long long s = d == 0 ? 1 : (d == 1 ? g.nx : g.nxy);
+      const bool has_m = d == 0 ? ii > 0 : (d == 1 ? j > 0 : k > 0);
+      const bool has_p = d == 0 ? ii + 1 < g.nx : (d == 1 ? j + 1 < g.ny : k + 1 < g.nz);
+      const double* Fd = Fbuf + (size_t)d * 3 * n;
+      if (has_m) {  // face (i - s, i): i is H; R_H += dt F; diag += +dt dF/dx_H = -J[i-s][+d]
+        const long long l = i - s;
+        fs[0] -= Fd[l]; fs[1] -= Fd[n + l]; fs[2] -= Fd[2 * n + l];
+        const DT* Jp = J + (size_t)(SL_XP + 2 * d) * 9 * n;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) dsum[e] += Jp[(size_t)e * n + l];
+      }
+      if (has_p) {  // face (i, i + s): i is L; R_L -= dt F; diag += -dt dF/dx_L = -J[i+s][-d]
+        const long long h = i + s;
+        fs[0] += Fd[i]; fs[1] += Fd[n + i]; fs[2] += Fd[2 * n + i];
+        const DT* Jm = J + (size_t)(SL_XM + 2 * d) * 9 * n;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) dsum[e] += Jm[(size_t)e * n + h];
+      }
+    }
+    R[3 * i] -= dt * fs[0];
+    R[3 * i + 1] -= dt * fs[1];
+    R[3 * i + 2] -= dt * fs[2];
+    DT* Jd = J + (size_t)SL_D * 9 * n;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Jd[(size_t)e * n + i] -= dsum[e];
+  }
+}
+
+template <typename DT>
+void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st) {
+  k_gather<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, Fbuf, dt, R, J);
+}
+
+// ---------------------------------------------------------------------------
+// wells: one warp per well
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename DT>
+__global__ void k_wells(Grid g, Phys ph, Wells w, const double* __restrict__ x, const double* __restrict__ pv,
+                        const DT* __restrict__ pd, double dt, double* __restrict__ R, DT* __restrict__ J,
+                        DT* __restrict__ Bw, DT* __restrict__ Cw, DT* __restrict__ Dw) {
+  const int wi = blockIdx.x;
+  if (wi >= w.nw) return;
+  const int lane = threadIdx.x;
+  const long long n = g.n;
+  const long long npf = w.npf;
+  const double Pb = x[3 * n + wi];
+  const double gam = w.gamma[wi];
+  const int kind = w.kind[wi];
+  const int ctrl = w.ctrl[wi];
+  const double sw = w.sw[wi], so = w.so[wi];
+  const double cinj = w.cinj[wi];
+  double sum_q = 0.0, sum_dPb = 0.0;
+  DT* Jd = J + (size_t)SL_D * 9 * n;
+  for (int m = w.ptr[wi] + lane; m < w.ptr[wi + 1]; m += 32) {
+    const long long c = w.cell[m];
+    const double WI = w.wi[m];
+    const double P = x[3 * c], C = x[3 * c + 2];
+    const double rho_o = pv[PV_RHO_O * n + c], rho_w = pv[PV_RHO_W * n + c];
+    const double Pw = pv[PV_PW * n + c];
+    const double krw = pv[PV_KRW * n + c], kro = pv[PV_KRO * n + c];
+    const double Rk = pv[PV_RK * n + c], mu_we = pv[PV_MUWE * n + c];
+    const double drho_o = pd[PD_RHO_O * n + c], drho_wP = pd[PD_RHO_WP * n + c];
+    const double drho_wS = pd[PD_RHO_WS * n + c], dPw_S = pd[PD_PW_S * n + c];
+    const double dkrw = pd[PD_KRW * n + c], dkro = pd[PD_KRO * n + c];
+    const double dRk = pd[PD_RK * n + c], dmu_we = pd[PD_MUWE * n + c];
+    const double Pbm = Pb + gam * w.dzb[m];
+    // water mobility and derivatives (S, C)
+    const double lw = krw / (Rk * mu_we);
+    const double dlw_S = dkrw / (Rk * mu_we);
+    const double dlw_C = -lw * (dRk / Rk + dmu_we / mu_we);
+    const double lo = kro / ph.mu_o;
+    const double dlo_S = dkro / ph.mu_o;
+    const double dw = Pbm - Pw;  // water drawdown
+    double qw, qo, qp;
+    double dqw[4], dqo[4], dqp[4];  // d/d(P, S, C, Pb)
+    if (kind == PF_WELL_INJECTOR) {
+      const double lt = lw + lo, dlt_S = dlw_S + dlo_S, dlt_C = dlw_C;
+      qw = WI * lt * rho_w * dw;
+      dqw[0] = WI * lt * (drho_wP * dw - rho_w);
+      dqw[1] = WI * (dlt_S * rho_w * dw + lt * drho_wS * dw - lt * rho_w * dPw_S);
+      dqw[2] = WI * dlt_C * rho_w * dw;
+      dqw[3] = WI * lt * rho_w;
+      qo = 0.0;
+      dqo[0] = dqo[1] = dqo[2] = dqo[3] = 0.0;
+      const double cf = cinj * ph.inv_rho_w;
+      qp = qw * cf;
+      for (int t = 0; t < 4; ++t) dqp[t] = dqw[t] * cf;
+    } else {
+      qw = WI * lw * rho_w * dw;
+      dqw[0] = WI * lw * (drho_wP * dw - rho_w);
+      dqw[1] = WI * (dlw_S * rho_w * dw + lw * drho_wS * dw - lw * rho_w * dPw_S);
+      dqw[2] = WI * dlw_C * rho_w * dw;
+      dqw[3] = WI * lw * rho_w;
+      const double dox = Pbm - P;
+      qo = WI * lo * rho_o * dox;
+      dqo[0] = WI * lo * (drho_o * dox - rho_o);
+      dqo[1] = WI * dlo_S * rho_o * dox;
+      dqo[2] = 0.0;
+      dqo[3] = WI * lo * rho_o;
+      const double cf = C * ph.inv_rho_w;
+      qp = qw * cf;
+      dqp[0] = dqw[0] * cf;
+      dqp[1] = dqw[1] * cf;
+      dqp[2] = dqw[2] * cf + qw * ph.inv_rho_w;
+      dqp[3] = dqw[3] * cf;
+    }
+    // cell rows (a cell holds at most one perforation: no race)
+    R[3 * c] -= dt * qo;
+    R[3 * c + 1] -= dt * qw;
+    R[3 * c + 2] -= dt * qp;
+    for (int b = 0; b < 3; ++b) {
+      Jd[(size_t)(0 + b) * n + c] -= (DT)(dt * dqo[b]);
+      Jd[(size_t)(3 + b) * n + c] -= (DT)(dt * dqw[b]);
+      Jd[(size_t)(6 + b) * n + c] -= (DT)(dt * dqp[b]);
+    }
+    Bw[0 * npf + m] = (DT)(-dt * dqo[3]);
+    Bw[1 * npf + m] = (DT)(-dt * dqw[3]);
+    Bw[2 * npf + m] = (DT)(-dt * dqp[3]);
+    if (ctrl == PF_CTRL_BHP) {
+      Cw[0 * npf + m] = (DT)0; Cw[1 * npf + m] = (DT)0; Cw[2 * npf + m] = (DT)0;
+    } else {
+      for (int b = 0; b < 3; ++b) Cw[(size_t)b * npf + m] = (DT)(dt * (sw * dqw[b] + so * dqo[b]));
+      sum_q += sw * qw + so * qo;
+      sum_dPb += sw * dqw[3] + so * dqo[3];
+    }
+  }
+  sum_q = warp_sum(sum_q);
+  sum_dPb = warp_sum(sum_dPb);
+  if (lane == 0) {
+    if (ctrl == PF_CTRL_BHP) {
+      R[3 * n + wi] = dt * w.W[wi] * (Pb - w.target[wi]);
+      Dw[wi] = (DT)(dt * w.W[wi]);
+    } else {
+      R[3 * n + wi] = dt * (sum_q - w.target[wi]);
+      Dw[wi] = (DT)(dt * sum_dPb);
+    }
+  }
+}
+
+template <typename DT>
+void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv, const DT* pd,
+                  double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st) {
+  if (w.nw == 0) return;
+  k_wells<DT><<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, pd, dt, R, J, Bw, Cw, Dw);
+}
+
+// Lagged wellbore unit weight (frozen over a step): rho_w(P_b) g for an
+// injector, the mobility-weighted mixture density over the perforations
+// times g for a producer.  Needs pv from a mode-1 cell_props pass.
+__global__ void k_well_gamma(Grid g, Phys ph, Wells w, const double* __restrict__ x,
+                             const double* __restrict__ pv, double* __restrict__ gamma) {
+  const int wi = blockIdx.x;
+  if (wi >= w.nw) return;
+  const int lane = threadIdx.x;
+  const long long n = g.n;
+  if (w.kind[wi] == PF_WELL_INJECTOR) {
+    if (lane == 0) gamma[wi] = ph.g * ph.rho_w * (1.0 + ph.c_w * (x[3 * n + wi] - ph.p_ref));
+    return;
+  }
+  double num = 0.0, den = 0.0;
+  for (int m = w.ptr[wi] + lane; m < w.ptr[wi + 1]; m += 32) {
+    const long long c = w.cell[m];
+    const double lw = pv[PV_KRW * n + c] / (pv[PV_RK * n + c] * pv[PV_MUWE * n + c]);
+    const double lo = pv[PV_KRO * n + c] / ph.mu_o;
+    num += lw * pv[PV_RHO_W * n + c] + lo * pv[PV_RHO_O * n + c];
+    den += lw + lo;
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if (lane == 0) {
+    if (den > 0.0) gamma[wi] = ph.g * num / den;
+    else gamma[wi] = ph.g * pv[PV_RHO_O * n + w.cell[w.ptr[wi]]];
+  }
+}
+
+// Summed water, oil and polymer mass rates of each well at the current state
+// (values of eq. (ssw:Q) with the lagged gamma); needs pv from a mode-2 pass.
+__global__ void k_well_totals(Grid g, Phys ph, Wells w, const double* __restrict__ x,
+                              const double* __restrict__ pv, double* __restrict__ out) {
+  const int wi = blockIdx.x;
+  if (wi >= w.nw) return;
+  const int lane = threadIdx.x;
+  const long long n = g.n;
+  const double Pb = x[3 * n + wi];
+  double sw = 0.0, so = 0.0, sp = 0.0;
+  for (int m = w.ptr[wi] + lane; m < w.ptr[wi + 1]; m += 32) {
+    const long long c = w.cell[m];
+    const double Pbm = Pb + w.gamma[wi] * w.dzb[m];
+    const double lw = pv[PV_KRW * n + c] / (pv[PV_RK * n + c] * pv[PV_MUWE * n + c]);
+    const double lo = pv[PV_KRO * n + c] / ph.mu_o;
+    const double rho_w = pv[PV_RHO_W * n + c], rho_o = pv[PV_RHO_O * n + c];
+    const double dw = Pbm - pv[PV_PW * n + c];
+    if (w.kind[wi] == PF_WELL_INJECTOR) {
+      const double qw = w.wi[m] * (lw + lo) * rho_w * dw;
+      sw += qw;
+      sp += qw * w.cinj[wi] * ph.inv_rho_w;
+    } else {
+      const double qw = w.wi[m] * lw * rho_w * dw;
+      sw += qw;
+      so += w.wi[m] * lo * rho_o * (Pbm - x[3 * c]);
+      sp += qw * x[3 * c + 2] * ph.inv_rho_w;
+    }
+  }
+  sw = warp_sum(sw);
+  so = warp_sum(so);
+  sp = warp_sum(sp);
+  if (lane == 0) {
+    out[3 * wi] = sw;
+    out[3 * wi + 1] = so;
+    out[3 * wi + 2] = sp;
+  }
+}
+
+void launch_well_totals(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
+                        double* out, cudaStream_t st) {
+  if (w.nw == 0) return;
+  k_well_totals<<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, out);
+}
+
+void launch_well_gamma(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
+                       double* gamma, cudaStream_t st) {
+  if (w.nw == 0) return;
+  k_well_gamma<<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, gamma);
+}
+
+// ---------------------------------------------------------------------------
+// residual norms
+// ---------------------------------------------------------------------------
+
+// max that propagates NaN (fmax would drop it and hide a broken iterate)
+__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_res_norm_partial(Grid g, Phys ph, const double* __restrict__ phi_r,
+                                                          const double* __restrict__ R, double* __restrict__ partial) {
+  const long long n = g.n;
+  double mx = 0.0, ss = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double pv = g.V * phi_r[i];
+    const double r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+    mx = nanmax(mx, fabs(r0) / (pv * ph.rho_o));
+    mx = nanmax(mx, fabs(r1) / (pv * ph.rho_w));
+    mx = nanmax(mx, fabs(r2) / (pv * ph.c_ref));
+    ss += r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  __shared__ double smx[8], sss[8];
+  mx = warp_max(mx);
+  ss = warp_sum(ss);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { smx[wid] = mx; sss[wid] = ss; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) { a = nanmax(a, smx[t]); b += sss[t]; }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_res_norm_final(int nblocks, Wells w, long long n, const double* __restrict__ R, double dt,
+                                 const double* __restrict__ partial, double* __restrict__ out) {
+  // one warp: fixed-order reduction of the block partials, then the well rows
+  const int lane = threadIdx.x;
+  double mx = 0.0, ss = 0.0;
+  for (int b = lane; b < nblocks; b += 32) { mx = nanmax(mx, partial[2 * b]); ss += partial[2 * b + 1]; }
+  for (int wi = lane; wi < w.nw; wi += 32) {
+    const double r = R[3 * n + wi];
+    mx = nanmax(mx, fabs(r) / (dt * w.scale[wi]));
+    ss += r * r;
+  }
+  mx = warp_max(mx);
+  ss = warp_sum(ss);
+  if (lane == 0) { out[0] = mx; out[1] = ss; }
+}
+
+void launch_residual_norms(const Grid& g, const Phys& ph, const double* phi_r, const Wells& w, const double* R,
+                           double dt, double* partial, int nblocks, double* out, cudaStream_t st) {
+  k_res_norm_partial<<<nblocks, 256, 0, st>>>(g, ph, phi_r, R, partial);
+  k_res_norm_final<<<1, 32, 0, st>>>(nblocks, w, g.n, R, dt, partial, out);
+}
+
+// ---------------------------------------------------------------------------
+// Newton update with the saturation chop and the bounds on S and C
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_newton_update(long long n, int nw, double* __restrict__ x,
+                                                       const double* __restrict__ dx, double ds_max) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nw;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i >= n) { x[3 * n + (i - n)] += dx[3 * n + (i - n)]; continue; }
+    x[3 * i] += dx[3 * i];
+    const double ds = fmin(fmax(dx[3 * i + 1], -ds_max), ds_max);
+    x[3 * i + 1] = fmin(fmax(x[3 * i + 1] + ds, 0.0), 1.0);
+    x[3 * i + 2] = fmax(x[3 * i + 2] + dx[3 * i + 2], 0.0);
+  }
+}
+
+void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max, cudaStream_t st) {
+  k_newton_update<<<grid_for(g.n + nw, 256), 256, 0, st>>>(g.n, nw, x, dx, ds_max);
+}
+
+// explicit instantiations
+template void launch_cell_props<double>(const Grid&, const Phys&, const double*, const double*, double*, double*,
+                                        const double*, double*, double*, double*, int, cudaStream_t);
+template void launch_cell_props<float>(const Grid&, const Phys&, const double*, const double*, double*, float*,
+                                       const double*, double*, float*, double*, int, cudaStream_t);
+template void launch_face_flux<double>(const Grid&, const Phys&, const double*, const double*, const double*,
+                                       const double*, const double*, double, double*, double*, cudaStream_t);
+template void launch_face_flux<float>(const Grid&, const Phys&, const double*, const double*, const double*,
+                                      const double*, const float*, double, float*, double*, cudaStream_t);
+template void launch_gather<double>(const Grid&, const double*, double, double*, double*, cudaStream_t);
+template void launch_gather<float>(const Grid&, const double*, double, double*, float*, cudaStream_t);
+template void launch_wells<double>(const Grid&, const Phys&, const Wells&, const double*, const double*,
+                                   const double*, double, double*, double*, double*, double*, double*, cudaStream_t);
+template void launch_wells<float>(const Grid&, const Phys&, const Wells&, const double*, const double*,
+                                  const float*, double, double*, float*, float*, float*, float*, cudaStream_t);
+
+}  // namespace pf

@@ -1,0 +1,52 @@
+// CPR-FP preconditioner (Alg. 2): y = D_r(J)^{-1} f by block-Jacobi (one
+// subdomain per GPU, so the restricted additive Schwarz step reduces to its
+// local block solve); r = f - J y; y += Pi_p M_g(A_p)^{-1} Pi_r r with M_g a
+// multigrid cycle on the pressure matrix.
+//
+// The pressure matrix A_p takes the P-columns of the oil and water rows of J
+// weighted by 1/rho_o,ref and 1/rho_w,ref (a volume-balance decoupling: it
+// cancels the saturation derivative of the accumulation); Pi_r applies the
+// same weights to the residual and Pi_p injects the pressure correction into
+// the P component of every cell (well unknowns untouched).
+//
+// The multigrid uses 2x2x2 (or 2x2 / 2) aggregates of the structured grid with
+// piecewise-constant transfer, so each Galerkin coarse operator is again a
+// 7-point stencil; red-black Gauss-Seidel smoothing; a dense inverse on the
+// coarsest level (at most 64 cells).
+#pragma once
+
+#include <vector>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+struct CprLevel {
+  int nx = 0, ny = 0, nz = 0;
+  long long n = 0;
+  void* A = nullptr;     // [7][n] stencil (slot order of SL_*), type T
+  void* dinv = nullptr;  // [n] 1 / diagonal
+  void* x = nullptr;     // [n]
+  void* b = nullptr;     // [n]
+};
+
+struct CprData {
+  bool ready = false;
+  int nlev = 0;
+  int pre = 1, post = 1, cycle_gamma = 1, coarse_limit = 64;
+  double w_o = 0.0, w_w = 0.0;
+  std::vector<CprLevel> lev;
+  void* coarse_inv = nullptr;   // [nc][nc] dense inverse of the coarsest matrix
+  int* coarse_status = nullptr; // device flag: 1 if a zero pivot was met
+};
+
+// Lays out the CPR arrays in the arena (base == nullptr: sizing only).
+void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base);
+pf_status cpr_init(CprData& c, const Grid& g, bool mixed, const pf_solver_opts& o, cudaStream_t st);
+void cpr_setup(CprData& c, const Grid& g, const Phys& ph, const double* phi_r, const Wells& w, bool mixed,
+               const void* J, const void* Bw, const void* Dw, cudaStream_t st, int* launches);
+void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw, const void* Cw,
+               const void* Dw, const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp,
+               cudaStream_t st, int* launches);
+
+}  // namespace pf

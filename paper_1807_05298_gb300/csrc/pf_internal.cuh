@@ -1,0 +1,132 @@
+// Internal declarations of the polyflood CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "polyflood.h"
+
+namespace pf {
+
+// Rock, fluid and polymer constants with the derived quantities the kernels
+// use (passed by value as a kernel argument).
+struct Phys {
+  double rho_w, rho_o, c_w, c_o, p_ref, mu_w, mu_o, c_r, p_r;
+  double swc, sor, nw, no, krw_max, kro_max, pc_e, pc_n;
+  double ads_a, ads_b, rrf, ipv, omega, mu_p0, c_ref, g;
+  int mixing;
+  // derived
+  double inv_den;        // 1 / (1 - swc - sor)
+  double ln_mu_w, ln_mu_ratio;   // ln mu_w, ln mu_p0 - ln mu_w
+  double rk_coef;        // (rrf - 1) / A_d,max, or 0 without adsorption
+  double mu_p0_pow, mu_w_pow;    // mu_p0^(1-omega), mu_w^(1-omega)
+  double inv_c_ref, inv_rho_w;   // 1 / c_ref, 1 / rho_w,ref
+};
+
+struct Grid {
+  int nx, ny, nz;
+  long long n, nxy;
+  double dx, dy, dz, top, V;
+};
+
+// Per-cell property scratch: values (FP64) and derivatives (DT).
+enum {
+  PV_RHO_O = 0, PV_RHO_W, PV_PW, PV_KRW, PV_KRO, PV_RK, PV_MUWE, PV_MUPE, PV_COUNT
+};
+enum {
+  PD_RHO_O = 0, PD_RHO_WP, PD_RHO_WS, PD_PW_S, PD_KRW, PD_KRO, PD_RK, PD_MUWE, PD_MUPE, PD_COUNT
+};
+
+// Jacobian block slots of a cell row.
+enum { SL_D = 0, SL_XM, SL_XP, SL_YM, SL_YP, SL_ZM, SL_ZP, SL_COUNT };
+
+// Device views of the well data.
+struct Wells {
+  int nw;
+  long long npf;
+  const int* ptr;          // [nw+1] perforation range of each well
+  const long long* cell;   // [npf]
+  const double* wi;        // [npf] Peaceman index
+  const double* dzb;       // [npf] z_m - z_b
+  const int* kind;         // [nw]
+  const int* ctrl;         // [nw]
+  const double* target;    // [nw] Pa or mass rate coefficient target (rho_t * q)
+  const double* cinj;      // [nw]
+  const double* W;         // [nw] BHP row scale sum(WI) rho_w / mu_w
+  const double* sw;        // [nw] rate coefficient of the water sum
+  const double* so;        // [nw] rate coefficient of the oil sum
+  const double* scale;     // [nw] scaled-residual denominator / dt
+  const double* gamma;     // [nw] lagged wellbore unit weight
+};
+
+// Launch helpers ------------------------------------------------------------
+inline int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return (int)g;
+}
+
+// Assembly (pf_assembly.cu) -------------------------------------------------
+// mode 0: properties + accumulation into R and the diagonal; mode 1: old masses
+// (and the values the lagged wellbore weight needs); mode 2: property values only.
+template <typename DT>
+void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x,
+                       double* pv, DT* pd, const double* Mold, double* R, DT* J, double* Mold_out,
+                       int mode, cudaStream_t st);
+template <typename DT>
+void launch_face_flux(const Grid& g, const Phys& ph, const double* phi_r, const double* T3,
+                      const double* x, const double* pv, const DT* pd, double dt, DT* J,
+                      double* Fbuf, cudaStream_t st);
+template <typename DT>
+void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st);
+template <typename DT>
+void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
+                  const DT* pd, double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st);
+void launch_well_gamma(const Grid& g, const Phys& ph, const Wells& w, const double* x,
+                       const double* pv, double* gamma, cudaStream_t st);
+// out[3w + {0,1,2}] = water, oil, polymer mass rate of well w (needs a mode-2 pv).
+void launch_well_totals(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
+                        double* out, cudaStream_t st);
+// Scaled max-norm and squared 2-norm of R: out[0] = max, out[1] = sum of squares.
+void launch_residual_norms(const Grid& g, const Phys& ph, const double* phi_r, const Wells& w,
+                           const double* R, double dt, double* partial, int nblocks, double* out,
+                           cudaStream_t st);
+void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max,
+                          cudaStream_t st);
+
+// Linear algebra (pf_linalg.cu) ---------------------------------------------
+template <typename DT>
+void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const DT* Cw,
+                 const DT* Dw, const double* x, double* y, cudaStream_t st);
+template <typename DT, typename PT>
+void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
+                          PT* Dwinv, cudaStream_t st);
+template <typename PT>
+void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
+                          double* z, cudaStream_t st);
+
+// Vector kernels over n FP64 entries.
+void launch_copy(long long n, const double* a, double* b, cudaStream_t st);
+void launch_fill(long long n, double v, double* a, cudaStream_t st);
+void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b,
+                         cudaStream_t st);  // b = a * s[0] or a / sqrt(s[0])
+void launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t st);
+void launch_xpay(long long n, const double* x, double beta, double* y, cudaStream_t st); // y = x + beta y
+void launch_sub(long long n, const double* a, const double* b, double* c, cudaStream_t st); // c = a - b
+// out[j] = sum_i V[j*ld + i] w[i], j < k  (two-stage, deterministic)
+void launch_multidot(long long n, int k, const double* V, long long ld, const double* w,
+                     double* partial, int nblocks, double* out, cudaStream_t st);
+// w -= sum_j V[j] h[j]; then out[j] = sum_i V[j][i] w_new[i] (j<k) and out[k] = |w_new|^2
+void launch_multi_axpy_dot(long long n, int k, const double* V, long long ld, const double* h,
+                           double* w, double* partial, int nblocks, double* out, cudaStream_t st);
+// x += sum_j Z[j] y[j]
+void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y,
+                           double* x, cudaStream_t st);
+void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks,
+                double* out, cudaStream_t st);
+
+}  // namespace pf

@@ -1,0 +1,76 @@
+"""Helpers shared by the GPU parity tests: rebuild the library's exported
+block layout as a sparse matrix in the oracle's unknown ordering."""
+
+import numpy as np
+import scipy.sparse as sp
+
+SLOT_OFFSETS = ["d", "xm", "xp", "ym", "yp", "zm", "zp"]
+
+
+def neighbor_cols(nx, ny, nz):
+    n = nx * ny * nz
+    idx = np.arange(n)
+    k, rem = np.divmod(idx, nx * ny)
+    j, i = np.divmod(rem, nx)
+    out = []
+    for s in SLOT_OFFSETS:
+        if s == "d":
+            out.append((idx, np.ones(n, bool)))
+        elif s == "xm":
+            out.append((idx - 1, i > 0))
+        elif s == "xp":
+            out.append((idx + 1, i + 1 < nx))
+        elif s == "ym":
+            out.append((idx - nx, j > 0))
+        elif s == "yp":
+            out.append((idx + nx, j + 1 < ny))
+        elif s == "zm":
+            out.append((idx - nx * ny, k > 0))
+        else:
+            out.append((idx + nx * ny, k + 1 < nz))
+    return out
+
+
+def gpu_system_to_csr(sc, Jc, Bw, Cw, Dw, well_cells):
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    n = nx * ny * nz
+    nw = len(well_cells)
+    nunk = 3 * n + nw
+    rows, cols, vals = [], [], []
+    for s, (col, mask) in enumerate(neighbor_cols(nx, ny, nz)):
+        cells = np.nonzero(mask)[0]
+        for e in range(9):
+            r, c = divmod(e, 3)
+            rows.append(3 * cells + r)
+            cols.append(3 * col[cells] + c)
+            vals.append(Jc[s, e, cells])
+    m = 0
+    for w, cells in enumerate(well_cells):
+        for c in cells:
+            for r in range(3):
+                rows.append(np.array([3 * c + r])); cols.append(np.array([3 * n + w])); vals.append(np.array([Bw[r, m]]))
+                rows.append(np.array([3 * n + w])); cols.append(np.array([3 * c + r])); vals.append(np.array([Cw[r, m]]))
+            m += 1
+        rows.append(np.array([3 * n + w])); cols.append(np.array([3 * n + w])); vals.append(np.array([Dw[w]]))
+    J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nunk, nunk))
+    return J.tocsr()
+
+
+def _row_max_abs(A):
+    A = abs(A).tocsr()
+    A.sum_duplicates()
+    out = np.zeros(A.shape[0])
+    nnz = np.diff(A.indptr) > 0
+    if A.nnz:
+        out[nnz] = np.maximum.reduceat(A.data, A.indptr[:-1][nnz])
+    return out
+
+
+def rel_matrix_error(Jg, Jo):
+    """max |Jg - Jo| per row, relative to the row's largest |Jo| entry."""
+    dmax = _row_max_abs((Jg - Jo).tocsr())
+    amax = _row_max_abs(Jo)
+    nz = amax > 0
+    if np.any(dmax[~nz] > 0):
+        return np.inf
+    return float(np.max(dmax[nz] / amax[nz])) if nz.any() else 0.0

@@ -374,3 +374,37 @@ def test_viscosity_special_cases():
     assert pr["mu_we"].v[2] == pytest.approx(8.0 * CP)        # alpha = 1 -> polymer
     # alpha = 1/2, omega = 0: harmonic mean of mu_w and mu_p0
     assert pr["mu_we"].v[0] == pytest.approx(1.0 / (0.5 / (8.0 * CP) + 0.5 / (0.5 * CP)))
+
+
+# ---------------------------------------------------------------------------
+# well constraints with a BHP limit (Sec. 2.4, Sec. 4.1.2)
+# ---------------------------------------------------------------------------
+
+def limited_injector_scenario(rate_day, limit_bar, n_steps=4):
+    ph = G.default_physics()
+    nx, ny, nz = 6, 6, 2
+    n = nx * ny * nz
+    k = np.full(n, 20.0 * MD)
+    wells = [dict(kind="inj", cells=[0, nx * ny]), dict(kind="prod", cells=[n - 1 - nx * ny, n - 1])]
+    ctl = [dict(ctrl="wrate", target=rate_day / DAY, limit=limit_bar * BAR, c_inj=1.0),
+           dict(ctrl="bhp", target=150.0 * BAR, limit=None, c_inj=0.0)]
+    return G.make_scenario(nx, ny, nz, 20.0, 20.0, 5.0, 2000.0, k, k, k, np.full(n, 0.2), ph, wells,
+                           [dict(n_steps=n_steps, dt=2.0 * DAY, controls=ctl)])
+
+
+def test_bhp_limit_switches_rate_injector():
+    sc = limited_injector_scenario(2000.0, 260.0)
+    st, x, hist = M.run(sc)
+    assert hist[-1]["switched"][0]
+    assert x[3 * st.n] == pytest.approx(260.0 * BAR, rel=1e-12)
+    gam = M.well_gamma(st, hist[-2]["x"], M.effective_controls(st, sc["schedule"][0]["controls"],
+                                                                 hist[-1]["switched"]))
+    qw, qo, pb = M.well_totals(st, x, sc["schedule"][0]["controls"], gam)[0]
+    assert 0.0 < qw / st.ph["rho_w"] < 2000.0 / DAY
+
+
+def test_rate_injector_below_limit_stays_on_rate():
+    sc = limited_injector_scenario(20.0, 400.0)
+    st, x, hist = M.run(sc)
+    assert not any(h["switched"][0] for h in hist)
+    assert x[3 * st.n] < 400.0 * BAR
