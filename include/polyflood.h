@@ -120,7 +120,7 @@ typedef struct pf_solver_opts {
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
   int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 1, 1) */
-  int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 64) */
+  int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
 } pf_solver_opts;
 

@@ -67,7 +67,7 @@ def build(force=False, verbose=False):
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+        run([nvcc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs)
         os.replace(tmp, LIB)
     return LIB
 

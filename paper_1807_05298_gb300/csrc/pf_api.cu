@@ -65,6 +65,7 @@ struct pf_sim {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   // device arrays
+  double *wL3 = nullptr, *inv_pv = nullptr;
   double *phi_r = nullptr, *T3 = nullptr, *x = nullptr, *x_old = nullptr, *Mold = nullptr, *R = nullptr;
   double *pv = nullptr, *Fbuf = nullptr, *dx = nullptr, *b = nullptr, *r = nullptr, *tmp = nullptr;
   void *pd = nullptr, *J = nullptr, *Bw = nullptr, *Cw = nullptr, *Dw = nullptr;
@@ -75,6 +76,7 @@ struct pf_sim {
   double *w_sw = nullptr, *w_so = nullptr, *w_scale = nullptr, *w_gamma = nullptr;
   double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
   double* wtot = nullptr;  // [3 nw] well totals
+  unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
   double* h_pinned = nullptr;
   CprData cpr;
   // opt-in CUDA-event timing of selected kernels
@@ -84,6 +86,16 @@ struct pf_sim {
   int64_t kt_count[PF_KT_COUNT] = {0};
   double kt_ms[PF_KT_COUNT] = {0.0};
   int switch_attempt = 0;
+  // CUDA graphs of the Krylov iteration, per Arnoldi index j: preconditioner,
+  // SpMV, orthogonalisation (captured once, replayed every iteration)
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
+  bool use_graphs = true;
+  struct IterGraphs {
+    cudaGraphExec_t pre = nullptr, spmv = nullptr, ortho = nullptr;
+    int k_pre = 0, k_spmv = 0, k_ortho = 0;
+  };
+  std::vector<IterGraphs> graphs;
   // step state
   double dt = 0.0;
   bool in_step = false;
@@ -111,7 +123,7 @@ struct KtScope {
   int which;
   cudaEvent_t a = nullptr, b = nullptr;
   KtScope(pf_sim* s_, int w) : s(s_), which(w) {
-    if (s->kt_on) {
+    if (s->kt_on && !s->capturing) {
       a = kt_event(s);
       b = kt_event(s);
       cudaEventRecord(a, s->stream);
@@ -192,6 +204,7 @@ Phys derive_phys(const pf_physics& p) {
   ph.mu_w_pow = pow(p.mu_w, 1.0 - p.omega);
   ph.inv_c_ref = 1.0 / p.c_ref;
   ph.inv_rho_w = 1.0 / p.rho_w;
+  ph.inv_mu_o = 1.0 / p.mu_o;
   return ph;
 }
 
@@ -268,6 +281,8 @@ size_t carve(pf_sim* s, char* base) {
   const int m = s->opts.gmres_restart;
   s->phi_r = c.take<double>(n);
   s->T3 = c.take<double>(3 * n);
+  s->wL3 = c.take<double>(3 * n);
+  s->inv_pv = c.take<double>(n);
   s->x = c.take<double>(s->nunk);
   s->x_old = c.take<double>(s->nunk);
   s->Mold = c.take<double>(3 * n);
@@ -305,6 +320,7 @@ size_t carve(pf_sim* s, char* base) {
   s->norms = c.take<double>(4);
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
+  s->red_counter = c.take<unsigned int>(64);
   if (s->opts.precond == PF_PC_CPR) cpr_carve(s->cpr, s->g, s->mixed, c.off, base);
   return align_up(c.off, 256);
 }
@@ -319,7 +335,7 @@ pf_status assemble_t(pf_sim* s) {
   }
   {
     KtScope t(s, PF_KT_FACE);
-    launch_face_flux<DT>(s->g, s->ph, s->phi_r, s->T3, s->x, s->pv, (const DT*)s->pd, s->dt, (DT*)s->J, s->Fbuf, st);
+    launch_face_flux<DT>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv, (const DT*)s->pd, s->dt, (DT*)s->J, s->Fbuf, st);
   }
   {
     KtScope t(s, PF_KT_GATHER);
@@ -388,8 +404,8 @@ pf_status precond_apply(pf_sim* s, const double* v, double* z) {
 }
 
 pf_status dev_norm2(pf_sim* s, const double* a, double* out_host) {
-  launch_dot(s->nunk, a, a, s->partial, s->nblocks, s->norms, s->stream);
-  PF_LAUNCHED(2);
+  launch_dot(s->nunk, a, a, s->partial, s->nblocks, s->norms, s->red_counter, s->stream);
+  PF_LAUNCHED(1);
   PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->norms, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   PF_CUDA(cudaStreamSynchronize(s->stream));
   *out_host = sqrt(s->h_pinned[0]);
@@ -400,6 +416,92 @@ void scale_vec(pf_sim* s, const double* a, double f, double* b) {
   launch_fill(1, f, s->norms + 3, s->stream);
   launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, b, s->stream);
   s->launches += 2;
+}
+
+// Work of Arnoldi step j, in three pieces: z_j = M^{-1} v_j; w = J z_j into
+// v_{j+1}; two classical Gram-Schmidt passes against v_0..v_j (fused), the
+// normalisation of v_{j+1} by its device-side norm and the copy of the
+// Hessenberg column to pinned host memory.
+pf_status piece_pre(pf_sim* s, int j) {
+  return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld);
+}
+pf_status piece_spmv(pf_sim* s, int j) {
+  return spmv(s, s->Z + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld);
+}
+pf_status piece_ortho(pf_sim* s, int j) {
+  const long long n = s->nunk, ld = s->ld;
+  const int k = j + 1;
+  double* w = s->V + (size_t)(j + 1) * ld;
+  cudaStream_t st = s->stream;
+  KtScope t(s, PF_KT_ORTHO);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st);
+  launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st);
+  launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, st,
+                        1);
+  launch_scale_by_dev(n, w, s->hbuf + 256 + k + 1, 0, w, st);
+  PF_LAUNCHED(4);
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, 3 * 128 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return PF_OK;
+}
+
+// Captures one piece into an executable graph on the private capture stream.
+pf_status capture(pf_sim* s, pf_status (*piece)(pf_sim*, int), int j, cudaGraphExec_t* exec, int* kernels) {
+  cudaStream_t orig = s->stream;
+  const int64_t l0 = s->launches;
+  s->stream = s->cap_stream;
+  s->capturing = true;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+  pf_status rc = PF_OK;
+  if (e == cudaSuccess) {
+    rc = piece(s, j);
+    cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (e2 != cudaSuccess && rc == PF_OK) e = e2;
+  }
+  s->capturing = false;
+  s->stream = orig;
+  if (rc != PF_OK) return rc;
+  PF_CUDA(e);
+  PF_CUDA(cudaGraphInstantiate(exec, graph, 0));
+  cudaGraphDestroy(graph);
+  *kernels = (int)(s->launches - l0);
+  s->launches = l0;
+  return PF_OK;
+}
+
+pf_status arnoldi_step(pf_sim* s, int j) {
+  cudaStream_t st = s->stream;
+  if (!s->use_graphs) {
+    pf_status rc;
+    if ((rc = piece_pre(s, j)) != PF_OK) return rc;
+    if ((rc = piece_spmv(s, j)) != PF_OK) return rc;
+    if ((rc = piece_ortho(s, j)) != PF_OK) return rc;
+    PF_CUDA(cudaStreamSynchronize(st));
+    return PF_OK;
+  }
+  if ((int)s->graphs.size() <= j) s->graphs.resize(j + 1);
+  pf_sim::IterGraphs& G = s->graphs[j];
+  pf_status rc;
+  if (!G.pre) {
+    if ((rc = capture(s, piece_pre, j, &G.pre, &G.k_pre)) != PF_OK) return rc;
+    if ((rc = capture(s, piece_spmv, j, &G.spmv, &G.k_spmv)) != PF_OK) return rc;
+    if ((rc = capture(s, piece_ortho, j, &G.ortho, &G.k_ortho)) != PF_OK) return rc;
+  }
+  {
+    KtScope t(s, PF_KT_PRECOND);
+    PF_CUDA(cudaGraphLaunch(G.pre, st));
+  }
+  {
+    KtScope t(s, PF_KT_SPMV);
+    PF_CUDA(cudaGraphLaunch(G.spmv, st));
+  }
+  {
+    KtScope t(s, PF_KT_ORTHO);
+    PF_CUDA(cudaGraphLaunch(G.ortho, st));
+  }
+  s->launches += G.k_pre + G.k_spmv + G.k_ortho;
+  PF_CUDA(cudaStreamSynchronize(st));
+  return PF_OK;
 }
 
 // Restarted flexible GMRES (right preconditioning) for J x = b, x0 = 0.
@@ -435,28 +537,14 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
     gv[0] = beta;
     int jdone = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
-      double* vj = s->V + (size_t)j * ld;
-      double* zj = s->Z + (size_t)j * ld;
-      double* w = s->V + (size_t)(j + 1) * ld;
-      if ((rc = precond_apply(s, vj, zj)) != PF_OK) return rc;
-      if ((rc = spmv(s, zj, w)) != PF_OK) return rc;
+      if ((rc = arnoldi_step(s, j)) != PF_OK) return rc;
       const int k = j + 1;
-      {
-        KtScope t(s, PF_KT_ORTHO);
-        launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, st);
-        launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 128, st);
-        launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, st);
-      }
-      s->launches += 6;
-      PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, 3 * 128 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      PF_CUDA(cudaStreamSynchronize(st));
       const double* h1 = s->h_pinned;
       const double* h2 = s->h_pinned + 128;
       const double hn = sqrt(std::max(s->h_pinned[256 + k], 0.0));
       double* col = &H[(size_t)j * (m + 1)];
       for (int i = 0; i < k; ++i) col[i] = h1[i] + h2[i];
       col[k] = hn;
-      if (hn > 0.0) scale_vec(s, w, 1.0 / hn, w);
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
         col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
@@ -500,7 +588,7 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
 }
 
 pf_status residual_norms(pf_sim* s, double* scaled, double* norm2) {
-  launch_residual_norms(s->g, s->ph, s->phi_r, wells_view(s), s->R, s->dt, s->partial, s->nblocks, s->norms,
+  launch_residual_norms(s->g, s->ph, s->inv_pv, wells_view(s), s->R, s->dt, s->partial, s->nblocks, s->norms,
                         s->stream);
   PF_LAUNCHED(2);
   PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -546,7 +634,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->ds_max = 0.2;
   o->amg_pre_sweeps = 1;
   o->amg_post_sweeps = 1;
-  o->amg_coarse_size = 64;
+  o->amg_coarse_size = 8;
   o->amg_cycle = 1;
   return PF_OK;
 }
@@ -606,6 +694,16 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
           T3[2 * n + c] = (g.dx * g.dy) / (g.dz / (2.0 * m->kz[c]) + g.dz / (2.0 * m->kz[h]));
         }
       }
+  // pore-volume weights of the face averages (Sec. 3.2) and 1 / (V phi_r)
+  std::vector<double> wL3((size_t)3 * n, 0.0), inv_pv((size_t)n);
+  for (long long c = 0; c < n; ++c) {
+    inv_pv[c] = 1.0 / (g.V * m->phi[c]);
+    const long long st3[3] = {1, g.nx, g.nxy};
+    for (int d = 0; d < 3; ++d) {
+      const long long h = c + st3[d];
+      if (T3[d * n + c] != 0.0) wL3[d * n + c] = m->phi[c] / (m->phi[c] + m->phi[h]);
+    }
+  }
   std::vector<long long> cell(std::max(1LL, s->npf));
   std::vector<double> wi(std::max(1LL, s->npf)), dzb(std::max(1LL, s->npf));
   std::vector<int> kind(std::max(1, s->nw));
@@ -649,6 +747,15 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
     }
   }
   carve(s, s->arena);
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaFree(s->arena);
+      cudaFreeHost(s->h_pinned);
+      delete s;
+      return fail(PF_ECUDA, std::string("capture stream: ") + cudaGetErrorString(e));
+    }
+  }
   // upload
   std::vector<double> x0((size_t)s->nunk);
   for (long long i = 0; i < n; ++i) {
@@ -661,6 +768,8 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   PF_CUDA(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st));
   PF_CUDA(cudaMemcpyAsync(s->phi_r, m->phi, n * sizeof(double), cudaMemcpyHostToDevice, st));
   PF_CUDA(cudaMemcpyAsync(s->T3, T3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->wL3, wL3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->inv_pv, inv_pv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
   PF_CUDA(cudaMemcpyAsync(s->x, x0.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, st));
   PF_CUDA(cudaMemcpyAsync(s->w_ptr, s->h_ptr.data(), (s->nw + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   if (s->nw > 0) {
@@ -682,6 +791,13 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
 pf_status pf_destroy(pf_sim* s) {
   if (!s) return PF_OK;
   cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& G : s->graphs) {
+    if (G.pre) cudaGraphExecDestroy(G.pre);
+    if (G.spmv) cudaGraphExecDestroy(G.spmv);
+    if (G.ortho) cudaGraphExecDestroy(G.ortho);
+  }
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->arena) cudaFree(s->arena);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   for (auto& p : s->kt_pending) { s->kt_pool.push_back(p.second.first); s->kt_pool.push_back(p.second.second); }

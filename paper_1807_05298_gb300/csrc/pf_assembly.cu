@@ -245,7 +245,7 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const bool upHo = dPo >= 0.0;
   const double kro = upHo ? b.kro : a.kro;
   const DT dkro = upHo ? db.dkro : da.dkro;
-  const double To = T / ph.mu_o;
+  const double To = T * ph.inv_mu_o;
   F[0] = To * kro * rho_o * dPo;
   {
     const DT Tk = (DT)(To * kro);
@@ -271,8 +271,11 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const double mu_we = wL * a.mu_we + wH * b.mu_we;
   const double mu_pe = wL * a.mu_pe + wH * b.mu_pe;
   const double A = rho_w * dPw;
-  const double mw = krw / (Rk * mu_we);
-  const double mp = krw / (Rk * mu_pe);
+  // two FP64 divisions per face; 1/mu and 1/R_k follow by multiplication
+  const double irw = 1.0 / (Rk * mu_we), irp = 1.0 / (Rk * mu_pe);
+  const double inv_mu_we = Rk * irw, inv_mu_pe = Rk * irp, inv_Rk = mu_we * irw;
+  const double mw = krw * irw;
+  const double mp = krw * irp;
   const double cf = Cu * ph.inv_rho_w;
   F[1] = T * mw * A;
   F[2] = T * mp * A * cf;
@@ -293,15 +296,16 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   dH[7] = Tmp * dA_SH;
   // concentration columns through the averaged viscosities
   const DT TA = (DT)(T * A);
-  dL[5] = -TA * (DT)mw * (DT)wL * da.dmu_we / (DT)mu_we;
-  dH[5] = -TA * (DT)mw * (DT)wH * db.dmu_we / (DT)mu_we;
-  dL[8] = -TA * (DT)(mp * cf) * (DT)wL * da.dmu_pe / (DT)mu_pe;
-  dH[8] = -TA * (DT)(mp * cf) * (DT)wH * db.dmu_pe / (DT)mu_pe;
+  const DT cw = -TA * (DT)(mw * inv_mu_we), cp = -TA * (DT)(mp * cf * inv_mu_pe);
+  dL[5] = cw * (DT)wL * da.dmu_we;
+  dH[5] = cw * (DT)wH * db.dmu_we;
+  dL[8] = cp * (DT)wL * da.dmu_pe;
+  dH[8] = cp * (DT)wH * db.dmu_pe;
   // upstream cell: k_rw (saturation), R_k and the carried concentration
-  const DT dFw_S = TA * dkrw / (DT)(Rk * mu_we);
-  const DT dFp_S = TA * (DT)cf * dkrw / (DT)(Rk * mu_pe);
-  const DT dFw_C = -TA * (DT)mw * dRk / (DT)Rk;
-  const DT dFp_C = TA * ((DT)(mp * cf) * (-dRk / (DT)Rk) + (DT)(mp * ph.inv_rho_w));
+  const DT dFw_S = TA * dkrw * (DT)irw;
+  const DT dFp_S = TA * (DT)cf * dkrw * (DT)irp;
+  const DT dFw_C = -TA * (DT)(mw * inv_Rk) * dRk;
+  const DT dFp_C = TA * ((DT)(mp * cf * inv_Rk) * (-dRk) + (DT)(mp * ph.inv_rho_w));
   if (upHw) {
     dH[4] += dFw_S; dH[7] += dFp_S; dH[5] += dFw_C; dH[8] += dFp_C;
   } else {
@@ -310,7 +314,7 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
 }
 
 template <typename DT>
-__global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double* __restrict__ phi_r,
+__global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double* __restrict__ wL3,
                                                    const double* __restrict__ T3, const double* __restrict__ x,
                                                    const double* __restrict__ pv, const DT* __restrict__ pd,
                                                    double dt, DT* __restrict__ J, double* __restrict__ Fbuf) {
@@ -323,7 +327,6 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
     const long long ii = rem - j * g.nx;
     SideV a; SideD<DT> da;
     load_side<DT>(i, n, x, pv, pd, a, da);
-    const double phL = phi_r[i];
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       bool has;
@@ -340,8 +343,7 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
       const long long h = i + s;
       SideV b; SideD<DT> db;
       load_side<DT>(h, n, x, pv, pd, b, db);
-      const double phH = phi_r[h];
-      const double wL = phL / (phL + phH);
+      const double wL = wL3[(size_t)d * n + i];
       double F[3]; DT dL[9], dH[9];
       face_flux<DT>(ph, T3[(size_t)d * n + i], gdz, wL, a, da, b, db, F, dL, dH);
       Fd[i] = F[0]; Fd[n + i] = F[1]; Fd[2 * n + i] = F[2];
@@ -367,9 +369,9 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
 }
 
 template <typename DT>
-void launch_face_flux(const Grid& g, const Phys& ph, const double* phi_r, const double* T3, const double* x,
+void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3, const double* x,
                       const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st) {
-  k_face_flux<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, phi_r, T3, x, pv, pd, dt, J, Fbuf);
+  k_face_flux<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -637,17 +639,18 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_res_norm_partial(Grid g, Phys ph, const double* __restrict__ phi_r,
+__global__ void __launch_bounds__(256) k_res_norm_partial(Grid g, Phys ph, const double* __restrict__ inv_pv,
                                                           const double* __restrict__ R, double* __restrict__ partial) {
   const long long n = g.n;
   double mx = 0.0, ss = 0.0;
+  const double io = 1.0 / ph.rho_o, iw = ph.inv_rho_w, ic = ph.inv_c_ref;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double pv = g.V * phi_r[i];
+    const double ip = inv_pv[i];  // 1 / (V phi_r)
     const double r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
-    mx = nanmax(mx, fabs(r0) / (pv * ph.rho_o));
-    mx = nanmax(mx, fabs(r1) / (pv * ph.rho_w));
-    mx = nanmax(mx, fabs(r2) / (pv * ph.c_ref));
+    mx = nanmax(mx, fabs(r0) * ip * io);
+    mx = nanmax(mx, fabs(r1) * ip * iw);
+    mx = nanmax(mx, fabs(r2) * ip * ic);
     ss += r0 * r0 + r1 * r1 + r2 * r2;
   }
   __shared__ double smx[8], sss[8];
@@ -680,9 +683,9 @@ __global__ void k_res_norm_final(int nblocks, Wells w, long long n, const double
   if (lane == 0) { out[0] = mx; out[1] = ss; }
 }
 
-void launch_residual_norms(const Grid& g, const Phys& ph, const double* phi_r, const Wells& w, const double* R,
+void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, const Wells& w, const double* R,
                            double dt, double* partial, int nblocks, double* out, cudaStream_t st) {
-  k_res_norm_partial<<<nblocks, 256, 0, st>>>(g, ph, phi_r, R, partial);
+  k_res_norm_partial<<<nblocks, 256, 0, st>>>(g, ph, inv_pv, R, partial);
   k_res_norm_final<<<1, 32, 0, st>>>(nblocks, w, g.n, R, dt, partial, out);
 }
 

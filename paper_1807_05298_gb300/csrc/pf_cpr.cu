@@ -151,65 +151,227 @@ __global__ void __launch_bounds__(256) k_prolong_add(Dims f, Dims c, const T* __
 
 // Dense inverse of the coarsest stencil matrix (n <= 64): LU with partial
 // pivoting in shared memory by one block, then one column of the inverse per
-// thread.  A zero pivot sets *status and leaves that column zero.
+// thread.  Storage is column-major (M[c * ld + r]) so that the threads of a
+// warp, one per row, touch consecutive words.  A zero pivot sets *status and
+// leaves that column zero.
+constexpr int kLd = kMaxCoarse + 1;
+constexpr size_t kCoarseSmem = sizeof(double) * (2 * kMaxCoarse * kLd) + sizeof(int) * (kMaxCoarse + 1);
+
 template <typename T>
 __global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__ inv, int* status) {
-  __shared__ double M[kMaxCoarse][kMaxCoarse];
-  __shared__ int perm[kMaxCoarse];
-  __shared__ int piv;
+  extern __shared__ double sm[];
+  double* M = sm;                       // [n][kLd] column-major: M[c * kLd + r]
+  double* X = sm + kMaxCoarse * kLd;     // [n][kLd] column j of the inverse: X[j * kLd + r]
+  int* perm = reinterpret_cast<int*>(X + kMaxCoarse * kLd);
+  int* piv = perm + kMaxCoarse;
   const int n = (int)d.n;
   const int t = threadIdx.x;
-  for (int e = t; e < n * n; e += blockDim.x) M[e / n][e % n] = 0.0;
+  for (int e = t; e < kMaxCoarse * kLd; e += blockDim.x) M[e] = 0.0;
   if (t < n) perm[t] = t;
   if (t == 0) *status = 0;
   __syncthreads();
   if (t < n) {
     int x, y, z;
     coords(d, t, x, y, z);
-    M[t][t] = (double)A[t];
+    M[t * kLd + t] = (double)A[t];
     for (int s = 1; s < SL_COUNT; ++s) {
       long long j;
-      if (nbr(d, x, y, z, s, j)) M[t][j] = (double)A[(size_t)s * n + t];
+      if (nbr(d, x, y, z, s, j)) M[(int)j * kLd + t] = (double)A[(size_t)s * n + t];
     }
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (t == 0) {
+    if (t < 32) {  // pivot search by one warp
       int p = k;
-      double best = fabs(M[k][k]);
-      for (int r = k + 1; r < n; ++r)
-        if (fabs(M[r][k]) > best) { best = fabs(M[r][k]); p = r; }
-      piv = p;
-      if (best == 0.0) *status = 1;
+      double best = -1.0;
+      for (int r = k + t; r < n; r += 32) {
+        const double v = fabs(M[k * kLd + r]);
+        if (v > best) { best = v; p = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (t == 0) {
+        *piv = p;
+        if (!(best > 0.0)) *status = 1;
+      }
     }
     __syncthreads();
-    const int p = piv;
+    const int p = *piv;
     if (p != k) {
-      for (int cidx = t; cidx < n; cidx += blockDim.x) {
-        const double tmp = M[k][cidx]; M[k][cidx] = M[p][cidx]; M[p][cidx] = tmp;
+      for (int c = t; c < n; c += blockDim.x) {
+        const double tmp = M[c * kLd + k]; M[c * kLd + k] = M[c * kLd + p]; M[c * kLd + p] = tmp;
       }
       if (t == 0) { const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp; }
     }
     __syncthreads();
-    const double pk = M[k][k];
+    const double pk = M[k * kLd + k];
     if (t > k && t < n && pk != 0.0) {
-      const double m = M[t][k] / pk;
-      M[t][k] = m;
-      for (int cidx = k + 1; cidx < n; ++cidx) M[t][cidx] -= m * M[k][cidx];
+      const double m = M[k * kLd + t] / pk;
+      M[k * kLd + t] = m;
+      for (int c = k + 1; c < n; ++c) M[c * kLd + t] -= m * M[c * kLd + k];
     }
     __syncthreads();
   }
-  // column j of the inverse solves L U x = P e_j
+  // column j of the inverse solves L U x = P e_j; thread j owns X[j][*]
   if (t < n) {
-    double xcol[kMaxCoarse];
-    for (int r = 0; r < n; ++r) xcol[r] = (perm[r] == t) ? 1.0 : 0.0;
-    for (int r = 0; r < n; ++r)
-      for (int cidx = 0; cidx < r; ++cidx) xcol[r] -= M[r][cidx] * xcol[cidx];
-    for (int r = n - 1; r >= 0; --r) {
-      for (int cidx = r + 1; cidx < n; ++cidx) xcol[r] -= M[r][cidx] * xcol[cidx];
-      xcol[r] = M[r][r] != 0.0 ? xcol[r] / M[r][r] : 0.0;
+    double* xc = X + t * kLd;
+    for (int r = 0; r < n; ++r) {
+      double v = (perm[r] == t) ? 1.0 : 0.0;
+      for (int c = 0; c < r; ++c) v -= M[c * kLd + r] * xc[c];
+      xc[r] = v;
     }
-    for (int r = 0; r < n; ++r) inv[(size_t)r * n + t] = (T)xcol[r];
+    for (int r = n - 1; r >= 0; --r) {
+      double v = xc[r];
+      for (int c = r + 1; c < n; ++c) v -= M[c * kLd + r] * xc[c];
+      const double dg = M[r * kLd + r];
+      xc[r] = dg != 0.0 ? v / dg : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e % n;
+    inv[e] = (T)X[c * kLd + r];
+  }
+}
+
+// All levels from l0 down run inside one thread block (levels small enough
+// that launch latency, not work, would dominate): the same smoother,
+// restriction, prolongation and coarse inverse as the per-level kernels.
+constexpr int kMaxLev = 24;
+// FP64 runs at a small fraction of the FP32 rate per SM, so one block may only
+// take the tiny FP64 levels; FP32 levels up to 4096 cells fit one block well.
+template <typename T> constexpr long long block_level_cells() { return sizeof(T) == 8 ? 256 : 4096; }
+
+template <typename T>
+struct BlockLevels {
+  int l0, nlev, pre, post, gamma;
+  Dims d[kMaxLev];
+  T* A[kMaxLev];
+  T* dinv[kMaxLev];
+  T* x[kMaxLev];
+  T* b[kMaxLev];
+  const T* inv;
+};
+
+template <typename T>
+__device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* x, int color, bool zero_init) {
+  for (long long i = threadIdx.x; i < d.n; i += blockDim.x) {
+    int cx, cy, cz;
+    coords(d, i, cx, cy, cz);
+    if (((cx + cy + cz) & 1) != color) continue;
+    T s = b[i];
+    if (!zero_init) {
+      for (int sl = 1; sl < SL_COUNT; ++sl) {
+        long long j;
+        if (nbr(d, cx, cy, cz, sl, j)) s -= A[(size_t)sl * d.n + i] * x[j];
+      }
+    }
+    x[i] = s * dinv[i];
+  }
+  __syncthreads();
+}
+
+// The cycle below the block levels, written as a loop over an explicit level
+// pointer (no device recursion, no per-thread copy of the descriptors: they
+// live in shared memory).  cnt[l] counts the coarse cycles finished at level
+// l in the current visit; level l runs gamma_l of them (1 at the finest
+// level, L.gamma below), the first from a zero initial guess.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zero_init) {
+  __shared__ BlockLevels<T> L;
+  __shared__ int cnt[kMaxLev];
+  __shared__ int zi[kMaxLev];
+  if (threadIdx.x == 0) {
+    L = Lp;
+    zi[L.l0] = zero_init;
+  }
+  __syncthreads();
+  const int last = L.nlev - 1;
+  int l = L.l0;
+  bool down = true;
+  for (int guard = 0; guard < (1 << 20); ++guard) {
+    if (down) {
+      const Dims d = L.d[l];
+      if (l == last) {  // coarsest: dense inverse
+        const int n = (int)d.n;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+          double sacc = 0.0;
+          for (int c = 0; c < n; ++c) sacc += (double)L.inv[(size_t)r * n + c] * (double)L.b[l][c];
+          L.x[l][r] = (T)sacc;
+        }
+        __syncthreads();
+        if (l == L.l0) return;
+        --l;
+        down = false;
+        continue;
+      }
+      for (int sweep = 0; sweep < L.pre; ++sweep) {
+        b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, zi[l] && sweep == 0);
+        b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
+      }
+      const Dims c = L.d[l + 1];
+      const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
+      const T* A = L.A[l];
+      const T* x = L.x[l];
+      const T* b = L.b[l];
+      for (long long I = threadIdx.x; I < c.n; I += blockDim.x) {
+        int cx, cy, cz;
+        coords(c, I, cx, cy, cz);
+        T acc = 0;
+        for (int dz = 0; dz < fz; ++dz)
+          for (int dy = 0; dy < fy; ++dy)
+            for (int dx = 0; dx < fx; ++dx) {
+              const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
+              if (X >= d.nx || Y >= d.ny || Z >= d.nz) continue;
+              const long long i = X + d.nx * (Y + (long long)d.ny * Z);
+              T r = b[i] - A[i] * x[i];
+              for (int sl = 1; sl < SL_COUNT; ++sl) {
+                long long j;
+                if (nbr(d, X, Y, Z, sl, j)) r -= A[(size_t)sl * d.n + i] * x[j];
+              }
+              acc += r;
+            }
+        L.b[l + 1][I] = acc;
+      }
+      if (threadIdx.x == 0) {
+        cnt[l] = 0;
+        zi[l + 1] = 1;
+      }
+      __syncthreads();
+      ++l;
+      continue;
+    }
+    // back at level l from a finished cycle on level l + 1
+    const int gamma_l = (l == 0) ? 1 : L.gamma;
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[l] += 1;
+    __syncthreads();
+    if (cnt[l] < gamma_l) {  // another coarse cycle from the current coarse iterate
+      if (threadIdx.x == 0) zi[l + 1] = 0;
+      __syncthreads();
+      // the coarse right-hand side is unchanged: re-enter level l + 1 directly
+      ++l;
+      down = true;
+      continue;
+    }
+    const Dims d = L.d[l];
+    const Dims c = L.d[l + 1];
+    const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
+    for (long long i = threadIdx.x; i < d.n; i += blockDim.x) {
+      int X, Y, Z;
+      coords(d, i, X, Y, Z);
+      L.x[l][i] += L.x[l + 1][X / fx + c.nx * (Y / fy + (long long)c.ny * (Z / fz))];
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < L.post; ++sweep) {
+      b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
+      b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, false);
+    }
+    if (l == L.l0) return;
+    --l;
   }
 }
 
@@ -252,6 +414,18 @@ void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
     k += 1;
     return;
   }
+  if (L.n <= block_level_cells<T>()) {  // this level and all coarser ones in one block
+    BlockLevels<T> B;
+    B.l0 = l; B.nlev = c.nlev; B.pre = c.pre; B.post = c.post; B.gamma = c.cycle_gamma;
+    for (int q = 0; q < c.nlev; ++q) {
+      B.d[q] = dims_of(c.lev[q]);
+      B.A[q] = (T*)c.lev[q].A; B.dinv[q] = (T*)c.lev[q].dinv; B.x[q] = (T*)c.lev[q].x; B.b[q] = (T*)c.lev[q].b;
+    }
+    B.inv = (const T*)c.coarse_inv;
+    k_block_cycle<T><<<1, 1024, 0, st>>>(B, zero_init ? 1 : 0);
+    k += 1;
+    return;
+  }
   for (int sweep = 0; sweep < c.pre; ++sweep) {
     k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0);
     k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 1, 0);
@@ -283,7 +457,9 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
     k += 1;
   }
   CprLevel& Lc = c.lev[c.nlev - 1];
-  k_coarse_factor<T><<<1, kMaxCoarse, 0, st>>>(dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv, c.coarse_status);
+  cudaFuncSetAttribute(k_coarse_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
+  k_coarse_factor<T><<<1, kMaxCoarse, kCoarseSmem, st>>>(dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
+                                                         c.coarse_status);
   k += 1;
 }
 
@@ -313,7 +489,7 @@ void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
   CprLevel L;
   L.nx = g.nx; L.ny = g.ny; L.nz = g.nz; L.n = g.n;
   c.lev.push_back(L);
-  while (c.lev.back().n > limit && c.lev.size() < 24) {
+  while (c.lev.back().n > limit && (int)c.lev.size() < kMaxLev) {
     const CprLevel& F = c.lev.back();
     CprLevel C;
     C.nx = F.nx > 1 ? (F.nx + 1) / 2 : 1;

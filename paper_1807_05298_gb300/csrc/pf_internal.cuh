@@ -24,6 +24,7 @@ struct Phys {
   double rk_coef;        // (rrf - 1) / A_d,max, or 0 without adsorption
   double mu_p0_pow, mu_w_pow;    // mu_p0^(1-omega), mu_w^(1-omega)
   double inv_c_ref, inv_rho_w;   // 1 / c_ref, 1 / rho_w,ref
+  double inv_mu_o;               // 1 / mu_o
 };
 
 struct Grid {
@@ -78,7 +79,8 @@ void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const
                        double* pv, DT* pd, const double* Mold, double* R, DT* J, double* Mold_out,
                        int mode, cudaStream_t st);
 template <typename DT>
-void launch_face_flux(const Grid& g, const Phys& ph, const double* phi_r, const double* T3,
+// wL3[d * N + i]: pore-volume weight of cell i on its face towards +d
+void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3,
                       const double* x, const double* pv, const DT* pd, double dt, DT* J,
                       double* Fbuf, cudaStream_t st);
 template <typename DT>
@@ -92,7 +94,7 @@ void launch_well_gamma(const Grid& g, const Phys& ph, const Wells& w, const doub
 void launch_well_totals(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                         double* out, cudaStream_t st);
 // Scaled max-norm and squared 2-norm of R: out[0] = max, out[1] = sum of squares.
-void launch_residual_norms(const Grid& g, const Phys& ph, const double* phi_r, const Wells& w,
+void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, const Wells& w,
                            const double* R, double dt, double* partial, int nblocks, double* out,
                            cudaStream_t st);
 void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max,
@@ -117,16 +119,20 @@ void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_
 void launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t st);
 void launch_xpay(long long n, const double* x, double beta, double* y, cudaStream_t st); // y = x + beta y
 void launch_sub(long long n, const double* a, const double* b, double* c, cudaStream_t st); // c = a - b
-// out[j] = sum_i V[j*ld + i] w[i], j < k  (two-stage, deterministic)
+// out[j] = sum_i V[j*ld + i] w[i], j < k.  Per-block rows go to `partial`;
+// the last block reduces them in a fixed order (deterministic) and re-arms
+// `counter` (a zeroed device word shared by all reductions of one stream).
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w,
-                     double* partial, int nblocks, double* out, cudaStream_t st);
+                     double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st);
 // w -= sum_j V[j] h[j]; then out[j] = sum_i V[j][i] w_new[i] (j<k) and out[k] = |w_new|^2
+// (inv_norm: also out[k+1] = 1 / sqrt(out[k]))
 void launch_multi_axpy_dot(long long n, int k, const double* V, long long ld, const double* h,
-                           double* w, double* partial, int nblocks, double* out, cudaStream_t st);
+                           double* w, double* partial, int nblocks, double* out, unsigned int* counter,
+                           cudaStream_t st, int inv_norm = 0);
 // x += sum_j Z[j] y[j]
 void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y,
                            double* x, cudaStream_t st);
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks,
-                double* out, cudaStream_t st);
+                double* out, unsigned int* counter, cudaStream_t st);
 
 }  // namespace pf

@@ -207,9 +207,40 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[KM], int k, dou
   }
 }
 
+// The last block to finish sums the per-block rows in a fixed order (one warp
+// per value, lanes over blocks, then a shuffle tree), so the result does not
+// depend on which block came last; it then re-arms the counter.
+__device__ __forceinline__ void last_block_reduce(const double* partial, int stride, int k, double* out,
+                                                  unsigned int* counter, bool inv_norm = false) {
+  __shared__ bool last;
+  __threadfence();  // every thread that wrote a partial publishes it before the count
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int done = atomicAdd(counter, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = wid; j < k; j += nw) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)b * stride + j);
+    s = wsum(s);
+    if (lane == 0) {
+      out[j] = s;
+      // out[k] = 1 / sqrt(last value): one FP64 sqrt and divide for the whole
+      // vector instead of one per thread of the scaling kernel
+      if (inv_norm && j == k - 1) out[k] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 template <int KM>
 __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const double* __restrict__ V, long long ld,
-                                                  const double* __restrict__ w, double* __restrict__ partial) {
+                                                  const double* __restrict__ w, double* __restrict__ partial,
+                                                  double* __restrict__ out, unsigned int* counter) {
   double acc[KM];
 #pragma unroll
   for (int j = 0; j < KM; ++j) acc[j] = 0.0;
@@ -220,13 +251,15 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
       if (j < k) acc[j] += V[(size_t)j * ld + i] * wi;
   }
   block_reduce_write<KM>(acc, k, partial + (size_t)blockIdx.x * (KM + 1));
+  last_block_reduce(partial, KM + 1, k, out, counter);
 }
 
 // w -= V h; partial dots of the updated w with V (j < k) and with itself (slot k)
 template <int KM>
 __global__ void __launch_bounds__(256) k_multi_axpy_dot(long long n, int k, const double* __restrict__ V, long long ld,
                                                         const double* __restrict__ h, double* __restrict__ w,
-                                                        double* __restrict__ partial) {
+                                                        double* __restrict__ partial, double* __restrict__ out,
+                                                        unsigned int* counter, int inv_norm) {
   __shared__ double hs[KM];
   if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
@@ -248,35 +281,24 @@ __global__ void __launch_bounds__(256) k_multi_axpy_dot(long long n, int k, cons
 #pragma unroll
   for (int j = 0; j <= KM; ++j) accr[j] = (j < k) ? acc[j] : (j == k ? acc[KM] : 0.0);
   block_reduce_write<KM + 1>(accr, k + 1, partial + (size_t)blockIdx.x * (KM + 1));
-}
-
-__global__ void k_reduce_partials(int nblocks, int k, int stride, const double* __restrict__ partial,
-                                  double* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= k) return;
-  double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * stride + j];
-  out[j] = s;
+  last_block_reduce(partial, KM + 1, k + 1, out, counter, inv_norm != 0);
 }
 
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
-                     double* out, cudaStream_t st) {
-  if (k <= 8) k_multidot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial);
-  else if (k <= 16) k_multidot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial);
-  else if (k <= 32) k_multidot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial);
-  else k_multidot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial);
-  const int km = k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : 64));
-  k_reduce_partials<<<1, 128, 0, st>>>(nblocks, k, km + 1, partial, out);
+                     double* out, unsigned int* counter, cudaStream_t st) {
+  if (k <= 8) k_multidot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
+  else if (k <= 16) k_multidot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
+  else if (k <= 32) k_multidot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
+  else k_multidot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
 }
 
 void launch_multi_axpy_dot(long long n, int k, const double* V, long long ld, const double* h, double* w,
-                           double* partial, int nblocks, double* out, cudaStream_t st) {
-  int km;
-  if (k <= 8) { km = 8; k_multi_axpy_dot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial); }
-  else if (k <= 16) { km = 16; k_multi_axpy_dot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial); }
-  else if (k <= 32) { km = 32; k_multi_axpy_dot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial); }
-  else { km = 64; k_multi_axpy_dot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial); }
-  k_reduce_partials<<<1, 128, 0, st>>>(nblocks, k + 1, km + 1, partial, out);
+                           double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st,
+                           int inv_norm) {
+  if (k <= 8) k_multi_axpy_dot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
+  else if (k <= 16) k_multi_axpy_dot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
+  else if (k <= 32) k_multi_axpy_dot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
+  else k_multi_axpy_dot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
@@ -297,9 +319,8 @@ void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, co
 }
 
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
-                cudaStream_t st) {
-  k_multidot<8><<<nblocks, 256, 0, st>>>(n, 1, a, 0, b, partial);
-  k_reduce_partials<<<1, 32, 0, st>>>(nblocks, 1, 9, partial, out);
+                unsigned int* counter, cudaStream_t st) {
+  k_multidot<8><<<nblocks, 256, 0, st>>>(n, 1, a, 0, b, partial, out, counter);
 }
 
 // explicit instantiations

@@ -204,11 +204,12 @@ def scenario_c2(seed=2, nx=100, ny=100, nz=10, n_steps=100, dt_days=10.0, slug_s
 
 
 def scenario_c3(seed=3, nx=600, ny=450, nz=100, n_steps=3, dt_days=10.0, n_inj=(5, 8),
-                n_prod=(8, 10), channels=6):
+                n_prod=(8, 10), channels=6, q_inj_m3_day=2000.0):
     """Channelised reservoir: background log k ~ N(ln 20 mD, 0.5); per layer
     ``channels`` sinusoidal channels with log k ~ N(ln 1000 mD, 0.3), porosity
-    0.25 in channels and 0.15 outside, kv/kh 0.1; injectors and producers on
-    offset lattices, fully perforated; 20x20x2 m cells."""
+    0.25 in channels and 0.15 outside, kv/kh 0.1; injectors (water at
+    ``q_inj_m3_day`` each with 1 kg/m^3 polymer, 400 bar cap) and producers
+    (150 bar) on offset lattices, fully perforated; 20x20x2 m cells."""
     n = nx * ny * nz
     dx, dy, dz = 20.0, 20.0, 2.0
     back = np.exp(math.log(20.0) + 0.5 * normal(seed, 1, n))
@@ -242,8 +243,7 @@ def scenario_c3(seed=3, nx=600, ny=450, nz=100, n_steps=3, dt_days=10.0, n_inj=(
             j = int((b + 0.25) * ny / n_prod[1])
             wells.append(dict(kind="prod", cells=_column(nx, ny, nz, min(i, nx - 1), min(j, ny - 1))))
     ninj = n_inj[0] * n_inj[1]
-    pv = float(phi.sum()) * dx * dy * dz
-    q_inj = pv / (2000.0 * DAY) / ninj
+    q_inj = q_inj_m3_day / DAY
     phys = default_physics()
     controls = [_ctrl("wrate", q_inj, limit=400.0 * BAR, c_inj=1.0)] * ninj + \
                [_ctrl("bhp", 150.0 * BAR)] * (len(wells) - ninj)
