@@ -243,6 +243,36 @@ pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* tota
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);
 
+/* Residual norms without any device allocation.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc
+ * (code running while a stream is captured into a CUDA graph, plugins of a
+ * framework that owns all device memory, loops that forbid allocation after
+ * start-up).  It computes what the residual-norm step of pf_newton_iteration
+ * computes, from caller-owned device buffers:
+ *   out[0] = max over cells of |R_oil| / (V phi_r rho_o), |R_water| /
+ *            (V phi_r rho_w), |R_polymer| / (V phi_r c_ref) and over wells of
+ *            |R_well| / well_denom, the Newton convergence measure;
+ *   out[1] = 2-norm of R, the measure of the forcing term eq. (fterm).
+ * Arguments (device pointers unless stated): R[3 n_cells + n_wells] block-wise
+ * residual; inv_pv[n_cells] = 1 / (V phi_r); well_denom[n_wells] the well
+ * rows' scale (dt * W * 1e5 Pa for a BHP row, dt * rho_ref * |target| for a
+ * rate row; may be NULL without wells); rho_o, rho_w, c_ref host scalars;
+ * out[2] device output; stream a cudaStream_t (NULL = legacy stream).
+ * Limits: n_cells <= 16,777,216 and n_wells <= 4096 (PF_EINVAL with a message
+ * from pf_noalloc_last_error() otherwise).  Its scratch is one fixed 64 KiB
+ * device array per GPU that loads the library, held until the process exits;
+ * the function calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on each device resolves the array's device address (a
+ * symbol lookup, no allocation): make that first call outside any stream
+ * capture.  All calls on a device share the array, so calls that overlap on
+ * the GPU (other streams, concurrent host threads) race; serialise them.
+ * Asynchronous: out is written in stream order. */
+pf_status pf_residual_norms_noalloc(int64_t n_cells, int n_wells, const double* R, const double* inv_pv,
+                                    const double* well_denom, double rho_o, double rho_w, double c_ref,
+                                    double* out, void* stream);
+/* Message of the last failed pf_residual_norms_noalloc call on this thread. */
+const char* pf_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif
