@@ -119,6 +119,7 @@ typedef struct pf_solver_opts {
   double lin_rtol;      /* fixed relative linear tolerance (default 1e-12) */
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
+  double dc_frac;       /* per-iteration concentration change limit as a fraction of c_ref (default 0.5) */
   int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 1, 1) */
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
@@ -242,6 +243,78 @@ pf_status pf_kernel_timing_enable(pf_sim* s, int on);
 pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* total_ms);
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);
+
+/* ---------------------------------------------------------------------------
+ * Time loop, batch engine and serving loop (host runtime, pf_runtime.cu)
+ * ------------------------------------------------------------------------- */
+
+/* A schedule: periods of n_steps fixed steps of length dt [s] under fixed
+ * well controls (controls[n_wells] host array), Sec. 3 step 4(b). */
+typedef struct pf_period {
+  int n_steps;
+  double dt;
+  const pf_well_control* controls;
+} pf_period;
+typedef struct pf_schedule {
+  int n_periods;
+  const pf_period* periods;
+} pf_schedule;
+typedef struct pf_run_report {
+  int steps, newton_iters, krylov_iters, cuts;
+  pf_status status;
+  double seconds;      /* host wall time of the run */
+} pf_run_report;
+
+/* Runs the whole schedule on s: per step pf_step, halving the step on Newton
+ * failure (Sec. 3 step 4(a)) at most max_cuts times per step; the next step
+ * starts from the full dt again.  rep may be NULL. */
+pf_status pf_run_schedule(pf_sim* s, const pf_schedule* sched, int max_cuts, pf_run_report* rep);
+/* Message of the last failed runtime call (pf_run_schedule, pf_batch_*, pf_server_*) on this thread. */
+const char* pf_runtime_last_error(void);
+
+/* Device bytes pf_create would allocate for this model and these options
+ * (one arena per simulator; used for admission by footprint). */
+pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* bytes);
+
+/* Batch engine: n scenarios, each a pf_sim with its own stream and CUDA
+ * graphs on the current device; pf_batch_run drives them from n_threads host
+ * threads so their kernels overlap on the GPU.  schedules[n], reports[n]
+ * (may be NULL).  Returns the first failing member's status. */
+typedef struct pf_batch pf_batch;
+pf_status pf_batch_create(const pf_model_desc* const* models, int n, const pf_solver_opts* o, int n_threads,
+                          pf_batch** out);
+pf_status pf_batch_run(pf_batch* b, const pf_schedule* const* schedules, int max_cuts, pf_run_report* reports);
+pf_status pf_batch_member(pf_batch* b, int i, pf_sim** out);
+pf_status pf_batch_destroy(pf_batch* b);
+
+/* Serving loop: requests (a model and a schedule, deep-copied at submit) are
+ * queued in arrival order; n_workers host threads admit the first queued
+ * request whose footprint fits the free part of hbm_budget, create its pf_sim
+ * (device state stays resident for the whole run), run its schedule, keep
+ * the final state on the host and free the device memory.  Requests that
+ * arrive while others run are admitted as memory and workers free up, and
+ * their work overlaps on the GPU.  PF_EBUSY at submit: the request can never
+ * fit the budget.  Times are host steady-clock seconds. */
+enum { PF_REQ_QUEUED = 0, PF_REQ_RUNNING = 1, PF_REQ_DONE = 2, PF_REQ_FAILED = 3 };
+typedef struct pf_result {
+  int state;           /* PF_REQ_* */
+  pf_status status;
+  pf_run_report report;
+  double t_submit, t_start, t_end;
+  size_t footprint;
+} pf_result;
+typedef struct pf_server pf_server;
+pf_status pf_server_create(size_t hbm_budget, int n_workers, const pf_solver_opts* o, int max_cuts,
+                           pf_server** out);
+pf_status pf_server_submit(pf_server* srv, const pf_model_desc* m, const pf_schedule* sched, uint64_t* ticket);
+pf_status pf_server_poll(pf_server* srv, uint64_t ticket, pf_result* out);
+/* Blocks until the request is done or failed (PF_ETIMEOUT after timeout_s). */
+pf_status pf_server_wait(pf_server* srv, uint64_t ticket, double timeout_s, pf_result* out);
+/* Final P, S, C [N] and Pb [W] of a finished request (host arrays, any NULL). */
+pf_status pf_server_fetch_state(pf_server* srv, uint64_t ticket, double* P, double* S, double* C, double* Pb);
+pf_status pf_server_stats(pf_server* srv, size_t* in_use, int* running, int* queued);
+/* Stops the workers after their current requests; queued requests are dropped. */
+pf_status pf_server_destroy(pf_server* srv);
 
 /* Residual norms without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc

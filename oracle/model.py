@@ -50,8 +50,8 @@ takes the same ones):
   * residuals are masses [kg]; a BHP well row is dt * W (P_b - target) with
     W = sum(WI) rho_w,ref / mu_w; a rate row is dt (sum of signed phase mass
     rates - rho_ref * target).
-  * Newton update: S change per cell chopped to +-ds_max, then S clipped to
-    [0, 1] and C to >= 0.
+  * Newton update: S change per cell chopped to +-ds_max and C change to
+    +-0.5 C_ref, then S clipped to [0, 1] and C to >= 0.
 """
 
 import math
@@ -451,13 +451,18 @@ def forcing_term(norm_b, norm_b_prev, gamma=0.5, beta=GOLDEN, lo=0.01, hi=0.1):
     return min(max(eta, lo), hi)
 
 
-def update(st, x, dx, ds_max):
+def update(st, x, dx, ds_max, dc_frac=0.5):
+    """x + dx with the saturation change chopped to +-ds_max and the
+    concentration change to +-dc_frac * C_ref per cell, then S clipped to
+    [0, 1] and C to >= 0 (these limits shape the path, not the root)."""
     n = st.n
     y = x.copy()
     y[0:3 * n:3] += dx[0:3 * n:3]
     ds = np.clip(dx[1:3 * n:3], -ds_max, ds_max)
     y[1:3 * n:3] = np.clip(x[1:3 * n:3] + ds, 0.0, 1.0)
-    y[2:3 * n:3] = np.maximum(x[2:3 * n:3] + dx[2:3 * n:3], 0.0)
+    dc_max = dc_frac * st.ph["c_ref"]
+    dc = np.clip(dx[2:3 * n:3], -dc_max, dc_max)
+    y[2:3 * n:3] = np.maximum(x[2:3 * n:3] + dc, 0.0)
     y[3 * n:] += dx[3 * n:]
     return y
 
@@ -478,16 +483,37 @@ def initial_state(st):
     return x
 
 
-def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, record=None):
-    """One backward-Euler step by Newton's method (Algorithm 1).
+def limit_crossings(st, x, controls, switched):
+    """In-iteration limit check: a rate well with a BHP limit whose current
+    P_b crosses it (above for an injector, below for a producer) is moved onto
+    BHP = limit for the rest of the step.  Returns True if anything switched."""
+    changed = False
+    for w, c in enumerate(controls):
+        if c["ctrl"] == "bhp" or not c.get("limit") or switched[w]:
+            continue
+        pb = x[3 * st.n + w]
+        kind = st.wells[w]["kind"]
+        if (kind == "inj" and pb > c["limit"]) or (kind == "prod" and pb < c["limit"]):
+            switched[w] = True
+            changed = True
+    return changed
+
+
+def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, record=None, switched=None):
+    """One backward-Euler step by Newton's method (Algorithm 1) under the user
+    controls; rate wells flagged in ``switched`` (updated in place by the
+    in-iteration limit check) run on their BHP limit.
 
     Returns (x_new, converged, iterations)."""
+    if switched is None:
+        switched = [False] * st.nw
+    eff = effective_controls(st, controls, switched)
     M_old = masses(st, x_old)
-    gamma = well_gamma(st, x_old, controls)
+    gamma = well_gamma(st, x_old, eff)
     x = x_old.copy()
     for it in range(max_iter + 1):
-        R, J = assemble(st, x, M_old, dt, controls, gamma)
-        res = scaled_residual(st, R, dt, controls)
+        R, J = assemble(st, x, M_old, dt, eff, gamma)
+        res = scaled_residual(st, R, dt, eff)
         if record is not None:
             record.append(res)
         if res <= tol:
@@ -496,6 +522,8 @@ def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, rec
             break
         dx = solve_linear(J, -R)
         x = update(st, x, dx, ds_max)
+        if limit_crossings(st, x, controls, switched):
+            eff = effective_controls(st, controls, switched)
     return x_old, False, max_iter
 
 
@@ -562,8 +590,10 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_sw
         callback=None):
     """Time loop over the scenario schedule with fixed steps; on a Newton
     failure the step is cut in half and retried (Sec. 3, step 4(a)); controls
-    stay fixed within a step (step 4(b)) and BHP limits are applied by
-    ``update_switches`` with up to ``max_switch_solves`` re-solves."""
+    stay fixed within a step (step 4(b)) except that a rate well crossing its
+    BHP limit during the iterations moves onto the limit (``limit_crossings``);
+    after convergence ``update_switches`` may switch it back, with up to
+    ``max_switch_solves`` re-solves."""
     st = Setup(sc)
     x = initial_state(st)
     t = 0.0
@@ -588,11 +618,12 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_sw
             while dt_left > 0.0:
                 dt = min(dt, dt_left)
                 for attempt in range(max_switch_solves + 1):
-                    eff = effective_controls(st, ctl, switched)
-                    xn, ok, its = newton_step(st, x, dt, eff, tol=tol, max_iter=max_iter, ds_max=ds_max)
+                    xn, ok, its = newton_step(st, x, dt, ctl, tol=tol, max_iter=max_iter, ds_max=ds_max,
+                                              switched=switched)
                     newton_total += its
                     if not ok or attempt == max_switch_solves:
                         break
+                    eff = effective_controls(st, ctl, switched)
                     gam = well_gamma(st, x, eff)
                     if not update_switches(st, ctl, switched, well_totals(st, xn, eff, gam)):
                         break

@@ -60,6 +60,7 @@ class pf_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("gmres_restart", C.c_int),
                 ("gmres_max_iter", C.c_int), ("newton_max_iter", C.c_int), ("use_forcing", C.c_int),
                 ("lin_rtol", C.c_double), ("newton_tol", C.c_double), ("ds_max", C.c_double),
+                ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
                 ("amg_cycle", C.c_int)]
 
@@ -77,6 +78,26 @@ class pf_step_report(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("converged", C.c_int),
                 ("res_scaled", C.c_double)]
 
+
+class pf_period(C.Structure):
+    _fields_ = [("n_steps", C.c_int), ("dt", C.c_double), ("controls", C.POINTER(pf_well_control))]
+
+
+class pf_schedule(C.Structure):
+    _fields_ = [("n_periods", C.c_int), ("periods", C.POINTER(pf_period))]
+
+
+class pf_run_report(C.Structure):
+    _fields_ = [("steps", C.c_int), ("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("cuts", C.c_int),
+                ("status", C.c_int), ("seconds", C.c_double)]
+
+
+class pf_result(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("report", pf_run_report), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_end", C.c_double), ("footprint", C.c_size_t)]
+
+
+PF_REQ_QUEUED, PF_REQ_RUNNING, PF_REQ_DONE, PF_REQ_FAILED = range(4)
 
 _lib = None
 
@@ -117,6 +138,24 @@ def lib():
             "pf_set_x": ([vp, _dp], C.c_int),
             "pf_kernel_timing_enable": ([vp, C.c_int], C.c_int),
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
+            "pf_run_schedule": ([vp, C.POINTER(pf_schedule), C.c_int, C.POINTER(pf_run_report)], C.c_int),
+            "pf_runtime_last_error": ([], C.c_char_p),
+            "pf_footprint": ([C.POINTER(pf_model_desc), C.POINTER(pf_solver_opts), C.POINTER(C.c_size_t)],
+                             C.c_int),
+            "pf_batch_create": ([C.POINTER(C.POINTER(pf_model_desc)), C.c_int, C.POINTER(pf_solver_opts), C.c_int,
+                                 C.POINTER(vp)], C.c_int),
+            "pf_batch_run": ([vp, C.POINTER(C.POINTER(pf_schedule)), C.c_int, C.POINTER(pf_run_report)], C.c_int),
+            "pf_batch_member": ([vp, C.c_int, C.POINTER(vp)], C.c_int),
+            "pf_batch_destroy": ([vp], C.c_int),
+            "pf_server_create": ([C.c_size_t, C.c_int, C.POINTER(pf_solver_opts), C.c_int, C.POINTER(vp)],
+                                 C.c_int),
+            "pf_server_submit": ([vp, C.POINTER(pf_model_desc), C.POINTER(pf_schedule), C.POINTER(C.c_uint64)],
+                                 C.c_int),
+            "pf_server_poll": ([vp, C.c_uint64, C.POINTER(pf_result)], C.c_int),
+            "pf_server_wait": ([vp, C.c_uint64, C.c_double, C.POINTER(pf_result)], C.c_int),
+            "pf_server_fetch_state": ([vp, C.c_uint64, _dp, _dp, _dp, _dp], C.c_int),
+            "pf_server_stats": ([vp, C.POINTER(C.c_size_t), _ip, _ip], C.c_int),
+            "pf_server_destroy": ([vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -369,3 +408,143 @@ class Simulator:
                 if callback is not None:
                     callback(self, rec)
         return hist
+
+
+def _rt_check(rc):
+    if rc != PF_OK:
+        raise PfError(rc, lib().pf_runtime_last_error().decode())
+    return rc
+
+
+class Schedule:
+    """pf_schedule built from a scenario's schedule list (keeps arrays alive);
+    ``n_steps`` truncates it."""
+
+    def __init__(self, schedule, n_steps=None):
+        periods = []
+        left = n_steps
+        for p in schedule:
+            k = p["n_steps"] if left is None else min(p["n_steps"], left)
+            if k <= 0:
+                break
+            periods.append((k, p["dt"], controls_array(p["controls"])))
+            if left is not None:
+                left -= k
+        self.arr = (pf_period * max(1, len(periods)))()
+        self.keep = []
+        for i, (k, dt, ctl) in enumerate(periods):
+            self.arr[i].n_steps = k
+            self.arr[i].dt = dt
+            self.arr[i].controls = C.cast(ctl, C.POINTER(pf_well_control))
+            self.keep.append(ctl)
+        self.s = pf_schedule(len(periods), C.cast(self.arr, C.POINTER(pf_period)))
+        self.n_steps = sum(p[0] for p in periods)
+
+
+def run_schedule(sim, schedule, max_cuts=6):
+    """Native time loop (pf_run_schedule) over a scenario schedule."""
+    rep = pf_run_report()
+    _rt_check(lib().pf_run_schedule(sim.h, C.byref(schedule.s), max_cuts, C.byref(rep)))
+    return rep
+
+
+def footprint(sc, opts=None, **over):
+    m = Model(sc)
+    o = opts if opts is not None else default_opts(**over)
+    b = C.c_size_t()
+    _check(lib().pf_footprint(C.byref(m.desc), C.byref(o), C.byref(b)))
+    return b.value
+
+
+class Batch:
+    """Many scenarios resident at once, each with its own stream; pf_batch_run
+    drives them from ``n_threads`` host threads."""
+
+    def __init__(self, scenarios, n_threads=8, opts=None, **over):
+        self.models = [Model(sc) for sc in scenarios]
+        self.opts = opts if opts is not None else default_opts(**over)
+        arr = (C.POINTER(pf_model_desc) * len(self.models))(*[C.pointer(m.desc) for m in self.models])
+        h = C.c_void_p()
+        _rt_check(lib().pf_batch_create(arr, len(self.models), C.byref(self.opts), n_threads, C.byref(h)))
+        self.h = h
+        self.scenarios = scenarios
+
+    def run(self, n_steps=None, max_cuts=6, raise_on_failure=True):
+        scheds = [Schedule(sc["schedule"], n_steps) for sc in self.scenarios]
+        arr = (C.POINTER(pf_schedule) * len(scheds))(*[C.pointer(s.s) for s in scheds])
+        reps = (pf_run_report * len(scheds))()
+        rc = lib().pf_batch_run(self.h, arr, max_cuts, reps)
+        if rc != PF_OK and raise_on_failure:
+            _rt_check(rc)
+        return list(reps)
+
+    def member_x(self, i):
+        p = C.c_void_p()
+        _rt_check(lib().pf_batch_member(self.h, i, C.byref(p)))
+        n = C.c_int64(); nw = C.c_int(); npf = C.c_int64()
+        _check(lib().pf_sizes(p, C.byref(n), C.byref(nw), C.byref(npf)))
+        x = np.empty(3 * n.value + nw.value)
+        _check(lib().pf_get_x(p, _ptr(x)))
+        return x
+
+    def close(self):
+        if self.h:
+            lib().pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server with admission by device footprint."""
+
+    def __init__(self, hbm_budget, n_workers=8, opts=None, max_cuts=6, **over):
+        self.opts = opts if opts is not None else default_opts(**over)
+        h = C.c_void_p()
+        _rt_check(lib().pf_server_create(int(hbm_budget), n_workers, C.byref(self.opts), max_cuts, C.byref(h)))
+        self.h = h
+        self.meta = {}
+
+    def submit(self, sc, n_steps=None):
+        m = Model(sc)
+        s = Schedule(sc["schedule"], n_steps)
+        t = C.c_uint64()
+        _rt_check(lib().pf_server_submit(self.h, C.byref(m.desc), C.byref(s.s), C.byref(t)))
+        self.meta[t.value] = (sc["nx"] * sc["ny"] * sc["nz"], len(sc["wells"]))
+        return t.value
+
+    def poll(self, ticket):
+        r = pf_result()
+        _rt_check(lib().pf_server_poll(self.h, ticket, C.byref(r)))
+        return r
+
+    def wait(self, ticket, timeout=3600.0):
+        r = pf_result()
+        _rt_check(lib().pf_server_wait(self.h, ticket, timeout, C.byref(r)))
+        return r
+
+    def state(self, ticket):
+        n, nw = self.meta[ticket]
+        P, S, Cc, Pb = np.empty(n), np.empty(n), np.empty(n), np.empty(max(1, nw))
+        _rt_check(lib().pf_server_fetch_state(self.h, ticket, _ptr(P), _ptr(S), _ptr(Cc), _ptr(Pb)))
+        return P, S, Cc, Pb[:nw]
+
+    def stats(self):
+        u = C.c_size_t(); r = C.c_int(); q = C.c_int()
+        _rt_check(lib().pf_server_stats(self.h, C.byref(u), C.byref(r), C.byref(q)))
+        return u.value, r.value, q.value
+
+    def close(self):
+        if self.h:
+            lib().pf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

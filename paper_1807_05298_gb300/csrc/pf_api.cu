@@ -632,6 +632,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->lin_rtol = 1e-12;
   o->newton_tol = 1e-10;
   o->ds_max = 0.2;
+  o->dc_frac = 0.5;
   o->amg_pre_sweeps = 1;
   o->amg_post_sweeps = 1;
   o->amg_coarse_size = 8;
@@ -733,7 +734,10 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   s->cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
   s->arena_bytes = carve(s, nullptr);
   {
-    cudaError_t e = cudaMalloc((void**)&s->arena, s->arena_bytes);
+    // stream-ordered allocation: no device-wide synchronisation, so creating
+    // or destroying one simulator does not stall the others' streams
+    cudaError_t e = cudaMallocAsync((void**)&s->arena, s->arena_bytes, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       delete s;
@@ -741,7 +745,8 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
     }
     e = cudaMallocHost((void**)&s->h_pinned, 4 * 128 * sizeof(double));
     if (e != cudaSuccess) {
-      cudaFree(s->arena);
+      cudaFreeAsync(s->arena, s->stream);
+      cudaStreamSynchronize(s->stream);
       delete s;
       return fail(PF_ENOMEM, "pinned host buffer");
     }
@@ -750,7 +755,8 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   {
     cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-      cudaFree(s->arena);
+      cudaFreeAsync(s->arena, s->stream);
+      cudaStreamSynchronize(s->stream);
       cudaFreeHost(s->h_pinned);
       delete s;
       return fail(PF_ECUDA, std::string("capture stream: ") + cudaGetErrorString(e));
@@ -788,6 +794,31 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   return PF_OK;
 }
 
+pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* bytes) {
+  if (!bytes) return fail(PF_EINVAL, "bytes is NULL");
+  pf_solver_opts opts;
+  pf_default_opts(&opts);
+  if (o) opts = *o;
+  pf_status rc = validate(m, &opts);
+  if (rc != PF_OK) return rc;
+  pf_sim tmp;
+  tmp.opts = opts;
+  tmp.mixed = opts.precision == PF_PREC_MIXED;
+  tmp.g.nx = m->nx; tmp.g.ny = m->ny; tmp.g.nz = m->nz;
+  tmp.g.nxy = (long long)m->nx * m->ny;
+  tmp.g.n = tmp.g.nxy * m->nz;
+  tmp.nw = m->n_wells;
+  tmp.npf = 0;
+  for (int w = 0; w < m->n_wells; ++w) tmp.npf += m->wells[w].n_perf;
+  tmp.nunk = 3 * tmp.g.n + tmp.nw;
+  tmp.ld = (long long)align_up((size_t)tmp.nunk, 64);
+  tmp.nblocks = 2 * 152;
+  tmp.cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
+  // arena + pinned staging + graph and context overheads (a fixed allowance)
+  *bytes = carve(&tmp, nullptr) + ((size_t)8 << 20);
+  return PF_OK;
+}
+
 pf_status pf_destroy(pf_sim* s) {
   if (!s) return PF_OK;
   cudaSetDevice(s->device);
@@ -798,7 +829,10 @@ pf_status pf_destroy(pf_sim* s) {
     if (G.ortho) cudaGraphExecDestroy(G.ortho);
   }
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-  if (s->arena) cudaFree(s->arena);
+  if (s->arena) {
+    cudaFreeAsync(s->arena, s->stream);
+    cudaStreamSynchronize(s->stream);
+  }
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   for (auto& p : s->kt_pending) { s->kt_pool.push_back(p.second.first); s->kt_pool.push_back(p.second.second); }
   for (cudaEvent_t e : s->kt_pool) cudaEventDestroy(e);
@@ -920,6 +954,31 @@ pf_status pf_assemble(pf_sim* s) {
   return PF_OK;
 }
 
+static bool has_limits(const pf_sim* s);
+
+// In-iteration limit check after an update: a rate well whose P_b crosses its
+// BHP limit (above for an injector, below for a producer) moves onto BHP =
+// limit for the rest of the step; the effective controls are re-uploaded.
+static pf_status limit_crossings(pf_sim* s) {
+  if (!has_limits(s)) return PF_OK;
+  std::vector<double> pb(s->nw);
+  PF_CUDA(cudaMemcpyAsync(pb.data(), s->x + 3 * s->g.n, s->nw * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  bool changed = false;
+  for (int w = 0; w < s->nw; ++w) {
+    const pf_well_control& c = s->h_ctl[w];
+    if (c.ctrl == PF_CTRL_BHP || c.limit == 0.0 || s->switched[w]) continue;
+    const int kind = s->h_kind[w];
+    if ((kind == PF_WELL_INJECTOR && pb[w] > c.limit) || (kind == PF_WELL_PRODUCER && pb[w] < c.limit)) {
+      s->switched[w] = 1;
+      changed = true;
+    }
+  }
+  if (!changed) return PF_OK;
+  std::vector<pf_well_control> eff = effective_controls(s);
+  return upload_controls(s, eff.data(), s->nw);
+}
+
 static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_update) {
   pf_status rc;
   if ((rc = assemble(s)) != PF_OK) return rc;
@@ -957,8 +1016,9 @@ static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_upd
     if (rep) *rep = r;
     return rc;
   }
-  launch_newton_update(s->g, s->nw, s->x, s->dx, s->opts.ds_max, s->stream);
+  launch_newton_update(s->g, s->nw, s->x, s->dx, s->opts.ds_max, s->opts.dc_frac * s->ph.c_ref, s->stream);
   PF_LAUNCHED(1);
+  if ((rc = limit_crossings(s)) != PF_OK) return rc;
   s->prev_norm = nrm;
   s->iter_in_step++;
   if (rep) *rep = r;

@@ -694,19 +694,21 @@ void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, 
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_newton_update(long long n, int nw, double* __restrict__ x,
-                                                       const double* __restrict__ dx, double ds_max) {
+                                                       const double* __restrict__ dx, double ds_max, double dc_max) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nw;
        i += (long long)gridDim.x * blockDim.x) {
     if (i >= n) { x[3 * n + (i - n)] += dx[3 * n + (i - n)]; continue; }
     x[3 * i] += dx[3 * i];
     const double ds = fmin(fmax(dx[3 * i + 1], -ds_max), ds_max);
     x[3 * i + 1] = fmin(fmax(x[3 * i + 1] + ds, 0.0), 1.0);
-    x[3 * i + 2] = fmax(x[3 * i + 2] + dx[3 * i + 2], 0.0);
+    const double dc = fmin(fmax(dx[3 * i + 2], -dc_max), dc_max);
+    x[3 * i + 2] = fmax(x[3 * i + 2] + dc, 0.0);
   }
 }
 
-void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max, cudaStream_t st) {
-  k_newton_update<<<grid_for(g.n + nw, 256), 256, 0, st>>>(g.n, nw, x, dx, ds_max);
+void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max, double dc_max,
+                          cudaStream_t st) {
+  k_newton_update<<<grid_for(g.n + nw, 256), 256, 0, st>>>(g.n, nw, x, dx, ds_max, dc_max);
 }
 
 // explicit instantiations

@@ -97,7 +97,8 @@ void launch_well_totals(const Grid& g, const Phys& ph, const Wells& w, const dou
 void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, const Wells& w,
                            const double* R, double dt, double* partial, int nblocks, double* out,
                            cudaStream_t st);
-void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max,
+// x += dx with |dS| <= ds_max and |dC| <= dc_max per cell, then S in [0, 1], C >= 0
+void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max, double dc_max,
                           cudaStream_t st);
 
 // Linear algebra (pf_linalg.cu) ---------------------------------------------

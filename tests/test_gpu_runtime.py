@@ -1,0 +1,113 @@
+"""Native time loop, batch engine and serving loop on the GPU.
+
+* pf_run_schedule reproduces the oracle's time loop (1e-6 per step field).
+* A scenario gives bit-identical states alone and as a member of a batch or
+  of a server's mix (deterministic kernels; streams and host threads do not
+  enter the arithmetic).
+* The server never holds more device memory than its budget and refuses a
+  request that can never fit with PF_EBUSY.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from scenarios import generate as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.set_device(0)
+    from paper_1807_05298_gb300 import build as bld
+    bld.build()
+    from paper_1807_05298_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def small_members(k, n_steps=3):
+    out = []
+    for i in range(k):
+        nx = 12 + 5 * i
+        sc = G.scenario_c2(seed=200 + i, nx=nx, ny=nx + 3, nz=3 + (i % 3), n_steps=n_steps, slug_steps=2,
+                           c_slug=0.5 + 0.3 * i, rrf=1.2 + 0.1 * i, dt_days=2.0)
+        out.append(sc)
+    return out
+
+
+def alone(B, sc, n_steps, **opt):
+    sim = B.Simulator(sc, **opt)
+    B.run_schedule(sim, B.Schedule(sc["schedule"], n_steps))
+    x = sim.get_x()
+    sim.close()
+    return x
+
+
+def test_native_time_loop_matches_oracle(B):
+    sc = G.scenario_c1(n_steps=10)
+    sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=1)
+    rep = B.run_schedule(sim, B.Schedule(sc["schedule"]))
+    x = sim.get_x()
+    sim.close()
+    st, xo, hist = M.run(sc)
+    assert rep.steps == 10 and rep.status == 0
+    n = st.n
+    for a in range(3):
+        ref = max(np.abs(xo[a:3 * n:3]).max(), 1e-12)
+        assert np.abs(x[a:3 * n:3] - xo[a:3 * n:3]).max() <= 1e-6 * ref
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_members_equal_alone(B, precision):
+    scs = small_members(5)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+    batch = B.Batch(scs, n_threads=4, **opt)
+    reps = batch.run(n_steps=3)
+    assert all(r.status == 0 and r.steps == 3 for r in reps)
+    xs = [batch.member_x(i) for i in range(len(scs))]
+    batch.close()
+    for sc, xb in zip(scs, xs):
+        xa = alone(B, sc, 3, **opt)
+        assert np.array_equal(xa, xb)
+
+
+def test_server_same_alone_and_in_mix_and_admission(B):
+    scs = small_members(6, n_steps=2)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=B.PF_PREC_MIXED)
+    fps = [B.footprint(sc, precond=B.PF_PC_CPR, precision=B.PF_PREC_MIXED) for sc in scs]
+    budget = int(sorted(fps)[-1] + sorted(fps)[-2])   # at most about two requests resident
+    srv = B.Server(budget, n_workers=4, **opt)
+    tickets = []
+    peak = 0
+    for sc in scs:
+        tickets.append(srv.submit(sc, n_steps=2))
+        peak = max(peak, srv.stats()[0])
+    done = False
+    t0 = time.time()
+    while not done and time.time() - t0 < 300:
+        used, running, queued = srv.stats()
+        peak = max(peak, used)
+        done = all(srv.poll(t).state in (B.PF_REQ_DONE, B.PF_REQ_FAILED) for t in tickets)
+        time.sleep(0.001)
+    assert done
+    assert peak <= budget
+    results = [srv.wait(t) for t in tickets]
+    assert all(r.state == B.PF_REQ_DONE and r.report.steps == 2 for r in results)
+    assert all(r.t_end >= r.t_start >= r.t_submit for r in results)
+    for sc, t in zip(scs, tickets):
+        P, S, C, Pb = srv.state(t)
+        xa = alone(B, sc, 2, **opt)
+        n = sc["nx"] * sc["ny"] * sc["nz"]
+        assert np.array_equal(P, xa[0:3 * n:3]) and np.array_equal(S, xa[1:3 * n:3])
+        assert np.array_equal(C, xa[2:3 * n:3]) and np.array_equal(Pb, xa[3 * n:])
+    big = G.scenario_c2(nx=60, ny=60, nz=10)
+    with pytest.raises(B.PfError) as e:
+        srv.submit(big)
+    assert e.value.status == B.PF_EBUSY
+    srv.close()
