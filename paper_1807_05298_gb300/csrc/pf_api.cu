@@ -74,6 +74,7 @@ struct pf_sim {
   long long* w_cell = nullptr;
   double *w_wi = nullptr, *w_dzb = nullptr, *w_target = nullptr, *w_cinj = nullptr, *w_W = nullptr;
   double *w_sw = nullptr, *w_so = nullptr, *w_scale = nullptr, *w_gamma = nullptr;
+  float* Zf = nullptr;  // mixed precision: FP32 copies of the preconditioned vectors
   double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
   double* wtot = nullptr;  // [3 nw] well totals
   unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
@@ -315,8 +316,9 @@ size_t carve(pf_sim* s, char* base) {
   s->tmp = c.take<double>(s->nunk);
   s->V = c.take<double>((size_t)(m + 1) * s->ld);
   s->Z = c.take<double>((size_t)m * s->ld);
-  s->hbuf = c.take<double>(4 * 128);
-  s->partial = c.take<double>((size_t)s->nblocks * 70);
+  s->Zf = s->mixed ? c.take<float>((size_t)m * s->ld) : nullptr;
+  s->hbuf = c.take<double>(4 * 128 + 8);
+  s->partial = c.take<double>((size_t)s->nblocks * 72);
   s->norms = c.take<double>(4);
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
@@ -387,19 +389,23 @@ pf_status precond_setup(pf_sim* s) {
   return PF_OK;
 }
 
-// z = M^{-1} v
-pf_status precond_apply(pf_sim* s, const double* v, double* z) {
+// z = M^{-1} v (and, in mixed precision, an FP32 copy zf of z when zf != null)
+pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullptr) {
   if (s->opts.precond == PF_PC_CPR) {
     int k = 0;
     KtScope t(s, PF_KT_PRECOND);
     cpr_apply(s->cpr, s->g, wells_view(s), s->mixed, s->J, s->Bw, s->Cw, s->Dw, s->Dinv, s->Dwinv, v, z, s->tmp,
-              s->stream, &k);
+              zf, s->stream, &k);
     PF_LAUNCHED(k);
     return PF_OK;
   }
   if (s->mixed) launch_bjacobi_apply<float>(s->g, s->nw, (const float*)s->Dinv, (const float*)s->Dwinv, v, z, s->stream);
   else launch_bjacobi_apply<double>(s->g, s->nw, (const double*)s->Dinv, (const double*)s->Dwinv, v, z, s->stream);
   PF_LAUNCHED(1);
+  if (s->mixed && zf) {
+    launch_to_f32(s->nunk, z, zf, s->stream);
+    PF_LAUNCHED(1);
+  }
   return PF_OK;
 }
 
@@ -423,10 +429,17 @@ void scale_vec(pf_sim* s, const double* a, double f, double* b) {
 // normalisation of v_{j+1} by its device-side norm and the copy of the
 // Hessenberg column to pinned host memory.
 pf_status piece_pre(pf_sim* s, int j) {
-  return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld);
+  return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld,
+                       s->mixed ? s->Zf + (size_t)j * s->ld : nullptr);
 }
 pf_status piece_spmv(pf_sim* s, int j) {
-  return spmv(s, s->Z + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld);
+  if (!s->mixed) return spmv(s, s->Z + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld);
+  // mixed precision: FP32 operator on the FP32 copy of z_j
+  KtScope t(s, PF_KT_SPMV);
+  launch_spmv_f32(s->g, wells_view(s), (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw,
+                  (const float*)s->Dw, s->Zf + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld, s->stream);
+  PF_LAUNCHED(1 + (s->nw > 0));
+  return PF_OK;
 }
 pf_status piece_ortho(pf_sim* s, int j) {
   const long long n = s->nunk, ld = s->ld;
@@ -434,13 +447,20 @@ pf_status piece_ortho(pf_sim* s, int j) {
   double* w = s->V + (size_t)(j + 1) * ld;
   cudaStream_t st = s->stream;
   KtScope t(s, PF_KT_ORTHO);
-  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st);
-  launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st);
-  launch_multi_axpy_dot(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, st,
-                        1);
-  launch_scale_by_dev(n, w, s->hbuf + 256 + k + 1, 0, w, st);
-  PF_LAUNCHED(4);
-  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, 3 * 128 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // pass 1: hbuf[0..k) = V^T w and hbuf[k] = |w|^2; w -= V h1 with |w|^2 and
+  // 1/|w| at hbuf[256..257] and the reorthogonalisation flag at hbuf+384.
+  // pass 2 runs only if flagged: hbuf[128..128+k) = V^T w, w -= V h2, and it
+  // overwrites hbuf[256..257].
+  int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr);
+  launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, s->hbuf + k,
+                   reorth, nullptr, st);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
+  launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
+                   nullptr, reorth, st);
+  launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st);
+  PF_LAUNCHED(5);
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, (3 * 128 + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   return PF_OK;
 }
 
@@ -541,9 +561,10 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
       const int k = j + 1;
       const double* h1 = s->h_pinned;
       const double* h2 = s->h_pinned + 128;
-      const double hn = sqrt(std::max(s->h_pinned[256 + k], 0.0));
+      const bool second_pass = reinterpret_cast<const int*>(s->h_pinned + 384)[0] != 0;
+      const double hn = sqrt(std::max(s->h_pinned[256], 0.0));
       double* col = &H[(size_t)j * (m + 1)];
-      for (int i = 0; i < k; ++i) col[i] = h1[i] + h2[i];
+      for (int i = 0; i < k; ++i) col[i] = h1[i] + (second_pass ? h2[i] : 0.0);
       col[k] = hn;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -672,7 +693,7 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   s->ld = (long long)align_up((size_t)s->nunk, 64);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  s->nblocks = 2 * sms;
+  s->nblocks = 4 * sms;  // reduction grids: 4 blocks of 256 per SM
   s->h_ctl.resize(s->nw);
   s->switched.assign(s->nw, 0);
   // host set-up: transmissibilities and well indices
@@ -743,7 +764,7 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
       delete s;
       return fail(PF_ENOMEM, "device arena of " + std::to_string(s->arena_bytes) + " bytes: " + cudaGetErrorString(e));
     }
-    e = cudaMallocHost((void**)&s->h_pinned, 4 * 128 * sizeof(double));
+    e = cudaMallocHost((void**)&s->h_pinned, (4 * 128 + 8) * sizeof(double));
     if (e != cudaSuccess) {
       cudaFreeAsync(s->arena, s->stream);
       cudaStreamSynchronize(s->stream);
@@ -812,7 +833,7 @@ pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* 
   for (int w = 0; w < m->n_wells; ++w) tmp.npf += m->wells[w].n_perf;
   tmp.nunk = 3 * tmp.g.n + tmp.nw;
   tmp.ld = (long long)align_up((size_t)tmp.nunk, 64);
-  tmp.nblocks = 2 * 152;
+  tmp.nblocks = 4 * 152;
   tmp.cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
   // arena + pinned staging + graph and context overheads (a fixed allowance)
   *bytes = carve(&tmp, nullptr) + ((size_t)8 << 20);

@@ -321,10 +321,11 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long k = i / g.nxy;
-    const long long rem = i - k * g.nxy;
-    const long long j = rem / g.nx;
-    const long long ii = rem - j * g.nx;
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
     SideV a; SideD<DT> da;
     load_side<DT>(i, n, x, pv, pd, a, da);
 #pragma unroll 1
@@ -384,10 +385,11 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long k = i / g.nxy;
-    const long long rem = i - k * g.nxy;
-    const long long j = rem / g.nx;
-    const long long ii = rem - j * g.nx;
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
     double fs[3] = {0.0, 0.0, 0.0};
     DT dsum[9];
 #pragma unroll

@@ -19,11 +19,15 @@ struct Dims {
 
 Dims dims_of(const CprLevel& L) { return Dims{L.nx, L.ny, L.nz, L.n, (long long)L.nx * L.ny}; }
 
+// 32-bit division: grids hold fewer than 2^31 cells (pf_create checks)
 __device__ __forceinline__ void coords(const Dims& d, long long i, int& x, int& y, int& z) {
-  z = (int)(i / d.nxy);
-  const long long r = i - (long long)z * d.nxy;
-  y = (int)(r / d.nx);
-  x = (int)(r - (long long)y * d.nx);
+  const unsigned int ui = (unsigned int)i, nxy = (unsigned int)d.nxy, nx = (unsigned int)d.nx;
+  const unsigned int zz = ui / nxy;
+  const unsigned int r = ui - zz * nxy;
+  const unsigned int yy = r / nx;
+  z = (int)zz;
+  y = (int)yy;
+  x = (int)(r - yy * nx);
 }
 
 // neighbour of (x,y,z) in slot s (1..6) if inside the grid
@@ -55,38 +59,58 @@ __global__ void __launch_bounds__(256) k_extract_pressure(long long n, const T* 
   }
 }
 
+// Eight lanes per coarse cell, one per child (dx, dy, dz) = bits of the lane
+// index within its group; groups are warp-aligned and every lane of a warp
+// takes part in every round, so the shuffles see full warps.  The child sums
+// use a fixed xor tree (deterministic).
+__device__ __forceinline__ double grp8_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
 // Galerkin coarse operator with piecewise-constant aggregation
 template <typename T>
 __global__ void __launch_bounds__(256) k_galerkin(Dims f, Dims c, const T* __restrict__ Af, T* __restrict__ Ac,
                                                   T* __restrict__ dinv_c) {
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
-  GSTRIDE(I, c.n) {
-    int cx, cy, cz;
-    coords(c, I, cx, cy, cz);
+  const long long total = 8 * c.n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const long long t = base + threadIdx.x;
+    const long long I = t >> 3;
+    const int child = (int)(t & 7);
+    const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
     double acc[SL_COUNT];
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) acc[s] = 0.0;
-    for (int dz = 0; dz < fz; ++dz)
-      for (int dy = 0; dy < fy; ++dy)
-        for (int dx = 0; dx < fx; ++dx) {
-          const int x = cx * fx + dx, y = cy * fy + dy, z = cz * fz + dz;
-          if (x >= f.nx || y >= f.ny || z >= f.nz) continue;
-          const long long i = x + f.nx * (y + (long long)f.ny * z);
-          acc[SL_D] += (double)Af[i];
+    if (t < total && dx < fx && dy < fy && dz < fz) {
+      int cx, cy, cz;
+      coords(c, I, cx, cy, cz);
+      const int x = cx * fx + dx, y = cy * fy + dy, z = cz * fz + dz;
+      if (x < f.nx && y < f.ny && z < f.nz) {
+        const long long i = x + f.nx * (y + (long long)f.ny * z);
+        acc[SL_D] = (double)Af[i];
 #pragma unroll
-          for (int s = 1; s < SL_COUNT; ++s) {
-            const double a = (double)Af[(size_t)s * f.n + i];
-            long long j;
-            if (!nbr(f, x, y, z, s, j)) continue;
-            int jx, jy, jz;
-            coords(f, j, jx, jy, jz);
-            if (jx / fx == cx && jy / fy == cy && jz / fz == cz) acc[SL_D] += a;
-            else acc[s] += a;
-          }
+        for (int s = 1; s < SL_COUNT; ++s) {
+          long long j;
+          if (!nbr(f, x, y, z, s, j)) continue;
+          const double a = (double)Af[(size_t)s * f.n + i];
+          int jx, jy, jz;
+          coords(f, j, jx, jy, jz);
+          if (jx / fx == cx && jy / fy == cy && jz / fz == cz) acc[SL_D] += a;
+          else acc[s] += a;
         }
+      }
+    }
 #pragma unroll
-    for (int s = 0; s < SL_COUNT; ++s) Ac[(size_t)s * c.n + I] = (T)acc[s];
-    dinv_c[I] = (T)(1.0 / acc[SL_D]);
+    for (int s = 0; s < SL_COUNT; ++s) acc[s] = grp8_sum(acc[s]);
+    if (t < total && child == 0) {
+#pragma unroll
+      for (int s = 0; s < SL_COUNT; ++s) Ac[(size_t)s * c.n + I] = (T)acc[s];
+      dinv_c[I] = (T)(1.0 / acc[SL_D]);
+    }
   }
 }
 
@@ -117,25 +141,31 @@ __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const
                                                            const T* __restrict__ b, const T* __restrict__ x,
                                                            T* __restrict__ bc) {
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
-  GSTRIDE(I, c.n) {
-    int cx, cy, cz;
-    coords(c, I, cx, cy, cz);
-    T acc = 0;
-    for (int dz = 0; dz < fz; ++dz)
-      for (int dy = 0; dy < fy; ++dy)
-        for (int dx = 0; dx < fx; ++dx) {
-          const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
-          if (X >= f.nx || Y >= f.ny || Z >= f.nz) continue;
-          const long long i = X + f.nx * (Y + (long long)f.ny * Z);
-          T r = b[i] - A[i] * x[i];
+  const long long total = 8 * c.n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const long long t = base + threadIdx.x;
+    const long long I = t >> 3;
+    const int child = (int)(t & 7);
+    const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
+    double r = 0.0;
+    if (t < total && dx < fx && dy < fy && dz < fz) {
+      int cx, cy, cz;
+      coords(c, I, cx, cy, cz);
+      const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
+      if (X < f.nx && Y < f.ny && Z < f.nz) {
+        const long long i = X + f.nx * (Y + (long long)f.ny * Z);
+        T ri = b[i] - A[i] * x[i];
 #pragma unroll
-          for (int sl = 1; sl < SL_COUNT; ++sl) {
-            long long j;
-            if (nbr(f, X, Y, Z, sl, j)) r -= A[(size_t)sl * f.n + i] * x[j];
-          }
-          acc += r;
+        for (int sl = 1; sl < SL_COUNT; ++sl) {
+          long long j;
+          if (nbr(f, X, Y, Z, sl, j)) ri -= A[(size_t)sl * f.n + i] * x[j];
         }
-    bc[I] = acc;
+        r = (double)ri;
+      }
+    }
+    r = grp8_sum(r);
+    if (t < total && child == 0) bc[I] = (T)r;
   }
 }
 
@@ -433,7 +463,7 @@ void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
   }
   CprLevel& C = c.lev[l + 1];
   const Dims dc = dims_of(C);
-  k_residual_restrict<T><<<grid_for(C.n, 256), 256, 0, st>>>(d, dc, A, b, x, (T*)C.b);
+  k_residual_restrict<T><<<grid_for(8 * C.n, 256), 256, 0, st>>>(d, dc, A, b, x, (T*)C.b);
   k += 1;
   for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k);
   k_prolong_add<T><<<gb, 256, 0, st>>>(d, dc, (const T*)C.x, x);
@@ -453,7 +483,8 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
   for (int l = 0; l + 1 < c.nlev; ++l) {
     CprLevel& F = c.lev[l];
     CprLevel& C = c.lev[l + 1];
-    k_galerkin<T><<<grid_for(C.n, 256), 256, 0, st>>>(dims_of(F), dims_of(C), (const T*)F.A, (T*)C.A, (T*)C.dinv);
+    k_galerkin<T><<<grid_for(8 * C.n, 256), 256, 0, st>>>(dims_of(F), dims_of(C), (const T*)F.A, (T*)C.A,
+                                                          (T*)C.dinv);
     k += 1;
   }
   CprLevel& Lc = c.lev[c.nlev - 1];
@@ -461,6 +492,90 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
   k_coarse_factor<T><<<1, kMaxCoarse, kCoarseSmem, st>>>(dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
                                                          c.coarse_status);
   k += 1;
+}
+
+// ----- FP32 CPR apply (mixed precision): every stage in FP32 -----
+
+// stage 1 in FP32: zf = D^{-1} (float) v, cells and wells
+__global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const float* __restrict__ Dinv,
+                                                    const float* __restrict__ Dwinv, const double* __restrict__ v,
+                                                    float* __restrict__ zf) {
+  GSTRIDE(i, n + nw) {
+    if (i >= n) { zf[3 * n + (i - n)] = Dwinv[i - n] * (float)v[3 * n + (i - n)]; continue; }
+    const float r0 = (float)v[3 * i], r1 = (float)v[3 * i + 1], r2 = (float)v[3 * i + 2];
+    const float* D = Dinv + i;
+    zf[3 * i] = D[0] * r0 + D[n] * r1 + D[2 * n] * r2;
+    zf[3 * i + 1] = D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2;
+    zf[3 * i + 2] = D[6 * n] * r0 + D[7 * n] * r1 + D[8 * n] * r2;
+  }
+}
+
+// stage 2 in FP32, restricted on the fly: b0 = w_o (v - J zf)_oil + w_w (v - J zf)_water
+// (only the oil and water rows of J are read)
+__global__ void __launch_bounds__(256, 4) k_stage2_f32(Grid g, const float* __restrict__ J, const float* __restrict__ zf,
+                                                    const double* __restrict__ v, float w_o, float w_w,
+                                                    float* __restrict__ b0) {
+  const long long n = g.n;
+  GSTRIDE(i, n) {
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
+    float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+    for (int s = 0; s < SL_COUNT; ++s) {
+      long long c;
+      bool has;
+      switch (s) {
+        case SL_D: c = i; has = true; break;
+        case SL_XM: c = i - 1; has = ii > 0; break;
+        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
+        case SL_YM: c = i - g.nx; has = j > 0; break;
+        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
+        case SL_ZM: c = i - g.nxy; has = k > 0; break;
+        default: c = i + g.nxy; has = k + 1 < g.nz; break;
+      }
+      if (!has) continue;
+      const float* B = J + (size_t)s * 9 * n + i;
+      const float x0 = zf[3 * c], x1 = zf[3 * c + 1], x2 = zf[3 * c + 2];
+      t0 += B[0] * x0 + B[n] * x1 + B[2 * n] * x2;
+      t1 += B[3 * n] * x0 + B[4 * n] * x1 + B[5 * n] * x2;
+    }
+    b0[i] = w_o * ((float)v[3 * i] - t0) + w_w * ((float)v[3 * i + 1] - t1);
+  }
+}
+
+// the well border's share of J zf in the oil and water rows of perforated cells
+__global__ void k_stage2_wells_f32(Wells w, long long n, const float* __restrict__ Bw, const float* __restrict__ zf,
+                                   float w_o, float w_w, float* __restrict__ b0) {
+  const int wi = blockIdx.x;
+  if (wi >= w.nw) return;
+  const float zw = zf[3 * n + wi];
+  for (int m = w.ptr[wi] + threadIdx.x; m < w.ptr[wi + 1]; m += 32) {
+    const long long c = w.cell[m];
+    b0[c] -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * zw;
+  }
+}
+
+// z = zf + Pi_p x0, written as FP64 for the Krylov basis and as an FP32 copy
+// for the mixed-precision operator (the two hold the same float values)
+__global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const float* __restrict__ zf,
+                                                 const float* __restrict__ x0, double* __restrict__ z,
+                                                 float* __restrict__ zf_out) {
+  GSTRIDE(i, n + nw) {
+    if (i >= n) {
+      const float v = zf[3 * n + (i - n)];
+      z[3 * n + (i - n)] = (double)v;
+      if (zf_out) zf_out[3 * n + (i - n)] = v;
+      continue;
+    }
+    const float p = zf[3 * i] + x0[i], sv = zf[3 * i + 1], cv = zf[3 * i + 2];
+    z[3 * i] = (double)p;
+    z[3 * i + 1] = (double)sv;
+    z[3 * i + 2] = (double)cv;
+    if (zf_out) { zf_out[3 * i] = p; zf_out[3 * i + 1] = sv; zf_out[3 * i + 2] = cv; }
+  }
 }
 
 template <typename T>
@@ -536,10 +651,28 @@ void cpr_setup(CprData& c, const Grid&, const Phys& ph, const double*, const Wel
 
 void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw, const void* Cw,
                const void* Dw, const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp,
-               cudaStream_t st, int* launches) {
+               float* zf_out, cudaStream_t st, int* launches) {
   int k = 0;
-  if (mixed) apply_t<float>(c, g, w, J, Bw, Cw, Dw, Dinv, Dwinv, v, z, tmp, st, k);
-  else apply_t<double>(c, g, w, J, Bw, Cw, Dw, Dinv, Dwinv, v, z, tmp, st, k);
+  if (mixed) {
+    // every stage in FP32; tmp serves as the FP32 stage-1 vector
+    float* zf = reinterpret_cast<float*>(tmp);
+    CprLevel& L0 = c.lev[0];
+    const int gb = grid_for(g.n + w.nw, 256);
+    k_stage1_f32<<<gb, 256, 0, st>>>(g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
+    k_stage2_f32<<<grid_for(g.n, 256), 256, 0, st>>>(g, (const float*)J, zf, v, (float)c.w_o, (float)c.w_w,
+                                                     (float*)L0.b);
+    k += 2;
+    if (w.nw > 0) {
+      k_stage2_wells_f32<<<w.nw, 32, 0, st>>>(w, g.n, (const float*)Bw, zf, (float)c.w_o, (float)c.w_w,
+                                              (float*)L0.b);
+      k += 1;
+    }
+    cycle<float>(c, 0, true, st, k);
+    k_out_f32<<<gb, 256, 0, st>>>(g.n, w.nw, zf, (const float*)L0.x, z, zf_out);
+    k += 1;
+  } else {
+    apply_t<double>(c, g, w, J, Bw, Cw, Dw, Dinv, Dwinv, v, z, tmp, st, k);
+  }
   *launches = k;
 }
 

@@ -114,22 +114,28 @@ void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv
 
 // Vector kernels over n FP64 entries.
 void launch_copy(long long n, const double* a, double* b, cudaStream_t st);
+void launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
 void launch_fill(long long n, double v, double* a, cudaStream_t st);
 void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b,
                          cudaStream_t st);  // b = a * s[0] or a / sqrt(s[0])
 void launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t st);
 void launch_xpay(long long n, const double* x, double beta, double* y, cudaStream_t st); // y = x + beta y
 void launch_sub(long long n, const double* a, const double* b, double* c, cudaStream_t st); // c = a - b
-// out[j] = sum_i V[j*ld + i] w[i], j < k.  Per-block rows go to `partial`;
-// the last block reduces them in a fixed order (deterministic) and re-arms
-// `counter` (a zeroed device word shared by all reductions of one stream).
+// out[j] = sum_i V[j*ld + i] w[i], j < k (and out[k] = <w, w> with
+// self_dot).  Per-block rows (stride 72) go to `partial`; the last block
+// reduces them in a fixed order (deterministic) and re-arms `counter` (a
+// zeroed device word shared by the reductions of one stream).  run_if (may
+// be null): skip the whole kernel unless *run_if.
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w,
-                     double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st);
-// w -= sum_j V[j] h[j]; then out[j] = sum_i V[j][i] w_new[i] (j<k) and out[k] = |w_new|^2
-// (inv_norm: also out[k+1] = 1 / sqrt(out[k]))
-void launch_multi_axpy_dot(long long n, int k, const double* V, long long ld, const double* h,
-                           double* w, double* partial, int nblocks, double* out, unsigned int* counter,
-                           cudaStream_t st, int inv_norm = 0);
+                     double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st,
+                     int self_dot = 0, const int* run_if = nullptr);
+// w -= sum_j V[j] h[j]; out[0] = |w|^2, out[1] = 1/|w|; *decide = 1 if
+// |w|^2 < norm0[0] / 2 (a second Gram-Schmidt pass is needed)
+void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w,
+                      double* partial, int nblocks, double* out, unsigned int* counter, const double* norm0,
+                      int* decide, const int* run_if, cudaStream_t st);
+void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
+                     const float* Dw, const float* x, double* y, cudaStream_t st);
 // x += sum_j Z[j] y[j]
 void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y,
                            double* x, cudaStream_t st);

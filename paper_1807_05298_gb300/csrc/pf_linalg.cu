@@ -24,10 +24,11 @@ __global__ void __launch_bounds__(256) k_spmv_cells(Grid g, const DT* __restrict
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long k = i / g.nxy;
-    const long long rem = i - k * g.nxy;
-    const long long j = rem / g.nx;
-    const long long ii = rem - j * g.nx;
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
@@ -74,6 +75,70 @@ __global__ void k_spmv_wells(Grid g, Wells w, const DT* __restrict__ Bw, const D
   if (threadIdx.x == 0) y[3 * n + wi] = acc + (double)Dw[wi] * xw;
 }
 
+// Mixed-precision operator: FP32 Jacobian times an FP32 copy of the vector,
+// accumulated in FP32 per row, written as FP64 (no FP64 arithmetic).
+__global__ void __launch_bounds__(256) k_spmv_cells_f32(Grid g, const float* __restrict__ J, const float* __restrict__ x,
+                                                        double* __restrict__ y) {
+  const long long n = g.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < SL_COUNT; ++s) {
+      long long c;
+      bool has;
+      switch (s) {
+        case SL_D: c = i; has = true; break;
+        case SL_XM: c = i - 1; has = ii > 0; break;
+        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
+        case SL_YM: c = i - g.nx; has = j > 0; break;
+        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
+        case SL_ZM: c = i - g.nxy; has = k > 0; break;
+        default: c = i + g.nxy; has = k + 1 < g.nz; break;
+      }
+      if (!has) continue;
+      const float* B = J + (size_t)s * 9 * n + i;
+      const float x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+      acc0 += B[0] * x0 + B[n] * x1 + B[2 * n] * x2;
+      acc1 += B[3 * n] * x0 + B[4 * n] * x1 + B[5 * n] * x2;
+      acc2 += B[6 * n] * x0 + B[7 * n] * x1 + B[8 * n] * x2;
+    }
+    y[3 * i] = (double)acc0;
+    y[3 * i + 1] = (double)acc1;
+    y[3 * i + 2] = (double)acc2;
+  }
+}
+
+__global__ void k_spmv_wells_f32(Grid g, Wells w, const float* __restrict__ Bw, const float* __restrict__ Cw,
+                                 const float* __restrict__ Dw, const float* __restrict__ x, double* __restrict__ y) {
+  const int wi = blockIdx.x;
+  if (wi >= w.nw) return;
+  const long long n = g.n, npf = w.npf;
+  const float xw = x[3 * n + wi];
+  float acc = 0.f;
+  for (int m = w.ptr[wi] + threadIdx.x; m < w.ptr[wi + 1]; m += 32) {
+    const long long c = w.cell[m];
+    y[3 * c] += (double)(Bw[m] * xw);
+    y[3 * c + 1] += (double)(Bw[npf + m] * xw);
+    y[3 * c + 2] += (double)(Bw[2 * npf + m] * xw);
+    acc += Cw[m] * x[3 * c] + Cw[npf + m] * x[3 * c + 1] + Cw[2 * npf + m] * x[3 * c + 2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) y[3 * n + wi] = (double)(acc + Dw[wi] * xw);
+}
+
+void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
+                     const float* Dw, const float* x, double* y, cudaStream_t st) {
+  k_spmv_cells_f32<<<grid_for(g.n, 256), 256, 0, st>>>(g, J, x, y);
+  if (w.nw > 0) k_spmv_wells_f32<<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
+}
+
 template <typename DT>
 void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const DT* Cw, const DT* Dw,
                  const double* x, double* y, cudaStream_t st) {
@@ -85,19 +150,21 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
 // block-Jacobi: inverse of each 3x3 diagonal block (adjugate / determinant)
 // ---------------------------------------------------------------------------
 
+// (the inverse is formed in the storage precision PT: FP64 for the plain
+// path, FP32 for the mixed one)
 template <typename DT, typename PT>
 __global__ void __launch_bounds__(256) k_bjacobi_setup(long long n, const DT* __restrict__ J, PT* __restrict__ Dinv) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double a[9];
+    PT a[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) a[e] = (double)J[(size_t)e * n + i];
-    const double c00 = a[4] * a[8] - a[5] * a[7];
-    const double c01 = a[5] * a[6] - a[3] * a[8];
-    const double c02 = a[3] * a[7] - a[4] * a[6];
-    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    const double id = 1.0 / det;
-    double inv[9];
+    for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
+    const PT c00 = a[4] * a[8] - a[5] * a[7];
+    const PT c01 = a[5] * a[6] - a[3] * a[8];
+    const PT c02 = a[3] * a[7] - a[4] * a[6];
+    const PT det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const PT id = (PT)1 / det;
+    PT inv[9];
     inv[0] = c00 * id;
     inv[1] = (a[2] * a[7] - a[1] * a[8]) * id;
     inv[2] = (a[1] * a[5] - a[2] * a[4]) * id;
@@ -170,6 +237,13 @@ __global__ void k_sub(long long n, const double* a, const double* b, double* c) 
   GRID_STRIDE(i, n) c[i] = a[i] - b[i];
 }
 
+__global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  GRID_STRIDE(i, n) b[i] = (float)a[i];
+}
+void launch_to_f32(long long n, const double* a, float* b, cudaStream_t st) {
+  k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
+}
+
 void launch_copy(long long n, const double* a, double* b, cudaStream_t st) {
   k_copy<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
 }
@@ -211,7 +285,8 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[KM], int k, dou
 // per value, lanes over blocks, then a shuffle tree), so the result does not
 // depend on which block came last; it then re-arms the counter.
 __device__ __forceinline__ void last_block_reduce(const double* partial, int stride, int k, double* out,
-                                                  unsigned int* counter, bool inv_norm = false) {
+                                                  unsigned int* counter, bool inv_norm = false,
+                                                  const double* norm0 = nullptr, int* decide = nullptr) {
   __shared__ bool last;
   __threadfence();  // every thread that wrote a partial publishes it before the count
   __syncthreads();
@@ -232,73 +307,118 @@ __device__ __forceinline__ void last_block_reduce(const double* partial, int str
       // out[k] = 1 / sqrt(last value): one FP64 sqrt and divide for the whole
       // vector instead of one per thread of the scaling kernel
       if (inv_norm && j == k - 1) out[k] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+      // selective reorthogonalisation: a second pass is needed only if the
+      // first removed more than half of |w|^2 (norm1^2 < norm0^2 / 2)
+      if (decide && j == k - 1) *decide = (s > 0.5 * norm0[0]) ? 1 : 0;
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-template <int KM>
-__global__ void __launch_bounds__(256) k_multidot(long long n, int k, const double* __restrict__ V, long long ld,
-                                                  const double* __restrict__ w, double* __restrict__ partial,
-                                                  double* __restrict__ out, unsigned int* counter) {
-  double acc[KM];
+// One tile of the multi-dot: NT columns of V (and <w, w> when SELF), with a
+// compile-time width so that no FP64 FMA is issued for an unused slot (on
+// this part a predicated-off FP64 instruction still costs its pipe cycles).
+template <int NT, bool SELF>
+__device__ __forceinline__ void md_tile(long long n, const double* __restrict__ V, long long ld,
+                                        const double* __restrict__ w, int j0, double* partial_row) {
+  constexpr int KM = NT + (SELF ? 1 : 0);
+  constexpr int KA = KM > 0 ? KM : 1;  // storage (NT = 0 without SELF is never called)
+  double acc[KA];
 #pragma unroll
-  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  for (int t = 0; t < KM; ++t) acc[t] = 0.0;
   GRID_STRIDE(i, n) {
     const double wi = w[i];
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] += V[(size_t)j * ld + i] * wi;
+    for (int t = 0; t < NT; ++t) acc[t] += V[(size_t)(j0 + t) * ld + i] * wi;
+    if (SELF) acc[KM - 1] += wi * wi;
   }
-  block_reduce_write<KM>(acc, k, partial + (size_t)blockIdx.x * (KM + 1));
-  last_block_reduce(partial, KM + 1, k, out, counter);
+  block_reduce_write<KA>(acc, KM, partial_row + j0);
+  __syncthreads();
 }
 
-// w -= V h; partial dots of the updated w with V (j < k) and with itself (slot k)
-template <int KM>
-__global__ void __launch_bounds__(256) k_multi_axpy_dot(long long n, int k, const double* __restrict__ V, long long ld,
-                                                        const double* __restrict__ h, double* __restrict__ w,
-                                                        double* __restrict__ partial, double* __restrict__ out,
-                                                        unsigned int* counter, int inv_norm) {
-  __shared__ double hs[KM];
-  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+template <bool SELF>
+__device__ __forceinline__ void md_dispatch(int nt, long long n, const double* V, long long ld, const double* w,
+                                            int j0, double* row) {
+  switch (nt) {
+    case 0: md_tile<0, SELF>(n, V, ld, w, j0, row); break;
+    case 1: md_tile<1, SELF>(n, V, ld, w, j0, row); break;
+    case 2: md_tile<2, SELF>(n, V, ld, w, j0, row); break;
+    case 3: md_tile<3, SELF>(n, V, ld, w, j0, row); break;
+    case 4: md_tile<4, SELF>(n, V, ld, w, j0, row); break;
+    case 5: md_tile<5, SELF>(n, V, ld, w, j0, row); break;
+    case 6: md_tile<6, SELF>(n, V, ld, w, j0, row); break;
+    case 7: md_tile<7, SELF>(n, V, ld, w, j0, row); break;
+    default: md_tile<8, SELF>(n, V, ld, w, j0, row); break;
+  }
+}
+
+// out[j] = <V_j, w> for j < k and, with self_dot, out[k] = <w, w>; columns in
+// tiles of up to 8 (few registers, high occupancy), w re-read per tile.
+// run_if (may be null): the kernel returns at once unless *run_if is set.
+__global__ void __launch_bounds__(256) k_multidot(long long n, int k, const double* __restrict__ V, long long ld,
+                                                  const double* __restrict__ w, double* __restrict__ partial,
+                                                  int stride, double* __restrict__ out, unsigned int* counter,
+                                                  int self_dot, const int* run_if) {
+  if (run_if && !*run_if) return;
+  double* row = partial + (size_t)blockIdx.x * stride;
+  int j0 = 0;
+  for (; j0 + 8 < k || (j0 + 8 == k && self_dot); j0 += 8) md_dispatch<false>(8, n, V, ld, w, j0, row);
+  const int nt = k - j0;  // 0..8 columns left
+  if (self_dot) md_dispatch<true>(nt, n, V, ld, w, j0, row);
+  else if (nt > 0) md_dispatch<false>(nt, n, V, ld, w, j0, row);
+  last_block_reduce(partial, stride, k + (self_dot ? 1 : 0), out, counter);
+}
+
+// w -= sum_{j<k} V_j h[j], then out[0] = |w|^2 and out[1] = 1 / |w|.  With
+// norm0 and decide: *decide = 1 when the update removed more than half of
+// |w|^2 (|w_new|^2 < |w_old|^2 / 2 = norm0 / 2), i.e. when a second
+// Gram-Schmidt pass is needed ("twice is enough").  run_if as in k_multidot.
+__global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const double* __restrict__ V, long long ld,
+                                                   const double* __restrict__ h, double* __restrict__ w,
+                                                   double* __restrict__ partial, int stride, double* __restrict__ out,
+                                                   unsigned int* counter, const double* norm0, int* decide,
+                                                   const int* run_if) {
+  if (run_if && !*run_if) return;
+  __shared__ double hs[128];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
-  double acc[KM + 1];
-#pragma unroll
-  for (int j = 0; j <= KM; ++j) acc[j] = 0.0;
+  double acc[1] = {0.0};
   GRID_STRIDE(i, n) {
     double wi = w[i];
     for (int j = 0; j < k; ++j) wi -= V[(size_t)j * ld + i] * hs[j];
     w[i] = wi;
-    // second read of the basis column hits L1: the same thread just loaded it
-#pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] += V[(size_t)j * ld + i] * wi;
-    acc[KM] += wi * wi;
+    acc[0] += wi * wi;
   }
-  // move the norm into slot k before the block reduction
-  double accr[KM + 1];
-#pragma unroll
-  for (int j = 0; j <= KM; ++j) accr[j] = (j < k) ? acc[j] : (j == k ? acc[KM] : 0.0);
-  block_reduce_write<KM + 1>(accr, k + 1, partial + (size_t)blockIdx.x * (KM + 1));
-  last_block_reduce(partial, KM + 1, k + 1, out, counter, inv_norm != 0);
+  block_reduce_write<1>(acc, 1, partial + (size_t)blockIdx.x * stride);
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double sum = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) sum += __ldcg(partial + (size_t)b * stride);
+    sum = wsum(sum);
+    if (threadIdx.x == 0) {
+      out[0] = sum;
+      out[1] = sum > 0.0 ? 1.0 / sqrt(sum) : 0.0;
+      if (decide) *decide = (sum < 0.5 * norm0[0]) ? 1 : 0;
+      *counter = 0u;
+    }
+  }
 }
 
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
-                     double* out, unsigned int* counter, cudaStream_t st) {
-  if (k <= 8) k_multidot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
-  else if (k <= 16) k_multidot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
-  else if (k <= 32) k_multidot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
-  else k_multidot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, out, counter);
+                     double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if) {
+  k_multidot<<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if);
 }
 
-void launch_multi_axpy_dot(long long n, int k, const double* V, long long ld, const double* h, double* w,
-                           double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st,
-                           int inv_norm) {
-  if (k <= 8) k_multi_axpy_dot<8><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
-  else if (k <= 16) k_multi_axpy_dot<16><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
-  else if (k <= 32) k_multi_axpy_dot<32><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
-  else k_multi_axpy_dot<64><<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, out, counter, inv_norm);
+void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w, double* partial,
+                      int nblocks, double* out, unsigned int* counter, const double* norm0, int* decide,
+                      const int* run_if, cudaStream_t st) {
+  k_axpy_norm<<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
@@ -320,7 +440,7 @@ void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, co
 
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
                 unsigned int* counter, cudaStream_t st) {
-  k_multidot<8><<<nblocks, 256, 0, st>>>(n, 1, a, 0, b, partial, out, counter);
+  k_multidot<<<nblocks, 256, 0, st>>>(n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr);
 }
 
 // explicit instantiations
