@@ -117,6 +117,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per SpMV launch from
+# the ncu captures summarised in profiles/ (None where no capture of the
+# current kernel exists); the 27M-cell figure is the 2M-cell capture scaled by
+# the number of 3x3 blocks.
+SPMV_TRAFFIC = {("c2", "fp64"): 51.35e6, ("c3s", "mixed"): 570.6e6,
+                ("c3", "mixed"): 570.6e6 * 188250000 / 14008500}
+
+
 def spmv_algorithmic(sc, nwell_perf):
     """Bytes and FP64 flops of one SpMV launch (structured 3x3 blocks)."""
     nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
@@ -257,7 +265,8 @@ def run_ours(args, rank, world, dist):
         if t_alu > t_hbm:
             roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "alu", "achieved": round(tfl, 4),
                     "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s (FP64)",
-                    "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4), "traffic": None,
+                    "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4),
+                    "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
                     "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 4 FP64 FMA/clk), measured 1.20",
                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
                     "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
@@ -265,7 +274,8 @@ def run_ours(args, rank, world, dist):
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
         else:
             roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "hbm", "achieved": round(gbs, 1),
-                    "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                    "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
                     "peak_kind": hbm_kind, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
     kernel_ms = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()}
