@@ -125,6 +125,23 @@ SPMV_TRAFFIC = {("c2", "fp64"): 51.35e6, ("c3s", "mixed"): 570.6e6,
                 ("c3", "mixed"): 570.6e6 * 188250000 / 14008500}
 
 
+def max_over_ranks(values, dist, device="cpu"):
+    """Element-wise maximum of per-rank timings (the slowest rank defines the
+    job's time); identity without a process group."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_throughput(world, cells, iters, seconds):
+    """Whole-job cells x Newton iterations per second for ``world`` replicas
+    that each ran ``iters`` iterations on ``cells`` cells in ``seconds``
+    (max over ranks)."""
+    return world * cells * iters / seconds
+
+
 def spmv_algorithmic(sc, nwell_perf):
     """Bytes and FP64 flops of one SpMV launch (structured 3x3 blocks)."""
     nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
@@ -145,7 +162,8 @@ def run_ours(args, rank, world, dist):
     pc = B.PF_PC_CPR if args.precond == "cpr" else B.PF_PC_BJACOBI
     stream = torch.cuda.Stream()
     opts = dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
-                gmres_max_iter=300)
+                gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
+                amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle)
     with torch.cuda.stream(stream):
         sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
     n = sim.n
@@ -237,13 +255,9 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
 
-    t_dev = dev_ms / 1000.0
-    times = torch.tensor([t_dev, e2e_wall, wall], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    t_dev, e2e_wall, wall = [float(v) for v in times.cpu()]
-    value = world * n * args.steps / t_dev
-    e2e_value = world * n * e2e_steps / e2e_wall
+    t_dev, e2e_wall, wall = max_over_ranks([dev_ms / 1000.0, e2e_wall, wall], dist, device="cuda")
+    value = replica_throughput(world, n, args.steps, t_dev)
+    e2e_value = replica_throughput(world, n, e2e_steps, e2e_wall)
 
     # roofline of the SpMV (the Krylov operator; the metric names SpMV GB/s)
     blocks, ncell, faces = spmv_algorithmic(sc, sim.npf)
@@ -296,6 +310,7 @@ def run_ours(args, rank, world, dist):
             "dtype": "f64" if prec == B.PF_PREC_FP64 else "f64-residual/f32-jacobian",
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
+                       "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle],
                        "precond": args.precond, "gmres_restart": 30, "forcing_term": "eq. (fterm) third form",
                        "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
                        "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
@@ -423,7 +438,8 @@ def run_batch(args):
     from paper_1807_05298_gb300 import binding as B
     torch.cuda.set_device(0)
     prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
-    opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol)
+    opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
+               autotune=args.autotune)
     members = [G.scenario_member(i) for i in range(args.members)]
     cells = [sc["nx"] * sc["ny"] * sc["nz"] for sc in members]
     out = {}
@@ -460,7 +476,8 @@ def run_serve(args):
     from scenarios.generate import uniform01
     torch.cuda.set_device(0)
     prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
-    opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol)
+    opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
+               autotune=args.autotune)
     u = uniform01(5, 9, 2 * args.requests)
     reqs = []
     for r in range(args.requests):
@@ -522,6 +539,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--autotune", type=int, default=1, help="tune the per-cell kernels' block sizes at set-up")
+    ap.add_argument("--amg-pre", type=int, default=2)
+    ap.add_argument("--amg-post", type=int, default=2)
+    ap.add_argument("--amg-cycle", type=int, default=1)
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=48)

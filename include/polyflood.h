@@ -120,15 +120,16 @@ typedef struct pf_solver_opts {
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
   double dc_frac;       /* per-iteration concentration change limit as a fraction of c_ref (default 0.5) */
-  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 1, 1) */
+  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 2, 2) */
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
+  int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
   int ctrl;             /* PF_CTRL_* */
   double target;        /* Pa for BHP, else m^3/s at reference conditions */
-  double limit;         /* BHP limit [Pa] or 0 for none (not enforced inside a step) */
+  double limit;         /* BHP limit [Pa] or 0 for none (see pf_step: applied by switching) */
   double c_inj;         /* injected polymer concentration [kg/m^3] */
 } pf_well_control;
 
@@ -241,6 +242,17 @@ enum { PF_KT_SPMV = 0, PF_KT_PROPS, PF_KT_FACE, PF_KT_GATHER, PF_KT_WELLS, PF_KT
        PF_KT_COUNT };
 pf_status pf_kernel_timing_enable(pf_sim* s, int on);
 pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* total_ms);
+/* Launch-shape tuner (not in the paper: a GB300 launch detail).  Times block
+ * sizes 64, 128 and 256 for the per-cell kernels (properties, face flux,
+ * gather, SpMV, FP32 stage 2, finest-level smoother) on s's own data and keeps
+ * the fastest.  Each cell's arithmetic does not depend on the block size, so
+ * results are bit-identical whatever is chosen; reduction grids are never
+ * tuned for the same reason.  Overwrites scratch (call between Newton
+ * iterations, not inside one); out may be NULL. */
+typedef struct pf_tuning {
+  int props, face, gather, spmv, stage2, rbgs;
+} pf_tuning;
+pf_status pf_autotune(pf_sim* s, pf_tuning* out);
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);
 

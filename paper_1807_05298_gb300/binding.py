@@ -62,7 +62,11 @@ class pf_solver_opts(C.Structure):
                 ("lin_rtol", C.c_double), ("newton_tol", C.c_double), ("ds_max", C.c_double),
                 ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
-                ("amg_cycle", C.c_int)]
+                ("amg_cycle", C.c_int), ("autotune", C.c_int)]
+
+
+class pf_tuning(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("props", "face", "gather", "spmv", "stage2", "rbgs")]
 
 
 class pf_well_control(C.Structure):
@@ -138,6 +142,7 @@ def lib():
             "pf_set_x": ([vp, _dp], C.c_int),
             "pf_kernel_timing_enable": ([vp, C.c_int], C.c_int),
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
+            "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_run_schedule": ([vp, C.POINTER(pf_schedule), C.c_int, C.POINTER(pf_run_report)], C.c_int),
             "pf_runtime_last_error": ([], C.c_char_p),
             "pf_footprint": ([C.POINTER(pf_model_desc), C.POINTER(pf_solver_opts), C.POINTER(C.c_size_t)],
@@ -342,6 +347,11 @@ class Simulator:
 
     def abort_step(self):
         _check(lib().pf_abort_step(self.h))
+
+    def autotune(self):
+        t = pf_tuning()
+        _check(lib().pf_autotune(self.h, C.byref(t)))
+        return {n: getattr(t, n) for n, _ in pf_tuning._fields_}
 
     def kernel_timing_enable(self, on=True):
         _check(lib().pf_kernel_timing_enable(self.h, 1 if on else 0))

@@ -80,6 +80,7 @@ struct pf_sim {
   unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
   double* h_pinned = nullptr;
   CprData cpr;
+  Tuning tune;  // block sizes of the per-cell kernels
   // opt-in CUDA-event timing of selected kernels
   bool kt_on = false;
   std::vector<cudaEvent_t> kt_pool;
@@ -333,15 +334,17 @@ pf_status assemble_t(pf_sim* s) {
   cudaStream_t st = s->stream;
   {
     KtScope t(s, PF_KT_PROPS);
-    launch_cell_props<DT>(s->g, s->ph, s->phi_r, s->x, s->pv, (DT*)s->pd, s->Mold, s->R, (DT*)s->J, nullptr, 0, st);
+    launch_cell_props<DT>(s->g, s->ph, s->phi_r, s->x, s->pv, (DT*)s->pd, s->Mold, s->R, (DT*)s->J, nullptr, 0, st,
+                          s->tune.props);
   }
   {
     KtScope t(s, PF_KT_FACE);
-    launch_face_flux<DT>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv, (const DT*)s->pd, s->dt, (DT*)s->J, s->Fbuf, st);
+    launch_face_flux<DT>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv, (const DT*)s->pd, s->dt, (DT*)s->J, s->Fbuf, st,
+                         s->tune.face);
   }
   {
     KtScope t(s, PF_KT_GATHER);
-    launch_gather<DT>(s->g, s->Fbuf, s->dt, s->R, (DT*)s->J, st);
+    launch_gather<DT>(s->g, s->Fbuf, s->dt, s->R, (DT*)s->J, st, s->tune.gather);
   }
   {
     KtScope t(s, PF_KT_WELLS);
@@ -364,10 +367,10 @@ pf_status spmv(pf_sim* s, const double* xin, double* y) {
   KtScope t(s, PF_KT_SPMV);
   if (s->mixed)
     launch_spmv<float>(s->g, w, (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw, (const float*)s->Dw, xin,
-                       y, s->stream);
+                       y, s->stream, s->tune.spmv);
   else
     launch_spmv<double>(s->g, w, (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
-                        (const double*)s->Dw, xin, y, s->stream);
+                        (const double*)s->Dw, xin, y, s->stream, s->tune.spmv);
   PF_LAUNCHED(1 + (s->nw > 0));
   return PF_OK;
 }
@@ -437,7 +440,8 @@ pf_status piece_spmv(pf_sim* s, int j) {
   // mixed precision: FP32 operator on the FP32 copy of z_j
   KtScope t(s, PF_KT_SPMV);
   launch_spmv_f32(s->g, wells_view(s), (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw,
-                  (const float*)s->Dw, s->Zf + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld, s->stream);
+                  (const float*)s->Dw, s->Zf + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld, s->stream,
+                  s->tune.spmv);
   PF_LAUNCHED(1 + (s->nw > 0));
   return PF_OK;
 }
@@ -654,10 +658,11 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->newton_tol = 1e-10;
   o->ds_max = 0.2;
   o->dc_frac = 0.5;
-  o->amg_pre_sweeps = 1;
-  o->amg_post_sweeps = 1;
+  o->amg_pre_sweeps = 2;
+  o->amg_post_sweeps = 2;
   o->amg_coarse_size = 8;
   o->amg_cycle = 1;
+  o->autotune = 0;
   return PF_OK;
 }
 
@@ -811,6 +816,14 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
     if (r2 != PF_OK) { pf_destroy(s); return fail(r2, "CPR set-up failed"); }
   }
   PF_CUDA(cudaStreamSynchronize(st));
+  if (s->opts.autotune) {
+    pf_status r3 = pf_autotune(s, nullptr);
+    if (r3 != PF_OK) {
+      std::string msg = pf_last_error();
+      pf_destroy(s);
+      return fail(r3, "launch-shape tuning failed: " + msg);
+    }
+  }
   *out = s;
   return PF_OK;
 }
@@ -1301,6 +1314,95 @@ pf_status pf_sizes(const pf_sim* s, int64_t* n_cells, int* n_wells, int64_t* n_p
 pf_status pf_device_state(pf_sim* s, double** x_dev) {
   if (!s || !x_dev) return fail(PF_EINVAL, "NULL argument");
   *x_dev = s->x;
+  return PF_OK;
+}
+
+}  // extern "C"
+
+// Mean time of `reps` launches issued by fn on the sim's stream (after one warm-up).
+template <typename F>
+static float time_launch(pf_sim* s, F fn, int reps) {
+  fn();
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, s->stream);
+  for (int r = 0; r < reps; ++r) fn();
+  cudaEventRecord(b, s->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+template <typename F>
+static int pick_block(pf_sim* s, F fn_of_block) {
+  static const int cand[3] = {64, 128, 256};
+  int best = 256;
+  float tbest = 1e30f;
+  for (int c : cand) {
+    const float t = time_launch(s, [&] { fn_of_block(c); }, 3);
+    if (t < tbest) { tbest = t; best = c; }
+  }
+  return best;
+}
+
+extern "C" {
+
+pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  cudaStream_t st = s->stream;
+  Tuning t;
+  const double dt = s->dt > 0.0 ? s->dt : 86400.0;
+  // the kernels run on the current buffers; what they write is scratch for
+  // the next assembly (residual, Jacobian, property scratch, multigrid vectors)
+  if (s->mixed) {
+    t.props = pick_block(s, [&](int b) { launch_cell_props<float>(s->g, s->ph, s->phi_r, s->x, s->pv, (float*)s->pd,
+                                                                 s->Mold, s->R, (float*)s->J, nullptr, 0, st, b); });
+    t.face = pick_block(s, [&](int b) { launch_face_flux<float>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv,
+                                                               (const float*)s->pd, dt, (float*)s->J, s->Fbuf, st, b); });
+    t.gather = pick_block(s, [&](int b) { launch_gather<float>(s->g, s->Fbuf, dt, s->R, (float*)s->J, st, b); });
+    t.spmv = pick_block(s, [&](int b) {
+      launch_spmv_f32(s->g, wells_view(s), (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw,
+                      (const float*)s->Dw, s->Zf, s->r, st, b);
+    });
+    if (s->opts.precond == PF_PC_CPR)
+      t.stage2 = pick_block(s, [&](int b) { cpr_time_stage2(s->cpr, s->g, s->J, s->x, s->tmp, b, st); });
+  } else {
+    t.props = pick_block(s, [&](int b) { launch_cell_props<double>(s->g, s->ph, s->phi_r, s->x, s->pv,
+                                                                  (double*)s->pd, s->Mold, s->R, (double*)s->J,
+                                                                  nullptr, 0, st, b); });
+    t.face = pick_block(s, [&](int b) { launch_face_flux<double>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv,
+                                                                (const double*)s->pd, dt, (double*)s->J, s->Fbuf, st,
+                                                                b); });
+    t.gather = pick_block(s, [&](int b) { launch_gather<double>(s->g, s->Fbuf, dt, s->R, (double*)s->J, st, b); });
+    t.spmv = pick_block(s, [&](int b) {
+      launch_spmv<double>(s->g, wells_view(s), (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
+                          (const double*)s->Dw, s->b, s->r, st, b);
+    });
+  }
+  if (s->opts.precond == PF_PC_CPR)
+    t.rbgs = pick_block(s, [&](int b) { cpr_time_rbgs0(s->cpr, s->mixed, b, st); });
+  PF_CUDA(cudaGetLastError());
+  PF_CUDA(cudaStreamSynchronize(st));
+  s->tune = t;
+  s->cpr.block_rbgs0 = t.rbgs;
+  s->cpr.block_stage2 = t.stage2;
+  // captured graphs hold the old launch shapes
+  for (auto& G : s->graphs) {
+    if (G.pre) cudaGraphExecDestroy(G.pre);
+    if (G.spmv) cudaGraphExecDestroy(G.spmv);
+    if (G.ortho) cudaGraphExecDestroy(G.ortho);
+  }
+  s->graphs.clear();
+  s->assembled = false;
+  if (out) {
+    out->props = t.props; out->face = t.face; out->gather = t.gather;
+    out->spmv = t.spmv; out->stage2 = t.stage2; out->rbgs = t.rbgs;
+  }
   return PF_OK;
 }
 

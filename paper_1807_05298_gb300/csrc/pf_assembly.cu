@@ -67,10 +67,11 @@ __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P
   c.rho_w = ph.rho_w * (1.0 + ph.c_w * (c.Pw - ph.p_ref));
   c.drho_wP = ph.rho_w * ph.c_w;
   c.drho_wS = ph.rho_w * ph.c_w * c.dPw_S;
-  // Langmuir adsorption and permeability reduction
-  const double den = 1.0 + ph.ads_b * C;
-  c.ads = ph.ads_a * C / den;
-  c.dads = ph.ads_a / (den * den);
+  // Langmuir adsorption and permeability reduction (one reciprocal: FP64
+  // division is costly on this part)
+  const double rden = 1.0 / (1.0 + ph.ads_b * C);
+  c.ads = ph.ads_a * C * rden;
+  c.dads = ph.ads_a * rden * rden;
   c.Rk = 1.0 + ph.rk_coef * c.ads;
   c.dRk = ph.rk_coef * c.dads;
   // mixing rule
@@ -87,18 +88,23 @@ __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P
   double alpha = beta, dalpha = ph.inv_c_ref;
   if (alpha < 0.0) { alpha = 0.0; dalpha = 0.0; }
   if (alpha > 1.0) { alpha = 1.0; dalpha = 0.0; }
-  double mu_pe, dmu_pe, mu_wp, dmu_wp;
+  // 1/mu_w,e = alpha/mu_p,e + (1-alpha)/mu_w,partial, with one reciprocal per
+  // viscosity (both are mu_m when omega = 1)
+  double mu_pe, dmu_pe, mu_wp, dmu_wp, rpe, rwp;
   if (ph.omega == 1.0) {
     mu_pe = mu_m; dmu_pe = dmu_m; mu_wp = mu_m; dmu_wp = dmu_m;
+    rpe = 1.0 / mu_m;
+    rwp = rpe;
   } else {
     const double mo = pow(mu_m, ph.omega);
     const double dmo = ph.omega * mo / mu_m * dmu_m;
     mu_pe = mo * ph.mu_p0_pow; dmu_pe = dmo * ph.mu_p0_pow;
     mu_wp = mo * ph.mu_w_pow; dmu_wp = dmo * ph.mu_w_pow;
+    rpe = 1.0 / mu_pe;
+    rwp = 1.0 / mu_wp;
   }
-  const double inv = alpha / mu_pe + (1.0 - alpha) / mu_wp;
-  const double dinv = dalpha / mu_pe - alpha * dmu_pe / (mu_pe * mu_pe) - dalpha / mu_wp -
-                      (1.0 - alpha) * dmu_wp / (mu_wp * mu_wp);
+  const double inv = alpha * rpe + (1.0 - alpha) * rwp;
+  const double dinv = dalpha * rpe - alpha * dmu_pe * rpe * rpe - dalpha * rwp - (1.0 - alpha) * dmu_wp * rwp * rwp;
   c.mu_we = 1.0 / inv;
   c.dmu_we = -dinv * c.mu_we * c.mu_we;
   c.mu_pe = mu_pe;
@@ -190,8 +196,8 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
 template <typename DT>
 void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x, double* pv,
                        DT* pd, const double* Mold, double* R, DT* J, double* Mold_out, int mode,
-                       cudaStream_t st) {
-  k_cell_props<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
+                       cudaStream_t st, int block) {
+  k_cell_props<DT><<<grid_for(g.n, block), block, 0, st>>>(g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,8 +377,8 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
 
 template <typename DT>
 void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3, const double* x,
-                      const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st) {
-  k_face_flux<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
+                      const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st, int block) {
+  k_face_flux<DT><<<grid_for(g.n, block), block, 0, st>>>(g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,8 +431,8 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
 }
 
 template <typename DT>
-void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st) {
-  k_gather<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, Fbuf, dt, R, J);
+void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st, int block) {
+  k_gather<DT><<<grid_for(g.n, block), block, 0, st>>>(g, Fbuf, dt, R, J);
 }
 
 // ---------------------------------------------------------------------------
@@ -715,15 +721,15 @@ void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, do
 
 // explicit instantiations
 template void launch_cell_props<double>(const Grid&, const Phys&, const double*, const double*, double*, double*,
-                                        const double*, double*, double*, double*, int, cudaStream_t);
+                                        const double*, double*, double*, double*, int, cudaStream_t, int);
 template void launch_cell_props<float>(const Grid&, const Phys&, const double*, const double*, double*, float*,
-                                       const double*, double*, float*, double*, int, cudaStream_t);
+                                       const double*, double*, float*, double*, int, cudaStream_t, int);
 template void launch_face_flux<double>(const Grid&, const Phys&, const double*, const double*, const double*,
-                                       const double*, const double*, double, double*, double*, cudaStream_t);
+                                       const double*, const double*, double, double*, double*, cudaStream_t, int);
 template void launch_face_flux<float>(const Grid&, const Phys&, const double*, const double*, const double*,
-                                      const double*, const float*, double, float*, double*, cudaStream_t);
-template void launch_gather<double>(const Grid&, const double*, double, double*, double*, cudaStream_t);
-template void launch_gather<float>(const Grid&, const double*, double, double*, float*, cudaStream_t);
+                                      const double*, const float*, double, float*, double*, cudaStream_t, int);
+template void launch_gather<double>(const Grid&, const double*, double, double*, double*, cudaStream_t, int);
+template void launch_gather<float>(const Grid&, const double*, double, double*, float*, cudaStream_t, int);
 template void launch_wells<double>(const Grid&, const Phys&, const Wells&, const double*, const double*,
                                    const double*, double, double*, double*, double*, double*, double*, cudaStream_t);
 template void launch_wells<float>(const Grid&, const Phys&, const Wells&, const double*, const double*,

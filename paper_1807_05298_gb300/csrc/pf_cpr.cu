@@ -115,10 +115,16 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims f, Dims c, const T* __res
 }
 
 // one colour of a red-black Gauss-Seidel sweep; zero_init: x holds no valid
-// values yet (first half-sweep), so neighbours count as zero
+// values yet (first half-sweep), so neighbours count as zero.  With xc (the
+// coarse correction of dims c): the neighbours are read as x_j + xc[agg(j)],
+// i.e. the prolongation x += P xc is applied on the fly.  A colour pass
+// overwrites every cell of its colour, so only the other colour's values
+// (the neighbours) need the correction; the next pass overwrites those.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
-                                              const T* __restrict__ b, T* __restrict__ x, int color, int zero_init) {
+                                              const T* __restrict__ b, T* __restrict__ x, int color, int zero_init,
+                                              const T* __restrict__ xc = nullptr, Dims c = Dims{}) {
+  const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
   GSTRIDE(i, d.n) {
     int cx, cy, cz;
     coords(d, i, cx, cy, cz);
@@ -128,7 +134,14 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
 #pragma unroll
       for (int sl = 1; sl < SL_COUNT; ++sl) {
         long long j;
-        if (nbr(d, cx, cy, cz, sl, j)) s -= A[(size_t)sl * d.n + i] * x[j];
+        if (!nbr(d, cx, cy, cz, sl, j)) continue;
+        T xj = x[j];
+        if (xc) {
+          int jx, jy, jz;
+          coords(d, j, jx, jy, jz);
+          xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
+        }
+        s -= A[(size_t)sl * d.n + i] * xj;
       }
     }
     x[i] = s * dinv[i];
@@ -456,9 +469,11 @@ void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
     k += 1;
     return;
   }
+  const int bs = l == 0 ? c.block_rbgs0 : 256;
+  const int gs = grid_for(L.n, bs);
   for (int sweep = 0; sweep < c.pre; ++sweep) {
-    k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0);
-    k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 1, 0);
+    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0);
+    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0);
     k += 2;
   }
   CprLevel& C = c.lev[l + 1];
@@ -466,11 +481,15 @@ void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
   k_residual_restrict<T><<<grid_for(8 * C.n, 256), 256, 0, st>>>(d, dc, A, b, x, (T*)C.b);
   k += 1;
   for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k);
-  k_prolong_add<T><<<gb, 256, 0, st>>>(d, dc, (const T*)C.x, x);
-  k += 1;
+  if (c.post == 0) {
+    k_prolong_add<T><<<gb, 256, 0, st>>>(d, dc, (const T*)C.x, x);
+    k += 1;
+  }
   for (int sweep = 0; sweep < c.post; ++sweep) {
-    k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 1, 0);
-    k_rbgs<T><<<gb, 256, 0, st>>>(d, A, dinv, b, x, 0, 0);
+    // the first black pass applies the prolongation to the red neighbours it reads
+    if (sweep == 0) k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0, (const T*)C.x, dc);
+    else k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0);
+    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 0, 0);
     k += 2;
   }
 }
@@ -597,6 +616,23 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
 
 }  // namespace
 
+void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
+  CprLevel& L = c.lev[0];
+  const Dims d = dims_of(L);
+  if (mixed)
+    k_rbgs<float><<<grid_for(L.n, block), block, 0, st>>>(d, (const float*)L.A, (const float*)L.dinv,
+                                                          (const float*)L.b, (float*)L.x, 0, 0);
+  else
+    k_rbgs<double><<<grid_for(L.n, block), block, 0, st>>>(d, (const double*)L.A, (const double*)L.dinv,
+                                                           (const double*)L.b, (double*)L.x, 0, 0);
+}
+
+void cpr_time_stage2(CprData& c, const Grid& g, const void* J, const double* v, double* tmp, int block,
+                     cudaStream_t st) {
+  k_stage2_f32<<<grid_for(g.n, block), block, 0, st>>>(g, (const float*)J, reinterpret_cast<const float*>(tmp), v,
+                                                       (float)c.w_o, (float)c.w_w, (float*)c.lev[0].b);
+}
+
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
   const size_t ts = mixed ? sizeof(float) : sizeof(double);
   const int limit = std::min(std::max(c.coarse_limit, 1), kMaxCoarse);
@@ -659,8 +695,8 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
     CprLevel& L0 = c.lev[0];
     const int gb = grid_for(g.n + w.nw, 256);
     k_stage1_f32<<<gb, 256, 0, st>>>(g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
-    k_stage2_f32<<<grid_for(g.n, 256), 256, 0, st>>>(g, (const float*)J, zf, v, (float)c.w_o, (float)c.w_w,
-                                                     (float*)L0.b);
+    k_stage2_f32<<<grid_for(g.n, c.block_stage2), c.block_stage2, 0, st>>>(g, (const float*)J, zf, v, (float)c.w_o,
+                                                                         (float)c.w_w, (float*)L0.b);
     k += 2;
     if (w.nw > 0) {
       k_stage2_wells_f32<<<w.nw, 32, 0, st>>>(w, g.n, (const float*)Bw, zf, (float)c.w_o, (float)c.w_w,

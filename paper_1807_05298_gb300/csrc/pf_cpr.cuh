@@ -34,11 +34,19 @@ struct CprData {
   bool ready = false;
   int nlev = 0;
   int pre = 1, post = 1, cycle_gamma = 1, coarse_limit = 64;
+  int block_rbgs0 = 256, block_stage2 = 256;  // launch shapes of the finest smoother and stage 2
   double w_o = 0.0, w_w = 0.0;
   std::vector<CprLevel> lev;
   void* coarse_inv = nullptr;   // [nc][nc] dense inverse of the coarsest matrix
   int* coarse_status = nullptr; // device flag: 1 if a zero pivot was met
 };
+
+// One launch of the finest-level smoother colour / of the FP32 stage 2 with a
+// given block size (used by the launch-shape tuner; the values computed are
+// scratch).
+void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st);
+void cpr_time_stage2(CprData& c, const Grid& g, const void* J, const double* v, double* tmp, int block,
+                     cudaStream_t st);
 
 // Lays out the CPR arrays in the arena (base == nullptr: sizing only).
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base);

@@ -63,6 +63,13 @@ struct Wells {
   const double* gamma;     // [nw] lagged wellbore unit weight
 };
 
+// Block sizes of the per-cell kernels (autotuned or 256).  Every cell's
+// arithmetic is independent of the launch shape, so results do not depend on
+// these values.
+struct Tuning {
+  int props = 256, face = 256, gather = 256, spmv = 256, stage2 = 256, rbgs = 256;
+};
+
 // Launch helpers ------------------------------------------------------------
 inline int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
@@ -77,14 +84,15 @@ inline int grid_for(long long n, int block) {
 template <typename DT>
 void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x,
                        double* pv, DT* pd, const double* Mold, double* R, DT* J, double* Mold_out,
-                       int mode, cudaStream_t st);
+                       int mode, cudaStream_t st, int block = 256);
 template <typename DT>
 // wL3[d * N + i]: pore-volume weight of cell i on its face towards +d
 void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3,
                       const double* x, const double* pv, const DT* pd, double dt, DT* J,
-                      double* Fbuf, cudaStream_t st);
+                      double* Fbuf, cudaStream_t st, int block = 256);
 template <typename DT>
-void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st);
+void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st,
+                   int block = 256);
 template <typename DT>
 void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                   const DT* pd, double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st);
@@ -104,7 +112,7 @@ void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, do
 // Linear algebra (pf_linalg.cu) ---------------------------------------------
 template <typename DT>
 void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const DT* Cw,
-                 const DT* Dw, const double* x, double* y, cudaStream_t st);
+                 const DT* Dw, const double* x, double* y, cudaStream_t st, int block = 256);
 template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
                           PT* Dwinv, cudaStream_t st);
@@ -135,7 +143,7 @@ void launch_axpy_norm(long long n, int k, const double* V, long long ld, const d
                       double* partial, int nblocks, double* out, unsigned int* counter, const double* norm0,
                       int* decide, const int* run_if, cudaStream_t st);
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
-                     const float* Dw, const float* x, double* y, cudaStream_t st);
+                     const float* Dw, const float* x, double* y, cudaStream_t st, int block = 256);
 // x += sum_j Z[j] y[j]
 void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y,
                            double* x, cudaStream_t st);

@@ -134,15 +134,15 @@ __global__ void k_spmv_wells_f32(Grid g, Wells w, const float* __restrict__ Bw, 
 }
 
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
-                     const float* Dw, const float* x, double* y, cudaStream_t st) {
-  k_spmv_cells_f32<<<grid_for(g.n, 256), 256, 0, st>>>(g, J, x, y);
+                     const float* Dw, const float* x, double* y, cudaStream_t st, int block) {
+  k_spmv_cells_f32<<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
   if (w.nw > 0) k_spmv_wells_f32<<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
 }
 
 template <typename DT>
 void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const DT* Cw, const DT* Dw,
-                 const double* x, double* y, cudaStream_t st) {
-  k_spmv_cells<DT><<<grid_for(g.n, 256), 256, 0, st>>>(g, J, x, y);
+                 const double* x, double* y, cudaStream_t st, int block) {
+  k_spmv_cells<DT><<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
   if (w.nw > 0) k_spmv_wells<DT><<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
 }
 
@@ -445,9 +445,9 @@ void launch_dot(long long n, const double* a, const double* b, double* partial, 
 
 // explicit instantiations
 template void launch_spmv<double>(const Grid&, const Wells&, const double*, const double*, const double*,
-                                  const double*, const double*, double*, cudaStream_t);
+                                  const double*, const double*, double*, cudaStream_t, int);
 template void launch_spmv<float>(const Grid&, const Wells&, const float*, const float*, const float*, const float*,
-                                 const double*, double*, cudaStream_t);
+                                 const double*, double*, cudaStream_t, int);
 template void launch_bjacobi_setup<double, double>(const Grid&, const Wells&, const double*, const double*, double*,
                                                    double*, cudaStream_t);
 template void launch_bjacobi_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,

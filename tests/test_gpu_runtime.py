@@ -111,3 +111,17 @@ def test_server_same_alone_and_in_mix_and_admission(B):
         srv.submit(big)
     assert e.value.status == B.PF_EBUSY
     srv.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_launch_shapes_give_identical_results(B, precision):
+    sc = G.scenario_c1(nx=17, ny=11, nz=3, n_steps=3)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+    base = alone(B, sc, 3, **opt)
+    sim = B.Simulator(sc, autotune=1, **opt)
+    t = sim.autotune()
+    assert all(v in (64, 128, 256) for v in t.values())
+    B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
+    x = sim.get_x()
+    sim.close()
+    assert np.array_equal(base, x)
