@@ -1,7 +1,8 @@
 """Benchmark of the polymer-flooding Newton step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c2|c3|c1] [--precision fp64|mixed] [--precond cpr|bjacobi]
+                    [--workload c2|c3|c3s|c1|paper] [--precision fp64|mixed]
+                    [--precond cpr|bjacobi] [--mode single|batch|serve]
 
 A step is one full Newton iteration of the fully implicit water/oil/polymer
 model (Alg. 1): property evaluation, residual and 3x3 block-Jacobian assembly
@@ -48,6 +49,10 @@ def workload(name):
     if name == "c3s":
         return (G.scenario_c3(nx=300, ny=225, nz=30),
                 "300x225x30 (2,025,000 cells) channelised recipe, 40 injectors / 80 producers (profiling size)")
+    if name == "paper":
+        return (G.scenario_layered_table4(nx=951, ny=1920, refine_z=3, dt_days=1.0),
+                "951x1920x15 (27,388,800 cells): the paper's high-resolution grid over the Table 4 layers "
+                "(each split in three), 20x20x1.33 m cells, 4 corner injectors, horizontal producer, 1-day steps")
     return G.scenario_c2(), "100x100x10 (100,000 cells) layered lognormal, 5-spot, 0.3 PV slug"
 
 
@@ -163,7 +168,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream()
     opts = dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
                 gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
-                amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle)
+                amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form)
     with torch.cuda.stream(stream):
         sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
     n = sim.n
@@ -255,6 +260,11 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
 
+    prec_check = None
+    if prec == B.PF_PREC_MIXED and args.check_fp64 and rank == 0:
+        with torch.cuda.stream(stream):
+            prec_check = precision_check(B, sim, sc, opts, dt, state["in_step"], B.current_stream_handle())
+
     t_dev, e2e_wall, wall = max_over_ranks([dev_ms / 1000.0, e2e_wall, wall], dist, device="cuda")
     value = replica_throughput(world, n, args.steps, t_dev)
     e2e_value = replica_throughput(world, n, e2e_steps, e2e_wall)
@@ -311,7 +321,7 @@ def run_ours(args, rank, world, dist):
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
                        "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle],
-                       "precond": args.precond, "gmres_restart": 30, "forcing_term": "eq. (fterm) third form",
+                       "precond": args.precond, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
                        "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
                        "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
             "krylov_iters_per_newton": round(krylov / args.steps, 2),
@@ -325,6 +335,8 @@ def run_ours(args, rank, world, dist):
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if prec_check is not None:
+            out["precision_check"] = prec_check
     sim.close()
     return out
 
@@ -337,6 +349,9 @@ def oracle_sample(args):
     if args.workload == "c3":
         sc = G.scenario_c3(nx=120, ny=90, nz=2)
         return sc, "120x90x2 sample of the channelised recipe"
+    if args.workload == "paper":
+        sc = G.scenario_layered_table4(nx=40, ny=48, refine_z=1, dz=4.0 / 3.0, dt_days=1.0)
+        return sc, "40x48x5 sample of the 951x1920x15 recipe (same cell size, one cell per layer)"
     sc = G.scenario_c2(nz=1)
     return sc, "100x100x1 slab (top layer) of the 100x100x10 recipe, injectors on their 400 bar limit"
 
@@ -396,6 +411,53 @@ def time_oracle(sc, budget_s, max_iters):
         r.iteration()
         its += 1
     return its, time.perf_counter() - t0, r.n
+
+
+def precision_check(B, sim, sc, opts, dt, in_step, stream):
+    """Error of the mixed-precision result against the FP64 path: both take
+    one time step from the same state under the same controls (switched rate
+    wells pinned on their BHP limit, no further switching), each to the same
+    Newton tolerance on the FP64 residual; reports the max-norm differences of
+    the fields relative to each field's max-norm.  The FP64 path is the one the
+    parity tests pin to the oracle at 1e-6."""
+    if in_step:
+        sim.abort_step()
+    ctl = [dict(c) for c in sc["schedule"][0]["controls"]]
+    for w, sw in enumerate(sim.switched()):
+        if sw:
+            ctl[w] = dict(ctl[w], ctrl="bhp", target=ctl[w]["limit"])
+    ctl = [dict(c, limit=None) for c in ctl]
+    x0 = sim.get_x()
+    o64 = dict(opts, precision=B.PF_PREC_FP64)
+    s64 = B.Simulator(sc, stream=stream, **o64)
+    s64.set_controls(ctl)
+    sim.set_controls(ctl)
+    res = None
+    for _ in range(4):
+        s64.set_x(x0)
+        sim.set_x(x0)
+        rc_m, rep_m = sim.step(dt, raise_on_failure=False)
+        rc_d, rep_d = s64.step(dt, raise_on_failure=False)
+        if rc_m == B.PF_OK and rc_d == B.PF_OK:
+            xm, xd = sim.get_x(), s64.get_x()
+            n = sim.n
+            err = {}
+            for name, a in (("P", 0), ("S", 1), ("C", 2)):
+                ref = max(float(np.abs(xd[a:3 * n:3]).max()), 1e-300)
+                err[name] = float(np.abs(xm[a:3 * n:3] - xd[a:3 * n:3]).max()) / ref
+            if sim.nw:
+                ref = float(np.abs(xd[3 * n:]).max())
+                err["Pb"] = float(np.abs(xm[3 * n:] - xd[3 * n:]).max()) / ref
+            res = {"vs": "FP64 GPU path (pinned to the FP64 oracle at 1e-6 by the parity tests), same start "
+                         "state and controls, one time step", "dt_days": dt / G.DAY,
+                   "max_rel_err": {k: float("%.3e" % v) for k, v in err.items()},
+                   "newton_iters": {"mixed": rep_m.newton_iters, "fp64": rep_d.newton_iters},
+                   "krylov_iters": {"mixed": rep_m.krylov_iters, "fp64": rep_d.krylov_iters},
+                   "newton_tol": opts["newton_tol"]}
+            break
+        dt *= 0.5
+    s64.close()
+    return res or {"vs": "FP64 GPU path", "error": "step did not converge in either precision"}
 
 
 def cpu_baseline(args):
@@ -531,7 +593,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c3s"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c3s", "paper"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="cpr", choices=["cpr", "bjacobi"])
     ap.add_argument("--newton-tol", type=float, default=1e-8)
@@ -543,6 +605,10 @@ def main():
     ap.add_argument("--amg-pre", type=int, default=2)
     ap.add_argument("--amg-post", type=int, default=2)
     ap.add_argument("--amg-cycle", type=int, default=1)
+    ap.add_argument("--check-fp64", type=int, default=1,
+                    help="mixed precision: state the error against the FP64 path on one step")
+    ap.add_argument("--forcing-form", type=int, default=3, choices=[1, 2, 3],
+                    help="which choice of the forcing term eq. (fterm); 3 is the paper's")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=48)

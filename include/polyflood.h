@@ -114,8 +114,8 @@ typedef struct pf_solver_opts {
   int gmres_restart;    /* Krylov basis size m (default 30) */
   int gmres_max_iter;   /* cap on Krylov iterations per linear solve (default 300) */
   int newton_max_iter;  /* cap on Newton iterations per step (default 25) */
-  int use_forcing;      /* 1: linear tolerance eta from eq. (fterm), third form;
-                           0: fixed lin_rtol */
+  int use_forcing;      /* 1: linear tolerance eta from eq. (fterm) in the form
+                           forcing_form selects; 0: fixed lin_rtol */
   double lin_rtol;      /* fixed relative linear tolerance (default 1e-12) */
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
@@ -124,6 +124,14 @@ typedef struct pf_solver_opts {
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
   int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
+  int forcing_form;     /* which choice of eq. (fterm), all restricted to [0.01, 0.1],
+                           first Newton iteration of a step 0.1 (default 3):
+                           1: |b^l - r^{l-1}| / |b^{l-1}|, r^{l-1} = b^{l-1} - J dx^{l-1}
+                              the residual the previous linear solve left (one
+                              extra device vector and one SpMV per iteration);
+                           2: (|b^l| - |r^{l-1}|) / |b^{l-1}| (one extra SpMV);
+                           3: 0.5 (|b^l| / |b^{l-1}|)^((1 + sqrt 5) / 2), the
+                              paper's choice.  b = -R; 2-norms over all unknowns. */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
@@ -245,14 +253,21 @@ pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* tota
 /* Launch-shape tuner (not in the paper: a GB300 launch detail).  Times block
  * sizes 64, 128 and 256 for the per-cell kernels (properties, face flux,
  * gather, SpMV, FP32 stage 2, finest-level smoother) on s's own data and keeps
- * the fastest.  Each cell's arithmetic does not depend on the block size, so
- * results are bit-identical whatever is chosen; reduction grids are never
- * tuned for the same reason.  Overwrites scratch (call between Newton
- * iterations, not inside one); out may be NULL. */
+ * the fastest.  The FP64 SpMV also tries one thread per block row (reported
+ * as a negative spmv: -96, -192 or -384 threads per block).  Each row's
+ * arithmetic does not depend on the launch shape, so results are
+ * bit-identical whatever is chosen; reduction grids are never tuned for the
+ * same reason.  Overwrites scratch (call between Newton iterations, not
+ * inside one); out may be NULL. */
 typedef struct pf_tuning {
   int props, face, gather, spmv, stage2, rbgs;
 } pf_tuning;
 pf_status pf_autotune(pf_sim* s, pf_tuning* out);
+/* Sets the launch shapes directly (for example a shape pf_autotune chose
+ * earlier): every block size a multiple of 32 in [32, 256]; spmv may also be
+ * -96, -192 or -384 (one thread per block row) in FP64 precision.  Results do
+ * not depend on the shapes.  PF_EINVAL for any other value. */
+pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t);
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);
 
@@ -278,8 +293,10 @@ typedef struct pf_run_report {
 } pf_run_report;
 
 /* Runs the whole schedule on s: per step pf_step, halving the step on Newton
- * failure (Sec. 3 step 4(a)) at most max_cuts times per step; the next step
- * starts from the full dt again.  rep may be NULL. */
+ * failure (Sec. 3 step 4(a)) at most max_cuts times per step; after each
+ * accepted sub-step the step doubles again, capped by the period's dt and by
+ * what is left of the step (step 4(c)-(d)); the next step starts from the full
+ * dt.  rep may be NULL. */
 pf_status pf_run_schedule(pf_sim* s, const pf_schedule* sched, int max_cuts, pf_run_report* rep);
 /* Message of the last failed runtime call (pf_run_schedule, pf_batch_*, pf_server_*) on this thread. */
 const char* pf_runtime_last_error(void);

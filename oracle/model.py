@@ -153,27 +153,62 @@ def _clip01_dual(x):
     return D.where(x.v > 1.0, 1.0, x)
 
 
+def table_lookup(xs, ys, u):
+    """Piecewise-linear interpolation of the knots (xs, ys) at the Dual u:
+    on [x_k, x_{k+1}) the segment's line (so the derivative at a knot is the
+    right-hand slope); below x_0 and from x_{K-1} on, the end value with
+    derivative 0."""
+    xs = np.asarray(xs, dtype=np.float64)
+    ys = np.asarray(ys, dtype=np.float64)
+    K = len(xs)
+    k = np.searchsorted(xs, u.v, side="right") - 1          # x_k <= u < x_{k+1}
+    inside = (k >= 0) & (k < K - 1)
+    kk = np.clip(k, 0, max(K - 2, 0))
+    if K > 1:
+        slope = (ys[kk + 1] - ys[kk]) / (xs[kk + 1] - xs[kk])
+        line = (u - xs[kk]) * slope + ys[kk]
+    else:
+        line = Dual.const(np.full_like(u.v, ys[0]), u.k)
+    end = Dual.const(np.where(k < 0, ys[0], ys[K - 1]), u.k)
+    return D.where(inside, line, end)
+
+
 def cell_properties(ph, phi_r, P, S, C):
     """All per-cell quantities as Duals in the cell's own (P, S, C)."""
     phi = phi_r + ph["c_r"] * (P - ph["p_r"])                       # porosity law
     rho_o = ph["rho_o"] * (1.0 + ph["c_o"] * (P - ph["p_ref"]))
-    sn = _clip01_dual((S - ph["swc"]) / (1.0 - ph["swc"] - ph["sor"]))
-    krw = ph["krw_max"] * (sn ** ph["nw"])
-    kro = ph["kro_max"] * ((1.0 - sn) ** ph["no"])
-    if ph["pc_e"] != 0.0:
-        pc = ph["pc_e"] * ((1.0 - sn) ** ph["pc_n"])
+    sat = ph.get("sat_table")
+    if sat is not None:                      # tabulated k_rw, k_ro, P_c (Sec. 2.2)
+        sat = np.asarray(sat, dtype=np.float64)
+        krw = table_lookup(sat[:, 0], sat[:, 1], S)
+        kro = table_lookup(sat[:, 0], sat[:, 2], S)
+        pc = table_lookup(sat[:, 0], sat[:, 3], S)
     else:
-        pc = Dual.const(np.zeros_like(P.v), P.k)
+        sn = _clip01_dual((S - ph["swc"]) / (1.0 - ph["swc"] - ph["sor"]))
+        krw = ph["krw_max"] * (sn ** ph["nw"])
+        kro = ph["kro_max"] * ((1.0 - sn) ** ph["no"])
+        if ph["pc_e"] != 0.0:
+            pc = ph["pc_e"] * ((1.0 - sn) ** ph["pc_n"])
+        else:
+            pc = Dual.const(np.zeros_like(P.v), P.k)
     Pw = P - pc                                                      # P_c = P_o - P_w
     rho_w = ph["rho_w"] * (1.0 + ph["c_w"] * (Pw - ph["p_ref"]))
-    ads = ph["ads_a"] * C / (1.0 + ph["ads_b"] * C)                  # Langmuir A_d(C)
-    ads_max = ph["ads_a"] / ph["ads_b"]
+    poly = ph.get("poly_table")
+    if poly is not None:                     # tabulated A_d(C) and viscosity multiplier (Sec. 2.3)
+        poly = np.asarray(poly, dtype=np.float64)
+        ads = table_lookup(poly[:, 0], poly[:, 2], C)
+        ads_max = float(poly[:, 2].max())
+    else:
+        ads = ph["ads_a"] * C / (1.0 + ph["ads_b"] * C)              # Langmuir A_d(C)
+        ads_max = ph["ads_a"] / ph["ads_b"]
     if ads_max > 0.0:                                                # permeability reduction
         Rk = 1.0 + (ph["rrf"] - 1.0) * ads / ads_max
     else:                                                            # no adsorption: R_k = 1
         Rk = Dual.const(np.ones_like(P.v), P.k)
     beta = C / ph["c_ref"]
-    if ph["mixing"] == 0:                    # nonlinear rule mu_p0^beta mu_w^(1-beta)
+    if poly is not None:                     # mu_m = mu_w x multiplier(C)
+        mu_m = table_lookup(poly[:, 0], poly[:, 1], C) * ph["mu_w"]
+    elif ph["mixing"] == 0:                  # nonlinear rule mu_p0^beta mu_w^(1-beta)
         mu_m = D.exp(beta * math.log(ph["mu_p0"]) + (1.0 - beta) * math.log(ph["mu_w"]))
     else:                                                            # linear rule
         mu_m = beta * ph["mu_p0"] + (1.0 - beta) * ph["mu_w"]
@@ -207,6 +242,126 @@ def unpack(st, x):
     n = st.n
     xc = x[: 3 * n]
     return xc[0::3], xc[1::3], xc[2::3], x[3 * n:]
+
+
+# ---------------------------------------------------------------------------
+# capillary-gravity equilibrium initialisation (Sec. 4.1.3)
+# ---------------------------------------------------------------------------
+
+def _phase_density(ph, a, P):
+    key, c = ("rho_o", "c_o") if a == "o" else ("rho_w", "c_w")
+    return ph[key] * (1.0 + ph[c] * (P - ph["p_ref"]))
+
+
+def _march_continuous(ph, a, p0, z0, z1, steps=4000):
+    """dP/dz = g rho_a(P) from (z0, p0) to z1 by many small RK4 steps (the
+    paper marches the hydrostatic pressure in small steps, recomputing the
+    density at each one)."""
+    if z1 == z0:
+        return p0
+    h = (z1 - z0) / steps
+    g = ph["g"]
+    f = lambda P: g * _phase_density(ph, a, P)
+    P = p0
+    for _ in range(steps):
+        k1 = f(P)
+        k2 = f(P + 0.5 * h * k1)
+        k3 = f(P + 0.5 * h * k2)
+        k4 = f(P + h * k3)
+        P = P + h * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+    return P
+
+
+def _face_balance_step(ph, a, P_known, known_is_upper, wU, wD, dz):
+    """Pressure of the neighbouring cell that makes the discrete potential
+    difference of phase a across a vertical face vanish:
+    P_D - P_U = (wU rho(P_U) + wD rho(P_D)) g dz, U the upper (lower index)
+    cell, D the lower; solved for the unknown side by scalar Newton."""
+    g = ph["g"]
+    P = P_known
+    for _ in range(50):
+        if known_is_upper:
+            F = P - P_known - (wU * _phase_density(ph, a, P_known) + wD * _phase_density(ph, a, P)) * g * dz
+            dF = 1.0 - wD * g * dz * (_phase_density(ph, a, P + 1.0) - _phase_density(ph, a, P))
+        else:
+            F = P_known - P - (wU * _phase_density(ph, a, P) + wD * _phase_density(ph, a, P_known)) * g * dz
+            dF = -1.0 - wU * g * dz * (_phase_density(ph, a, P + 1.0) - _phase_density(ph, a, P))
+        step = F / dF
+        P -= step
+        if abs(step) <= 1e-13 * abs(P):
+            break
+    return P
+
+
+def _capillary_pressure(ph, S):
+    """P_c = P_o - P_w of the model at the saturations S (array)."""
+    S = np.atleast_1d(np.asarray(S, dtype=np.float64))
+    z = np.zeros_like(S)
+    pr = cell_properties(ph, z, Dual.variable(z, 3, 0), Dual.variable(S, 3, 1), Dual.variable(z, 3, 2))
+    return -pr["Pw"].v
+
+
+def _saturation_for(ph, dP):
+    """Per entry of dP: the largest S in [0, 1] with P_c(S) >= dP (P_c is
+    non-increasing in S), by bisection; the irreducible saturation where no S
+    qualifies."""
+    dP = np.asarray(dP, dtype=np.float64)
+    sat = ph.get("sat_table")
+    s_irr = float(np.asarray(sat)[0, 0]) if sat is not None else ph["swc"]
+    ones = np.ones_like(dP)
+    at_one = _capillary_pressure(ph, ones) >= dP
+    none = _capillary_pressure(ph, 0.0 * ones) < dP
+    lo, hi = np.zeros_like(dP), ones.copy()          # P_c(lo) >= dP > P_c(hi) where bracketed
+    for _ in range(1100):
+        mid = 0.5 * (lo + hi)
+        moving = (mid != lo) & (mid != hi)
+        if not moving.any():
+            break
+        up = _capillary_pressure(ph, mid) >= dP
+        lo = np.where(moving & up, mid, lo)
+        hi = np.where(moving & ~up, mid, hi)
+    return np.where(at_one, 1.0, np.where(none, s_irr, lo))
+
+
+def equilibrium_state(sc, datum_depth, datum_p, contact_depth):
+    """Capillary-gravity equilibrium (Sec. 4.1.3): oil pressure from the
+    datum, water pressure from the oil-water contact (free water level, where
+    P_o = P_w), each column marched cell to cell so that the discrete phase
+    potential difference of every vertical face is zero with the face density
+    of the discretisation (pore-volume weighted); saturations then balance
+    the capillary pressure, S = max{S : P_c(S) >= P_o - P_w}.  Below the
+    contact (no S balances it) the oil pressure of a cell is set to
+    P_w + P_c(S) so that its water pressure stays on the water gradient.
+    The datum-to-cell and contact-to-cell legs are continuous marches.
+    Returns (P_o, S_w) per cell."""
+    ph = sc["physics"]
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    top, dz = sc["top"], sc["dz"]
+    zc = top + (np.arange(nz) + 0.5) * dz
+    phi = np.asarray(sc["phi"], dtype=np.float64).reshape(nz, ny * nx)
+    kd = int(min(max(math.floor((datum_depth - top) / dz), 0), nz - 1))
+    kc = int(min(max(math.floor((contact_depth - top) / dz), 0), nz - 1))
+    P_o = np.empty((nz, ny * nx))
+    P_w = np.empty((nz, ny * nx))
+    for col in range(ny * nx):
+        def march(a, k0, p_k0, out):
+            out[k0] = p_k0
+            for k in range(k0, nz - 1):                  # downwards
+                wU = phi[k, col] / (phi[k, col] + phi[k + 1, col])
+                out[k + 1] = _face_balance_step(ph, a, out[k], True, wU, 1.0 - wU, dz)
+            for k in range(k0, 0, -1):                   # upwards
+                wU = phi[k - 1, col] / (phi[k - 1, col] + phi[k, col])
+                out[k - 1] = _face_balance_step(ph, a, out[k], False, wU, 1.0 - wU, dz)
+        march("o", kd, _march_continuous(ph, "o", datum_p, datum_depth, zc[kd]), P_o[:, col])
+        p_contact = _march_continuous(ph, "o", P_o[kc, col], zc[kc], contact_depth)
+        march("w", kc, _march_continuous(ph, "w", p_contact, contact_depth, zc[kc]), P_w[:, col])
+    P = P_o.ravel().copy()
+    Pw = P_w.ravel()
+    S = _saturation_for(ph, P - Pw)
+    pc = _capillary_pressure(ph, S)
+    below = pc > P - Pw                                 # below the contact
+    P[below] = Pw[below] + pc[below]
+    return P, S
 
 
 # ---------------------------------------------------------------------------
@@ -451,6 +606,29 @@ def forcing_term(norm_b, norm_b_prev, gamma=0.5, beta=GOLDEN, lo=0.01, hi=0.1):
     return min(max(eta, lo), hi)
 
 
+def forcing_term_difference(b, r_prev, norm_b_prev, lo=0.01, hi=0.1):
+    """First choice of eq. (fterm): |b^l - r^{l-1}| / |b^{l-1}|, where b^l is
+    the current right-hand side (-R) and r^{l-1} = b^{l-1} - J^{l-1} dx^{l-1}
+    the residual the previous Newton iteration's linear solve left; the
+    numerator measures how far the linear model of the previous iteration
+    missed the new residual.  Restricted to [0.01, 0.1]; the first iteration
+    (no previous solve) takes the upper bound."""
+    if r_prev is None or norm_b_prev is None or norm_b_prev <= 0.0:
+        return hi
+    eta = float(np.linalg.norm(np.asarray(b) - np.asarray(r_prev))) / norm_b_prev
+    return min(max(eta, lo), hi)
+
+
+def forcing_term_norms(norm_b, norm_r_prev, norm_b_prev, lo=0.01, hi=0.1):
+    """Second choice of eq. (fterm): (|b^l| - |r^{l-1}|) / |b^{l-1}|, taken
+    as printed (no absolute value: a negative value is restricted to the
+    lower bound).  Restricted to [0.01, 0.1]; first iteration: upper bound."""
+    if norm_r_prev is None or norm_b_prev is None or norm_b_prev <= 0.0:
+        return hi
+    eta = (norm_b - norm_r_prev) / norm_b_prev
+    return min(max(eta, lo), hi)
+
+
 def update(st, x, dx, ds_max, dc_frac=0.5):
     """x + dx with the saturation change chopped to +-ds_max and the
     concentration change to +-dc_frac * C_ref per cell, then S clipped to
@@ -593,7 +771,9 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_sw
     stay fixed within a step (step 4(b)) except that a rate well crossing its
     BHP limit during the iterations moves onto the limit (``limit_crossings``);
     after convergence ``update_switches`` may switch it back, with up to
-    ``max_switch_solves`` re-solves."""
+    ``max_switch_solves`` re-solves.  After an accepted sub-step the step
+    doubles again, never beyond the schedule's step, so the loop keeps trying
+    to lengthen the step (step 4(c)-(d))."""
     st = Setup(sc)
     x = initial_state(st)
     t = 0.0
@@ -615,6 +795,7 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_sw
             dt = dt_left
             cuts = 0
             newton_total = 0
+            accepted = []
             while dt_left > 0.0:
                 dt = min(dt, dt_left)
                 for attempt in range(max_switch_solves + 1):
@@ -631,13 +812,18 @@ def run(sc, n_steps=None, tol=1e-10, max_iter=25, ds_max=0.2, max_cuts=6, max_sw
                     x = xn
                     t += dt
                     dt_left -= dt
+                    accepted.append(dt)
+                    # after a cut the step grows again, doubling up to the
+                    # schedule's step (Sec. 3 step 4(c)-(d))
+                    dt = min(2.0 * dt, period["dt"])
                 else:
                     cuts += 1
                     if cuts > max_cuts:
                         raise RuntimeError("time step cut limit reached")
                     dt = 0.5 * dt
             done += 1
-            history.append(dict(t=t, x=x.copy(), newton=newton_total, cuts=cuts, switched=list(switched)))
+            history.append(dict(t=t, x=x.copy(), newton=newton_total, cuts=cuts, switched=list(switched),
+                                substeps=accepted))
             if callback is not None:
                 callback(st, x, history[-1])
     return st, x, history

@@ -62,7 +62,7 @@ class pf_solver_opts(C.Structure):
                 ("lin_rtol", C.c_double), ("newton_tol", C.c_double), ("ds_max", C.c_double),
                 ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
-                ("amg_cycle", C.c_int), ("autotune", C.c_int)]
+                ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int)]
 
 
 class pf_tuning(C.Structure):
@@ -143,6 +143,7 @@ def lib():
             "pf_kernel_timing_enable": ([vp, C.c_int], C.c_int),
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
             "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
+            "pf_set_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_run_schedule": ([vp, C.POINTER(pf_schedule), C.c_int, C.POINTER(pf_run_report)], C.c_int),
             "pf_runtime_last_error": ([], C.c_char_p),
             "pf_footprint": ([C.POINTER(pf_model_desc), C.POINTER(pf_solver_opts), C.POINTER(C.c_size_t)],
@@ -353,6 +354,14 @@ class Simulator:
         _check(lib().pf_autotune(self.h, C.byref(t)))
         return {n: getattr(t, n) for n, _ in pf_tuning._fields_}
 
+    def set_tuning(self, **shapes):
+        t = pf_tuning()
+        cur = dict(props=256, face=256, gather=256, spmv=256, stage2=256, rbgs=256)
+        cur.update(shapes)
+        for k, v in cur.items():
+            setattr(t, k, int(v))
+        _check(lib().pf_set_tuning(self.h, C.byref(t)))
+
     def kernel_timing_enable(self, on=True):
         _check(lib().pf_kernel_timing_enable(self.h, 1 if on else 0))
 
@@ -407,6 +416,7 @@ class Simulator:
                     krylov += rep.krylov_iters
                     if rc == PF_OK:
                         left -= dt
+                        dt = min(2.0 * dt, period["dt"])   # grow back after a cut
                     else:
                         cuts += 1
                         if cuts > max_cuts:

@@ -102,7 +102,9 @@ struct pf_sim {
   double dt = 0.0;
   bool in_step = false;
   bool assembled = false;
-  double prev_norm = -1.0;
+  double prev_norm = -1.0;      // |b^{l-1}| of the previous Newton iteration (< 0: none)
+  double prev_lin_norm = 0.0;   // |r^{l-1}| (forcing form 2)
+  double* rlin = nullptr;       // r^{l-1} (forcing form 1)
   int iter_in_step = 0;
 };
 
@@ -256,6 +258,7 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (o->amg_cycle != 1 && o->amg_cycle != 2) return fail(PF_EINVAL, "amg_cycle must be 1 or 2");
     if (o->amg_pre_sweeps < 0 || o->amg_post_sweeps < 0 || o->amg_coarse_size < 1)
       return fail(PF_EINVAL, "invalid multigrid parameters");
+    if (o->forcing_form < 1 || o->forcing_form > 3) return fail(PF_EINVAL, "forcing_form must be 1, 2 or 3");
   }
   return PF_OK;
 }
@@ -315,6 +318,7 @@ size_t carve(pf_sim* s, char* base) {
   s->b = c.take<double>(s->nunk);
   s->r = c.take<double>(s->nunk);
   s->tmp = c.take<double>(s->nunk);
+  s->rlin = (s->opts.use_forcing && s->opts.forcing_form == 1) ? c.take<double>(s->nunk) : nullptr;
   s->V = c.take<double>((size_t)(m + 1) * s->ld);
   s->Z = c.take<double>((size_t)m * s->ld);
   s->Zf = s->mixed ? c.take<float>((size_t)m * s->ld) : nullptr;
@@ -630,12 +634,13 @@ pf_status check(pf_sim* s) {
   return PF_OK;
 }
 
+double clamp_eta(double eta) { return std::isnan(eta) ? 0.1 : std::min(std::max(eta, 0.01), 0.1); }
+
 double forcing_term(double nb, double nb_prev) {
   // eq. (fterm), third choice: gamma (|b^l| / |b^{l-1}|)^beta, gamma = 0.5,
   // beta = (sqrt(5) + 1) / 2, restricted to [0.01, 0.1]; first iteration 0.1
   if (!(nb_prev > 0.0)) return 0.1;
-  const double eta = 0.5 * pow(nb / nb_prev, (sqrt(5.0) + 1.0) / 2.0);
-  return std::min(std::max(eta, 0.01), 0.1);
+  return clamp_eta(0.5 * pow(nb / nb_prev, (sqrt(5.0) + 1.0) / 2.0));
 }
 
 }  // namespace
@@ -663,6 +668,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->amg_coarse_size = 8;
   o->amg_cycle = 1;
   o->autotune = 0;
+  o->forcing_form = 3;
   return PF_OK;
 }
 
@@ -1034,13 +1040,29 @@ static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_upd
     if (rep) *rep = r;
     return fail(PF_ENOT_CONVERGED, "Newton iteration cap reached");
   }
-  const double eta = s->opts.use_forcing ? forcing_term(nrm, s->prev_norm) : s->opts.lin_rtol;
-  r.eta = eta;
-  if ((rc = precond_setup(s)) != PF_OK) return rc;
   // b = -R
   launch_fill(1, -1.0, s->norms + 3, s->stream);
   launch_scale_by_dev(s->nunk, s->R, s->norms + 3, 0, s->b, s->stream);
   s->launches += 2;
+  const int form = s->opts.forcing_form;
+  double eta = s->opts.lin_rtol;
+  if (s->opts.use_forcing) {
+    if (!(s->prev_norm > 0.0)) {
+      eta = 0.1;                                          // first iteration of the step
+    } else if (form == 1) {                               // |b^l - r^{l-1}| / |b^{l-1}|
+      double d = 0.0;
+      launch_sub(s->nunk, s->b, s->rlin, s->tmp, s->stream);
+      s->launches += 1;
+      if ((rc = dev_norm2(s, s->tmp, &d)) != PF_OK) return rc;
+      eta = clamp_eta(d / s->prev_norm);
+    } else if (form == 2) {                               // (|b^l| - |r^{l-1}|) / |b^{l-1}|
+      eta = clamp_eta((nrm - s->prev_lin_norm) / s->prev_norm);
+    } else {
+      eta = forcing_term(nrm, s->prev_norm);
+    }
+  }
+  r.eta = eta;
+  if ((rc = precond_setup(s)) != PF_OK) return rc;
   int its = 0;
   double rr = 0.0;
   rc = gmres(s, s->b, s->dx, eta, s->opts.gmres_max_iter, &its, &rr);
@@ -1049,6 +1071,14 @@ static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_upd
   if (rc != PF_OK) {
     if (rep) *rep = r;
     return rc;
+  }
+  if (s->opts.use_forcing && form != 3) {
+    // r^l = b^l - J dx^l, the residual this linear solve left (forms 1 and 2)
+    double* rl = form == 1 ? s->rlin : s->tmp;
+    if ((rc = spmv(s, s->dx, rl)) != PF_OK) return rc;
+    launch_sub(s->nunk, s->b, rl, rl, s->stream);
+    s->launches += 1;
+    if (form == 2 && (rc = dev_norm2(s, rl, &s->prev_lin_norm)) != PF_OK) return rc;
   }
   launch_newton_update(s->g, s->nw, s->x, s->dx, s->opts.ds_max, s->opts.dc_frac * s->ph.c_ref, s->stream);
   PF_LAUNCHED(1);
@@ -1338,15 +1368,20 @@ static float time_launch(pf_sim* s, F fn, int reps) {
 }
 
 template <typename F>
-static int pick_block(pf_sim* s, F fn_of_block) {
-  static const int cand[3] = {64, 128, 256};
-  int best = 256;
+static int pick_from(pf_sim* s, const int* cand, int nc, F fn_of_block) {
+  int best = cand[nc - 1];
   float tbest = 1e30f;
-  for (int c : cand) {
-    const float t = time_launch(s, [&] { fn_of_block(c); }, 3);
-    if (t < tbest) { tbest = t; best = c; }
+  for (int q = 0; q < nc; ++q) {
+    const float t = time_launch(s, [&] { fn_of_block(cand[q]); }, 3);
+    if (t < tbest) { tbest = t; best = cand[q]; }
   }
   return best;
+}
+
+template <typename F>
+static int pick_block(pf_sim* s, F fn_of_block) {
+  static const int cand[3] = {64, 128, 256};
+  return pick_from(s, cand, 3, fn_of_block);
 }
 
 extern "C" {
@@ -1379,7 +1414,9 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
                                                                 (const double*)s->pd, dt, (double*)s->J, s->Fbuf, st,
                                                                 b); });
     t.gather = pick_block(s, [&](int b) { launch_gather<double>(s->g, s->Fbuf, dt, s->R, (double*)s->J, st, b); });
-    t.spmv = pick_block(s, [&](int b) {
+    // one thread per cell (64/128/256) or one per block row (-96/-192/-384)
+    static const int cand_spmv[6] = {64, 128, 256, -96, -192, -384};
+    t.spmv = pick_from(s, cand_spmv, 6, [&](int b) {
       launch_spmv<double>(s->g, wells_view(s), (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
                           (const double*)s->Dw, s->b, s->r, st, b);
     });
@@ -1403,6 +1440,29 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     out->props = t.props; out->face = t.face; out->gather = t.gather;
     out->spmv = t.spmv; out->stage2 = t.stage2; out->rbgs = t.rbgs;
   }
+  return PF_OK;
+}
+
+pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!t) return fail(PF_EINVAL, "tuning is NULL");
+  auto ok = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
+  const bool spmv_ok = ok(t->spmv) || (!s->mixed && (t->spmv == -96 || t->spmv == -192 || t->spmv == -384));
+  if (!ok(t->props) || !ok(t->face) || !ok(t->gather) || !spmv_ok || !ok(t->stage2) || !ok(t->rbgs))
+    return fail(PF_EINVAL, "invalid launch shape");
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  Tuning& u = s->tune;
+  u.props = t->props; u.face = t->face; u.gather = t->gather;
+  u.spmv = t->spmv; u.stage2 = t->stage2; u.rbgs = t->rbgs;
+  s->cpr.block_rbgs0 = u.rbgs;
+  s->cpr.block_stage2 = u.stage2;
+  for (auto& G : s->graphs) {
+    if (G.pre) cudaGraphExecDestroy(G.pre);
+    if (G.spmv) cudaGraphExecDestroy(G.spmv);
+    if (G.ortho) cudaGraphExecDestroy(G.ortho);
+  }
+  s->graphs.clear();
   return PF_OK;
 }
 

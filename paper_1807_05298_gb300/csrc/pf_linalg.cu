@@ -56,6 +56,48 @@ __global__ void __launch_bounds__(256) k_spmv_cells(Grid g, const DT* __restrict
   }
 }
 
+// The same product with one thread per (cell, row): a block holds groups of
+// three warps, one per block row, over the same 32 cells, so J streams
+// coalesced per row and the three warps share the x loads in L1.  Three times
+// the threads of k_spmv_cells fill the GPU at small N; each row's sum is
+// taken in the same order, so the result is identical.
+template <typename DT>
+__global__ void __launch_bounds__(384) k_spmv_rows(Grid g, const DT* __restrict__ J, const double* __restrict__ x,
+                                                   double* __restrict__ y) {
+  const long long n = g.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = warp % 3;
+  const int groups = blockDim.x / 96;
+  const long long stride = (long long)gridDim.x * groups * 32;
+  for (long long i = ((long long)blockIdx.x * groups + warp / 3) * 32 + lane; i < n; i += stride) {
+    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+    const unsigned int rem = ui - (unsigned int)k * nxy;
+    const long long j = rem / nxu;
+    const long long ii = rem - (unsigned int)j * nxu;
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 0; s < SL_COUNT; ++s) {
+      long long c;
+      bool has;
+      switch (s) {
+        case SL_D: c = i; has = true; break;
+        case SL_XM: c = i - 1; has = ii > 0; break;
+        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
+        case SL_YM: c = i - g.nx; has = j > 0; break;
+        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
+        case SL_ZM: c = i - g.nxy; has = k > 0; break;
+        default: c = i + g.nxy; has = k + 1 < g.nz; break;
+      }
+      if (!has) continue;
+      const DT* B = J + ((size_t)s * 9 + 3 * r) * n + i;
+      const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+      acc += (double)B[0] * x0 + (double)B[n] * x1 + (double)B[2 * n] * x2;
+    }
+    y[3 * i + r] = acc;
+  }
+}
+
 template <typename DT>
 __global__ void k_spmv_wells(Grid g, Wells w, const DT* __restrict__ Bw, const DT* __restrict__ Cw,
                              const DT* __restrict__ Dw, const double* __restrict__ x, double* __restrict__ y) {
@@ -142,7 +184,13 @@ void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float*
 template <typename DT>
 void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const DT* Cw, const DT* Dw,
                  const double* x, double* y, cudaStream_t st, int block) {
-  k_spmv_cells<DT><<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
+  if (block < 0) {
+    // row-split form: -block = threads per block, a multiple of 96 (<= 384)
+    const int tb = -block, cells_per_block = tb / 3;
+    k_spmv_rows<DT><<<grid_for(g.n, cells_per_block), tb, 0, st>>>(g, J, x, y);
+  } else {
+    k_spmv_cells<DT><<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
+  }
   if (w.nw > 0) k_spmv_wells<DT><<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
 }
 

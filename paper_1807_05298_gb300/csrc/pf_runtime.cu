@@ -122,6 +122,7 @@ pf_status pf_run_schedule(pf_sim* s, const pf_schedule* sched, int max_cuts, pf_
         out.krylov_iters += sr.krylov_iters;
         if (r == PF_OK) {
           left -= dt;
+          dt = std::min(2.0 * dt, per.dt);  // grow back after a cut (Sec. 3 step 4(c)-(d))
         } else if (r == PF_ENOT_CONVERGED && cuts < max_cuts) {
           ++cuts;
           ++out.cuts;

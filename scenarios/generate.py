@@ -101,6 +101,8 @@ def default_physics(**over):
         rrf=1.5, ipv=0.1,
         omega=1.0, mu_p0=5.0 * CP, c_ref=2.0, mixing=0,   # 0 nonlinear, 1 linear rule
         g=G,
+        sat_table=None,     # optional (K, 4) knots: S_w, k_rw, k_ro, P_c [Pa]
+        poly_table=None,    # optional (K, 3) knots: C, water viscosity multiplier, A_d [kg/m^3 rock]
     )
     p.update(over)
     return p

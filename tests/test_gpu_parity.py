@@ -287,3 +287,53 @@ def test_bhp_limit_switching_matches_oracle(B):
     for xg, h in zip(states, hist):
         assert max(field_errors(st.n, xg, h["x"])) <= 1e-6
     sim.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_forcing_term_forms_match_oracle(B, form):
+    """First and second choices of eq. (fterm): the tolerance the library
+    picks at each Newton iteration equals the oracle's formula evaluated on
+    the iterates the library produced (the previous linear residual rebuilt as
+    b - J dx from the oracle's own R and J), and the step still lands on the
+    oracle's root.  Polymer is present everywhere at the start so no update
+    is clipped and dx is the difference of consecutive iterates."""
+    sc = G.scenario_c1(nx=9, ny=7, nz=3)
+    sc["C0"] = np.full(sc["C0"].shape, 0.5)
+    dt = 2.0 * DAY
+    ctl = M.controls_with_defaults(sc["schedule"][0]["controls"])
+    sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=1, forcing_form=form)
+    sim.set_controls(sc["schedule"][0]["controls"])
+    st = M.Setup(sc)
+    x_old = sim.get_x()
+    sim.begin_step(dt)
+    xs, etas = [x_old], []
+    for _ in range(12):
+        rep = sim.newton_iteration()
+        if rep.converged:
+            break
+        etas.append(rep.eta)
+        xs.append(sim.get_x())
+    assert rep.converged and len(etas) >= 3
+    assert not any(sim.switched())
+    sim.close()
+    n = st.n
+    gam = M.well_gamma(st, x_old, ctl)
+    Mold = M.masses(st, x_old)
+    assert etas[0] == 0.1
+    for l in range(1, len(etas)):
+        a, b = xs[l - 1], xs[l]
+        assert np.abs(b[1:3 * n:3] - a[1:3 * n:3]).max() < 0.2 and b[2:3 * n:3].min() > 0.0
+        assert 0.0 < b[1:3 * n:3].min() and b[1:3 * n:3].max() < 1.0
+        R_a, J_a = M.assemble(st, a, Mold, dt, ctl, gam)
+        R_b, _ = M.assemble(st, b, Mold, dt, ctl, gam)
+        r_prev = -R_a - J_a @ (b - a)
+        nb_prev = np.linalg.norm(R_a)
+        if form == 1:
+            want = M.forcing_term_difference(-R_b, r_prev, nb_prev)
+        else:
+            want = M.forcing_term_norms(np.linalg.norm(R_b), np.linalg.norm(r_prev), nb_prev)
+        assert etas[l] == pytest.approx(want, rel=1e-6, abs=1e-12)
+    x_o, ok, _ = M.newton_step(st, x_old, dt, ctl)
+    assert ok
+    err = field_errors(n, xs[-1], x_o)
+    assert max(err) <= 1e-6

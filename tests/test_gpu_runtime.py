@@ -18,6 +18,8 @@ from scenarios import generate as G
 
 pytestmark = pytest.mark.gpu
 
+DAY = G.DAY
+
 
 @pytest.fixture(scope="module")
 def B():
@@ -120,8 +122,61 @@ def test_autotuned_launch_shapes_give_identical_results(B, precision):
     base = alone(B, sc, 3, **opt)
     sim = B.Simulator(sc, autotune=1, **opt)
     t = sim.autotune()
-    assert all(v in (64, 128, 256) for v in t.values())
+    assert all(v in (64, 128, 256) for k, v in t.items() if k != "spmv")
+    assert t["spmv"] in ((64, 128, 256, -96, -192, -384) if precision == 0 else (64, 128, 256))
     B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
     x = sim.get_x()
     sim.close()
     assert np.array_equal(base, x)
+
+
+def test_native_time_loop_cuts_and_grows_like_oracle(B):
+    """A 30-day step with at most 6 Newton iterations fails and is cut; the
+    native loop cuts, grows the step back and lands on the oracle's state."""
+    sc = G.scenario_c1(n_steps=2, dt_days=30.0)
+    sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=0, lin_rtol=1e-12, newton_max_iter=6)
+    rep = B.run_schedule(sim, B.Schedule(sc["schedule"]))
+    x = sim.get_x()
+    sim.close()
+    st, xo, hist = M.run(sc, max_iter=6)
+    assert rep.status == 0 and rep.steps == 2
+    assert rep.cuts == sum(h["cuts"] for h in hist)
+    n = st.n
+    for a in range(3):
+        ref = max(np.abs(xo[a:3 * n:3]).max(), 1e-12)
+        assert np.abs(x[a:3 * n:3] - xo[a:3 * n:3]).max() <= 1e-6 * ref
+
+
+@pytest.mark.parametrize("shape", [-96, -192, -384])
+def test_row_split_spmv_gives_identical_results(B, shape):
+    """One thread per block row (FP64 SpMV) against one thread per cell: the
+    product and a whole 3-step run are bit-identical; shapes outside the
+    documented set are refused."""
+    sc = G.scenario_c1(nx=17, ny=11, nz=3, n_steps=3)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=0)
+    base = alone(B, sc, 3, **opt)
+    ref = B.Simulator(sc, **opt)
+    sim = B.Simulator(sc, **opt)
+    sim.set_tuning(spmv=shape)
+    v = np.random.default_rng(3).standard_normal(ref.nunk)
+    ref.set_controls(sc["schedule"][0]["controls"])
+    sim.set_controls(sc["schedule"][0]["controls"])
+    ref.begin_step(DAY)
+    sim.begin_step(DAY)
+    ref.assemble()
+    sim.assemble()
+    assert np.array_equal(ref.apply_jacobian(v), sim.apply_jacobian(v))
+    ref.close()
+    sim.close()
+    sim = B.Simulator(sc, **opt)
+    sim.set_tuning(spmv=shape)
+    B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
+    assert np.array_equal(base, sim.get_x())
+    with pytest.raises(B.PfError) as e:
+        sim.set_tuning(spmv=-100)
+    assert e.value.status == B.PF_EINVAL
+    sim.close()
+    mixed = B.Simulator(sc, **dict(opt, precision=1))
+    with pytest.raises(B.PfError):
+        mixed.set_tuning(spmv=shape)
+    mixed.close()

@@ -332,6 +332,44 @@ def test_forcing_term_third_choice():
     assert 0.5 * 0.1 ** beta == pytest.approx(0.0120486, rel=1e-5)
 
 
+def test_forcing_term_first_and_second_choices():
+    """Eq. (fterm), first and second choices.  For a linear F the previous
+    linear model is exact, so b^l = r^{l-1} whatever the step: both
+    numerators vanish and eta takes the lower bound.  For F(x) = x*x - c the
+    model misses by exactly s*s (closed form).  The second choice never
+    exceeds the first (triangle inequality) and, after an exact solve, is the
+    ratio of the right-hand side norms."""
+    inf = float("inf")
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((6, 6)) + 6.0 * np.eye(6)
+    c = rng.standard_normal(6)
+    x = rng.standard_normal(6)
+    s = 0.3 * rng.standard_normal(6)                      # any step, not the Newton one
+    b0, b1 = -(A @ x - c), -(A @ (x + s) - c)
+    r0 = b0 - A @ s
+    assert M.forcing_term_difference(b1, r0, np.linalg.norm(b0)) == 0.01
+    assert M.forcing_term_norms(np.linalg.norm(b1), np.linalg.norm(r0), np.linalg.norm(b0)) == 0.01
+    assert M.forcing_term_difference(b1, None, None) == 0.1
+    assert M.forcing_term_norms(1.0, None, None) == 0.1
+    # F(x) = x*x - c, J = diag(2x)
+    xq = np.array([1.0, 2.0, 3.0])
+    cq = np.array([0.5, 3.0, 8.0])
+    sq = np.array([-0.2, -0.2, -0.15])
+    F = lambda v: v * v - cq
+    b0, b1 = -F(xq), -F(xq + sq)
+    r0 = b0 - 2.0 * xq * sq
+    eta1 = M.forcing_term_difference(b1, r0, np.linalg.norm(b0))
+    assert eta1 == pytest.approx(math.sqrt(0.04 ** 2 + 0.04 ** 2 + 0.0225 ** 2) / 1.5, rel=1e-12)
+    assert 0.01 < eta1 < 0.1
+    for _ in range(20):
+        b0, b1, r0 = rng.standard_normal((3, 5))
+        e1 = M.forcing_term_difference(b1, r0, np.linalg.norm(b0), lo=-inf, hi=inf)
+        e2 = M.forcing_term_norms(np.linalg.norm(b1), np.linalg.norm(r0), np.linalg.norm(b0), lo=-inf, hi=inf)
+        assert e2 <= e1 + 1e-12
+        assert M.forcing_term_norms(np.linalg.norm(b1), 0.0, np.linalg.norm(b0), lo=-inf, hi=inf) == \
+            pytest.approx(np.linalg.norm(b1) / np.linalg.norm(b0))
+
+
 def test_peaceman_equivalent_radius():
     h, rw = 20.0, 0.1
     k = 100.0 * MD
@@ -408,3 +446,159 @@ def test_rate_injector_below_limit_stays_on_rate():
     st, x, hist = M.run(sc)
     assert not any(h["switched"][0] for h in hist)
     assert x[3 * st.n] < 400.0 * BAR
+
+
+def test_time_step_cut_then_grow():
+    """Sec. 3 step 4: a failed Newton solve halves the step, and the loop
+    then tries to lengthen it again (doubling, capped by the period's step and
+    by what is left of it); the accepted sub-steps cover the step exactly."""
+    sc = G.scenario_c1(n_steps=2, dt_days=30.0)
+    _, _, hist = M.run(sc, max_iter=6)
+    dt = sc["schedule"][0]["dt"]
+    first = hist[0]
+    assert first["cuts"] >= 1
+    sub = first["substeps"]
+    assert abs(sum(sub) - dt) <= 1e-9 * dt
+    grew = False
+    left = dt
+    for a, b in zip(sub, sub[1:]):
+        left -= a
+        assert b <= min(2.0 * a, left) * (1 + 1e-12)
+        grew |= b > a * (1 + 1e-12)
+    assert grew
+    assert hist[1]["cuts"] == 0 and hist[1]["substeps"] == [dt]
+
+
+# ---------------------------------------------------------------------------
+# tabulated properties (Sec. 2.2 k_r and P_c of saturation; Sec. 2.3 "specified
+# in the form of a table" for adsorption, and the water viscosity multiplier)
+# ---------------------------------------------------------------------------
+
+def _props(ph, P, S, C):
+    n = len(P)
+    return M.cell_properties(ph, np.full(n, 0.2), M.Dual.variable(np.asarray(P, float), 3, 0),
+                             M.Dual.variable(np.asarray(S, float), 3, 1), M.Dual.variable(np.asarray(C, float), 3, 2))
+
+
+def test_tables_reproduce_linear_closed_forms():
+    """Two-knot tables are straight lines, so they must give exactly the
+    linear Corey curves (n = 1), the linear mixing rule and a linear isotherm,
+    values and derivatives, including the flat ends outside the knots."""
+    swc, sor, pce, c_ref, mu_w, mu_p0, rrf, K = 0.15, 0.25, 0.7 * BAR, 2.0, 0.5 * CP, 6.0 * CP, 1.8, 0.03
+    corey = G.default_physics(swc=swc, sor=sor, nw=1.0, no=1.0, krw_max=0.6, kro_max=0.9, pc_e=pce, pc_n=1.0,
+                              mixing=1, c_ref=c_ref, mu_w=mu_w, mu_p0=mu_p0, rrf=rrf)
+    sat = np.array([[swc, 0.0, 0.9, pce], [1.0 - sor, 0.6, 0.0, 0.0]])
+    cmax = 40.0
+    poly = np.array([[0.0, 1.0, 0.0], [cmax, 1.0 + cmax / c_ref * (mu_p0 / mu_w - 1.0), K * cmax]])
+    tab = dict(corey, sat_table=sat, poly_table=poly)
+    rng = np.random.default_rng(11)
+    S = rng.uniform(0.0, 1.0, 64)
+    C = rng.uniform(0.0, 0.99 * cmax, 64)
+    P = rng.uniform(150.0, 250.0, 64) * BAR
+    a, b = _props(corey, P, S, C), _props(tab, P, S, C)
+    for key in ("krw", "kro", "Pw", "mu_we", "mu_pe", "rho_w"):
+        assert np.allclose(a[key].v, b[key].v, rtol=1e-13, atol=0.0), key
+        assert np.allclose(a[key].d, b[key].d, rtol=1e-11, atol=1e-300), key
+    assert np.allclose(b["ads"].v, K * C, rtol=1e-13)
+    assert np.allclose(b["ads"].d[:, 2], K, rtol=1e-13)
+    assert np.allclose(b["Rk"].v, 1.0 + (rrf - 1.0) * C / cmax, rtol=1e-13)
+
+
+def test_table_knots_take_the_right_slope_and_flat_ends():
+    ph = G.default_physics(sat_table=np.array([[0.2, 0.0, 1.0, 3.0e4], [0.5, 0.1, 0.3, 1.0e4],
+                                               [0.8, 0.7, 0.0, 0.0]]))
+    S = np.array([0.5, 0.2, 0.8, 0.1, 0.95, 0.35])
+    p = _props(ph, np.full(6, 200.0 * BAR), S, np.zeros(6))
+    krw_slope = np.array([2.0, 1.0 / 3.0, 0.0, 0.0, 0.0, 1.0 / 3.0])
+    assert np.allclose(p["krw"].d[:, 1], krw_slope, rtol=1e-12, atol=0.0)
+    assert np.allclose(p["krw"].v, [0.1, 0.0, 0.7, 0.0, 0.7, 0.05], rtol=1e-12, atol=1e-15)
+    assert np.allclose(p["Pw"].v, 200.0 * BAR - np.array([1.0e4, 3.0e4, 0.0, 3.0e4, 0.0, 2.0e4]), rtol=1e-15)
+
+
+def test_polymer_front_with_tabulated_linear_isotherm():
+    """Sec. 2.3 table form of A_d(C): a linear isotherm A_d = K C retards the
+    polymer front to u / (phi (1 - IPV) + (1 - phi) K) (mass balance of the
+    front)."""
+    K, cmax = 0.02, 20.0
+    poly = np.array([[0.0, 1.0, 0.0], [cmax, 5.0, K * cmax]])
+    ph = incompressible(swc=0.0, sor=0.0, ipv=0.1, rrf=1.5, mu_w=1.0 * CP, poly_table=poly)
+    n, t_end, dt = 200, 150.0, 0.5
+    sc = one_d(n, physics=ph, q_day=20.0, c_inj=1.0, s0=1.0, c0=0.0, dt_days=dt, n_steps=int(round(t_end / dt)))
+    st, x, hist = M.run(sc)
+    C = field(st, x, 2)
+    phi, u = 0.2, 20.0 / DAY / 100.0
+    vs = u / (phi * (1.0 - 0.1) + (1.0 - phi) * K)
+    xs = vs * t_end * DAY
+    dx = 1000.0 / n
+    xc = (np.arange(n) + 0.5) * dx
+    i = int(np.nonzero(C < 0.5)[0][0])
+    x_half = xc[i - 1] + (C[i - 1] - 0.5) / (C[i - 1] - C[i]) * dx
+    assert abs(x_half - xs) < 3.0 * dx, (x_half, xs)
+
+
+# ---------------------------------------------------------------------------
+# capillary-gravity equilibrium initialisation (Sec. 4.1.3)
+# ---------------------------------------------------------------------------
+
+def _layered_no_wells(ph, nz=30, dz=1.0, nx=3, ny=2):
+    n = nx * ny * nz
+    phi = np.repeat(np.linspace(0.12, 0.3, nz), nx * ny)
+    k = np.repeat(np.exp(np.linspace(math.log(20.0), math.log(500.0), nz)), nx * ny) * MD
+    sched = [dict(n_steps=1, dt=DAY, controls=[])]
+    return G.make_scenario(nx, ny, nz, 20.0, 20.0, dz, 2000.0, k, k, 0.1 * k, phi, ph, [], sched)
+
+
+@pytest.mark.parametrize("kind", ["corey", "table"])
+def test_equilibrium_state_is_a_discrete_rest_state(kind):
+    """With no wells the equilibrated state is a root of the discrete
+    equations for any step: every face flux cancels (both phases), across
+    the oil zone, the capillary transition zone and the water zone."""
+    if kind == "corey":
+        ph = G.default_physics(pc_e=0.8 * BAR, pc_n=2.0)
+    else:
+        ph = G.default_physics(sat_table=np.array([[0.2, 0.0, 1.0, 1.2 * BAR], [0.45, 0.08, 0.45, 0.35 * BAR],
+                                                   [0.8, 0.6, 0.0, 0.0], [1.0, 1.0, 0.0, 0.0]]))
+    sc = _layered_no_wells(ph)
+    P, S = M.equilibrium_state(sc, 2005.0, 200.0 * BAR, 2022.0)
+    trans = (S > 0.2 + 1e-6) & (S < 0.8 - 1e-6)
+    assert trans.sum() >= 6 * 5 and (S == 1.0).sum() >= 6 * 5
+    sc["P0"], sc["S0"] = P, S
+    st = M.Setup(sc)
+    x = M.initial_state(st)
+    for dt in (DAY, 100.0 * DAY):
+        R, _ = M.assemble(st, x, M.masses(st, x), dt, [], [], with_jacobian=False)
+        assert M.scaled_residual(st, R, dt, []) < 1e-11
+
+
+def test_equilibrium_incompressible_closed_form():
+    """Incompressible phases: hydrostatic lines from the datum (oil) and from
+    the contact (water); in the transition zone P_c(S) = (rho_w - rho_o) g
+    (z_c - z), the capillary rise of the textbook, inverted in closed form
+    for the Corey curve."""
+    pce, pcn, swc, sor = 0.8 * BAR, 2.0, 0.2, 0.2
+    ph = G.default_physics(c_w=0.0, c_o=0.0, pc_e=pce, pc_n=pcn, swc=swc, sor=sor)
+    sc = _layered_no_wells(ph, nz=40, dz=0.5)
+    zd, pd, zc_ = 2003.3, 190.0 * BAR, 2014.2
+    P, S = M.equilibrium_state(sc, zd, pd, zc_)
+    z = M.cell_depth(sc)
+    g, ro, rw = ph["g"], ph["rho_o"], ph["rho_w"]
+    Po = pd + ro * g * (z - zd)
+    Pw = pd + ro * g * (zc_ - zd) + rw * g * (z - zc_)
+    dP = Po - Pw
+    sn = 1.0 - np.clip(dP / pce, 0.0, 1.0) ** (1.0 / pcn)
+    S_expect = np.where(dP <= 0.0, 1.0, swc + sn * (1.0 - swc - sor))
+    # the datum and contact legs are marched in thousands of small steps, whose
+    # rounding (~1e-5 Pa) moves S by ~1e-10 on the steep part of the curve
+    assert np.allclose(S, S_expect, rtol=0.0, atol=1e-9)
+    expectP = np.where(dP < 0.0, Pw, Po)
+    assert np.allclose(P, expectP, rtol=1e-12, atol=0.0)
+
+
+def test_equilibrium_continuous_leg_is_the_exponential_profile():
+    """dP/dz = g rho_ref (1 + c (P - P_ref)) has the closed-form solution
+    P = P_ref - 1/c + (P_0 - P_ref + 1/c) exp(g rho_ref c (z - z_0))."""
+    ph = G.default_physics(c_o=5e-4 / BAR)
+    c, r, g, pref = ph["c_o"], ph["rho_o"], ph["g"], ph["p_ref"]
+    p0, z0, z1 = 180.0 * BAR, 1000.0, 1350.0
+    exact = pref - 1.0 / c + (p0 - pref + 1.0 / c) * math.exp(g * r * c * (z1 - z0))
+    assert M._march_continuous(ph, "o", p0, z0, z1) == pytest.approx(exact, rel=1e-13)
