@@ -39,6 +39,7 @@ from scenarios import generate as G  # noqa: E402
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate
 HBM_FALLBACK_GBS = 6800.0         # profiling recipe fallback when no measured peak exists
 L2_BYTES = 129 * 1024 * 1024
+STAGE1 = {"bjacobi": 0, "ilu0": 1}
 
 
 def workload(name):
@@ -168,7 +169,8 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream()
     opts = dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
                 gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
-                amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form)
+                amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form,
+                stage1=STAGE1[args.stage1])
     with torch.cuda.stream(stream):
         sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
     n = sim.n
@@ -321,7 +323,7 @@ def run_ours(args, rank, world, dist):
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
                        "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle],
-                       "precond": args.precond, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
+                       "precond": args.precond, "stage1": args.stage1, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
                        "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
                        "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
             "krylov_iters_per_newton": round(krylov / args.steps, 2),
@@ -501,7 +503,7 @@ def run_batch(args):
     torch.cuda.set_device(0)
     prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
     opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
-               autotune=args.autotune)
+               autotune=args.autotune, stage1=STAGE1[args.stage1])
     members = [G.scenario_member(i) for i in range(args.members)]
     cells = [sc["nx"] * sc["ny"] * sc["nz"] for sc in members]
     out = {}
@@ -539,7 +541,7 @@ def run_serve(args):
     torch.cuda.set_device(0)
     prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
     opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
-               autotune=args.autotune)
+               autotune=args.autotune, stage1=STAGE1[args.stage1])
     u = uniform01(5, 9, 2 * args.requests)
     reqs = []
     for r in range(args.requests):
@@ -605,6 +607,8 @@ def main():
     ap.add_argument("--amg-pre", type=int, default=2)
     ap.add_argument("--amg-post", type=int, default=2)
     ap.add_argument("--amg-cycle", type=int, default=1)
+    ap.add_argument("--stage1", default="ilu0", choices=["bjacobi", "ilu0"],
+                    help="local solve of the preconditioner (CPR first stage)")
     ap.add_argument("--check-fp64", type=int, default=1,
                     help="mixed precision: state the error against the FP64 path on one step")
     ap.add_argument("--forcing-form", type=int, default=3, choices=[1, 2, 3],

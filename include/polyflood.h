@@ -52,6 +52,11 @@ enum { PF_DIR_X = 0, PF_DIR_Y = 1, PF_DIR_Z = 2 };
 enum { PF_CTRL_BHP = 0, PF_CTRL_WRATE = 1, PF_CTRL_ORATE = 2, PF_CTRL_LRATE = 3 };
 enum { PF_PREC_FP64 = 0, PF_PREC_MIXED = 1 };
 enum { PF_PC_BJACOBI = 0, PF_PC_CPR = 1 };
+/* Local (first-stage) solve of the preconditioner: the restricted additive
+ * Schwarz step of CPR-FP (Alg. 2) with one subdomain per GPU, solved by
+ * block-Jacobi (3x3 diagonal blocks) or by block ILU(0) in red-black order
+ * (cells coloured by (i + j + k) mod 2; no fill between cells of a colour). */
+enum { PF_S1_BJACOBI = 0, PF_S1_ILU0 = 1 };
 enum { PF_MIX_NONLINEAR = 0, PF_MIX_LINEAR = 1 };
 
 /* Rock, fluid, relative permeability and polymer constants (Sec. 2.1-2.3).
@@ -103,14 +108,30 @@ typedef struct pf_model_desc {
   pf_physics phys;
   int n_wells;
   const pf_well_desc* wells;    /* host [n_wells] */
+  /* Optional tables (Sec. 2.2: relative permeability and capillary pressure
+   * as functions of saturation; Sec. 2.3: adsorption "in the form of a table"
+   * and the water viscosity multiplier of the polymer solution).  Between
+   * knots the value is the segment's straight line (its slope is the
+   * derivative, also at a knot); below the first and from the last knot on,
+   * the end value with derivative 0.  At most PF_MAX_KNOTS knots each; the
+   * abscissae strictly increase.  n_sat = 0: the Corey curves of phys. */
+  int n_sat;
+  const double* sat_table;      /* host [n_sat][4]: S_w in [0, 1], k_rw >= 0, k_ro >= 0, P_c [Pa] */
+  /* n_poly = 0: Langmuir and the mixing rule of phys.  Otherwise
+   * mu_m = mu_w * multiplier(C), A_d = A_d(C) [kg/m^3 rock] and
+   * A_d,max = the largest tabulated A_d (for R_k). */
+  int n_poly;
+  const double* poly_table;     /* host [n_poly][3]: C >= 0, multiplier > 0, A_d >= 0 */
 } pf_model_desc;
+
+#define PF_MAX_KNOTS 64
 
 typedef struct pf_solver_opts {
   int precision;        /* PF_PREC_FP64: all arithmetic FP64.  PF_PREC_MIXED:
                            FP32 Jacobian storage and assembly derivatives,
                            FP32 preconditioner; residual, norms, Krylov basis
                            and orthogonalisation stay FP64. */
-  int precond;          /* PF_PC_BJACOBI or PF_PC_CPR (Alg. 2) */
+  int precond;          /* PF_PC_BJACOBI (the local solve alone) or PF_PC_CPR (Alg. 2) */
   int gmres_restart;    /* Krylov basis size m (default 30) */
   int gmres_max_iter;   /* cap on Krylov iterations per linear solve (default 300) */
   int newton_max_iter;  /* cap on Newton iterations per step (default 25) */
@@ -132,6 +153,8 @@ typedef struct pf_solver_opts {
                            2: (|b^l| - |r^{l-1}|) / |b^{l-1}| (one extra SpMV);
                            3: 0.5 (|b^l| / |b^{l-1}|)^((1 + sqrt 5) / 2), the
                               paper's choice.  b = -R; 2-norms over all unknowns. */
+  int stage1;           /* PF_S1_BJACOBI or PF_S1_ILU0: the local solve, alone (PF_PC_BJACOBI)
+                           or as the first stage of CPR (default PF_S1_ILU0) */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
@@ -225,6 +248,9 @@ pf_status pf_assemble(pf_sim* s);
 pf_status pf_export_system(pf_sim* s, double* R, double* Jc, double* Jw_b, double* Jw_c, double* Jw_d);
 /* y = J x with the assembled Jacobian (host x[3N+W], host y[3N+W]). */
 pf_status pf_apply_jacobian(pf_sim* s, const double* x, double* y);
+/* z = M^-1 v with the configured preconditioner, set up from the assembled
+ * Jacobian (host v, z of length 3N+W; a test hook). */
+pf_status pf_apply_preconditioner(pf_sim* s, const double* v, double* z);
 /* Solves J x = b with the configured preconditioned Krylov method to relative
  * tolerance rtol (host b, x of length 3N+W).  *iters and *rel_res may be NULL. */
 pf_status pf_solve_linear(pf_sim* s, const double* b, double* x, double rtol, int* iters, double* rel_res);
@@ -300,6 +326,27 @@ typedef struct pf_run_report {
 pf_status pf_run_schedule(pf_sim* s, const pf_schedule* sched, int max_cuts, pf_run_report* rep);
 /* Message of the last failed runtime call (pf_run_schedule, pf_batch_*, pf_server_*) on this thread. */
 const char* pf_runtime_last_error(void);
+
+/* Capillary-gravity equilibrium initial state (Sec. 4.1.3): fills p0 (oil
+ * pressure) and s0 (water saturation), host arrays [N], for the grid, rock,
+ * fluid and capillary data of m (its own p0, s0, c0 and wells are ignored
+ * and may be NULL / 0).
+ *   - Oil pressure: from (datum_depth, datum_p) to the centre of the layer
+ *     holding the datum along dP/dz = g rho_o(P) (closed form for the linear
+ *     density law), then layer to layer in each column so that the discrete
+ *     oil potential difference of every vertical face is zero with the
+ *     discretisation's face density (reference-pore-volume weighted).
+ *   - Water pressure: P_w = P_o at contact_depth (the free water level), then
+ *     the same construction for water.
+ *   - S_w = the largest S in [0, 1] with P_c(S) >= P_o - P_w (P_c must not
+ *     increase with S), or the first saturation knot / swc when no S
+ *     qualifies; where P_c(S_w) exceeds P_o - P_w (below the contact) the oil
+ *     pressure is set to P_w + P_c(S_w).
+ * With layers of uniform porosity and no wells, the state is a rest state of
+ * the discrete equations.  Host code only (no device work).  PF_EINVAL on
+ * invalid data or an increasing P_c, with the message in pf_last_error. */
+pf_status pf_equilibrium_init(const pf_model_desc* m, double datum_depth, double datum_p, double contact_depth,
+                              double* p0, double* s0);
 
 /* Device bytes pf_create would allocate for this model and these options
  * (one arena per simulator; used for admission by footprint). */

@@ -20,6 +20,7 @@ PF_DIR = {"x": 0, "y": 1, "z": 2}
 PF_CTRL = {"bhp": 0, "wrate": 1, "orate": 2, "lrate": 3}
 PF_PREC_FP64, PF_PREC_MIXED = 0, 1
 PF_PC_BJACOBI, PF_PC_CPR = 0, 1
+PF_S1_BJACOBI, PF_S1_ILU0 = 0, 1
 PF_KT = {"spmv": 0, "props": 1, "face": 2, "gather": 3, "wells": 4, "ortho": 5, "precond": 6}
 
 _STATUS = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ENOT_CONVERGED", 4: "PF_ETIMEOUT",
@@ -53,7 +54,8 @@ class pf_model_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("top", C.c_double),
                 ("kx", _dp), ("ky", _dp), ("kz", _dp), ("phi", _dp), ("p0", _dp), ("s0", _dp), ("c0", _dp),
-                ("phys", pf_physics), ("n_wells", C.c_int), ("wells", C.POINTER(pf_well_desc))]
+                ("phys", pf_physics), ("n_wells", C.c_int), ("wells", C.POINTER(pf_well_desc)),
+                ("n_sat", C.c_int), ("sat_table", _dp), ("n_poly", C.c_int), ("poly_table", _dp)]
 
 
 class pf_solver_opts(C.Structure):
@@ -62,7 +64,8 @@ class pf_solver_opts(C.Structure):
                 ("lin_rtol", C.c_double), ("newton_tol", C.c_double), ("ds_max", C.c_double),
                 ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
-                ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int)]
+                ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int),
+                ("stage1", C.c_int)]
 
 
 class pf_tuning(C.Structure):
@@ -144,6 +147,9 @@ def lib():
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
             "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
+            "pf_apply_preconditioner": ([vp, _dp, _dp], C.c_int),
+            "pf_equilibrium_init": ([C.POINTER(pf_model_desc), C.c_double, C.c_double, C.c_double, _dp, _dp],
+                                    C.c_int),
             "pf_run_schedule": ([vp, C.POINTER(pf_schedule), C.c_int, C.POINTER(pf_run_report)], C.c_int),
             "pf_runtime_last_error": ([], C.c_char_p),
             "pf_footprint": ([C.POINTER(pf_model_desc), C.POINTER(pf_solver_opts), C.POINTER(C.c_size_t)],
@@ -228,11 +234,31 @@ class Model:
         self.keep.append(wells)
         d.n_wells = nw
         d.wells = C.cast(wells, C.POINTER(pf_well_desc))
+        ph = sc["physics"]
+        if ph.get("sat_table") is not None:
+            t = arr(np.asarray(ph["sat_table"], dtype=np.float64).reshape(-1, 4))
+            d.n_sat, d.sat_table = t.shape[0], _ptr(t)
+        if ph.get("poly_table") is not None:
+            t = arr(np.asarray(ph["poly_table"], dtype=np.float64).reshape(-1, 3))
+            d.n_poly, d.poly_table = t.shape[0], _ptr(t)
         self.desc = d
 
     def _keep(self, a):
         self.keep.append(a)
         return a
+
+
+def equilibrium_init(sc, datum_depth, datum_p, contact_depth):
+    """Capillary-gravity equilibrium (P_o, S_w) per cell for the scenario's
+    grid, rock and fluids (pf_equilibrium_init; host code in the library)."""
+    m = Model(dict(sc, P0=np.zeros(sc["nx"] * sc["ny"] * sc["nz"]), S0=np.zeros(sc["nx"] * sc["ny"] * sc["nz"]),
+                   C0=np.zeros(sc["nx"] * sc["ny"] * sc["nz"])))
+    n = sc["nx"] * sc["ny"] * sc["nz"]
+    P = np.empty(n)
+    S = np.empty(n)
+    _check(lib().pf_equilibrium_init(C.byref(m.desc), float(datum_depth), float(datum_p), float(contact_depth),
+                                     _ptr(P), _ptr(S)))
+    return P, S
 
 
 def controls_array(controls):
@@ -314,6 +340,12 @@ class Simulator:
         y = np.empty(self.nunk)
         _check(lib().pf_apply_jacobian(self.h, _ptr(x), _ptr(y)))
         return y
+
+    def apply_preconditioner(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        z = np.empty(self.nunk)
+        _check(lib().pf_apply_preconditioner(self.h, _ptr(v), _ptr(z)))
+        return z
 
     def solve_linear(self, b, rtol):
         b = np.ascontiguousarray(b, dtype=np.float64)

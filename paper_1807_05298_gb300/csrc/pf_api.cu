@@ -22,6 +22,10 @@ static pf_status fail(pf_status st, const std::string& msg) {
   return st;
 }
 
+namespace pf {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pf
+
 #define PF_CUDA(call)                                                                       \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
@@ -105,6 +109,8 @@ struct pf_sim {
   double prev_norm = -1.0;      // |b^{l-1}| of the previous Newton iteration (< 0: none)
   double prev_lin_norm = 0.0;   // |r^{l-1}| (forcing form 2)
   double* rlin = nullptr;       // r^{l-1} (forcing form 1)
+  double* d_sat = nullptr;      // saturation table (structure of arrays with slopes)
+  double* d_poly = nullptr;     // polymer table
   int iter_in_step = 0;
 };
 
@@ -212,6 +218,32 @@ Phys derive_phys(const pf_physics& p) {
   return ph;
 }
 
+// Table sizes and, with a polymer table, A_d,max = the largest tabulated A_d
+// (the device pointers are set once the arena exists).
+void set_tables(Phys& ph, const pf_model_desc& m) {
+  ph.n_sat = m.n_sat;
+  ph.n_poly = m.n_poly;
+  if (m.n_poly > 0) {
+    double amax = 0.0;
+    for (int k = 0; k < m.n_poly; ++k) amax = std::max(amax, m.poly_table[3 * k + 2]);
+    ph.rk_coef = amax > 0.0 ? (m.phys.rrf - 1.0) / amax : 0.0;
+  }
+}
+
+// Structure-of-arrays copy of a table with its segment slopes: `cols` value
+// columns after the abscissa; out = [x, y_1..y_cols, slope_1..slope_cols],
+// each K long (the last slope, beyond the table, is 0).
+std::vector<double> table_soa(const double* rows, int K, int cols) {
+  const int w = cols + 1;
+  std::vector<double> out((size_t)(2 * cols + 1) * K, 0.0);
+  for (int k = 0; k < K; ++k)
+    for (int c = 0; c <= cols; ++c) out[(size_t)c * K + k] = rows[w * k + c];
+  for (int k = 0; k + 1 < K; ++k)
+    for (int c = 1; c <= cols; ++c)
+      out[(size_t)(cols + c) * K + k] = (rows[w * (k + 1) + c] - rows[w * k + c]) / (rows[w * (k + 1)] - rows[w * k]);
+  return out;
+}
+
 pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
   if (!m) return fail(PF_EINVAL, "model description is NULL");
   if (m->nx < 1 || m->ny < 1 || m->nz < 1) return fail(PF_EINVAL, "grid dimensions must be >= 1");
@@ -234,6 +266,22 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     return fail(PF_EINVAL, "invalid fluid or polymer constants");
   if (p.ads_a < 0.0 || p.ads_b < 0.0 || p.ipv < 0.0 || p.ipv >= 1.0 || p.rrf < 1.0 || p.nw < 1.0 || p.no < 1.0)
     return fail(PF_EINVAL, "invalid adsorption, IPV, RRF or Corey exponent");
+  if (m->n_sat < 0 || m->n_sat > PF_MAX_KNOTS || (m->n_sat > 0 && !m->sat_table))
+    return fail(PF_EINVAL, "invalid saturation table size");
+  for (int k = 0; k < m->n_sat; ++k) {
+    const double* r = m->sat_table + 4 * k;
+    if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]) || !std::isfinite(r[3]) || r[0] < 0.0 ||
+        r[0] > 1.0 || r[1] < 0.0 || r[2] < 0.0 || (k > 0 && !(r[0] > r[-4])))
+      return fail(PF_EINVAL, "saturation table row " + std::to_string(k) + " is invalid");
+  }
+  if (m->n_poly < 0 || m->n_poly > PF_MAX_KNOTS || (m->n_poly > 0 && !m->poly_table))
+    return fail(PF_EINVAL, "invalid polymer table size");
+  for (int k = 0; k < m->n_poly; ++k) {
+    const double* r = m->poly_table + 3 * k;
+    if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]) || r[0] < 0.0 || !(r[1] > 0.0) ||
+        r[2] < 0.0 || (k > 0 && !(r[0] > r[-3])))
+      return fail(PF_EINVAL, "polymer table row " + std::to_string(k) + " is invalid");
+  }
   if (m->n_wells < 0 || (m->n_wells > 0 && !m->wells)) return fail(PF_EINVAL, "invalid well list");
   std::vector<char> seen((size_t)n, 0);
   for (int w = 0; w < m->n_wells; ++w) {
@@ -259,6 +307,7 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (o->amg_pre_sweeps < 0 || o->amg_post_sweeps < 0 || o->amg_coarse_size < 1)
       return fail(PF_EINVAL, "invalid multigrid parameters");
     if (o->forcing_form < 1 || o->forcing_form > 3) return fail(PF_EINVAL, "forcing_form must be 1, 2 or 3");
+    if (o->stage1 != PF_S1_BJACOBI && o->stage1 != PF_S1_ILU0) return fail(PF_EINVAL, "invalid stage1");
   }
   return PF_OK;
 }
@@ -328,6 +377,8 @@ size_t carve(pf_sim* s, char* base) {
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
   s->red_counter = c.take<unsigned int>(64);
+  s->d_sat = s->ph.n_sat > 0 ? c.take<double>((size_t)7 * s->ph.n_sat) : nullptr;
+  s->d_poly = s->ph.n_poly > 0 ? c.take<double>((size_t)5 * s->ph.n_poly) : nullptr;
   if (s->opts.precond == PF_PC_CPR) cpr_carve(s->cpr, s->g, s->mixed, c.off, base);
   return align_up(c.off, 256);
 }
@@ -381,13 +432,23 @@ pf_status spmv(pf_sim* s, const double* xin, double* y) {
 
 pf_status precond_setup(pf_sim* s) {
   const Wells w = wells_view(s);
-  if (s->mixed)
-    launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
-                                       (float*)s->Dwinv, s->stream);
-  else
-    launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
-                                         (double*)s->Dwinv, s->stream);
-  PF_LAUNCHED(1 + (s->nw > 0));
+  const bool ilu = s->opts.stage1 == PF_S1_ILU0;
+  if (s->mixed) {
+    if (ilu)
+      launch_ilu_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
+                                     (float*)s->Dwinv, s->stream);
+    else
+      launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
+                                         (float*)s->Dwinv, s->stream);
+  } else {
+    if (ilu)
+      launch_ilu_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
+                                       (double*)s->Dwinv, s->stream);
+    else
+      launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
+                                           (double*)s->Dwinv, s->stream);
+  }
+  PF_LAUNCHED(1 + (s->nw > 0) + (ilu ? 1 : 0));
   if (s->opts.precond == PF_PC_CPR) {
     int k = 0;
     cpr_setup(s->cpr, s->g, s->ph, s->phi_r, wells_view(s), s->mixed, s->J, s->Bw, s->Dw, s->stream, &k);
@@ -406,9 +467,21 @@ pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullp
     PF_LAUNCHED(k);
     return PF_OK;
   }
-  if (s->mixed) launch_bjacobi_apply<float>(s->g, s->nw, (const float*)s->Dinv, (const float*)s->Dwinv, v, z, s->stream);
-  else launch_bjacobi_apply<double>(s->g, s->nw, (const double*)s->Dinv, (const double*)s->Dwinv, v, z, s->stream);
-  PF_LAUNCHED(1);
+  if (s->opts.stage1 == PF_S1_ILU0) {
+    if (s->mixed)
+      launch_ilu_apply<float, float, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
+                                             (const float*)s->Dwinv, v, z, s->stream);
+    else
+      launch_ilu_apply<double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
+                                               (const double*)s->Dwinv, v, z, s->stream);
+    PF_LAUNCHED(3);
+  } else {
+    if (s->mixed)
+      launch_bjacobi_apply<float>(s->g, s->nw, (const float*)s->Dinv, (const float*)s->Dwinv, v, z, s->stream);
+    else
+      launch_bjacobi_apply<double>(s->g, s->nw, (const double*)s->Dinv, (const double*)s->Dwinv, v, z, s->stream);
+    PF_LAUNCHED(1);
+  }
   if (s->mixed && zf) {
     launch_to_f32(s->nunk, z, zf, s->stream);
     PF_LAUNCHED(1);
@@ -669,6 +742,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->amg_cycle = 1;
   o->autotune = 0;
   o->forcing_form = 3;
+  o->stage1 = PF_S1_ILU0;
   return PF_OK;
 }
 
@@ -696,6 +770,7 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   g.dx = m->dx; g.dy = m->dy; g.dz = m->dz; g.top = m->top;
   g.V = m->dx * m->dy * m->dz;
   s->ph = derive_phys(m->phys);
+  set_tables(s->ph, *m);
   s->nw = m->n_wells;
   s->h_ptr.assign(s->nw + 1, 0);
   for (int w = 0; w < s->nw; ++w) s->h_ptr[w + 1] = s->h_ptr[w] + m->wells[w].n_perf;
@@ -764,6 +839,7 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   s->h_W.assign(Wsc.begin(), Wsc.begin() + s->nw);
   // device arena
   s->cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
+  s->cpr.ilu = opts.stage1 == PF_S1_ILU0;
   s->arena_bytes = carve(s, nullptr);
   {
     // stream-ordered allocation: no device-wide synchronisation, so creating
@@ -810,6 +886,18 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   PF_CUDA(cudaMemcpyAsync(s->inv_pv, inv_pv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
   PF_CUDA(cudaMemcpyAsync(s->x, x0.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, st));
   PF_CUDA(cudaMemcpyAsync(s->w_ptr, s->h_ptr.data(), (s->nw + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<double> sat_soa, poly_soa;   // live until the stream synchronises below
+  if (m->n_sat > 0) {
+    sat_soa = table_soa(m->sat_table, m->n_sat, 3);
+    PF_CUDA(cudaMemcpyAsync(s->d_sat, sat_soa.data(), sat_soa.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    s->ph.sat = s->d_sat;
+  }
+  if (m->n_poly > 0) {
+    poly_soa = table_soa(m->poly_table, m->n_poly, 2);
+    PF_CUDA(cudaMemcpyAsync(s->d_poly, poly_soa.data(), poly_soa.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            st));
+    s->ph.poly = s->d_poly;
+  }
   if (s->nw > 0) {
     PF_CUDA(cudaMemcpyAsync(s->w_kind, kind.data(), s->nw * sizeof(int), cudaMemcpyHostToDevice, st));
     PF_CUDA(cudaMemcpyAsync(s->w_cell, cell.data(), s->npf * sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -848,6 +936,8 @@ pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* 
   tmp.g.nxy = (long long)m->nx * m->ny;
   tmp.g.n = tmp.g.nxy * m->nz;
   tmp.nw = m->n_wells;
+  tmp.ph.n_sat = m->n_sat;
+  tmp.ph.n_poly = m->n_poly;
   tmp.npf = 0;
   for (int w = 0; w < m->n_wells; ++w) tmp.npf += m->wells[w].n_perf;
   tmp.nunk = 3 * tmp.g.n + tmp.nw;
@@ -1279,6 +1369,19 @@ pf_status pf_apply_jacobian(pf_sim* s, const double* xh, double* yh) {
   PF_CUDA(cudaMemcpyAsync(s->tmp, xh, s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
   if ((rc = spmv(s, s->tmp, s->r)) != PF_OK) return rc;
   PF_CUDA(cudaMemcpyAsync(yh, s->r, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PF_CUDA(cudaStreamSynchronize(s->stream));
+  return PF_OK;
+}
+
+pf_status pf_apply_preconditioner(pf_sim* s, const double* vh, double* zh) {
+  pf_status rc = check(s);
+  if (rc != PF_OK) return rc;
+  if (!s->assembled) return fail(PF_EINVAL, "nothing assembled");
+  if (!vh || !zh) return fail(PF_EINVAL, "NULL vector");
+  if ((rc = precond_setup(s)) != PF_OK) return rc;
+  PF_CUDA(cudaMemcpyAsync(s->b, vh, s->nunk * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  if ((rc = precond_apply(s, s->b, s->dx)) != PF_OK) return rc;
+  PF_CUDA(cudaMemcpyAsync(zh, s->dx, s->nunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   PF_CUDA(cudaStreamSynchronize(s->stream));
   return PF_OK;
 }

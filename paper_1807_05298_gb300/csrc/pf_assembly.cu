@@ -42,42 +42,87 @@ __device__ __forceinline__ double powi_or_pow(double b, double e) {
   return pow(b, e);
 }
 
+// Segment of a strictly increasing abscissa table: k with x[k] <= u < x[k+1],
+// -1 below the first knot, K - 1 from the last knot on (binary search).
+__device__ __forceinline__ int table_segment(const double* __restrict__ x, int K, double u) {
+  if (u < __ldg(x)) return -1;
+  if (u >= __ldg(x + K - 1)) return K - 1;
+  int lo = 0, hi = K - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(x + mid) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Value and derivative of column col (1-based) of a structure-of-arrays
+// table with `cols` value columns: the segment's line inside the table, the
+// end value with derivative 0 outside it.
+__device__ __forceinline__ void table_eval(const double* __restrict__ T, int K, int cols, int col, int k, double u,
+                                           double& v, double& d) {
+  const double* y = T + (size_t)col * K;
+  if (k < 0) { v = __ldg(y); d = 0.0; return; }
+  if (k >= K - 1) { v = __ldg(y + K - 1); d = 0.0; return; }
+  const double sl = __ldg(T + (size_t)(cols + col) * K + k);
+  v = (u - __ldg(T + k)) * sl + __ldg(y + k);
+  d = sl;
+}
+
 __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P, double S, double C,
                                           CellEval& c) {
   c.phi = phi_r + ph.c_r * (P - ph.p_r);
   c.dphi = ph.c_r;
   c.rho_o = ph.rho_o * (1.0 + ph.c_o * (P - ph.p_ref));
   c.drho_o = ph.rho_o * ph.c_o;
-  // normalised saturation, clipped; derivative of the interior formula on [0, 1]
-  double sn = (S - ph.swc) * ph.inv_den, dsn = ph.inv_den;
-  if (sn < 0.0) { sn = 0.0; dsn = 0.0; }
-  if (sn > 1.0) { sn = 1.0; dsn = 0.0; }
-  const double so = 1.0 - sn;
-  c.krw = ph.krw_max * powi_or_pow(sn, ph.nw);
-  c.dkrw = (sn == 0.0 && ph.nw > 1.0) ? 0.0 : ph.krw_max * ph.nw * powi_or_pow(sn, ph.nw - 1.0) * dsn;
-  c.kro = ph.kro_max * powi_or_pow(so, ph.no);
-  c.dkro = (so == 0.0 && ph.no > 1.0) ? 0.0 : -ph.kro_max * ph.no * powi_or_pow(so, ph.no - 1.0) * dsn;
   double pc = 0.0, dpc = 0.0;
-  if (ph.pc_e != 0.0) {
-    pc = ph.pc_e * powi_or_pow(so, ph.pc_n);
-    dpc = (so == 0.0 && ph.pc_n > 1.0) ? 0.0 : -ph.pc_e * ph.pc_n * powi_or_pow(so, ph.pc_n - 1.0) * dsn;
+  if (ph.n_sat > 0) {  // tabulated k_rw, k_ro, P_c of S_w
+    const int k = table_segment(ph.sat, ph.n_sat, S);
+    table_eval(ph.sat, ph.n_sat, 3, 1, k, S, c.krw, c.dkrw);
+    table_eval(ph.sat, ph.n_sat, 3, 2, k, S, c.kro, c.dkro);
+    table_eval(ph.sat, ph.n_sat, 3, 3, k, S, pc, dpc);
+  } else {
+    // normalised saturation, clipped; derivative of the interior formula on [0, 1]
+    double sn = (S - ph.swc) * ph.inv_den, dsn = ph.inv_den;
+    if (sn < 0.0) { sn = 0.0; dsn = 0.0; }
+    if (sn > 1.0) { sn = 1.0; dsn = 0.0; }
+    const double so = 1.0 - sn;
+    c.krw = ph.krw_max * powi_or_pow(sn, ph.nw);
+    c.dkrw = (sn == 0.0 && ph.nw > 1.0) ? 0.0 : ph.krw_max * ph.nw * powi_or_pow(sn, ph.nw - 1.0) * dsn;
+    c.kro = ph.kro_max * powi_or_pow(so, ph.no);
+    c.dkro = (so == 0.0 && ph.no > 1.0) ? 0.0 : -ph.kro_max * ph.no * powi_or_pow(so, ph.no - 1.0) * dsn;
+    if (ph.pc_e != 0.0) {
+      pc = ph.pc_e * powi_or_pow(so, ph.pc_n);
+      dpc = (so == 0.0 && ph.pc_n > 1.0) ? 0.0 : -ph.pc_e * ph.pc_n * powi_or_pow(so, ph.pc_n - 1.0) * dsn;
+    }
   }
   c.Pw = P - pc;
   c.dPw_S = -dpc;
   c.rho_w = ph.rho_w * (1.0 + ph.c_w * (c.Pw - ph.p_ref));
   c.drho_wP = ph.rho_w * ph.c_w;
   c.drho_wS = ph.rho_w * ph.c_w * c.dPw_S;
-  // Langmuir adsorption and permeability reduction (one reciprocal: FP64
-  // division is costly on this part)
-  const double rden = 1.0 / (1.0 + ph.ads_b * C);
-  c.ads = ph.ads_a * C * rden;
-  c.dads = ph.ads_a * rden * rden;
-  c.Rk = 1.0 + ph.rk_coef * c.ads;
-  c.dRk = ph.rk_coef * c.dads;
-  // mixing rule
   const double beta = C * ph.inv_c_ref;
   double mu_m, dmu_m;
-  if (ph.mixing == PF_MIX_NONLINEAR) {
+  if (ph.n_poly > 0) {  // tabulated A_d(C) and water viscosity multiplier
+    const int k = table_segment(ph.poly, ph.n_poly, C);
+    double mult, dmult;
+    table_eval(ph.poly, ph.n_poly, 2, 1, k, C, mult, dmult);
+    table_eval(ph.poly, ph.n_poly, 2, 2, k, C, c.ads, c.dads);
+    mu_m = mult * ph.mu_w;
+    dmu_m = dmult * ph.mu_w;
+  } else {
+    // Langmuir adsorption (one reciprocal: FP64 division is costly on this part)
+    const double rden = 1.0 / (1.0 + ph.ads_b * C);
+    c.ads = ph.ads_a * C * rden;
+    c.dads = ph.ads_a * rden * rden;
+  }
+  // permeability reduction
+  c.Rk = 1.0 + ph.rk_coef * c.ads;
+  c.dRk = ph.rk_coef * c.dads;
+  // mixing rule (the table already gave mu_m)
+  if (ph.n_poly > 0) {
+    // mu_m, dmu_m from the viscosity multiplier above
+  } else if (ph.mixing == PF_MIX_NONLINEAR) {
     mu_m = exp(ph.ln_mu_w + beta * ph.ln_mu_ratio);
     dmu_m = mu_m * ph.ln_mu_ratio * ph.inv_c_ref;
   } else {

@@ -600,11 +600,17 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
 template <typename T>
 void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const void* Cw, const void* Dw,
              const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp, cudaStream_t st, int& k) {
-  // stage 1: y = D^{-1} f (cells and wells)
-  launch_bjacobi_apply<T>(g, w.nw, (const T*)Dinv, (const T*)Dwinv, v, z, st);
+  // stage 1: y = D^{-1} f, or the red-black block ILU(0) solve (cells; wells by their diagonal)
+  if (c.ilu) {
+    launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, st);
+    k += 3;
+  } else {
+    launch_bjacobi_apply<T>(g, w.nw, (const T*)Dinv, (const T*)Dwinv, v, z, st);
+    k += 1;
+  }
   // stage 2: r = f - J y, restricted to the pressure equation
   launch_spmv<T>(g, w, (const T*)J, (const T*)Bw, (const T*)Cw, (const T*)Dw, z, tmp, st);
-  k += 2 + (w.nw > 0);
+  k += 1 + (w.nw > 0);
   CprLevel& L0 = c.lev[0];
   k_restrict_top<T><<<grid_for(g.n, 256), 256, 0, st>>>(g.n, v, tmp, c.w_o, c.w_w, (T*)L0.b);
   k += 1;
@@ -694,10 +700,17 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
     float* zf = reinterpret_cast<float*>(tmp);
     CprLevel& L0 = c.lev[0];
     const int gb = grid_for(g.n + w.nw, 256);
-    k_stage1_f32<<<gb, 256, 0, st>>>(g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
+    if (c.ilu) {
+      launch_ilu_apply<float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv, (const float*)Dwinv, v, zf,
+                                            st);
+      k += 3;
+    } else {
+      k_stage1_f32<<<gb, 256, 0, st>>>(g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
+      k += 1;
+    }
     k_stage2_f32<<<grid_for(g.n, c.block_stage2), c.block_stage2, 0, st>>>(g, (const float*)J, zf, v, (float)c.w_o,
                                                                          (float)c.w_w, (float*)L0.b);
-    k += 2;
+    k += 1;
     if (w.nw > 0) {
       k_stage2_wells_f32<<<w.nw, 32, 0, st>>>(w, g.n, (const float*)Bw, zf, (float)c.w_o, (float)c.w_w,
                                               (float*)L0.b);

@@ -35,6 +35,7 @@ struct CprData {
   int nlev = 0;
   int pre = 1, post = 1, cycle_gamma = 1, coarse_limit = 64;
   int block_rbgs0 = 256, block_stage2 = 256;  // launch shapes of the finest smoother and stage 2
+  bool ilu = false;             // first stage: red-black block ILU(0) instead of block-Jacobi
   double w_o = 0.0, w_w = 0.0;
   std::vector<CprLevel> lev;
   void* coarse_inv = nullptr;   // [nc][nc] dense inverse of the coarsest matrix

@@ -25,7 +25,16 @@ struct Phys {
   double mu_p0_pow, mu_w_pow;    // mu_p0^(1-omega), mu_w^(1-omega)
   double inv_c_ref, inv_rho_w;   // 1 / c_ref, 1 / rho_w,ref
   double inv_mu_o;               // 1 / mu_o
+  // optional tables on the device, structure of arrays with the segment
+  // slopes: sat = S, k_rw, k_ro, P_c, then their slopes (7 x n_sat);
+  // poly = C, multiplier, A_d, then their slopes (5 x n_poly)
+  const double* sat = nullptr;
+  const double* poly = nullptr;
+  int n_sat = 0, n_poly = 0;
 };
+
+// Message returned by pf_last_error on this thread (set by host code outside pf_api.cu).
+void set_last_error(const std::string& msg);
 
 struct Grid {
   int nx, ny, nz;
@@ -71,6 +80,9 @@ struct Tuning {
 };
 
 // Launch helpers ------------------------------------------------------------
+// slots of one colour of the red-black ordering: ceil(nx / 2) per (j, k) row
+inline long long colour_slots_host(const Grid& g) { return (long long)((g.nx + 1) / 2) * g.ny * g.nz; }
+
 inline int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -116,6 +128,11 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
 template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
                           PT* Dwinv, cudaStream_t st);
+template <typename DT, typename PT>
+void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, cudaStream_t st);
+template <typename DT, typename PT, typename OT>
+void launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+                      cudaStream_t st);
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);

@@ -200,6 +200,24 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
 
 // (the inverse is formed in the storage precision PT: FP64 for the plain
 // path, FP32 for the mixed one)
+template <typename PT>
+__device__ __forceinline__ void inverse3(const PT a[9], PT inv[9]) {
+  const PT c00 = a[4] * a[8] - a[5] * a[7];
+  const PT c01 = a[5] * a[6] - a[3] * a[8];
+  const PT c02 = a[3] * a[7] - a[4] * a[6];
+  const PT det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  const PT id = (PT)1 / det;
+  inv[0] = c00 * id;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  inv[3] = c01 * id;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  inv[6] = c02 * id;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+}
+
 template <typename DT, typename PT>
 __global__ void __launch_bounds__(256) k_bjacobi_setup(long long n, const DT* __restrict__ J, PT* __restrict__ Dinv) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -207,23 +225,10 @@ __global__ void __launch_bounds__(256) k_bjacobi_setup(long long n, const DT* __
     PT a[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
-    const PT c00 = a[4] * a[8] - a[5] * a[7];
-    const PT c01 = a[5] * a[6] - a[3] * a[8];
-    const PT c02 = a[3] * a[7] - a[4] * a[6];
-    const PT det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    const PT id = (PT)1 / det;
     PT inv[9];
-    inv[0] = c00 * id;
-    inv[1] = (a[2] * a[7] - a[1] * a[8]) * id;
-    inv[2] = (a[1] * a[5] - a[2] * a[4]) * id;
-    inv[3] = c01 * id;
-    inv[4] = (a[0] * a[8] - a[2] * a[6]) * id;
-    inv[5] = (a[2] * a[3] - a[0] * a[5]) * id;
-    inv[6] = c02 * id;
-    inv[7] = (a[1] * a[6] - a[0] * a[7]) * id;
-    inv[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+    inverse3(a, inv);
 #pragma unroll
-    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = (PT)inv[e];
+    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
   }
 }
 
@@ -253,6 +258,165 @@ __global__ void __launch_bounds__(256) k_bjacobi_apply(long long n, int nw, cons
     z[3 * i + 1] = (double)D[3 * n] * r0 + (double)D[4 * n] * r1 + (double)D[5 * n] * r2;
     z[3 * i + 2] = (double)D[6 * n] * r0 + (double)D[7 * n] * r1 + (double)D[8 * n] * r2;
   }
+}
+
+// ---------------------------------------------------------------------------
+// block ILU(0) in red-black order: the local solve of the restricted additive
+// Schwarz stage of CPR-FP (Alg. 2) with one subdomain
+// ---------------------------------------------------------------------------
+// Colour of cell (i, j, k): (i + j + k) mod 2, red 0, black 1.  With the red
+// cells ordered first, the 7-point block pattern couples no two cells of one
+// colour, so ILU(0) keeps the red diagonal blocks D_r, replaces each black
+// one by D_b - sum_j J_bj D_j^-1 J_jb (fill between black cells dropped), and
+// its two triangular solves become three sweeps over one colour each:
+//   y_r = D_r^-1 f_r;   y_b = D'_b^-1 (f_b - sum_j J_bj y_j);
+//   y_r = D_r^-1 (f_r - sum_k J_rk y_k).
+// Well rows keep their scalar inverse, as in block-Jacobi.
+
+// The q-th cell of a colour: rows (j, k) of ceil(nx / 2) slots; in row (j, k)
+// the colour's cells are x = ((j + k + colour) & 1) + 2m.  False for a slot
+// past the row's end.  Consecutive threads take consecutive cells of a row.
+__device__ __forceinline__ bool colour_cell(const Grid& g, int colour, long long q, long long& i, int& x, int& y,
+                                            int& z) {
+  const unsigned int hx = ((unsigned int)g.nx + 1u) >> 1;
+  const unsigned int uq = (unsigned int)q;
+  const unsigned int row = uq / hx, m = uq - row * hx;
+  const unsigned int ny = (unsigned int)g.ny;
+  z = (int)(row / ny);
+  y = (int)(row - (unsigned int)z * ny);
+  x = (int)(((unsigned int)(y + z + colour) & 1u) + 2u * m);
+  if (x >= g.nx) return false;
+  i = (long long)x + (long long)g.nx * row;
+  return true;
+}
+
+__device__ __forceinline__ long long colour_slots(const Grid& g) {
+  return (long long)((g.nx + 1) / 2) * g.ny * g.nz;
+}
+
+// neighbour of (x, y, z) through slot s (s != SL_D); false outside the grid
+__device__ __forceinline__ bool slot_nbr(const Grid& g, int s, long long i, int x, int y, int z, long long& c) {
+  switch (s) {
+    case SL_XM: c = i - 1; return x > 0;
+    case SL_XP: c = i + 1; return x + 1 < g.nx;
+    case SL_YM: c = i - g.nx; return y > 0;
+    case SL_YP: c = i + g.nx; return y + 1 < g.ny;
+    case SL_ZM: c = i - g.nxy; return z > 0;
+    default: c = i + g.nxy; return z + 1 < g.nz;
+  }
+}
+
+// black diagonal blocks: D'_b = D_b - sum_j J_bj D_j^-1 J_jb, then inverted;
+// the red blocks' inverses (from k_bjacobi_setup) are read, not written
+template <typename DT, typename PT>
+__global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+  const long long n = g.n, nq = colour_slots(g);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long i;
+    int x, y, z;
+    if (!colour_cell(g, 1, q, i, x, y, z)) continue;
+    PT a[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
+#pragma unroll
+    for (int s = 1; s < SL_COUNT; ++s) {
+      long long c;
+      if (!slot_nbr(g, s, i, x, y, z, c)) continue;
+      const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
+      PT T[9];  // J_bj D_j^-1
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const PT b0 = (PT)J[((size_t)s * 9 + 3 * r) * n + i], b1 = (PT)J[((size_t)s * 9 + 3 * r + 1) * n + i],
+                 b2 = (PT)J[((size_t)s * 9 + 3 * r + 2) * n + i];
+#pragma unroll
+        for (int col = 0; col < 3; ++col)
+          T[3 * r + col] = b0 * Dinv[(size_t)col * n + c] + b1 * Dinv[(size_t)(3 + col) * n + c] +
+                           b2 * Dinv[(size_t)(6 + col) * n + c];
+      }
+#pragma unroll
+      for (int col = 0; col < 3; ++col) {
+        const PT u0 = (PT)J[((size_t)so * 9 + col) * n + c], u1 = (PT)J[((size_t)so * 9 + 3 + col) * n + c],
+                 u2 = (PT)J[((size_t)so * 9 + 6 + col) * n + c];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a[3 * r + col] -= T[3 * r] * u0 + T[3 * r + 1] * u1 + T[3 * r + 2] * u2;
+      }
+    }
+    PT inv[9];
+    inverse3(a, inv);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+  }
+}
+
+// first sweep: y_r = D_r^-1 f_r on red cells, and the well rows
+template <typename PT, typename OT>
+__global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, int nw, const PT* __restrict__ Dinv,
+                                                      const PT* __restrict__ Dwinv, const double* __restrict__ f,
+                                                      OT* __restrict__ y) {
+  const long long n = g.n, nq = colour_slots(g);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq + nw;
+       q += (long long)gridDim.x * blockDim.x) {
+    if (q >= nq) {
+      const long long w = q - nq;
+      y[3 * n + w] = (OT)((PT)Dwinv[w] * (PT)f[3 * n + w]);
+      continue;
+    }
+    long long i;
+    int x, yy, z;
+    if (!colour_cell(g, 0, q, i, x, yy, z)) continue;
+    const PT r0 = (PT)f[3 * i], r1 = (PT)f[3 * i + 1], r2 = (PT)f[3 * i + 2];
+    const PT* D = Dinv + i;
+    y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
+    y[3 * i + 1] = (OT)(D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2);
+    y[3 * i + 2] = (OT)(D[6 * n] * r0 + D[7 * n] * r1 + D[8 * n] * r2);
+  }
+}
+
+// y_i = D_i^-1 (f_i - sum over neighbours J_ij y_j) on the cells of one colour
+// (the neighbours all have the other colour)
+template <typename DT, typename PT, typename OT>
+__global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, const DT* __restrict__ J,
+                                                   const PT* __restrict__ Dinv, const double* __restrict__ f,
+                                                   OT* __restrict__ y) {
+  const long long n = g.n, nq = colour_slots(g);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long i;
+    int x, yy, z;
+    if (!colour_cell(g, colour, q, i, x, yy, z)) continue;
+    PT r0 = (PT)f[3 * i], r1 = (PT)f[3 * i + 1], r2 = (PT)f[3 * i + 2];
+#pragma unroll
+    for (int s = 1; s < SL_COUNT; ++s) {
+      long long c;
+      if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
+      const DT* B = J + (size_t)s * 9 * n + i;
+      const PT y0 = (PT)y[3 * c], y1 = (PT)y[3 * c + 1], y2 = (PT)y[3 * c + 2];
+      r0 -= (PT)B[0] * y0 + (PT)B[n] * y1 + (PT)B[2 * n] * y2;
+      r1 -= (PT)B[3 * n] * y0 + (PT)B[4 * n] * y1 + (PT)B[5 * n] * y2;
+      r2 -= (PT)B[6 * n] * y0 + (PT)B[7 * n] * y1 + (PT)B[8 * n] * y2;
+    }
+    const PT* D = Dinv + i;
+    y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
+    y[3 * i + 1] = (OT)(D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2);
+    y[3 * i + 2] = (OT)(D[6 * n] * r0 + D[7 * n] * r1 + D[8 * n] * r2);
+  }
+}
+
+template <typename DT, typename PT>
+void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
+                      cudaStream_t st) {
+  launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
+  k_ilu_setup_black<DT, PT><<<grid_for(colour_slots_host(g), 256), 256, 0, st>>>(g, J, Dinv);
+}
+
+template <typename DT, typename PT, typename OT>
+void launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+                      cudaStream_t st) {
+  const long long nq = colour_slots_host(g);
+  k_ilu_red_diag<PT, OT><<<grid_for(nq + nw, 256), 256, 0, st>>>(g, nw, Dinv, Dwinv, f, y);
+  k_ilu_sweep<DT, PT, OT><<<grid_for(nq, 256), 256, 0, st>>>(g, 1, J, Dinv, f, y);
+  k_ilu_sweep<DT, PT, OT><<<grid_for(nq, 256), 256, 0, st>>>(g, 0, J, Dinv, f, y);
 }
 
 template <typename PT>
@@ -500,6 +664,16 @@ template void launch_bjacobi_setup<double, double>(const Grid&, const Wells&, co
                                                    double*, cudaStream_t);
 template void launch_bjacobi_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                                  cudaStream_t);
+template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const double*, const double*, double*,
+                                               double*, cudaStream_t);
+template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
+                                             cudaStream_t);
+template void launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
+                                                       const double*, const double*, double*, cudaStream_t);
+template void launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,
+                                                    const double*, float*, cudaStream_t);
+template void launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
+                                                     const double*, double*, cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,

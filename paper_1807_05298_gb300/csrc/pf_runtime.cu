@@ -42,7 +42,7 @@ double now_s() {
 // requests after the caller's buffers are gone).
 struct OwnedModel {
   pf_model_desc desc{};
-  std::vector<double> kx, ky, kz, phi, p0, s0, c0;
+  std::vector<double> kx, ky, kz, phi, p0, s0, c0, sat, poly;
   std::vector<std::vector<int64_t>> cells;
   std::vector<std::vector<int>> dirs;
   std::vector<pf_well_desc> wells;
@@ -69,6 +69,14 @@ struct OwnedModel {
       }
     }
     desc.wells = wells.empty() ? nullptr : wells.data();
+    if (m.n_sat > 0 && m.sat_table) {
+      sat.assign(m.sat_table, m.sat_table + 4 * (size_t)m.n_sat);
+      desc.sat_table = sat.data();
+    }
+    if (m.n_poly > 0 && m.poly_table) {
+      poly.assign(m.poly_table, m.poly_table + 3 * (size_t)m.n_poly);
+      desc.poly_table = poly.data();
+    }
     controls.resize(s.n_periods);
     periods.resize(s.n_periods);
     for (int p = 0; p < s.n_periods; ++p) {

@@ -100,6 +100,13 @@ PHYS_VARIANTS = [
     G.default_physics(),
     G.default_physics(omega=0.6, pc_e=0.4 * BAR, mixing=1, ads_a=0.8, ads_b=4.0, rrf=2.3, ipv=0.15),
     G.default_physics(omega=0.3, nw=2.5, no=1.7, c_r=0.0, krw_max=0.6, kro_max=0.9),
+    # tabulated k_rw, k_ro, P_c (Sec. 2.2) and A_d, viscosity multiplier (Sec. 2.3)
+    G.default_physics(omega=0.7, rrf=1.9,
+                      sat_table=np.array([[0.1, 0.0, 1.0, 0.9 * BAR], [0.25, 0.02, 0.7, 0.5 * BAR],
+                                          [0.4, 0.1, 0.4, 0.3 * BAR], [0.6, 0.3, 0.12, 0.12 * BAR],
+                                          [0.85, 0.8, 0.0, 0.01 * BAR]]),
+                      poly_table=np.array([[0.0, 1.0, 0.0], [0.3, 1.8, 0.02], [1.0, 3.5, 0.05],
+                                           [2.5, 6.0, 0.065]])),
 ]
 
 
@@ -148,8 +155,9 @@ def test_assembly_degenerate_grids(B, shape):
     sim.close()
 
 
-@pytest.mark.parametrize("precond,cycle", [("bjacobi", 1), ("cpr", 1), ("cpr", 2)])
-def test_linear_solve_matches_direct(B, precond, cycle):
+@pytest.mark.parametrize("precond,cycle,stage1", [("bjacobi", 1, 0), ("cpr", 1, 0), ("cpr", 2, 0),
+                                                  ("bjacobi", 1, 1), ("cpr", 1, 1)])
+def test_linear_solve_matches_direct(B, precond, cycle, stage1):
     sc, ctl = ragged_scenario(nx=17, ny=9, nz=4)
     st = M.Setup(sc)
     rng = np.random.default_rng(3)
@@ -160,7 +168,7 @@ def test_linear_solve_matches_direct(B, precond, cycle):
     dt = 0.5 * DAY
     pc = B.PF_PC_CPR if precond == "cpr" else B.PF_PC_BJACOBI
     st, sim, R_o, J_o, R_g, J_g = assemble_both(B, sc, ctl, x_old, x, dt, gmres_max_iter=2000, precond=pc,
-                                                amg_cycle=cycle)
+                                                amg_cycle=cycle, stage1=stage1)
     b = -R_o
     xg, its, rr = sim.solve_linear(b, 1e-12)
     xo = spla.spsolve(J_o.tocsc(), b)
@@ -337,3 +345,95 @@ def test_forcing_term_forms_match_oracle(B, form):
     assert ok
     err = field_errors(n, xs[-1], x_o)
     assert max(err) <= 1e-6
+
+
+def test_equilibrium_state_is_a_rest_state_on_the_gpu(B):
+    """Capillary-gravity equilibrium (Sec. 4.1.3) from the library's host
+    initialiser, tabulated P_c: with no wells the GPU residual at that state
+    vanishes and a time step leaves it unchanged (Newton converges before
+    any update)."""
+    sat = np.array([[0.2, 0.0, 1.0, 1.2 * BAR], [0.45, 0.08, 0.45, 0.35 * BAR], [0.8, 0.6, 0.0, 0.0],
+                    [1.0, 1.0, 0.0, 0.0]])
+    ph = G.default_physics(sat_table=sat)
+    nx, ny, nz = 5, 4, 30
+    n = nx * ny * nz
+    phi = np.repeat(np.linspace(0.12, 0.3, nz), nx * ny)
+    k = np.repeat(np.exp(np.linspace(np.log(20.0), np.log(500.0), nz)), nx * ny) * G.MD
+    sched = [dict(n_steps=2, dt=10.0 * DAY, controls=[])]
+    sc = G.make_scenario(nx, ny, nz, 20.0, 20.0, 1.0, 2000.0, k, k, 0.1 * k, phi, ph, [], sched)
+    P, S = B.equilibrium_init(sc, 2005.0, 200.0 * BAR, 2022.0)
+    sc["P0"], sc["S0"] = P, S
+    st = M.Setup(sc)
+    x0 = M.initial_state(st)
+    sim = B.Simulator(sc, stream=B.current_stream_handle(), newton_tol=1e-10)
+    sim.set_controls([])
+    sim.begin_step(10.0 * DAY)
+    sim.assemble()
+    R_g = sim.export_system()[0]
+    assert M.scaled_residual(st, R_g, 10.0 * DAY, []) < 1e-11
+    sim.abort_step()
+    rc, rep = sim.step(10.0 * DAY)
+    assert rep.newton_iters == 0
+    assert np.array_equal(sim.get_x(), x0)
+    sim.close()
+
+
+def rb_block_ilu0_apply(sc, J_csr, v):
+    """Reference red-black block ILU(0) solve, written from its definition:
+    red cells (i + j + k even) first; the factor keeps the red diagonal
+    blocks and replaces each black one by D_b - sum_j J_bj D_j^-1 J_jb; then
+    forward and backward substitution.  Well rows: v_w / D_w."""
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    n = nx * ny * nz
+    J = J_csr.tocsr()
+    idx = np.arange(n)
+    i_, j_, k_ = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    red = (i_ + j_ + k_) % 2 == 0
+    blk = lambda r, c: J[3 * r:3 * r + 3, 3 * c:3 * c + 3].toarray()
+
+    def nbrs(c):
+        out = []
+        for d, (coord, lim, st_) in enumerate(((i_[c], nx, 1), (j_[c], ny, nx), (k_[c], nz, nx * ny))):
+            if coord > 0:
+                out.append(c - st_)
+            if coord < lim - 1:
+                out.append(c + st_)
+        return out
+    Dinv = {c: np.linalg.inv(blk(c, c)) for c in idx[red]}
+    Dp = {}
+    for c in idx[~red]:
+        D = blk(c, c)
+        for r in nbrs(c):
+            D = D - blk(c, r) @ Dinv[r] @ blk(r, c)
+        Dp[c] = np.linalg.inv(D)
+    f = v[:3 * n].reshape(n, 3)
+    y = np.zeros((n, 3))
+    for c in idx[red]:
+        y[c] = Dinv[c] @ f[c]
+    for c in idx[~red]:
+        y[c] = Dp[c] @ (f[c] - sum(blk(c, r) @ y[r] for r in nbrs(c)))
+    for c in idx[red]:
+        y[c] = Dinv[c] @ (f[c] - sum(blk(c, r) @ y[r] for r in nbrs(c)))
+    out = np.empty_like(v)
+    out[:3 * n] = y.ravel()
+    diag = J.diagonal()
+    out[3 * n:] = v[3 * n:] / diag[3 * n:]
+    return out
+
+
+@pytest.mark.parametrize("shape", [(7, 5, 4), (9, 1, 3), (3, 3, 5), (4, 3, 1)])
+def test_block_ilu0_matches_its_definition(B, shape):
+    """The red-black block ILU(0) first stage (PF_S1_ILU0) against a dense
+    reference of the same factorisation on the GPU's own Jacobian, FP64."""
+    nx, ny, nz = shape
+    sc, ctl = ragged_scenario(nx=nx, ny=ny, nz=nz)
+    st = M.Setup(sc)
+    rng = np.random.default_rng(8)
+    x0 = M.initial_state(st)
+    x_old, x = random_state(st, rng, x0), random_state(st, rng, x0)
+    st, sim, R_o, J_o, R_g, J_g = assemble_both(B, sc, ctl, x_old, x, DAY, precond=B.PF_PC_BJACOBI, stage1=1)
+    v = rng.normal(size=st.nunk)
+    z_g = sim.apply_preconditioner(v)
+    z_r = rb_block_ilu0_apply(sc, J_g, v)
+    assert np.allclose(z_g, z_r, rtol=1e-10, atol=1e-12 * np.abs(z_r).max())
+    sim.close()
