@@ -141,7 +141,7 @@ typedef struct pf_solver_opts {
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
   double dc_frac;       /* per-iteration concentration change limit as a fraction of c_ref (default 0.5) */
-  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps (default 2, 2) */
+  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps on the finest level (default 2, 2) */
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
   int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
@@ -155,6 +155,8 @@ typedef struct pf_solver_opts {
                               paper's choice.  b = -R; 2-norms over all unknowns. */
   int stage1;           /* PF_S1_BJACOBI or PF_S1_ILU0: the local solve, alone (PF_PC_BJACOBI)
                            or as the first stage of CPR (default PF_S1_ILU0) */
+  int amg_coarse_sweeps;  /* pre- and post-smoothing sweeps on the levels below the finest;
+                             -1: the finest level's counts (default -1) */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
@@ -177,6 +179,13 @@ typedef struct pf_step_report {
   int newton_iters, krylov_iters, converged;
   double res_scaled;
 } pf_step_report;
+
+/* Process-wide: launch the solver's kernels with programmatic dependent
+ * launch (a kernel may be scheduled while its predecessor in the stream
+ * drains; it waits for that grid's completion before reading anything).  On
+ * by default; results do not depend on it.  Affects launches and graphs
+ * captured after the call. */
+pf_status pf_set_programmatic_launch(int on);
 
 /* Library version string (static storage). */
 const char* pf_version(void);
@@ -278,8 +287,8 @@ pf_status pf_kernel_timing_enable(pf_sim* s, int on);
 pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* total_ms);
 /* Launch-shape tuner (not in the paper: a GB300 launch detail).  Times block
  * sizes 64, 128 and 256 for the per-cell kernels (properties, face flux,
- * gather, SpMV, FP32 stage 2, finest-level smoother) on s's own data and keeps
- * the fastest.  The FP64 SpMV also tries one thread per block row (reported
+ * gather, SpMV, stage 2, finest-level smoother) and the two- or three-launch
+ * ILU(0) solve on s's own data and keeps the fastest.  The FP64 SpMV also tries one thread per block row (reported
  * as a negative spmv: -96, -192 or -384 threads per block).  Each row's
  * arithmetic does not depend on the launch shape, so results are
  * bit-identical whatever is chosen; reduction grids are never tuned for the
@@ -287,12 +296,17 @@ pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* tota
  * inside one); out may be NULL. */
 typedef struct pf_tuning {
   int props, face, gather, spmv, stage2, rbgs;
+  int block_cells;  /* CPR: multigrid levels of at most this many cells (and all coarser ones) run in
+                       one thread block (default 256 in FP64, 4096 in FP32; the tuner keeps it) */
+  int ilu_fused;    /* ILU(0) solve in two launches, the diagonal red sweep folded into the black
+                       sweep (1), or three launches (0); the same arithmetic either way */
 } pf_tuning;
 pf_status pf_autotune(pf_sim* s, pf_tuning* out);
 /* Sets the launch shapes directly (for example a shape pf_autotune chose
  * earlier): every block size a multiple of 32 in [32, 256]; spmv may also be
- * -96, -192 or -384 (one thread per block row) in FP64 precision.  Results do
- * not depend on the shapes.  PF_EINVAL for any other value. */
+ * -96, -192 or -384 (one thread per block row) in FP64 precision; block_cells
+ * in [1, 65536]; ilu_fused 0 or 1.  Results do not depend on the shapes.  PF_EINVAL for any
+ * other value. */
 pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t);
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);

@@ -65,11 +65,12 @@ class pf_solver_opts(C.Structure):
                 ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
                 ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int),
-                ("stage1", C.c_int)]
+                ("stage1", C.c_int), ("amg_coarse_sweeps", C.c_int)]
 
 
 class pf_tuning(C.Structure):
-    _fields_ = [(n, C.c_int) for n in ("props", "face", "gather", "spmv", "stage2", "rbgs")]
+    _fields_ = [(n, C.c_int) for n in ("props", "face", "gather", "spmv", "stage2", "rbgs", "block_cells",
+                                         "ilu_fused")]
 
 
 class pf_well_control(C.Structure):
@@ -147,6 +148,7 @@ def lib():
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
             "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
+            "pf_set_programmatic_launch": ([C.c_int], C.c_int),
             "pf_apply_preconditioner": ([vp, _dp, _dp], C.c_int),
             "pf_equilibrium_init": ([C.POINTER(pf_model_desc), C.c_double, C.c_double, C.c_double, _dp, _dp],
                                     C.c_int),
@@ -246,6 +248,11 @@ class Model:
     def _keep(self, a):
         self.keep.append(a)
         return a
+
+
+def set_programmatic_launch(on):
+    """Process-wide switch for programmatic dependent launch (default on)."""
+    _check(lib().pf_set_programmatic_launch(1 if on else 0))
 
 
 def equilibrium_init(sc, datum_depth, datum_p, contact_depth):
@@ -388,7 +395,8 @@ class Simulator:
 
     def set_tuning(self, **shapes):
         t = pf_tuning()
-        cur = dict(props=256, face=256, gather=256, spmv=256, stage2=256, rbgs=256)
+        cur = dict(props=256, face=256, gather=256, spmv=256, stage2=256, rbgs=256,
+                   block_cells=4096 if self.opts.precision == PF_PREC_MIXED else 256, ilu_fused=1)
         cur.update(shapes)
         for k, v in cur.items():
             setattr(t, k, int(v))

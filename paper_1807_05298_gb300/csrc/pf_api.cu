@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -22,8 +23,11 @@ static pf_status fail(pf_status st, const std::string& msg) {
   return st;
 }
 
+static std::atomic<bool> g_pdl{true};
+
 namespace pf {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed); }
 }  // namespace pf
 
 #define PF_CUDA(call)                                                                       \
@@ -109,6 +113,8 @@ struct pf_sim {
   double prev_norm = -1.0;      // |b^{l-1}| of the previous Newton iteration (< 0: none)
   double prev_lin_norm = 0.0;   // |r^{l-1}| (forcing form 2)
   double* rlin = nullptr;       // r^{l-1} (forcing form 1)
+  int* w_perf_of = nullptr;     // [N] perforation of each cell, -1 if none
+  int* w_pwell = nullptr;       // [npf] well of each perforation
   double* d_sat = nullptr;      // saturation table (structure of arrays with slopes)
   double* d_poly = nullptr;     // polymer table
   int iter_in_step = 0;
@@ -178,6 +184,8 @@ Wells wells_view(const pf_sim* s) {
   w.so = s->w_so;
   w.scale = s->w_scale;
   w.gamma = s->w_gamma;
+  w.perf_of = s->w_perf_of;
+  w.pwell = s->w_pwell;
   return w;
 }
 
@@ -304,7 +312,7 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (o->precision != PF_PREC_FP64 && o->precision != PF_PREC_MIXED) return fail(PF_EINVAL, "invalid precision");
     if (o->precond != PF_PC_BJACOBI && o->precond != PF_PC_CPR) return fail(PF_EINVAL, "invalid preconditioner");
     if (o->amg_cycle != 1 && o->amg_cycle != 2) return fail(PF_EINVAL, "amg_cycle must be 1 or 2");
-    if (o->amg_pre_sweeps < 0 || o->amg_post_sweeps < 0 || o->amg_coarse_size < 1)
+    if (o->amg_pre_sweeps < 0 || o->amg_post_sweeps < 0 || o->amg_coarse_size < 1 || o->amg_coarse_sweeps < -1)
       return fail(PF_EINVAL, "invalid multigrid parameters");
     if (o->forcing_form < 1 || o->forcing_form > 3) return fail(PF_EINVAL, "forcing_form must be 1, 2 or 3");
     if (o->stage1 != PF_S1_BJACOBI && o->stage1 != PF_S1_ILU0) return fail(PF_EINVAL, "invalid stage1");
@@ -377,6 +385,8 @@ size_t carve(pf_sim* s, char* base) {
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
   s->red_counter = c.take<unsigned int>(64);
+  s->w_perf_of = c.take<int>(n);
+  s->w_pwell = c.take<int>(std::max(1LL, s->npf));
   s->d_sat = s->ph.n_sat > 0 ? c.take<double>((size_t)7 * s->ph.n_sat) : nullptr;
   s->d_poly = s->ph.n_poly > 0 ? c.take<double>((size_t)5 * s->ph.n_poly) : nullptr;
   if (s->opts.precond == PF_PC_CPR) cpr_carve(s->cpr, s->g, s->mixed, c.off, base);
@@ -426,7 +436,7 @@ pf_status spmv(pf_sim* s, const double* xin, double* y) {
   else
     launch_spmv<double>(s->g, w, (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
                         (const double*)s->Dw, xin, y, s->stream, s->tune.spmv);
-  PF_LAUNCHED(1 + (s->nw > 0));
+  PF_LAUNCHED(1);
   return PF_OK;
 }
 
@@ -468,13 +478,14 @@ pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullp
     return PF_OK;
   }
   if (s->opts.stage1 == PF_S1_ILU0) {
+    int nl;
     if (s->mixed)
-      launch_ilu_apply<float, float, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
-                                             (const float*)s->Dwinv, v, z, s->stream);
+      nl = launch_ilu_apply<float, float, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
+                                                  (const float*)s->Dwinv, v, z, s->tune.ilu_fused, s->stream);
     else
-      launch_ilu_apply<double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
-                                               (const double*)s->Dwinv, v, z, s->stream);
-    PF_LAUNCHED(3);
+      nl = launch_ilu_apply<double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
+                                                    (const double*)s->Dwinv, v, z, s->tune.ilu_fused, s->stream);
+    PF_LAUNCHED(nl);
   } else {
     if (s->mixed)
       launch_bjacobi_apply<float>(s->g, s->nw, (const float*)s->Dinv, (const float*)s->Dwinv, v, z, s->stream);
@@ -519,7 +530,7 @@ pf_status piece_spmv(pf_sim* s, int j) {
   launch_spmv_f32(s->g, wells_view(s), (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw,
                   (const float*)s->Dw, s->Zf + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld, s->stream,
                   s->tune.spmv);
-  PF_LAUNCHED(1 + (s->nw > 0));
+  PF_LAUNCHED(1);
   return PF_OK;
 }
 pf_status piece_ortho(pf_sim* s, int j) {
@@ -720,6 +731,11 @@ double forcing_term(double nb, double nb_prev) {
 
 extern "C" {
 
+pf_status pf_set_programmatic_launch(int on) {
+  g_pdl.store(on != 0);
+  return PF_OK;
+}
+
 const char* pf_version(void) { return "polyflood-gb300 0.1 (sm_103a)"; }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -743,6 +759,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->autotune = 0;
   o->forcing_form = 3;
   o->stage1 = PF_S1_ILU0;
+  o->amg_coarse_sweeps = -1;
   return PF_OK;
 }
 
@@ -898,6 +915,14 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
                             st));
     s->ph.poly = s->d_poly;
   }
+  std::vector<int> perf_of((size_t)n, -1), pwell((size_t)std::max(1LL, s->npf), 0);
+  for (int w = 0; w < s->nw; ++w)
+    for (int t = s->h_ptr[w]; t < s->h_ptr[w + 1]; ++t) {
+      perf_of[(size_t)cell[t]] = t;
+      pwell[(size_t)t] = w;
+    }
+  PF_CUDA(cudaMemcpyAsync(s->w_perf_of, perf_of.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemcpyAsync(s->w_pwell, pwell.data(), pwell.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (s->nw > 0) {
     PF_CUDA(cudaMemcpyAsync(s->w_kind, kind.data(), s->nw * sizeof(int), cudaMemcpyHostToDevice, st));
     PF_CUDA(cudaMemcpyAsync(s->w_cell, cell.data(), s->npf * sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -1508,7 +1533,9 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
                       (const float*)s->Dw, s->Zf, s->r, st, b);
     });
     if (s->opts.precond == PF_PC_CPR)
-      t.stage2 = pick_block(s, [&](int b) { cpr_time_stage2(s->cpr, s->g, s->J, s->x, s->tmp, b, st); });
+      t.stage2 = pick_block(s, [&](int b) {
+        cpr_time_stage2(s->cpr, s->g, wells_view(s), true, s->J, s->Bw, s->x, s->tmp, b, st);
+      });
   } else {
     t.props = pick_block(s, [&](int b) { launch_cell_props<double>(s->g, s->ph, s->phi_r, s->x, s->pv,
                                                                   (double*)s->pd, s->Mold, s->R, (double*)s->J,
@@ -1518,19 +1545,42 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
                                                                 b); });
     t.gather = pick_block(s, [&](int b) { launch_gather<double>(s->g, s->Fbuf, dt, s->R, (double*)s->J, st, b); });
     // one thread per cell (64/128/256) or one per block row (-96/-192/-384)
+    if (s->opts.precond == PF_PC_CPR)
+      t.stage2 = pick_block(s, [&](int b) {
+        cpr_time_stage2(s->cpr, s->g, wells_view(s), false, s->J, s->Bw, s->x, s->tmp, b, st);
+      });
     static const int cand_spmv[6] = {64, 128, 256, -96, -192, -384};
     t.spmv = pick_from(s, cand_spmv, 6, [&](int b) {
       launch_spmv<double>(s->g, wells_view(s), (const double*)s->J, (const double*)s->Bw, (const double*)s->Cw,
                           (const double*)s->Dw, s->b, s->r, st, b);
     });
   }
-  if (s->opts.precond == PF_PC_CPR)
+  if (s->opts.precond == PF_PC_CPR) {
     t.rbgs = pick_block(s, [&](int b) { cpr_time_rbgs0(s->cpr, s->mixed, b, st); });
+    s->cpr.block_rbgs0 = t.rbgs;
+    s->cpr.block_stage2 = t.stage2;
+    // whole preconditioner applications: ILU(0) solve in two or three launches
+    if (s->opts.stage1 == PF_S1_ILU0) {
+      static const int cand_fused[2] = {1, 0};
+      t.ilu_fused = pick_from(s, cand_fused, 2, [&](int f) {
+        s->cpr.ilu_fused = f;
+        precond_apply(s, s->b, s->dx, s->mixed ? s->Zf : nullptr);
+      });
+      s->cpr.ilu_fused = t.ilu_fused;
+    }
+    // the single-block threshold keeps its default: timed on the set-up's
+    // placeholder data the two candidates differ by less than the noise, and
+    // measured on live systems the default was the faster (256 cells in FP64,
+    // 4096 in FP32); pf_set_tuning can still change it
+    t.block_cells = (int)s->cpr.block_cells;
+  }
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaStreamSynchronize(st));
   s->tune = t;
   s->cpr.block_rbgs0 = t.rbgs;
   s->cpr.block_stage2 = t.stage2;
+  if (t.block_cells > 0) s->cpr.block_cells = t.block_cells;
+  s->cpr.ilu_fused = t.ilu_fused;
   // captured graphs hold the old launch shapes
   for (auto& G : s->graphs) {
     if (G.pre) cudaGraphExecDestroy(G.pre);
@@ -1542,6 +1592,8 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
   if (out) {
     out->props = t.props; out->face = t.face; out->gather = t.gather;
     out->spmv = t.spmv; out->stage2 = t.stage2; out->rbgs = t.rbgs;
+    out->block_cells = (int)s->cpr.block_cells;
+    out->ilu_fused = t.ilu_fused;
   }
   return PF_OK;
 }
@@ -1552,14 +1604,19 @@ pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t) {
   if (!t) return fail(PF_EINVAL, "tuning is NULL");
   auto ok = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
   const bool spmv_ok = ok(t->spmv) || (!s->mixed && (t->spmv == -96 || t->spmv == -192 || t->spmv == -384));
-  if (!ok(t->props) || !ok(t->face) || !ok(t->gather) || !spmv_ok || !ok(t->stage2) || !ok(t->rbgs))
+  if (!ok(t->props) || !ok(t->face) || !ok(t->gather) || !spmv_ok || !ok(t->stage2) || !ok(t->rbgs) ||
+      t->block_cells < 1 || t->block_cells > 65536 || (t->ilu_fused != 0 && t->ilu_fused != 1))
     return fail(PF_EINVAL, "invalid launch shape");
   PF_CUDA(cudaStreamSynchronize(s->stream));
   Tuning& u = s->tune;
   u.props = t->props; u.face = t->face; u.gather = t->gather;
   u.spmv = t->spmv; u.stage2 = t->stage2; u.rbgs = t->rbgs;
+  u.block_cells = t->block_cells;
+  u.ilu_fused = t->ilu_fused;
+  s->cpr.ilu_fused = t->ilu_fused;
   s->cpr.block_rbgs0 = u.rbgs;
   s->cpr.block_stage2 = u.stage2;
+  s->cpr.block_cells = t->block_cells;
   for (auto& G : s->graphs) {
     if (G.pre) cudaGraphExecDestroy(G.pre);
     if (G.spmv) cudaGraphExecDestroy(G.spmv);

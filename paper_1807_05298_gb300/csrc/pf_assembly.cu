@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
                                                     DT* __restrict__ pd, const double* __restrict__ Mold,
                                                     double* __restrict__ R, DT* __restrict__ J,
                                                     double* __restrict__ Mold_out, int mode) {
+  PF_PDL_ENTRY();
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -242,7 +243,7 @@ template <typename DT>
 void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x, double* pv,
                        DT* pd, const double* Mold, double* R, DT* J, double* Mold_out, int mode,
                        cudaStream_t st, int block) {
-  k_cell_props<DT><<<grid_for(g.n, block), block, 0, st>>>(g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
+  launch(k_cell_props<DT>, grid_for(g.n, block), block, 0, st, g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
                                                    const double* __restrict__ T3, const double* __restrict__ x,
                                                    const double* __restrict__ pv, const DT* __restrict__ pd,
                                                    double dt, DT* __restrict__ J, double* __restrict__ Fbuf) {
+  PF_PDL_ENTRY();
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
 template <typename DT>
 void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3, const double* x,
                       const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st, int block) {
-  k_face_flux<DT><<<grid_for(g.n, block), block, 0, st>>>(g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
+  launch(k_face_flux<DT>, grid_for(g.n, block), block, 0, st, g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
 }
 
 // ---------------------------------------------------------------------------
@@ -433,6 +435,7 @@ void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const do
 template <typename DT>
 __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict__ Fbuf, double dt,
                                                 double* __restrict__ R, DT* __restrict__ J) {
+  PF_PDL_ENTRY();
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
 
 template <typename DT>
 void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st, int block) {
-  k_gather<DT><<<grid_for(g.n, block), block, 0, st>>>(g, Fbuf, dt, R, J);
+  launch(k_gather<DT>, grid_for(g.n, block), block, 0, st, g, Fbuf, dt, R, J);
 }
 
 // ---------------------------------------------------------------------------
@@ -494,6 +497,7 @@ template <typename DT>
 __global__ void k_wells(Grid g, Phys ph, Wells w, const double* __restrict__ x, const double* __restrict__ pv,
                         const DT* __restrict__ pd, double dt, double* __restrict__ R, DT* __restrict__ J,
                         DT* __restrict__ Bw, DT* __restrict__ Cw, DT* __restrict__ Dw) {
+  PF_PDL_ENTRY();
   const int wi = blockIdx.x;
   if (wi >= w.nw) return;
   const int lane = threadIdx.x;
@@ -597,7 +601,7 @@ template <typename DT>
 void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv, const DT* pd,
                   double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st) {
   if (w.nw == 0) return;
-  k_wells<DT><<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, pd, dt, R, J, Bw, Cw, Dw);
+  launch(k_wells<DT>, w.nw, 32, 0, st, g, ph, w, x, pv, pd, dt, R, J, Bw, Cw, Dw);
 }
 
 // Lagged wellbore unit weight (frozen over a step): rho_w(P_b) g for an
@@ -605,6 +609,7 @@ void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x
 // times g for a producer.  Needs pv from a mode-1 cell_props pass.
 __global__ void k_well_gamma(Grid g, Phys ph, Wells w, const double* __restrict__ x,
                              const double* __restrict__ pv, double* __restrict__ gamma) {
+  PF_PDL_ENTRY();
   const int wi = blockIdx.x;
   if (wi >= w.nw) return;
   const int lane = threadIdx.x;
@@ -633,6 +638,7 @@ __global__ void k_well_gamma(Grid g, Phys ph, Wells w, const double* __restrict_
 // (values of eq. (ssw:Q) with the lagged gamma); needs pv from a mode-2 pass.
 __global__ void k_well_totals(Grid g, Phys ph, Wells w, const double* __restrict__ x,
                               const double* __restrict__ pv, double* __restrict__ out) {
+  PF_PDL_ENTRY();
   const int wi = blockIdx.x;
   if (wi >= w.nw) return;
   const int lane = threadIdx.x;
@@ -670,13 +676,13 @@ __global__ void k_well_totals(Grid g, Phys ph, Wells w, const double* __restrict
 void launch_well_totals(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                         double* out, cudaStream_t st) {
   if (w.nw == 0) return;
-  k_well_totals<<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, out);
+  launch(k_well_totals, w.nw, 32, 0, st, g, ph, w, x, pv, out);
 }
 
 void launch_well_gamma(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                        double* gamma, cudaStream_t st) {
   if (w.nw == 0) return;
-  k_well_gamma<<<w.nw, 32, 0, st>>>(g, ph, w, x, pv, gamma);
+  launch(k_well_gamma, w.nw, 32, 0, st, g, ph, w, x, pv, gamma);
 }
 
 // ---------------------------------------------------------------------------
@@ -694,6 +700,7 @@ __device__ __forceinline__ double warp_max(double v) {
 
 __global__ void __launch_bounds__(256) k_res_norm_partial(Grid g, Phys ph, const double* __restrict__ inv_pv,
                                                           const double* __restrict__ R, double* __restrict__ partial) {
+  PF_PDL_ENTRY();
   const long long n = g.n;
   double mx = 0.0, ss = 0.0;
   const double io = 1.0 / ph.rho_o, iw = ph.inv_rho_w, ic = ph.inv_c_ref;
@@ -722,6 +729,7 @@ __global__ void __launch_bounds__(256) k_res_norm_partial(Grid g, Phys ph, const
 
 __global__ void k_res_norm_final(int nblocks, Wells w, long long n, const double* __restrict__ R, double dt,
                                  const double* __restrict__ partial, double* __restrict__ out) {
+  PF_PDL_ENTRY();
   // one warp: fixed-order reduction of the block partials, then the well rows
   const int lane = threadIdx.x;
   double mx = 0.0, ss = 0.0;
@@ -738,8 +746,8 @@ __global__ void k_res_norm_final(int nblocks, Wells w, long long n, const double
 
 void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, const Wells& w, const double* R,
                            double dt, double* partial, int nblocks, double* out, cudaStream_t st) {
-  k_res_norm_partial<<<nblocks, 256, 0, st>>>(g, ph, inv_pv, R, partial);
-  k_res_norm_final<<<1, 32, 0, st>>>(nblocks, w, g.n, R, dt, partial, out);
+  launch(k_res_norm_partial, nblocks, 256, 0, st, g, ph, inv_pv, R, partial);
+  launch(k_res_norm_final, 1, 32, 0, st, nblocks, w, g.n, R, dt, partial, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,6 +756,7 @@ void launch_residual_norms(const Grid& g, const Phys& ph, const double* inv_pv, 
 
 __global__ void __launch_bounds__(256) k_newton_update(long long n, int nw, double* __restrict__ x,
                                                        const double* __restrict__ dx, double ds_max, double dc_max) {
+  PF_PDL_ENTRY();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nw;
        i += (long long)gridDim.x * blockDim.x) {
     if (i >= n) { x[3 * n + (i - n)] += dx[3 * n + (i - n)]; continue; }
@@ -761,7 +770,7 @@ __global__ void __launch_bounds__(256) k_newton_update(long long n, int nw, doub
 
 void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, double ds_max, double dc_max,
                           cudaStream_t st) {
-  k_newton_update<<<grid_for(g.n + nw, 256), 256, 0, st>>>(g.n, nw, x, dx, ds_max, dc_max);
+  launch(k_newton_update, grid_for(g.n + nw, 256), 256, 0, st, g.n, nw, x, dx, ds_max, dc_max);
 }
 
 // explicit instantiations

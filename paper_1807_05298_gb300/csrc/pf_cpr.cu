@@ -49,6 +49,7 @@ __device__ __forceinline__ bool nbr(const Dims& d, int x, int y, int z, int s, l
 template <typename T>
 __global__ void __launch_bounds__(256) k_extract_pressure(long long n, const T* __restrict__ J, T* __restrict__ A,
                                                           T* __restrict__ dinv, double w_o, double w_w) {
+  PF_PDL_ENTRY();
   GSTRIDE(i, n) {
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
@@ -63,6 +64,11 @@ __global__ void __launch_bounds__(256) k_extract_pressure(long long n, const T* 
 // index within its group; groups are warp-aligned and every lane of a warp
 // takes part in every round, so the shuffles see full warps.  The child sums
 // use a fixed xor tree (deterministic).
+// c - a b with one rounding (written out so that the per-level kernels and the
+// single-block cycle round identically whatever the compiler contracts)
+__device__ __forceinline__ double fnms(double a, double b, double c) { return __fma_rn(-a, b, c); }
+__device__ __forceinline__ float fnms(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+
 __device__ __forceinline__ double grp8_sum(double v) {
   v += __shfl_xor_sync(0xffffffffu, v, 1);
   v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -74,6 +80,7 @@ __device__ __forceinline__ double grp8_sum(double v) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_galerkin(Dims f, Dims c, const T* __restrict__ Af, T* __restrict__ Ac,
                                                   T* __restrict__ dinv_c) {
+  PF_PDL_ENTRY();
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
   const long long total = 8 * c.n;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -114,21 +121,57 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims f, Dims c, const T* __res
   }
 }
 
+// The preconditioner's output, written by the last post-smoothing pass on the
+// finest pressure level (saves a pass over the vector): mode 1 (FP64 path)
+// z[3i] += x_i on every cell; mode 2 (mixed) z = zf + Pi_p x in FP64 and its
+// FP32 copy zf_out (may be null), wells included.
+struct TopOut {
+  int mode = 0;
+  int nw = 0;
+  double* z = nullptr;
+  const float* zf = nullptr;
+  float* zf_out = nullptr;
+};
+
+template <typename T>
+__device__ __forceinline__ void top_write(const TopOut& t, long long i, T xi) {
+  if (t.mode == 1) {
+    t.z[3 * i] += (double)xi;
+  } else {
+    const float p = t.zf[3 * i] + (float)xi, sv = t.zf[3 * i + 1], cv = t.zf[3 * i + 2];
+    t.z[3 * i] = (double)p;
+    t.z[3 * i + 1] = (double)sv;
+    t.z[3 * i + 2] = (double)cv;
+    if (t.zf_out) { t.zf_out[3 * i] = p; t.zf_out[3 * i + 1] = sv; t.zf_out[3 * i + 2] = cv; }
+  }
+}
+
 // one colour of a red-black Gauss-Seidel sweep; zero_init: x holds no valid
 // values yet (first half-sweep), so neighbours count as zero.  With xc (the
 // coarse correction of dims c): the neighbours are read as x_j + xc[agg(j)],
 // i.e. the prolongation x += P xc is applied on the fly.  A colour pass
 // overwrites every cell of its colour, so only the other colour's values
 // (the neighbours) need the correction; the next pass overwrites those.
-template <typename T>
+template <typename T, bool TOP>
 __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
                                               const T* __restrict__ b, T* __restrict__ x, int color, int zero_init,
-                                              const T* __restrict__ xc = nullptr, Dims c = Dims{}) {
+                                              const T* __restrict__ xc, Dims c, TopOut top) {
+  PF_PDL_ENTRY();
   const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
-  GSTRIDE(i, d.n) {
+  GSTRIDE(i, d.n + (TOP && top.mode == 2 ? top.nw : 0)) {
+    if (TOP && i >= d.n) {  // well rows of the mixed output: stage-1 values
+      const long long wv = 3 * d.n + (i - d.n);
+      const float v = top.zf[wv];
+      top.z[wv] = (double)v;
+      if (top.zf_out) top.zf_out[wv] = v;
+      continue;
+    }
     int cx, cy, cz;
     coords(d, i, cx, cy, cz);
-    if (((cx + cy + cz) & 1) != color) continue;
+    if (((cx + cy + cz) & 1) != color) {
+      if (TOP) top_write(top, i, x[i]);  // final value of the other colour
+      continue;
+    }
     T s = b[i];
     if (!zero_init) {
 #pragma unroll
@@ -141,10 +184,12 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
           coords(d, j, jx, jy, jz);
           xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
         }
-        s -= A[(size_t)sl * d.n + i] * xj;
+        s = fnms(A[(size_t)sl * d.n + i], xj, s);
       }
     }
-    x[i] = s * dinv[i];
+    const T xi = s * dinv[i];
+    x[i] = xi;
+    if (TOP) top_write(top, i, xi);
   }
 }
 
@@ -153,6 +198,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const T* __restrict__ A,
                                                            const T* __restrict__ b, const T* __restrict__ x,
                                                            T* __restrict__ bc) {
+  PF_PDL_ENTRY();
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
   const long long total = 8 * c.n;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -168,11 +214,11 @@ __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const
       const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
       if (X < f.nx && Y < f.ny && Z < f.nz) {
         const long long i = X + f.nx * (Y + (long long)f.ny * Z);
-        T ri = b[i] - A[i] * x[i];
+        T ri = fnms(A[i], x[i], b[i]);
 #pragma unroll
         for (int sl = 1; sl < SL_COUNT; ++sl) {
           long long j;
-          if (nbr(f, X, Y, Z, sl, j)) ri -= A[(size_t)sl * f.n + i] * x[j];
+          if (nbr(f, X, Y, Z, sl, j)) ri = fnms(A[(size_t)sl * f.n + i], x[j], ri);
         }
         r = (double)ri;
       }
@@ -184,6 +230,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(Dims f, Dims c, const T* __restrict__ xc, T* __restrict__ x) {
+  PF_PDL_ENTRY();
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
   GSTRIDE(i, f.n) {
     int X, Y, Z;
@@ -202,6 +249,7 @@ constexpr size_t kCoarseSmem = sizeof(double) * (2 * kMaxCoarse * kLd) + sizeof(
 
 template <typename T>
 __global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__ inv, int* status) {
+  PF_PDL_ENTRY();
   extern __shared__ double sm[];
   double* M = sm;                       // [n][kLd] column-major: M[c * kLd + r]
   double* X = sm + kMaxCoarse * kLd;     // [n][kLd] column j of the inverse: X[j * kLd + r]
@@ -284,13 +332,14 @@ __global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__
 // that launch latency, not work, would dominate): the same smoother,
 // restriction, prolongation and coarse inverse as the per-level kernels.
 constexpr int kMaxLev = 24;
-// FP64 runs at a small fraction of the FP32 rate per SM, so one block may only
-// take the tiny FP64 levels; FP32 levels up to 4096 cells fit one block well.
-template <typename T> constexpr long long block_level_cells() { return sizeof(T) == 8 ? 256 : 4096; }
+// The size up to which a level (and every coarser one) runs in the single
+// block is CprData::block_cells: FP64 runs at a small fraction of the FP32
+// rate per SM, so its default is lower; the launch-shape tuner may raise it.
 
 template <typename T>
 struct BlockLevels {
   int l0, nlev, pre, post, gamma;
+  int pre0, post0;  // sweeps on the finest level (pre, post: on the coarser ones)
   Dims d[kMaxLev];
   T* A[kMaxLev];
   T* dinv[kMaxLev];
@@ -309,7 +358,7 @@ __device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* 
     if (!zero_init) {
       for (int sl = 1; sl < SL_COUNT; ++sl) {
         long long j;
-        if (nbr(d, cx, cy, cz, sl, j)) s -= A[(size_t)sl * d.n + i] * x[j];
+        if (nbr(d, cx, cy, cz, sl, j)) s = fnms(A[(size_t)sl * d.n + i], x[j], s);
       }
     }
     x[i] = s * dinv[i];
@@ -324,6 +373,7 @@ __device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* 
 // level, L.gamma below), the first from a zero initial guess.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zero_init) {
+  PF_PDL_ENTRY();
   __shared__ BlockLevels<T> L;
   __shared__ int cnt[kMaxLev];
   __shared__ int zi[kMaxLev];
@@ -351,7 +401,8 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
         down = false;
         continue;
       }
-      for (int sweep = 0; sweep < L.pre; ++sweep) {
+      const int npre = l == 0 ? L.pre0 : L.pre;
+      for (int sweep = 0; sweep < npre; ++sweep) {
         b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, zi[l] && sweep == 0);
         b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
       }
@@ -363,21 +414,26 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
       for (long long I = threadIdx.x; I < c.n; I += blockDim.x) {
         int cx, cy, cz;
         coords(c, I, cx, cy, cz);
-        T acc = 0;
-        for (int dz = 0; dz < fz; ++dz)
-          for (int dy = 0; dy < fy; ++dy)
-            for (int dx = 0; dx < fx; ++dx) {
-              const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
-              if (X >= d.nx || Y >= d.ny || Z >= d.nz) continue;
-              const long long i = X + d.nx * (Y + (long long)d.ny * Z);
-              T r = b[i] - A[i] * x[i];
-              for (int sl = 1; sl < SL_COUNT; ++sl) {
-                long long j;
-                if (nbr(d, X, Y, Z, sl, j)) r -= A[(size_t)sl * d.n + i] * x[j];
-              }
-              acc += r;
-            }
-        L.b[l + 1][I] = acc;
+        // the children's residuals in FP64, summed in the pairing order of
+        // the per-level kernel's 8-lane reduction: ((0+1)+(2+3))+((4+5)+(6+7))
+        auto child_res = [&](int child) -> double {
+          const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
+          if (dx >= fx || dy >= fy || dz >= fz) return 0.0;
+          const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
+          if (X >= d.nx || Y >= d.ny || Z >= d.nz) return 0.0;
+          const long long i = X + d.nx * (Y + (long long)d.ny * Z);
+          T r = fnms(A[i], x[i], b[i]);
+          for (int sl = 1; sl < SL_COUNT; ++sl) {
+            long long j;
+            if (nbr(d, X, Y, Z, sl, j)) r = fnms(A[(size_t)sl * d.n + i], x[j], r);
+          }
+          return (double)r;
+        };
+        double lo = child_res(0) + child_res(1);
+        lo = lo + (child_res(2) + child_res(3));
+        double hi = child_res(4) + child_res(5);
+        hi = hi + (child_res(6) + child_res(7));
+        L.b[l + 1][I] = (T)(lo + hi);
       }
       if (threadIdx.x == 0) {
         cnt[l] = 0;
@@ -409,7 +465,8 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
       L.x[l][i] += L.x[l + 1][X / fx + c.nx * (Y / fy + (long long)c.ny * (Z / fz))];
     }
     __syncthreads();
-    for (int sweep = 0; sweep < L.post; ++sweep) {
+    const int npost = l == 0 ? L.post0 : L.post;
+    for (int sweep = 0; sweep < npost; ++sweep) {
       b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
       b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, false);
     }
@@ -420,6 +477,7 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
 
 template <typename T>
 __global__ void k_coarse_apply(int n, const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  PF_PDL_ENTRY();
   const int r = threadIdx.x;
   if (r >= n) return;
   double s = 0.0;
@@ -427,24 +485,20 @@ __global__ void k_coarse_apply(int n, const T* __restrict__ inv, const T* __rest
   x[r] = (T)s;
 }
 
-// Pi_r (f - J y): weighted oil and water rows of the residual, per cell
-template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_top(long long n, const double* __restrict__ f,
-                                                      const double* __restrict__ Jy, double w_o, double w_w,
-                                                      T* __restrict__ b0) {
-  GSTRIDE(i, n) b0[i] = (T)(w_o * (f[3 * i] - Jy[3 * i]) + w_w * (f[3 * i + 1] - Jy[3 * i + 1]));
-}
-
-// y += Pi_p x0
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_top(long long n, const T* __restrict__ x0, double* __restrict__ y) {
+  PF_PDL_ENTRY();
   GSTRIDE(i, n) y[3 * i] += (double)x0[i];
 }
 
 size_t aup(size_t v) { return (v + 255) / 256 * 256; }
 
+// One cycle on level l (and below).  With top.mode set (only at l = 0), the
+// last post-smoothing pass also writes the preconditioner's output; returns
+// whether it did (not when the level runs in the single block or has no
+// post-smoothing).
 template <typename T>
-void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
+bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const TopOut& top = TopOut{}) {
   CprLevel& L = c.lev[l];
   const Dims d = dims_of(L);
   const int gb = grid_for(L.n, 256);
@@ -453,62 +507,73 @@ void cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k) {
   const T* dinv = (const T*)L.dinv;
   const T* b = (const T*)L.b;
   if (l == c.nlev - 1) {
-    k_coarse_apply<T><<<1, kMaxCoarse, 0, st>>>((int)L.n, (const T*)c.coarse_inv, b, x);
+    launch(k_coarse_apply<T>, 1, kMaxCoarse, 0, st, (int)L.n, (const T*)c.coarse_inv, b, x);
     k += 1;
-    return;
+    return false;
   }
-  if (L.n <= block_level_cells<T>()) {  // this level and all coarser ones in one block
+  if (L.n <= c.block_cells) {  // this level and all coarser ones in one block
     BlockLevels<T> B;
-    B.l0 = l; B.nlev = c.nlev; B.pre = c.pre; B.post = c.post; B.gamma = c.cycle_gamma;
+    B.l0 = l; B.nlev = c.nlev; B.gamma = c.cycle_gamma;
+    B.pre0 = c.pre; B.post0 = c.post; B.pre = c.cpre; B.post = c.cpost;
     for (int q = 0; q < c.nlev; ++q) {
       B.d[q] = dims_of(c.lev[q]);
       B.A[q] = (T*)c.lev[q].A; B.dinv[q] = (T*)c.lev[q].dinv; B.x[q] = (T*)c.lev[q].x; B.b[q] = (T*)c.lev[q].b;
     }
     B.inv = (const T*)c.coarse_inv;
-    k_block_cycle<T><<<1, 1024, 0, st>>>(B, zero_init ? 1 : 0);
+    launch(k_block_cycle<T>, 1, 1024, 0, st, B, zero_init ? 1 : 0);
     k += 1;
-    return;
+    return false;
   }
+  const int npre = l == 0 ? c.pre : c.cpre, npost = l == 0 ? c.post : c.cpost;
   const int bs = l == 0 ? c.block_rbgs0 : 256;
   const int gs = grid_for(L.n, bs);
-  for (int sweep = 0; sweep < c.pre; ++sweep) {
-    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0);
-    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0);
+  const TopOut none;
+  for (int sweep = 0; sweep < npre; ++sweep) {
+    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0, (const T*)nullptr,
+           Dims{}, none);
+    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 1, 0, (const T*)nullptr, Dims{}, none);
     k += 2;
   }
   CprLevel& C = c.lev[l + 1];
   const Dims dc = dims_of(C);
-  k_residual_restrict<T><<<grid_for(8 * C.n, 256), 256, 0, st>>>(d, dc, A, b, x, (T*)C.b);
+  launch(k_residual_restrict<T>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b);
   k += 1;
   for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k);
-  if (c.post == 0) {
-    k_prolong_add<T><<<gb, 256, 0, st>>>(d, dc, (const T*)C.x, x);
+  if (npost == 0) {
+    launch(k_prolong_add<T>, gb, 256, 0, st, d, dc, (const T*)C.x, x);
     k += 1;
+    return false;
   }
-  for (int sweep = 0; sweep < c.post; ++sweep) {
+  for (int sweep = 0; sweep < npost; ++sweep) {
     // the first black pass applies the prolongation to the red neighbours it reads
-    if (sweep == 0) k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0, (const T*)C.x, dc);
-    else k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 1, 0);
-    k_rbgs<T><<<gs, bs, 0, st>>>(d, A, dinv, b, x, 0, 0);
+    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 1, 0, sweep == 0 ? (const T*)C.x : (const T*)nullptr,
+           sweep == 0 ? dc : Dims{}, none);
+    const bool last = sweep + 1 == npost && top.mode != 0;
+    const int gs_last = last ? grid_for(L.n + (top.mode == 2 ? top.nw : 0), bs) : gs;
+    if (last)
+      launch(k_rbgs<T, true>, gs_last, bs, 0, st, d, A, dinv, b, x, 0, 0, (const T*)nullptr, Dims{}, top);
+    else
+      launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 0, 0, (const T*)nullptr, Dims{}, none);
     k += 2;
   }
+  return top.mode != 0;
 }
 
 template <typename T>
 void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
   CprLevel& L0 = c.lev[0];
-  k_extract_pressure<T><<<grid_for(L0.n, 256), 256, 0, st>>>(L0.n, (const T*)J, (T*)L0.A, (T*)L0.dinv, c.w_o, c.w_w);
+  launch(k_extract_pressure<T>, grid_for(L0.n, 256), 256, 0, st, L0.n, (const T*)J, (T*)L0.A, (T*)L0.dinv, c.w_o, c.w_w);
   k += 1;
   for (int l = 0; l + 1 < c.nlev; ++l) {
     CprLevel& F = c.lev[l];
     CprLevel& C = c.lev[l + 1];
-    k_galerkin<T><<<grid_for(8 * C.n, 256), 256, 0, st>>>(dims_of(F), dims_of(C), (const T*)F.A, (T*)C.A,
+    launch(k_galerkin<T>, grid_for(8 * C.n, 256), 256, 0, st, dims_of(F), dims_of(C), (const T*)F.A, (T*)C.A,
                                                           (T*)C.dinv);
     k += 1;
   }
   CprLevel& Lc = c.lev[c.nlev - 1];
   cudaFuncSetAttribute(k_coarse_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
-  k_coarse_factor<T><<<1, kMaxCoarse, kCoarseSmem, st>>>(dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
+  launch(k_coarse_factor<T>, 1, kMaxCoarse, kCoarseSmem, st, dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
                                                          c.coarse_status);
   k += 1;
 }
@@ -519,6 +584,7 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
 __global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const float* __restrict__ Dinv,
                                                     const float* __restrict__ Dwinv, const double* __restrict__ v,
                                                     float* __restrict__ zf) {
+  PF_PDL_ENTRY();
   GSTRIDE(i, n + nw) {
     if (i >= n) { zf[3 * n + (i - n)] = Dwinv[i - n] * (float)v[3 * n + (i - n)]; continue; }
     const float r0 = (float)v[3 * i], r1 = (float)v[3 * i + 1], r2 = (float)v[3 * i + 2];
@@ -529,11 +595,14 @@ __global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const f
   }
 }
 
-// stage 2 in FP32, restricted on the fly: b0 = w_o (v - J zf)_oil + w_w (v - J zf)_water
-// (only the oil and water rows of J are read)
-__global__ void __launch_bounds__(256, 4) k_stage2_f32(Grid g, const float* __restrict__ J, const float* __restrict__ zf,
-                                                    const double* __restrict__ v, float w_o, float w_w,
-                                                    float* __restrict__ b0) {
+// stage 2, restricted on the fly: b0 = w_o (v - J y)_oil + w_w (v - J y)_water in
+// the preconditioner's precision T (only the oil and water rows of J are read;
+// a perforated cell also takes its well column B y_w)
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __restrict__ J,
+                                                const T* __restrict__ Bw, const T* __restrict__ y,
+                                                const double* __restrict__ v, T w_o, T w_w, T* __restrict__ b0) {
+  PF_PDL_ENTRY();
   const long long n = g.n;
   GSTRIDE(i, n) {
     const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
@@ -541,7 +610,7 @@ __global__ void __launch_bounds__(256, 4) k_stage2_f32(Grid g, const float* __re
     const unsigned int rem = ui - (unsigned int)k * nxy;
     const long long j = rem / nxu;
     const long long ii = rem - (unsigned int)j * nxu;
-    float t0 = 0.f, t1 = 0.f;
+    T t0 = 0, t1 = 0;
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
       long long c;
@@ -556,24 +625,17 @@ __global__ void __launch_bounds__(256, 4) k_stage2_f32(Grid g, const float* __re
         default: c = i + g.nxy; has = k + 1 < g.nz; break;
       }
       if (!has) continue;
-      const float* B = J + (size_t)s * 9 * n + i;
-      const float x0 = zf[3 * c], x1 = zf[3 * c + 1], x2 = zf[3 * c + 2];
+      const T* B = J + (size_t)s * 9 * n + i;
+      const T x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
       t0 += B[0] * x0 + B[n] * x1 + B[2 * n] * x2;
       t1 += B[3 * n] * x0 + B[4 * n] * x1 + B[5 * n] * x2;
     }
-    b0[i] = w_o * ((float)v[3 * i] - t0) + w_w * ((float)v[3 * i + 1] - t1);
-  }
-}
-
-// the well border's share of J zf in the oil and water rows of perforated cells
-__global__ void k_stage2_wells_f32(Wells w, long long n, const float* __restrict__ Bw, const float* __restrict__ zf,
-                                   float w_o, float w_w, float* __restrict__ b0) {
-  const int wi = blockIdx.x;
-  if (wi >= w.nw) return;
-  const float zw = zf[3 * n + wi];
-  for (int m = w.ptr[wi] + threadIdx.x; m < w.ptr[wi + 1]; m += 32) {
-    const long long c = w.cell[m];
-    b0[c] -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * zw;
+    T r = w_o * ((T)v[3 * i] - t0) + w_w * ((T)v[3 * i + 1] - t1);
+    if (w.nw > 0) {
+      const int m = w.perf_of[i];
+      if (m >= 0) r -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * y[3 * n + w.pwell[m]];
+    }
+    b0[i] = r;
   }
 }
 
@@ -582,6 +644,7 @@ __global__ void k_stage2_wells_f32(Wells w, long long n, const float* __restrict
 __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const float* __restrict__ zf,
                                                  const float* __restrict__ x0, double* __restrict__ z,
                                                  float* __restrict__ zf_out) {
+  PF_PDL_ENTRY();
   GSTRIDE(i, n + nw) {
     if (i >= n) {
       const float v = zf[3 * n + (i - n)];
@@ -598,26 +661,28 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
 }
 
 template <typename T>
-void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const void* Cw, const void* Dw,
-             const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp, cudaStream_t st, int& k) {
+void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const void* Dinv,
+             const void* Dwinv, const double* v, double* z, cudaStream_t st, int& k) {
   // stage 1: y = D^{-1} f, or the red-black block ILU(0) solve (cells; wells by their diagonal)
   if (c.ilu) {
-    launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, st);
-    k += 3;
+    k += launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, c.ilu_fused, st);
   } else {
     launch_bjacobi_apply<T>(g, w.nw, (const T*)Dinv, (const T*)Dwinv, v, z, st);
     k += 1;
   }
-  // stage 2: r = f - J y, restricted to the pressure equation
-  launch_spmv<T>(g, w, (const T*)J, (const T*)Bw, (const T*)Cw, (const T*)Dw, z, tmp, st);
-  k += 1 + (w.nw > 0);
+  // stage 2: r = f - J y restricted to the pressure equation (oil and water rows only)
   CprLevel& L0 = c.lev[0];
-  k_restrict_top<T><<<grid_for(g.n, 256), 256, 0, st>>>(g.n, v, tmp, c.w_o, c.w_w, (T*)L0.b);
+  launch(k_stage2<T>, grid_for(g.n, c.block_stage2), c.block_stage2, 0, st, g, w, (const T*)J, (const T*)Bw,
+         (const T*)z, v, (T)c.w_o, (T)c.w_w, (T*)L0.b);
   k += 1;
-  // stage 3: pressure multigrid cycle, then y += Pi_p x
-  cycle<T>(c, 0, true, st, k);
-  k_prolong_top<T><<<grid_for(g.n, 256), 256, 0, st>>>(g.n, (const T*)L0.x, z);
-  k += 1;
+  // stage 3: pressure multigrid cycle, then y += Pi_p x (in the cycle's last pass when it can)
+  TopOut top;
+  top.mode = 1;
+  top.z = z;
+  if (!cycle<T>(c, 0, true, st, k, top)) {
+    launch(k_prolong_top<T>, grid_for(g.n, 256), 256, 0, st, g.n, (const T*)L0.x, z);
+    k += 1;
+  }
 }
 
 }  // namespace
@@ -626,17 +691,21 @@ void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
   CprLevel& L = c.lev[0];
   const Dims d = dims_of(L);
   if (mixed)
-    k_rbgs<float><<<grid_for(L.n, block), block, 0, st>>>(d, (const float*)L.A, (const float*)L.dinv,
-                                                          (const float*)L.b, (float*)L.x, 0, 0);
+    launch(k_rbgs<float, false>, grid_for(L.n, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
+                                                          (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
   else
-    k_rbgs<double><<<grid_for(L.n, block), block, 0, st>>>(d, (const double*)L.A, (const double*)L.dinv,
-                                                           (const double*)L.b, (double*)L.x, 0, 0);
+    launch(k_rbgs<double, false>, grid_for(L.n, block), block, 0, st, d, (const double*)L.A, (const double*)L.dinv,
+                                                           (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
 }
 
-void cpr_time_stage2(CprData& c, const Grid& g, const void* J, const double* v, double* tmp, int block,
-                     cudaStream_t st) {
-  k_stage2_f32<<<grid_for(g.n, block), block, 0, st>>>(g, (const float*)J, reinterpret_cast<const float*>(tmp), v,
-                                                       (float)c.w_o, (float)c.w_w, (float*)c.lev[0].b);
+void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
+                     const double* v, double* tmp, int block, cudaStream_t st) {
+  if (mixed)
+    launch(k_stage2<float>, grid_for(g.n, block), block, 0, st, g, w, (const float*)J, (const float*)Bw,
+           reinterpret_cast<const float*>(tmp), v, (float)c.w_o, (float)c.w_w, (float*)c.lev[0].b);
+  else
+    launch(k_stage2<double>, grid_for(g.n, block), block, 0, st, g, w, (const double*)J, (const double*)Bw,
+           (const double*)tmp, v, c.w_o, c.w_w, (double*)c.lev[0].b);
 }
 
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
@@ -672,9 +741,12 @@ void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
   c.coarse_status = (int*)take(sizeof(int));
 }
 
-pf_status cpr_init(CprData& c, const Grid&, bool, const pf_solver_opts& o, cudaStream_t) {
+pf_status cpr_init(CprData& c, const Grid&, bool mixed, const pf_solver_opts& o, cudaStream_t) {
+  c.block_cells = mixed ? 4096 : 256;
   c.pre = std::max(0, o.amg_pre_sweeps);
   c.post = std::max(0, o.amg_post_sweeps);
+  c.cpre = o.amg_coarse_sweeps >= 0 ? o.amg_coarse_sweeps : c.pre;
+  c.cpost = o.amg_coarse_sweeps >= 0 ? o.amg_coarse_sweeps : c.post;
   c.cycle_gamma = o.amg_cycle == 2 ? 2 : 1;
   if (c.lev.empty() || c.lev.back().n > kMaxCoarse) return PF_EINVAL;
   c.ready = true;
@@ -701,26 +773,27 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
     CprLevel& L0 = c.lev[0];
     const int gb = grid_for(g.n + w.nw, 256);
     if (c.ilu) {
-      launch_ilu_apply<float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv, (const float*)Dwinv, v, zf,
-                                            st);
-      k += 3;
+      k += launch_ilu_apply<float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv, (const float*)Dwinv, v,
+                                                 zf, c.ilu_fused, st);
     } else {
-      k_stage1_f32<<<gb, 256, 0, st>>>(g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
+      launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
       k += 1;
     }
-    k_stage2_f32<<<grid_for(g.n, c.block_stage2), c.block_stage2, 0, st>>>(g, (const float*)J, zf, v, (float)c.w_o,
-                                                                         (float)c.w_w, (float*)L0.b);
+    launch(k_stage2<float>, grid_for(g.n, c.block_stage2), c.block_stage2, 0, st, g, w, (const float*)J,
+           (const float*)Bw, (const float*)zf, v, (float)c.w_o, (float)c.w_w, (float*)L0.b);
     k += 1;
-    if (w.nw > 0) {
-      k_stage2_wells_f32<<<w.nw, 32, 0, st>>>(w, g.n, (const float*)Bw, zf, (float)c.w_o, (float)c.w_w,
-                                              (float*)L0.b);
+    TopOut top;
+    top.mode = 2;
+    top.nw = w.nw;
+    top.z = z;
+    top.zf = zf;
+    top.zf_out = zf_out;
+    if (!cycle<float>(c, 0, true, st, k, top)) {
+      launch(k_out_f32, gb, 256, 0, st, g.n, w.nw, zf, (const float*)L0.x, z, zf_out);
       k += 1;
     }
-    cycle<float>(c, 0, true, st, k);
-    k_out_f32<<<gb, 256, 0, st>>>(g.n, w.nw, zf, (const float*)L0.x, z, zf_out);
-    k += 1;
   } else {
-    apply_t<double>(c, g, w, J, Bw, Cw, Dw, Dinv, Dwinv, v, z, tmp, st, k);
+    apply_t<double>(c, g, w, J, Bw, Dinv, Dwinv, v, z, st, k);
   }
   *launches = k;
 }

@@ -34,8 +34,11 @@ struct CprData {
   bool ready = false;
   int nlev = 0;
   int pre = 1, post = 1, cycle_gamma = 1, coarse_limit = 64;
+  int cpre = 1, cpost = 1;      // sweeps on the levels below the finest
   int block_rbgs0 = 256, block_stage2 = 256;  // launch shapes of the finest smoother and stage 2
   bool ilu = false;             // first stage: red-black block ILU(0) instead of block-Jacobi
+  int ilu_fused = 1;            // ILU solve in two launches (1) or three (0); same results
+  long long block_cells = 256;  // levels of at most this many cells run in one thread block
   double w_o = 0.0, w_w = 0.0;
   std::vector<CprLevel> lev;
   void* coarse_inv = nullptr;   // [nc][nc] dense inverse of the coarsest matrix
@@ -46,8 +49,8 @@ struct CprData {
 // given block size (used by the launch-shape tuner; the values computed are
 // scratch).
 void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st);
-void cpr_time_stage2(CprData& c, const Grid& g, const void* J, const double* v, double* tmp, int block,
-                     cudaStream_t st);
+void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
+                     const double* v, double* tmp, int block, cudaStream_t st);
 
 // Lays out the CPR arrays in the arena (base == nullptr: sizing only).
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base);

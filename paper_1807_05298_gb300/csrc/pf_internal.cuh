@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "pf_launch.cuh"
 #include "polyflood.h"
 
 namespace pf {
@@ -70,6 +71,8 @@ struct Wells {
   const double* so;        // [nw] rate coefficient of the oil sum
   const double* scale;     // [nw] scaled-residual denominator / dt
   const double* gamma;     // [nw] lagged wellbore unit weight
+  const int* perf_of;      // [N] perforation index of each cell, -1 if none
+  const int* pwell;        // [npf] well of each perforation
 };
 
 // Block sizes of the per-cell kernels (autotuned or 256).  Every cell's
@@ -77,6 +80,8 @@ struct Wells {
 // these values.
 struct Tuning {
   int props = 256, face = 256, gather = 256, spmv = 256, stage2 = 256, rbgs = 256;
+  int block_cells = 0;  // single-block multigrid levels up to this size (0: the CPR default)
+  int ilu_fused = 1;    // ILU(0) solve: diagonal red sweep folded into the black sweep (1) or separate (0)
 };
 
 // Launch helpers ------------------------------------------------------------
@@ -131,8 +136,8 @@ void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* 
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, cudaStream_t st);
 template <typename DT, typename PT, typename OT>
-void launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
-                      cudaStream_t st);
+int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+                     int fused, cudaStream_t st);  // returns the number of launches
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);

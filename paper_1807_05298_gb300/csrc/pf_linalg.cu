@@ -15,40 +15,88 @@ __device__ __forceinline__ double wsum(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// y = J x  (cells), then the well border (one warp per well)
+// y = J x with the bordered well rows and columns, one launch: the first
+// cell_blocks blocks take the cells (a perforated cell adds its well column
+// B x_w), the blocks after them take the well rows C x + D x_w, one warp per
+// well.
 // ---------------------------------------------------------------------------
 
+// well rows, one warp per well (lanes stride the well's perforations, then a
+// butterfly sum), by the warps of the blocks from cell_blocks on
+template <typename DT, typename XT>
+__device__ __forceinline__ void spmv_well_rows(const Grid& g, const Wells& w, const DT* __restrict__ Cw,
+                                               const DT* __restrict__ Dw, const XT* __restrict__ x,
+                                               double* __restrict__ y, int cell_blocks) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const long long n = g.n, npf = w.npf;
+  for (int wi = (blockIdx.x - cell_blocks) * wpb + (threadIdx.x >> 5); wi < w.nw;
+       wi += (gridDim.x - cell_blocks) * wpb) {
+    double acc = 0.0;
+    for (int m = w.ptr[wi] + lane; m < w.ptr[wi + 1]; m += 32) {
+      const long long c = w.cell[m];
+      acc += (double)Cw[m] * (double)x[3 * c] + (double)Cw[npf + m] * (double)x[3 * c + 1] +
+             (double)Cw[2 * npf + m] * (double)x[3 * c + 2];
+    }
+    acc = wsum(acc);
+    if (lane == 0) y[3 * n + wi] = acc + (double)Dw[wi] * (double)x[3 * n + wi];
+  }
+}
+
+__device__ __forceinline__ void cell_coords(const Grid& g, long long i, long long& ii, long long& j, long long& k) {
+  const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
+  k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
+  const unsigned int rem = ui - (unsigned int)k * nxy;
+  j = rem / nxu;
+  ii = rem - (unsigned int)j * nxu;
+}
+
+__device__ __forceinline__ bool stencil_nbr(const Grid& g, int s, long long i, long long ii, long long j,
+                                            long long k, long long& c) {
+  switch (s) {
+    case SL_D: c = i; return true;
+    case SL_XM: c = i - 1; return ii > 0;
+    case SL_XP: c = i + 1; return ii + 1 < g.nx;
+    case SL_YM: c = i - g.nx; return j > 0;
+    case SL_YP: c = i + g.nx; return j + 1 < g.ny;
+    case SL_ZM: c = i - g.nxy; return k > 0;
+    default: c = i + g.nxy; return k + 1 < g.nz;
+  }
+}
+
 template <typename DT>
-__global__ void __launch_bounds__(256) k_spmv_cells(Grid g, const DT* __restrict__ J, const double* __restrict__ x,
-                                                    double* __restrict__ y) {
+__global__ void __launch_bounds__(256, 4) k_spmv_cells(Grid g, Wells w, const DT* __restrict__ J,
+                                                    const DT* __restrict__ Bw, const DT* __restrict__ Cw,
+                                                    const DT* __restrict__ Dw, const double* __restrict__ x,
+                                                    double* __restrict__ y, int cell_blocks) {
+  PF_PDL_ENTRY();
+  if ((int)blockIdx.x >= cell_blocks) {
+    spmv_well_rows(g, w, Cw, Dw, x, y, cell_blocks);
+    return;
+  }
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
-    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
-    const unsigned int rem = ui - (unsigned int)k * nxy;
-    const long long j = rem / nxu;
-    const long long ii = rem - (unsigned int)j * nxu;
+       i += (long long)cell_blocks * blockDim.x) {
+    long long ii, j, k;
+    cell_coords(g, i, ii, j, k);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
       long long c;
-      bool has;
-      switch (s) {
-        case SL_D: c = i; has = true; break;
-        case SL_XM: c = i - 1; has = ii > 0; break;
-        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
-        case SL_YM: c = i - g.nx; has = j > 0; break;
-        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
-        case SL_ZM: c = i - g.nxy; has = k > 0; break;
-        default: c = i + g.nxy; has = k + 1 < g.nz; break;
-      }
-      if (!has) continue;
+      if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + (size_t)s * 9 * n + i;
       const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
       acc0 += (double)B[0] * x0 + (double)B[n] * x1 + (double)B[2 * n] * x2;
       acc1 += (double)B[3 * n] * x0 + (double)B[4 * n] * x1 + (double)B[5 * n] * x2;
       acc2 += (double)B[6 * n] * x0 + (double)B[7 * n] * x1 + (double)B[8 * n] * x2;
+    }
+    if (w.nw > 0) {
+      const int m = w.perf_of[i];
+      if (m >= 0) {
+        const double xw = x[3 * n + w.pwell[m]];
+        acc0 = __fma_rn((double)Bw[m], xw, acc0);
+        acc1 = __fma_rn((double)Bw[w.npf + m], xw, acc1);
+        acc2 = __fma_rn((double)Bw[2 * w.npf + m], xw, acc2);
+      }
     }
     y[3 * i] = acc0;
     y[3 * i + 1] = acc1;
@@ -62,123 +110,93 @@ __global__ void __launch_bounds__(256) k_spmv_cells(Grid g, const DT* __restrict
 // the threads of k_spmv_cells fill the GPU at small N; each row's sum is
 // taken in the same order, so the result is identical.
 template <typename DT>
-__global__ void __launch_bounds__(384) k_spmv_rows(Grid g, const DT* __restrict__ J, const double* __restrict__ x,
-                                                   double* __restrict__ y) {
+__global__ void __launch_bounds__(384, 2) k_spmv_rows(Grid g, Wells w, const DT* __restrict__ J,
+                                                   const DT* __restrict__ Bw, const DT* __restrict__ Cw,
+                                                   const DT* __restrict__ Dw, const double* __restrict__ x,
+                                                   double* __restrict__ y, int cell_blocks) {
+  PF_PDL_ENTRY();
+  if ((int)blockIdx.x >= cell_blocks) {
+    spmv_well_rows(g, w, Cw, Dw, x, y, cell_blocks);
+    return;
+  }
   const long long n = g.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = warp % 3;
   const int groups = blockDim.x / 96;
-  const long long stride = (long long)gridDim.x * groups * 32;
+  const long long stride = (long long)cell_blocks * groups * 32;
   for (long long i = ((long long)blockIdx.x * groups + warp / 3) * 32 + lane; i < n; i += stride) {
-    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
-    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
-    const unsigned int rem = ui - (unsigned int)k * nxy;
-    const long long j = rem / nxu;
-    const long long ii = rem - (unsigned int)j * nxu;
+    long long ii, j, k;
+    cell_coords(g, i, ii, j, k);
     double acc = 0.0;
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
       long long c;
-      bool has;
-      switch (s) {
-        case SL_D: c = i; has = true; break;
-        case SL_XM: c = i - 1; has = ii > 0; break;
-        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
-        case SL_YM: c = i - g.nx; has = j > 0; break;
-        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
-        case SL_ZM: c = i - g.nxy; has = k > 0; break;
-        default: c = i + g.nxy; has = k + 1 < g.nz; break;
-      }
-      if (!has) continue;
+      if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + ((size_t)s * 9 + 3 * r) * n + i;
       const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
       acc += (double)B[0] * x0 + (double)B[n] * x1 + (double)B[2 * n] * x2;
+    }
+    if (w.nw > 0) {
+      const int m = w.perf_of[i];
+      if (m >= 0) acc = __fma_rn((double)Bw[r * w.npf + m], x[3 * n + w.pwell[m]], acc);
     }
     y[3 * i + r] = acc;
   }
 }
 
-template <typename DT>
-__global__ void k_spmv_wells(Grid g, Wells w, const DT* __restrict__ Bw, const DT* __restrict__ Cw,
-                             const DT* __restrict__ Dw, const double* __restrict__ x, double* __restrict__ y) {
-  const int wi = blockIdx.x;
-  if (wi >= w.nw) return;
-  const long long n = g.n, npf = w.npf;
-  const double xw = x[3 * n + wi];
-  double acc = 0.0;
-  for (int m = w.ptr[wi] + threadIdx.x; m < w.ptr[wi + 1]; m += 32) {
-    const long long c = w.cell[m];
-    y[3 * c] += (double)Bw[m] * xw;
-    y[3 * c + 1] += (double)Bw[npf + m] * xw;
-    y[3 * c + 2] += (double)Bw[2 * npf + m] * xw;
-    acc += (double)Cw[m] * x[3 * c] + (double)Cw[npf + m] * x[3 * c + 1] + (double)Cw[2 * npf + m] * x[3 * c + 2];
-  }
-  acc = wsum(acc);
-  if (threadIdx.x == 0) y[3 * n + wi] = acc + (double)Dw[wi] * xw;
-}
-
 // Mixed-precision operator: FP32 Jacobian times an FP32 copy of the vector,
-// accumulated in FP32 per row, written as FP64 (no FP64 arithmetic).
-__global__ void __launch_bounds__(256) k_spmv_cells_f32(Grid g, const float* __restrict__ J, const float* __restrict__ x,
-                                                        double* __restrict__ y) {
+// accumulated in FP32 per row, written as FP64 (no FP64 arithmetic in the
+// cell rows; the well column is added to the FP64 value).
+__global__ void __launch_bounds__(256, 4) k_spmv_cells_f32(Grid g, Wells w, const float* __restrict__ J,
+                                                        const float* __restrict__ Bw, const float* __restrict__ Cw,
+                                                        const float* __restrict__ Dw, const float* __restrict__ x,
+                                                        double* __restrict__ y, int cell_blocks) {
+  PF_PDL_ENTRY();
+  if ((int)blockIdx.x >= cell_blocks) {
+    spmv_well_rows(g, w, Cw, Dw, x, y, cell_blocks);
+    return;
+  }
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
-    const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
-    const unsigned int rem = ui - (unsigned int)k * nxy;
-    const long long j = rem / nxu;
-    const long long ii = rem - (unsigned int)j * nxu;
+       i += (long long)cell_blocks * blockDim.x) {
+    long long ii, j, k;
+    cell_coords(g, i, ii, j, k);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
       long long c;
-      bool has;
-      switch (s) {
-        case SL_D: c = i; has = true; break;
-        case SL_XM: c = i - 1; has = ii > 0; break;
-        case SL_XP: c = i + 1; has = ii + 1 < g.nx; break;
-        case SL_YM: c = i - g.nx; has = j > 0; break;
-        case SL_YP: c = i + g.nx; has = j + 1 < g.ny; break;
-        case SL_ZM: c = i - g.nxy; has = k > 0; break;
-        default: c = i + g.nxy; has = k + 1 < g.nz; break;
-      }
-      if (!has) continue;
+      if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const float* B = J + (size_t)s * 9 * n + i;
       const float x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
       acc0 += B[0] * x0 + B[n] * x1 + B[2 * n] * x2;
       acc1 += B[3 * n] * x0 + B[4 * n] * x1 + B[5 * n] * x2;
       acc2 += B[6 * n] * x0 + B[7 * n] * x1 + B[8 * n] * x2;
     }
-    y[3 * i] = (double)acc0;
-    y[3 * i + 1] = (double)acc1;
-    y[3 * i + 2] = (double)acc2;
+    double y0 = (double)acc0, y1 = (double)acc1, y2 = (double)acc2;
+    if (w.nw > 0) {
+      const int m = w.perf_of[i];
+      if (m >= 0) {
+        const float xw = x[3 * n + w.pwell[m]];
+        y0 += (double)(Bw[m] * xw);
+        y1 += (double)(Bw[w.npf + m] * xw);
+        y2 += (double)(Bw[2 * w.npf + m] * xw);
+      }
+    }
+    y[3 * i] = y0;
+    y[3 * i + 1] = y1;
+    y[3 * i + 2] = y2;
   }
 }
 
-__global__ void k_spmv_wells_f32(Grid g, Wells w, const float* __restrict__ Bw, const float* __restrict__ Cw,
-                                 const float* __restrict__ Dw, const float* __restrict__ x, double* __restrict__ y) {
-  const int wi = blockIdx.x;
-  if (wi >= w.nw) return;
-  const long long n = g.n, npf = w.npf;
-  const float xw = x[3 * n + wi];
-  float acc = 0.f;
-  for (int m = w.ptr[wi] + threadIdx.x; m < w.ptr[wi + 1]; m += 32) {
-    const long long c = w.cell[m];
-    y[3 * c] += (double)(Bw[m] * xw);
-    y[3 * c + 1] += (double)(Bw[npf + m] * xw);
-    y[3 * c + 2] += (double)(Bw[2 * npf + m] * xw);
-    acc += Cw[m] * x[3 * c] + Cw[npf + m] * x[3 * c + 1] + Cw[2 * npf + m] * x[3 * c + 2];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (threadIdx.x == 0) y[3 * n + wi] = (double)(acc + Dw[wi] * xw);
+inline int well_blocks(const Wells& w, int block) {
+  const int wpb = block / 32;
+  return w.nw > 0 ? (w.nw + wpb - 1) / wpb : 0;
 }
 
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
                      const float* Dw, const float* x, double* y, cudaStream_t st, int block) {
-  k_spmv_cells_f32<<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
-  if (w.nw > 0) k_spmv_wells_f32<<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
+  const int cb = grid_for(g.n, block);
+  launch(k_spmv_cells_f32, cb + well_blocks(w, block), block, 0, st, g, w, J, Bw, Cw, Dw, x, y, cb);
 }
 
 template <typename DT>
@@ -186,12 +204,12 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
                  const double* x, double* y, cudaStream_t st, int block) {
   if (block < 0) {
     // row-split form: -block = threads per block, a multiple of 96 (<= 384)
-    const int tb = -block, cells_per_block = tb / 3;
-    k_spmv_rows<DT><<<grid_for(g.n, cells_per_block), tb, 0, st>>>(g, J, x, y);
+    const int tb = -block, cb = grid_for(g.n, tb / 3);
+    launch(k_spmv_rows<DT>, cb + well_blocks(w, tb), tb, 0, st, g, w, J, Bw, Cw, Dw, x, y, cb);
   } else {
-    k_spmv_cells<DT><<<grid_for(g.n, block), block, 0, st>>>(g, J, x, y);
+    const int cb = grid_for(g.n, block);
+    launch(k_spmv_cells<DT>, cb + well_blocks(w, block), block, 0, st, g, w, J, Bw, Cw, Dw, x, y, cb);
   }
-  if (w.nw > 0) k_spmv_wells<DT><<<w.nw, 32, 0, st>>>(g, w, Bw, Cw, Dw, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -220,6 +238,7 @@ __device__ __forceinline__ void inverse3(const PT a[9], PT inv[9]) {
 
 template <typename DT, typename PT>
 __global__ void __launch_bounds__(256) k_bjacobi_setup(long long n, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+  PF_PDL_ENTRY();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     PT a[9];
@@ -234,6 +253,7 @@ __global__ void __launch_bounds__(256) k_bjacobi_setup(long long n, const DT* __
 
 template <typename DT, typename PT>
 __global__ void k_bjacobi_wells(int nw, const DT* __restrict__ Dw, PT* __restrict__ Dwinv) {
+  PF_PDL_ENTRY();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nw) Dwinv[t] = (PT)(1.0 / (double)Dw[t]);
 }
@@ -241,14 +261,15 @@ __global__ void k_bjacobi_wells(int nw, const DT* __restrict__ Dw, PT* __restric
 template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
                           cudaStream_t st) {
-  k_bjacobi_setup<DT, PT><<<grid_for(g.n, 256), 256, 0, st>>>(g.n, J, Dinv);
-  if (w.nw > 0) k_bjacobi_wells<DT, PT><<<grid_for(w.nw, 128), 128, 0, st>>>(w.nw, Dw, Dwinv);
+  launch(k_bjacobi_setup<DT, PT>, grid_for(g.n, 256), 256, 0, st, g.n, J, Dinv);
+  if (w.nw > 0) launch(k_bjacobi_wells<DT, PT>, grid_for(w.nw, 128), 128, 0, st, w.nw, Dw, Dwinv);
 }
 
 template <typename PT>
 __global__ void __launch_bounds__(256) k_bjacobi_apply(long long n, int nw, const PT* __restrict__ Dinv,
                                                        const PT* __restrict__ Dwinv, const double* __restrict__ r,
                                                        double* __restrict__ z) {
+  PF_PDL_ENTRY();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + nw;
        i += (long long)gridDim.x * blockDim.x) {
     if (i >= n) { z[3 * n + (i - n)] = (double)Dwinv[i - n] * r[3 * n + (i - n)]; continue; }
@@ -268,9 +289,10 @@ __global__ void __launch_bounds__(256) k_bjacobi_apply(long long n, int nw, cons
 // cells ordered first, the 7-point block pattern couples no two cells of one
 // colour, so ILU(0) keeps the red diagonal blocks D_r, replaces each black
 // one by D_b - sum_j J_bj D_j^-1 J_jb (fill between black cells dropped), and
-// its two triangular solves become three sweeps over one colour each:
-//   y_r = D_r^-1 f_r;   y_b = D'_b^-1 (f_b - sum_j J_bj y_j);
-//   y_r = D_r^-1 (f_r - sum_k J_rk y_k).
+// its two triangular solves become sweeps over one colour each:
+//   t_r = D_r^-1 f_r;   y_b = D'_b^-1 (f_b - sum_j J_bj t_j);
+//   y_r = D_r^-1 (f_r - sum_k J_rk y_k)
+// (two launches: the first line is formed inside the black sweep).
 // Well rows keep their scalar inverse, as in block-Jacobi.
 
 // The q-th cell of a colour: rows (j, k) of ceil(nx / 2) slots; in row (j, k)
@@ -310,6 +332,7 @@ __device__ __forceinline__ bool slot_nbr(const Grid& g, int s, long long i, int 
 // the red blocks' inverses (from k_bjacobi_setup) are read, not written
 template <typename DT, typename PT>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+  PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
        q += (long long)gridDim.x * blockDim.x) {
@@ -349,13 +372,39 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
   }
 }
 
-// first sweep: y_r = D_r^-1 f_r on red cells, and the well rows
+// diagonal-only first sweep: t_r = D_r^-1 f_r on the red cells, into y
 template <typename PT, typename OT>
-__global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, int nw, const PT* __restrict__ Dinv,
-                                                      const PT* __restrict__ Dwinv, const double* __restrict__ f,
-                                                      OT* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, const PT* __restrict__ Dinv,
+                                                      const double* __restrict__ f, OT* __restrict__ y) {
+  PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq + nw;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long i;
+    int x, yy, z;
+    if (!colour_cell(g, 0, q, i, x, yy, z)) continue;
+    const PT f0 = (PT)f[3 * i], f1 = (PT)f[3 * i + 1], f2 = (PT)f[3 * i + 2];
+    const PT* D = Dinv + i;
+    y[3 * i] = (OT)(D[0] * f0 + D[n] * f1 + D[2 * n] * f2);
+    y[3 * i + 1] = (OT)(D[3 * n] * f0 + D[4 * n] * f1 + D[5 * n] * f2);
+    y[3 * i + 2] = (OT)(D[6 * n] * f0 + D[7 * n] * f1 + D[8 * n] * f2);
+  }
+}
+
+// y_i = D_i^-1 (f_i - sum over neighbours J_ij t_j) on the cells of one
+// colour (the neighbours all have the other colour).  Black sweep (colour 1):
+// t_j = D_j^-1 f_j of the red neighbours, formed on the fly when fused (the
+// diagonal-only red sweep folded in), else read from y where k_ilu_red_diag
+// left it; red sweep (colour 0): t_j = y_j of the black neighbours, and the
+// threads past the cells take the well rows y_w = f_w / D_w.
+template <typename DT, typename PT, typename OT>
+__global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, int fused, int nw, const DT* __restrict__ J,
+                                                   const PT* __restrict__ Dinv, const PT* __restrict__ Dwinv,
+                                                   const double* __restrict__ f, OT* __restrict__ y) {
+  PF_PDL_ENTRY();
+  const long long n = g.n, nq = colour_slots(g);
+  const long long nt = nq + (colour == 0 ? nw : 0);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nt;
        q += (long long)gridDim.x * blockDim.x) {
     if (q >= nq) {
       const long long w = q - nq;
@@ -364,37 +413,28 @@ __global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, int nw, const PT* 
     }
     long long i;
     int x, yy, z;
-    if (!colour_cell(g, 0, q, i, x, yy, z)) continue;
-    const PT r0 = (PT)f[3 * i], r1 = (PT)f[3 * i + 1], r2 = (PT)f[3 * i + 2];
-    const PT* D = Dinv + i;
-    y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
-    y[3 * i + 1] = (OT)(D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2);
-    y[3 * i + 2] = (OT)(D[6 * n] * r0 + D[7 * n] * r1 + D[8 * n] * r2);
-  }
-}
-
-// y_i = D_i^-1 (f_i - sum over neighbours J_ij y_j) on the cells of one colour
-// (the neighbours all have the other colour)
-template <typename DT, typename PT, typename OT>
-__global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, const DT* __restrict__ J,
-                                                   const PT* __restrict__ Dinv, const double* __restrict__ f,
-                                                   OT* __restrict__ y) {
-  const long long n = g.n, nq = colour_slots(g);
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
-       q += (long long)gridDim.x * blockDim.x) {
-    long long i;
-    int x, yy, z;
     if (!colour_cell(g, colour, q, i, x, yy, z)) continue;
     PT r0 = (PT)f[3 * i], r1 = (PT)f[3 * i + 1], r2 = (PT)f[3 * i + 2];
 #pragma unroll
     for (int s = 1; s < SL_COUNT; ++s) {
       long long c;
       if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
+      PT t0, t1, t2;
+      if (colour == 1 && fused) {
+        const PT f0 = (PT)f[3 * c], f1 = (PT)f[3 * c + 1], f2 = (PT)f[3 * c + 2];
+        const PT* Dc = Dinv + c;
+        t0 = Dc[0] * f0 + Dc[n] * f1 + Dc[2 * n] * f2;
+        t1 = Dc[3 * n] * f0 + Dc[4 * n] * f1 + Dc[5 * n] * f2;
+        t2 = Dc[6 * n] * f0 + Dc[7 * n] * f1 + Dc[8 * n] * f2;
+      } else {
+        t0 = (PT)y[3 * c];
+        t1 = (PT)y[3 * c + 1];
+        t2 = (PT)y[3 * c + 2];
+      }
       const DT* B = J + (size_t)s * 9 * n + i;
-      const PT y0 = (PT)y[3 * c], y1 = (PT)y[3 * c + 1], y2 = (PT)y[3 * c + 2];
-      r0 -= (PT)B[0] * y0 + (PT)B[n] * y1 + (PT)B[2 * n] * y2;
-      r1 -= (PT)B[3 * n] * y0 + (PT)B[4 * n] * y1 + (PT)B[5 * n] * y2;
-      r2 -= (PT)B[6 * n] * y0 + (PT)B[7 * n] * y1 + (PT)B[8 * n] * y2;
+      r0 -= (PT)B[0] * t0 + (PT)B[n] * t1 + (PT)B[2 * n] * t2;
+      r1 -= (PT)B[3 * n] * t0 + (PT)B[4 * n] * t1 + (PT)B[5 * n] * t2;
+      r2 -= (PT)B[6 * n] * t0 + (PT)B[7 * n] * t1 + (PT)B[8 * n] * t2;
     }
     const PT* D = Dinv + i;
     y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
@@ -407,22 +447,23 @@ template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
                       cudaStream_t st) {
   launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
-  k_ilu_setup_black<DT, PT><<<grid_for(colour_slots_host(g), 256), 256, 0, st>>>(g, J, Dinv);
+  launch(k_ilu_setup_black<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv);
 }
 
 template <typename DT, typename PT, typename OT>
-void launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
-                      cudaStream_t st) {
+int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+                     int fused, cudaStream_t st) {
   const long long nq = colour_slots_host(g);
-  k_ilu_red_diag<PT, OT><<<grid_for(nq + nw, 256), 256, 0, st>>>(g, nw, Dinv, Dwinv, f, y);
-  k_ilu_sweep<DT, PT, OT><<<grid_for(nq, 256), 256, 0, st>>>(g, 1, J, Dinv, f, y);
-  k_ilu_sweep<DT, PT, OT><<<grid_for(nq, 256), 256, 0, st>>>(g, 0, J, Dinv, f, y);
+  if (!fused) launch(k_ilu_red_diag<PT, OT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
+  launch(k_ilu_sweep<DT, PT, OT>, grid_for(nq, 256), 256, 0, st, g, 1, fused, nw, J, Dinv, Dwinv, f, y);
+  launch(k_ilu_sweep<DT, PT, OT>, grid_for(nq + nw, 256), 256, 0, st, g, 0, fused, nw, J, Dinv, Dwinv, f, y);
+  return fused ? 2 : 3;
 }
 
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r, double* z,
                           cudaStream_t st) {
-  k_bjacobi_apply<PT><<<grid_for(g.n + nw, 256), 256, 0, st>>>(g.n, nw, Dinv, Dwinv, r, z);
+  launch(k_bjacobi_apply<PT>, grid_for(g.n + nw, 256), 256, 0, st, g.n, nw, Dinv, Dwinv, r, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -432,45 +473,52 @@ void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv
 #define GRID_STRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_copy(long long n, const double* __restrict__ a, double* __restrict__ b) { GRID_STRIDE(i, n) b[i] = a[i]; }
-__global__ void k_fill(long long n, double v, double* __restrict__ a) { GRID_STRIDE(i, n) a[i] = v; }
+__global__ void k_copy(long long n, const double* __restrict__ a, double* __restrict__ b) {
+  PF_PDL_ENTRY(); GRID_STRIDE(i, n) b[i] = a[i]; }
+__global__ void k_fill(long long n, double v, double* __restrict__ a) {
+  PF_PDL_ENTRY(); GRID_STRIDE(i, n) a[i] = v; }
 __global__ void k_scale_dev(long long n, const double* a, const double* __restrict__ s, int inv_sqrt,
                             double* b) {
+  PF_PDL_ENTRY();
   const double f = inv_sqrt ? 1.0 / sqrt(s[0]) : s[0];
   GRID_STRIDE(i, n) b[i] = a[i] * f;
 }
 __global__ void k_axpy(long long n, double al, const double* __restrict__ x, double* __restrict__ y) {
+  PF_PDL_ENTRY();
   GRID_STRIDE(i, n) y[i] += al * x[i];
 }
 __global__ void k_xpay(long long n, const double* __restrict__ x, double be, double* __restrict__ y) {
+  PF_PDL_ENTRY();
   GRID_STRIDE(i, n) y[i] = x[i] + be * y[i];
 }
 __global__ void k_sub(long long n, const double* a, const double* b, double* c) {
+  PF_PDL_ENTRY();
   GRID_STRIDE(i, n) c[i] = a[i] - b[i];
 }
 
 __global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  PF_PDL_ENTRY();
   GRID_STRIDE(i, n) b[i] = (float)a[i];
 }
 void launch_to_f32(long long n, const double* a, float* b, cudaStream_t st) {
-  k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
+  launch(k_to_f32, grid_for(n, 256), 256, 0, st, n, a, b);
 }
 
 void launch_copy(long long n, const double* a, double* b, cudaStream_t st) {
-  k_copy<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
+  launch(k_copy, grid_for(n, 256), 256, 0, st, n, a, b);
 }
-void launch_fill(long long n, double v, double* a, cudaStream_t st) { k_fill<<<grid_for(n, 256), 256, 0, st>>>(n, v, a); }
+void launch_fill(long long n, double v, double* a, cudaStream_t st) { launch(k_fill, grid_for(n, 256), 256, 0, st, n, v, a); }
 void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b, cudaStream_t st) {
-  k_scale_dev<<<grid_for(n, 256), 256, 0, st>>>(n, a, s, inv_sqrt, b);
+  launch(k_scale_dev, grid_for(n, 256), 256, 0, st, n, a, s, inv_sqrt, b);
 }
 void launch_axpy(long long n, double al, const double* x, double* y, cudaStream_t st) {
-  k_axpy<<<grid_for(n, 256), 256, 0, st>>>(n, al, x, y);
+  launch(k_axpy, grid_for(n, 256), 256, 0, st, n, al, x, y);
 }
 void launch_xpay(long long n, const double* x, double be, double* y, cudaStream_t st) {
-  k_xpay<<<grid_for(n, 256), 256, 0, st>>>(n, x, be, y);
+  launch(k_xpay, grid_for(n, 256), 256, 0, st, n, x, be, y);
 }
 void launch_sub(long long n, const double* a, const double* b, double* c, cudaStream_t st) {
-  k_sub<<<grid_for(n, 256), 256, 0, st>>>(n, a, b, c);
+  launch(k_sub, grid_for(n, 256), 256, 0, st, n, a, b, c);
 }
 
 // Block reduction of KM partial sums held per thread; thread 0 writes them.
@@ -571,6 +619,7 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
                                                   const double* __restrict__ w, double* __restrict__ partial,
                                                   int stride, double* __restrict__ out, unsigned int* counter,
                                                   int self_dot, const int* run_if) {
+  PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   double* row = partial + (size_t)blockIdx.x * stride;
   int j0 = 0;
@@ -590,6 +639,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
                                                    double* __restrict__ partial, int stride, double* __restrict__ out,
                                                    unsigned int* counter, const double* norm0, int* decide,
                                                    const int* run_if) {
+  PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   __shared__ double hs[128];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
@@ -624,17 +674,18 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
 
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
                      double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if) {
-  k_multidot<<<nblocks, 256, 0, st>>>(n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if);
+  launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if);
 }
 
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w, double* partial,
                       int nblocks, double* out, unsigned int* counter, const double* norm0, int* decide,
                       const int* run_if, cudaStream_t st) {
-  k_axpy_norm<<<nblocks, 256, 0, st>>>(n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if);
+  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
                                                         const double* __restrict__ y, double* __restrict__ x) {
+  PF_PDL_ENTRY();
   __shared__ double ys[128];
   if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
@@ -647,12 +698,12 @@ __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, cons
 
 void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y, double* x,
                            cudaStream_t st) {
-  k_multi_axpy_add<<<grid_for(n, 256), 256, 0, st>>>(n, k, Z, ld, y, x);
+  launch(k_multi_axpy_add, grid_for(n, 256), 256, 0, st, n, k, Z, ld, y, x);
 }
 
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
                 unsigned int* counter, cudaStream_t st) {
-  k_multidot<<<nblocks, 256, 0, st>>>(n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr);
+  launch(k_multidot, nblocks, 256, 0, st, n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr);
 }
 
 // explicit instantiations
@@ -668,12 +719,12 @@ template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const 
                                                double*, cudaStream_t);
 template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                              cudaStream_t);
-template void launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
-                                                       const double*, const double*, double*, cudaStream_t);
-template void launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,
-                                                    const double*, float*, cudaStream_t);
-template void launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
-                                                     const double*, double*, cudaStream_t);
+template int launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
+                                                      const double*, const double*, double*, int, cudaStream_t);
+template int launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,
+                                                   const double*, float*, int, cudaStream_t);
+template int launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
+                                                    const double*, double*, int, cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,

@@ -122,8 +122,10 @@ def test_autotuned_launch_shapes_give_identical_results(B, precision):
     base = alone(B, sc, 3, **opt)
     sim = B.Simulator(sc, autotune=1, **opt)
     t = sim.autotune()
-    assert all(v in (64, 128, 256) for k, v in t.items() if k != "spmv")
+    assert all(v in (64, 128, 256) for k, v in t.items() if k not in ("spmv", "block_cells", "ilu_fused"))
+    assert t["ilu_fused"] in (0, 1)
     assert t["spmv"] in ((64, 128, 256, -96, -192, -384) if precision == 0 else (64, 128, 256))
+    assert t["block_cells"] == (256 if precision == 0 else 4096)
     B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
     x = sim.get_x()
     sim.close()
@@ -169,7 +171,8 @@ def test_row_split_spmv_gives_identical_results(B, shape):
     ref.close()
     sim.close()
     sim = B.Simulator(sc, **opt)
-    sim.set_tuning(spmv=shape)
+    # also every multigrid level in one block, and the ILU(0) solve in three launches
+    sim.set_tuning(spmv=shape, block_cells=2048, ilu_fused=0)
     B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
     assert np.array_equal(base, sim.get_x())
     with pytest.raises(B.PfError) as e:
@@ -180,3 +183,19 @@ def test_row_split_spmv_gives_identical_results(B, shape):
     with pytest.raises(B.PfError):
         mixed.set_tuning(spmv=shape)
     mixed.close()
+
+
+def test_programmatic_launch_gives_identical_results(B):
+    """Kernels launched with programmatic dependent launch wait for their
+    predecessor before reading, so a run is bit-identical with the launch
+    attribute on and off (FP64 and mixed precision, CPR + ILU(0))."""
+    sc = G.scenario_c1(nx=13, ny=9, nz=3, n_steps=3)
+    for precision in (0, 1):
+        opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+        try:
+            B.set_programmatic_launch(False)
+            off = alone(B, sc, 3, **opt)
+        finally:
+            B.set_programmatic_launch(True)
+        on = alone(B, sc, 3, **opt)
+        assert np.array_equal(off, on)
