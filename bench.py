@@ -40,6 +40,8 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate
 HBM_FALLBACK_GBS = 6800.0         # profiling recipe fallback when no measured peak exists
 L2_BYTES = 129 * 1024 * 1024
 STAGE1 = {"bjacobi": 0, "ilu0": 1}
+SPMV_KERNEL = {False: "k_spmv_cells / k_spmv_rows (FP64, well border fused)",
+               True: "k_spmv_cells_f32 (FP32 J and vector, well border fused)"}
 
 
 def workload(name):
@@ -124,11 +126,11 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per SpMV launch from
-# the ncu captures summarised in profiles/ (None where no capture of the
-# current kernel exists); the 27M-cell figure is the 2M-cell capture scaled by
-# the number of 3x3 blocks.
-SPMV_TRAFFIC = {("c2", "fp64"): 51.35e6, ("c3s", "mixed"): 570.6e6,
-                ("c3", "mixed"): 570.6e6 * 188250000 / 14008500}
+# the ncu captures summarised in profiles/ (current kernels: the FP64 row-split
+# SpMV at 100k cells, the FP32 SpMV at 2M cells); the 27M-cell figure is the
+# 2M-cell capture scaled by the number of 3x3 blocks (traffic grows with them).
+SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 578.7e6,
+                ("c3", "mixed"): 578.7e6 * 188250000 / 14008500}
 
 
 def max_over_ranks(values, dist, device="cpu"):
@@ -290,7 +292,7 @@ def run_ours(args, rank, world, dist):
         # the FP64 operator is bound by the FP64 rate; the mixed one does FP32 arithmetic
         t_alu = spmv_flops / (FP64_PEAK_TFLOPS_NOMINAL * 1e12) if prec == B.PF_PREC_FP64 else 0.0
         if t_alu > t_hbm:
-            roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "alu", "achieved": round(tfl, 4),
+            roof = {"kernel": SPMV_KERNEL[prec == B.PF_PREC_MIXED], "bound": "alu", "achieved": round(tfl, 4),
                     "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s (FP64)",
                     "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4),
                     "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
@@ -300,7 +302,7 @@ def run_ours(args, rank, world, dist):
                     "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
         else:
-            roof = {"kernel": "k_spmv_cells+k_spmv_wells", "bound": "hbm", "achieved": round(gbs, 1),
+            roof = {"kernel": SPMV_KERNEL[prec == B.PF_PREC_MIXED], "bound": "hbm", "achieved": round(gbs, 1),
                     "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                     "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
                     "peak_kind": hbm_kind, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,

@@ -300,12 +300,15 @@ typedef struct pf_tuning {
                        one thread block (default 256 in FP64, 4096 in FP32; the tuner keeps it) */
   int ilu_fused;    /* ILU(0) solve in two launches, the diagonal red sweep folded into the black
                        sweep (1), or three launches (0); the same arithmetic either way */
+  int cluster_cells;  /* CPR: larger levels of at most this many cells (<= 16384) run in one
+                         thread-block cluster of up to 16 blocks with cluster barriers between
+                         phases; 0: none.  The same arithmetic as the per-level kernels. */
 } pf_tuning;
 pf_status pf_autotune(pf_sim* s, pf_tuning* out);
 /* Sets the launch shapes directly (for example a shape pf_autotune chose
  * earlier): every block size a multiple of 32 in [32, 256]; spmv may also be
  * -96, -192 or -384 (one thread per block row) in FP64 precision; block_cells
- * in [1, 65536]; ilu_fused 0 or 1.  Results do not depend on the shapes.  PF_EINVAL for any
+ * in [1, 65536]; ilu_fused 0 or 1; cluster_cells in [0, 16384].  Results do not depend on the shapes.  PF_EINVAL for any
  * other value. */
 pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t);
 /* Kernel launches issued by s so far (monotone counter). */

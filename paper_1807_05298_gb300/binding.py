@@ -70,7 +70,7 @@ class pf_solver_opts(C.Structure):
 
 class pf_tuning(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("props", "face", "gather", "spmv", "stage2", "rbgs", "block_cells",
-                                         "ilu_fused")]
+                                         "ilu_fused", "cluster_cells")]
 
 
 class pf_well_control(C.Structure):
@@ -396,7 +396,8 @@ class Simulator:
     def set_tuning(self, **shapes):
         t = pf_tuning()
         cur = dict(props=256, face=256, gather=256, spmv=256, stage2=256, rbgs=256,
-                   block_cells=4096 if self.opts.precision == PF_PREC_MIXED else 256, ilu_fused=1)
+                   block_cells=4096 if self.opts.precision == PF_PREC_MIXED else 256, ilu_fused=1,
+                   cluster_cells=0)
         cur.update(shapes)
         for k, v in cur.items():
             setattr(t, k, int(v))

@@ -1573,6 +1573,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     // measured on live systems the default was the faster (256 cells in FP64,
     // 4096 in FP32); pf_set_tuning can still change it
     t.block_cells = (int)s->cpr.block_cells;
+    t.cluster_cells = (int)s->cpr.cluster_cells;
   }
   PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaStreamSynchronize(st));
@@ -1580,6 +1581,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
   s->cpr.block_rbgs0 = t.rbgs;
   s->cpr.block_stage2 = t.stage2;
   if (t.block_cells > 0) s->cpr.block_cells = t.block_cells;
+  if (t.cluster_cells >= 0) s->cpr.cluster_cells = t.cluster_cells;
   s->cpr.ilu_fused = t.ilu_fused;
   // captured graphs hold the old launch shapes
   for (auto& G : s->graphs) {
@@ -1593,6 +1595,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     out->props = t.props; out->face = t.face; out->gather = t.gather;
     out->spmv = t.spmv; out->stage2 = t.stage2; out->rbgs = t.rbgs;
     out->block_cells = (int)s->cpr.block_cells;
+    out->cluster_cells = (int)s->cpr.cluster_cells;
     out->ilu_fused = t.ilu_fused;
   }
   return PF_OK;
@@ -1605,13 +1608,16 @@ pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t) {
   auto ok = [](int b) { return b >= 32 && b <= 256 && b % 32 == 0; };
   const bool spmv_ok = ok(t->spmv) || (!s->mixed && (t->spmv == -96 || t->spmv == -192 || t->spmv == -384));
   if (!ok(t->props) || !ok(t->face) || !ok(t->gather) || !spmv_ok || !ok(t->stage2) || !ok(t->rbgs) ||
-      t->block_cells < 1 || t->block_cells > 65536 || (t->ilu_fused != 0 && t->ilu_fused != 1))
+      t->block_cells < 1 || t->block_cells > 65536 || (t->ilu_fused != 0 && t->ilu_fused != 1) ||
+      t->cluster_cells < 0 || t->cluster_cells > 16384)
     return fail(PF_EINVAL, "invalid launch shape");
   PF_CUDA(cudaStreamSynchronize(s->stream));
   Tuning& u = s->tune;
   u.props = t->props; u.face = t->face; u.gather = t->gather;
   u.spmv = t->spmv; u.stage2 = t->stage2; u.rbgs = t->rbgs;
   u.block_cells = t->block_cells;
+  u.cluster_cells = t->cluster_cells;
+  s->cpr.cluster_cells = t->cluster_cells;
   u.ilu_fused = t->ilu_fused;
   s->cpr.ilu_fused = t->ilu_fused;
   s->cpr.block_rbgs0 = u.rbgs;

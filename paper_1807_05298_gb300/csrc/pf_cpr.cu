@@ -4,9 +4,13 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "pf_cpr.cuh"
 
 namespace pf {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -348,9 +352,33 @@ struct BlockLevels {
   const T* inv;
 };
 
-template <typename T>
-__device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* x, int color, bool zero_init) {
-  for (long long i = threadIdx.x; i < d.n; i += blockDim.x) {
+// The threads that run the small levels together: one block, or every block
+// of a thread-block cluster (up to 16 SMs) with the cluster barrier between
+// phases (its release/acquire ordering makes one block's writes to the level
+// arrays visible to the others).
+template <bool CL>
+struct Team {
+  int tid, stride;
+  __device__ Team() {
+    if (CL) {
+      cg::cluster_group c = cg::this_cluster();
+      tid = (int)(c.block_rank() * blockDim.x + threadIdx.x);
+      stride = (int)(c.num_blocks() * blockDim.x);
+    } else {
+      tid = threadIdx.x;
+      stride = blockDim.x;
+    }
+  }
+  __device__ void sync() const {
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+};
+
+template <typename T, bool CL>
+__device__ void b_rbgs(const Team<CL>& tm, const Dims& d, const T* A, const T* dinv, const T* b, T* x, int color,
+                       bool zero_init) {
+  for (long long i = tm.tid; i < d.n; i += tm.stride) {
     int cx, cy, cz;
     coords(d, i, cx, cy, cz);
     if (((cx + cy + cz) & 1) != color) continue;
@@ -363,7 +391,7 @@ __device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* 
     }
     x[i] = s * dinv[i];
   }
-  __syncthreads();
+  tm.sync();
 }
 
 // The cycle below the block levels, written as a loop over an explicit level
@@ -371,17 +399,18 @@ __device__ void b_rbgs(const Dims& d, const T* A, const T* dinv, const T* b, T* 
 // live in shared memory).  cnt[l] counts the coarse cycles finished at level
 // l in the current visit; level l runs gamma_l of them (1 at the finest
 // level, L.gamma below), the first from a zero initial guess.
-template <typename T>
+template <typename T, bool CL>
 __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zero_init) {
   PF_PDL_ENTRY();
   __shared__ BlockLevels<T> L;
   __shared__ int cnt[kMaxLev];
   __shared__ int zi[kMaxLev];
-  if (threadIdx.x == 0) {
+  const Team<CL> tm;
+  if (threadIdx.x == 0) {  // every block keeps its own copy of the (identical) control state
     L = Lp;
     zi[L.l0] = zero_init;
   }
-  __syncthreads();
+  tm.sync();
   const int last = L.nlev - 1;
   int l = L.l0;
   bool down = true;
@@ -390,12 +419,12 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
       const Dims d = L.d[l];
       if (l == last) {  // coarsest: dense inverse
         const int n = (int)d.n;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        for (int r = tm.tid; r < n; r += tm.stride) {
           double sacc = 0.0;
           for (int c = 0; c < n; ++c) sacc += (double)L.inv[(size_t)r * n + c] * (double)L.b[l][c];
           L.x[l][r] = (T)sacc;
         }
-        __syncthreads();
+        tm.sync();
         if (l == L.l0) return;
         --l;
         down = false;
@@ -403,15 +432,15 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
       }
       const int npre = l == 0 ? L.pre0 : L.pre;
       for (int sweep = 0; sweep < npre; ++sweep) {
-        b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, zi[l] && sweep == 0);
-        b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
+        b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, zi[l] && sweep == 0);
+        b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
       }
       const Dims c = L.d[l + 1];
       const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
       const T* A = L.A[l];
       const T* x = L.x[l];
       const T* b = L.b[l];
-      for (long long I = threadIdx.x; I < c.n; I += blockDim.x) {
+      for (long long I = tm.tid; I < c.n; I += tm.stride) {
         int cx, cy, cz;
         coords(c, I, cx, cy, cz);
         // the children's residuals in FP64, summed in the pairing order of
@@ -439,7 +468,7 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
         cnt[l] = 0;
         zi[l + 1] = 1;
       }
-      __syncthreads();
+      tm.sync();
       ++l;
       continue;
     }
@@ -459,16 +488,16 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
     const Dims d = L.d[l];
     const Dims c = L.d[l + 1];
     const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
-    for (long long i = threadIdx.x; i < d.n; i += blockDim.x) {
+    for (long long i = tm.tid; i < d.n; i += tm.stride) {
       int X, Y, Z;
       coords(d, i, X, Y, Z);
       L.x[l][i] += L.x[l + 1][X / fx + c.nx * (Y / fy + (long long)c.ny * (Z / fz))];
     }
-    __syncthreads();
+    tm.sync();
     const int npost = l == 0 ? L.post0 : L.post;
     for (int sweep = 0; sweep < npost; ++sweep) {
-      b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
-      b_rbgs<T>(d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, false);
+      b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
+      b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, false);
     }
     if (l == L.l0) return;
     --l;
@@ -511,7 +540,7 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
     k += 1;
     return false;
   }
-  if (L.n <= c.block_cells) {  // this level and all coarser ones in one block
+  if (L.n <= c.block_cells || L.n <= c.cluster_cells) {  // this level and all coarser ones in one block or cluster
     BlockLevels<T> B;
     B.l0 = l; B.nlev = c.nlev; B.gamma = c.cycle_gamma;
     B.pre0 = c.pre; B.post0 = c.post; B.pre = c.cpre; B.post = c.cpost;
@@ -520,7 +549,13 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
       B.A[q] = (T*)c.lev[q].A; B.dinv[q] = (T*)c.lev[q].dinv; B.x[q] = (T*)c.lev[q].x; B.b[q] = (T*)c.lev[q].b;
     }
     B.inv = (const T*)c.coarse_inv;
-    launch(k_block_cycle<T>, 1, 1024, 0, st, B, zero_init ? 1 : 0);
+    if (L.n <= c.block_cells) {
+      launch(k_block_cycle<T, false>, 1, 1024, 0, st, B, zero_init ? 1 : 0);
+    } else {
+      unsigned int cs = 2;  // a power of two, about one cell per thread, at most 16 blocks
+      while (cs < 16 && (long long)cs * 1024 < L.n) cs *= 2;
+      launch_cluster(k_block_cycle<T, true>, cs, 1024, st, B, zero_init ? 1 : 0);
+    }
     k += 1;
     return false;
   }

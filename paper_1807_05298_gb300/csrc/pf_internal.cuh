@@ -81,6 +81,7 @@ struct Wells {
 struct Tuning {
   int props = 256, face = 256, gather = 256, spmv = 256, stage2 = 256, rbgs = 256;
   int block_cells = 0;  // single-block multigrid levels up to this size (0: the CPR default)
+  int cluster_cells = -1;  // thread-block-cluster levels up to this size (-1: the CPR default)
   int ilu_fused = 1;    // ILU(0) solve: diagonal red sweep folded into the black sweep (1) or separate (0)
 };
 

@@ -40,4 +40,33 @@ inline void launch(void (*kern)(KArgs...), unsigned int grid, unsigned int block
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// One thread-block cluster of `cluster` blocks (<= 16; above 8 the kernel must
+// allow non-portable cluster sizes, which this sets once per kernel).
+template <typename... KArgs, typename... Args>
+inline void launch_cluster(void (*kern)(KArgs...), unsigned int cluster, unsigned int block, cudaStream_t st,
+                           Args... args) {
+  if (cluster > 8) {
+    static bool set = false;  // per kernel instantiation
+    if (!set) {
+      cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      set = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace pf

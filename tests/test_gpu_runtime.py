@@ -122,7 +122,8 @@ def test_autotuned_launch_shapes_give_identical_results(B, precision):
     base = alone(B, sc, 3, **opt)
     sim = B.Simulator(sc, autotune=1, **opt)
     t = sim.autotune()
-    assert all(v in (64, 128, 256) for k, v in t.items() if k not in ("spmv", "block_cells", "ilu_fused"))
+    assert all(v in (64, 128, 256) for k, v in t.items()
+               if k not in ("spmv", "block_cells", "ilu_fused", "cluster_cells"))
     assert t["ilu_fused"] in (0, 1)
     assert t["spmv"] in ((64, 128, 256, -96, -192, -384) if precision == 0 else (64, 128, 256))
     assert t["block_cells"] == (256 if precision == 0 else 4096)
@@ -199,3 +200,23 @@ def test_programmatic_launch_gives_identical_results(B):
             B.set_programmatic_launch(True)
         on = alone(B, sc, 3, **opt)
         assert np.array_equal(off, on)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_cycle_gives_identical_results(B, precision):
+    """The multigrid levels run by one thread-block cluster (cluster barriers
+    between phases) round exactly like the per-level kernels: a run is
+    bit-identical with the cluster path on and off."""
+    sc = G.scenario_c1(nx=40, ny=36, nz=6, n_steps=2)        # finest 8640 cells, next 1080
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+    base = B.Simulator(sc, **opt)
+    base.set_tuning(block_cells=64, cluster_cells=0)
+    B.run_schedule(base, B.Schedule(sc["schedule"], 2))
+    xb = base.get_x()
+    base.close()
+    for cells in (2048, 16384):
+        sim = B.Simulator(sc, **opt)
+        sim.set_tuning(block_cells=64, cluster_cells=cells)
+        B.run_schedule(sim, B.Schedule(sc["schedule"], 2))
+        assert np.array_equal(sim.get_x(), xb)
+        sim.close()
