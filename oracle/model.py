@@ -677,10 +677,13 @@ def limit_crossings(st, x, controls, switched):
     return changed
 
 
-def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, record=None, switched=None):
+def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, record=None, switched=None,
+                div=1e6):
     """One backward-Euler step by Newton's method (Algorithm 1) under the user
     controls; rate wells flagged in ``switched`` (updated in place by the
-    in-iteration limit check) run on their BHP limit.
+    in-iteration limit check) run on their BHP limit.  The step fails at the
+    iteration cap, on a non-finite residual, or once the scaled residual
+    exceeds ``div`` times its first value (runaway iterates; 0 disables).
 
     Returns (x_new, converged, iterations)."""
     if switched is None:
@@ -696,6 +699,10 @@ def newton_step(st, x_old, dt, controls, tol=1e-10, max_iter=25, ds_max=0.2, rec
             record.append(res)
         if res <= tol:
             return x, True, it
+        if it == 0:
+            res0 = res
+        elif div > 0.0 and res > div * res0:
+            break
         if it == max_iter or not np.all(np.isfinite(R)):
             break
         dx = solve_linear(J, -R)

@@ -65,7 +65,8 @@ class pf_solver_opts(C.Structure):
                 ("dc_frac", C.c_double),
                 ("amg_pre_sweeps", C.c_int), ("amg_post_sweeps", C.c_int), ("amg_coarse_size", C.c_int),
                 ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int),
-                ("stage1", C.c_int), ("amg_coarse_sweeps", C.c_int)]
+                ("stage1", C.c_int), ("amg_coarse_sweeps", C.c_int), ("reorth_eta", C.c_double),
+                ("ilu_guard", C.c_double), ("newton_div", C.c_double)]
 
 
 class pf_tuning(C.Structure):
@@ -251,7 +252,7 @@ class Model:
 
 
 def set_programmatic_launch(on):
-    """Process-wide switch for programmatic dependent launch (default on)."""
+    """Process-wide switch for programmatic dependent launch (default off)."""
     _check(lib().pf_set_programmatic_launch(1 if on else 0))
 
 

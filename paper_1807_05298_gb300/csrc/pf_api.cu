@@ -23,7 +23,7 @@ static pf_status fail(pf_status st, const std::string& msg) {
   return st;
 }
 
-static std::atomic<bool> g_pdl{true};
+static std::atomic<bool> g_pdl{false};
 
 namespace pf {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -118,6 +118,7 @@ struct pf_sim {
   double* d_sat = nullptr;      // saturation table (structure of arrays with slopes)
   double* d_poly = nullptr;     // polymer table
   int iter_in_step = 0;
+  double res0 = 0.0;            // scaled residual at the first iteration of the step
 };
 
 namespace {
@@ -316,6 +317,9 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
       return fail(PF_EINVAL, "invalid multigrid parameters");
     if (o->forcing_form < 1 || o->forcing_form > 3) return fail(PF_EINVAL, "forcing_form must be 1, 2 or 3");
     if (o->stage1 != PF_S1_BJACOBI && o->stage1 != PF_S1_ILU0) return fail(PF_EINVAL, "invalid stage1");
+    if (!(o->reorth_eta >= 0.0 && o->reorth_eta <= 1.0)) return fail(PF_EINVAL, "reorth_eta must lie in [0, 1]");
+    if (std::isnan(o->ilu_guard)) return fail(PF_EINVAL, "ilu_guard is NaN");
+    if (!(o->newton_div >= 0.0)) return fail(PF_EINVAL, "newton_div must be >= 0");
   }
   return PF_OK;
 }
@@ -446,14 +450,14 @@ pf_status precond_setup(pf_sim* s) {
   if (s->mixed) {
     if (ilu)
       launch_ilu_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
-                                     (float*)s->Dwinv, s->stream);
+                                     (float*)s->Dwinv, s->opts.ilu_guard, s->stream);
     else
       launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
                                          (float*)s->Dwinv, s->stream);
   } else {
     if (ilu)
       launch_ilu_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
-                                       (double*)s->Dwinv, s->stream);
+                                       (double*)s->Dwinv, s->opts.ilu_guard, s->stream);
     else
       launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
                                            (double*)s->Dwinv, s->stream);
@@ -545,8 +549,9 @@ pf_status piece_ortho(pf_sim* s, int j) {
   // overwrites hbuf[256..257].
   int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
   launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr);
+  const double eta2 = s->opts.reorth_eta * s->opts.reorth_eta;
   launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, s->hbuf + k,
-                   reorth, nullptr, st);
+                   reorth, nullptr, st, eta2);
   launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
   launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
                    nullptr, reorth, st);
@@ -760,6 +765,9 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->forcing_form = 3;
   o->stage1 = PF_S1_ILU0;
   o->amg_coarse_sweeps = -1;
+  o->reorth_eta = 0.70710678118654752;
+  o->ilu_guard = 0.1;
+  o->newton_div = 1e6;
   return PF_OK;
 }
 
@@ -1150,6 +1158,16 @@ static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_upd
     r.converged = 1;
     if (rep) *rep = r;
     return PF_OK;
+  }
+  if (s->iter_in_step == 0) {
+    s->res0 = scaled;
+  } else if (s->opts.newton_div > 0.0 && scaled > s->opts.newton_div * s->res0) {
+    // the iterates run away (a step too long for the start of a transient):
+    // give up now rather than at the iteration cap, so that the caller cuts
+    // the step before Krylov solves on runaway states cost hundreds of
+    // iterations each
+    if (rep) *rep = r;
+    return fail(PF_ENOT_CONVERGED, "Newton iteration diverged");
   }
   if (!allow_update) {
     if (rep) *rep = r;

@@ -135,7 +135,8 @@ template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
                           PT* Dwinv, cudaStream_t st);
 template <typename DT, typename PT>
-void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, cudaStream_t st);
+void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, double guard,
+                      cudaStream_t st);
 template <typename DT, typename PT, typename OT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
                      int fused, cudaStream_t st);  // returns the number of launches
@@ -164,7 +165,8 @@ void launch_multidot(long long n, int k, const double* V, long long ld, const do
 // |w|^2 < norm0[0] / 2 (a second Gram-Schmidt pass is needed)
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w,
                       double* partial, int nblocks, double* out, unsigned int* counter, const double* norm0,
-                      int* decide, const int* run_if, cudaStream_t st);
+                      int* decide, const int* run_if, cudaStream_t st,
+                      double eta2 = 0.5);
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
                      const float* Dw, const float* x, double* y, cudaStream_t st, int block = 256);
 // x += sum_j Z[j] y[j]

@@ -21,7 +21,7 @@
 
 namespace pf {
 
-// process-wide switch (pf_set_programmatic_launch); on by default
+// process-wide switch (pf_set_programmatic_launch); off by default
 bool pdl_enabled();
 
 template <typename... KArgs, typename... Args>

@@ -219,6 +219,11 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
 // (the inverse is formed in the storage precision PT: FP64 for the plain
 // path, FP32 for the mixed one)
 template <typename PT>
+__device__ __forceinline__ PT det3(const PT a[9]) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) + a[1] * (a[5] * a[6] - a[3] * a[8]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+
+template <typename PT>
 __device__ __forceinline__ void inverse3(const PT a[9], PT inv[9]) {
   const PT c00 = a[4] * a[8] - a[5] * a[7];
   const PT c01 = a[5] * a[6] - a[3] * a[8];
@@ -331,7 +336,8 @@ __device__ __forceinline__ bool slot_nbr(const Grid& g, int s, long long i, int 
 // black diagonal blocks: D'_b = D_b - sum_j J_bj D_j^-1 J_jb, then inverted;
 // the red blocks' inverses (from k_bjacobi_setup) are read, not written
 template <typename DT, typename PT>
-__global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+__global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
+                                                          PT guard) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -342,6 +348,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
     PT a[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
+    const PT det0 = det3(a);
 #pragma unroll
     for (int s = 1; s < SL_COUNT; ++s) {
       long long c;
@@ -364,6 +371,14 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
 #pragma unroll
         for (int r = 0; r < 3; ++r) a[3 * r + col] -= T[3 * r] * u0 + T[3 * r + 1] * u1 + T[3 * r + 2] * u2;
       }
+    }
+    // pivot guard: det(D'_b) / det(D_b) = det(I - D_b^-1 S) measures how much
+    // closer to singular the Schur update made the block; below `guard` (or
+    // of the other sign, or not finite) the cell keeps its own block D_b
+    const PT ratio = det3(a) / det0;
+    if (!(ratio > guard)) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
     }
     PT inv[9];
     inverse3(a, inv);
@@ -445,9 +460,9 @@ __global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, int fused
 
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
-                      cudaStream_t st) {
+                      double guard, cudaStream_t st) {
   launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
-  launch(k_ilu_setup_black<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv);
+  launch(k_ilu_setup_black<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv, (PT)guard);
 }
 
 template <typename DT, typename PT, typename OT>
@@ -631,14 +646,15 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
 }
 
 // w -= sum_{j<k} V_j h[j], then out[0] = |w|^2 and out[1] = 1 / |w|.  With
-// norm0 and decide: *decide = 1 when the update removed more than half of
-// |w|^2 (|w_new|^2 < |w_old|^2 / 2 = norm0 / 2), i.e. when a second
-// Gram-Schmidt pass is needed ("twice is enough").  run_if as in k_multidot.
+// norm0 and decide: *decide = 1 when |w_new|^2 < eta2 |w_old|^2 (eta2 =
+// norm0-relative threshold, 1/2 by default: the update removed more than half
+// of |w|^2), i.e. when a second Gram-Schmidt pass is needed ("twice is
+// enough").  run_if as in k_multidot.
 __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const double* __restrict__ V, long long ld,
                                                    const double* __restrict__ h, double* __restrict__ w,
                                                    double* __restrict__ partial, int stride, double* __restrict__ out,
                                                    unsigned int* counter, const double* norm0, int* decide,
-                                                   const int* run_if) {
+                                                   const int* run_if, double eta2) {
   PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   __shared__ double hs[128];
@@ -666,7 +682,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
     if (threadIdx.x == 0) {
       out[0] = sum;
       out[1] = sum > 0.0 ? 1.0 / sqrt(sum) : 0.0;
-      if (decide) *decide = (sum < 0.5 * norm0[0]) ? 1 : 0;
+      if (decide) *decide = (sum < eta2 * norm0[0]) ? 1 : 0;
       *counter = 0u;
     }
   }
@@ -679,8 +695,8 @@ void launch_multidot(long long n, int k, const double* V, long long ld, const do
 
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w, double* partial,
                       int nblocks, double* out, unsigned int* counter, const double* norm0, int* decide,
-                      const int* run_if, cudaStream_t st) {
-  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if);
+                      const int* run_if, cudaStream_t st, double eta2) {
+  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if, eta2);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
@@ -716,9 +732,9 @@ template void launch_bjacobi_setup<double, double>(const Grid&, const Wells&, co
 template void launch_bjacobi_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                                  cudaStream_t);
 template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const double*, const double*, double*,
-                                               double*, cudaStream_t);
+                                               double*, double, cudaStream_t);
 template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
-                                             cudaStream_t);
+                                             double, cudaStream_t);
 template int launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
                                                       const double*, const double*, double*, int, cudaStream_t);
 template int launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,

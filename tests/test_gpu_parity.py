@@ -378,11 +378,13 @@ def test_equilibrium_state_is_a_rest_state_on_the_gpu(B):
     sim.close()
 
 
-def rb_block_ilu0_apply(sc, J_csr, v):
+def rb_block_ilu0_apply(sc, J_csr, v, guard=0.1):
     """Reference red-black block ILU(0) solve, written from its definition:
     red cells (i + j + k even) first; the factor keeps the red diagonal
-    blocks and replaces each black one by D_b - sum_j J_bj D_j^-1 J_jb; then
-    forward and backward substitution.  Well rows: v_w / D_w."""
+    blocks and replaces each black one by D_b - sum_j J_bj D_j^-1 J_jb
+    (unless det of the result over det(D_b) is not above `guard`, when the
+    cell keeps D_b); then forward and backward substitution.  Well rows:
+    v_w / D_w."""
     nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
     n = nx * ny * nz
     J = J_csr.tocsr()
@@ -402,9 +404,12 @@ def rb_block_ilu0_apply(sc, J_csr, v):
     Dinv = {c: np.linalg.inv(blk(c, c)) for c in idx[red]}
     Dp = {}
     for c in idx[~red]:
-        D = blk(c, c)
+        D0 = blk(c, c)
+        D = D0
         for r in nbrs(c):
             D = D - blk(c, r) @ Dinv[r] @ blk(r, c)
+        if not np.linalg.det(D) / np.linalg.det(D0) > guard:
+            D = D0
         Dp[c] = np.linalg.inv(D)
     f = v[:3 * n].reshape(n, 3)
     y = np.zeros((n, 3))

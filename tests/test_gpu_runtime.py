@@ -193,12 +193,12 @@ def test_programmatic_launch_gives_identical_results(B):
     sc = G.scenario_c1(nx=13, ny=9, nz=3, n_steps=3)
     for precision in (0, 1):
         opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+        off = alone(B, sc, 3, **opt)
         try:
-            B.set_programmatic_launch(False)
-            off = alone(B, sc, 3, **opt)
-        finally:
             B.set_programmatic_launch(True)
-        on = alone(B, sc, 3, **opt)
+            on = alone(B, sc, 3, **opt)
+        finally:
+            B.set_programmatic_launch(False)
         assert np.array_equal(off, on)
 
 
@@ -220,3 +220,36 @@ def test_cluster_cycle_gives_identical_results(B, precision):
         B.run_schedule(sim, B.Schedule(sc["schedule"], 2))
         assert np.array_equal(sim.get_x(), xb)
         sim.close()
+
+
+def test_runaway_step_fails_early_and_restores_the_state(B):
+    """The library's divergence test: with near-exact linear solves (the
+    oracle's Newton path) a 30000-day first step runs away, so the step
+    fails with PF_ENOT_CONVERGED before the Newton cap and the state is
+    restored; with the test off it fails only at the cap."""
+    dt = 30000.0 * DAY
+    sc = G.scenario_c1(n_steps=1, dt_days=30000.0)
+    ctl = sc["schedule"][0]["controls"]
+    its = {}
+    for div in (1e6, 0.0):
+        sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=0, lin_rtol=1e-12, gmres_max_iter=600,
+                          newton_div=div)
+        sim.set_controls(ctl)
+        x0 = sim.get_x()
+        rc, rep = sim.step(dt, raise_on_failure=False)
+        assert rc == B.PF_ENOT_CONVERGED
+        assert np.array_equal(sim.get_x(), x0)
+        sim.begin_step(dt)
+        n = 0
+        while True:
+            try:
+                r = sim.newton_iteration()
+            except B.PfError as e:
+                assert e.status == B.PF_ENOT_CONVERGED
+                break
+            assert not r.converged
+            n += 1
+        sim.abort_step()
+        its[div] = n
+        sim.close()
+    assert its[1e6] < its[0.0] and its[1e6] < 25

@@ -602,3 +602,23 @@ def test_equilibrium_continuous_leg_is_the_exponential_profile():
     p0, z0, z1 = 180.0 * BAR, 1000.0, 1350.0
     exact = pref - 1.0 / c + (p0 - pref + 1.0 / c) * math.exp(g * r * c * (z1 - z0))
     assert M._march_continuous(ph, "o", p0, z0, z1) == pytest.approx(exact, rel=1e-13)
+
+
+def test_newton_gives_up_on_runaway_iterates():
+    """A 300-day first step on the 10x10x3 case runs away (the scaled
+    residual grows by orders of magnitude); with the divergence test the
+    step fails as soon as the residual passes 1e6 times its first value,
+    without it only at the iteration cap; the time loop then cuts."""
+    sc = G.scenario_c1(n_steps=1, dt_days=300.0)
+    st = M.Setup(sc)
+    x0 = M.initial_state(st)
+    ctl = M.controls_with_defaults(sc["schedule"][0]["controls"])
+    rec_off, rec_on = [], []
+    _, ok_off, _ = M.newton_step(st, x0, 300.0 * DAY, ctl, record=rec_off, switched=[False] * st.nw, div=0.0)
+    _, ok_on, _ = M.newton_step(st, x0, 300.0 * DAY, ctl, record=rec_on, switched=[False] * st.nw, div=1e6)
+    assert not ok_off and not ok_on
+    assert len(rec_off) == 26 and len(rec_on) < len(rec_off)
+    assert rec_on[-1] > 1e6 * rec_on[0] and max(rec_on[:-1]) <= 1e6 * rec_on[0]
+    assert rec_on == rec_off[:len(rec_on)]
+    _, _, hist = M.run(sc)
+    assert hist[0]["cuts"] >= 1 and abs(sum(hist[0]["substeps"]) - 300.0 * DAY) <= 1e-6 * DAY
