@@ -165,6 +165,11 @@ typedef struct pf_solver_opts {
   double newton_div;    /* Newton gives up on the step (PF_ENOT_CONVERGED) once the scaled residual
                            exceeds newton_div times its value at the step's first iteration
                            (default 1e6; 0: only the iteration cap) */
+  int ilu_store;        /* ILU(0) sweeps read 0: J itself (whose cache lines also hold the other
+                           colour's rows), 1: a compact copy of each colour's off-diagonal blocks
+                           in J's precision, 2: the same copy in BF16 (mixed precision only);
+                           made at each preconditioner set-up.  -1 (default): 2 in mixed and 1 in
+                           FP64 precision from 1,000,000 cells on, else 0 */
 } pf_solver_opts;
 
 typedef struct pf_well_control {

@@ -320,6 +320,8 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (!(o->reorth_eta >= 0.0 && o->reorth_eta <= 1.0)) return fail(PF_EINVAL, "reorth_eta must lie in [0, 1]");
     if (std::isnan(o->ilu_guard)) return fail(PF_EINVAL, "ilu_guard is NaN");
     if (!(o->newton_div >= 0.0)) return fail(PF_EINVAL, "newton_div must be >= 0");
+    if (o->ilu_store < -1 || o->ilu_store > 2 || (o->ilu_store == 2 && o->precision != PF_PREC_MIXED))
+      return fail(PF_EINVAL, "ilu_store must be -1, 0, 1, or 2 (BF16, mixed precision only)");
   }
   return PF_OK;
 }
@@ -389,6 +391,16 @@ size_t carve(pf_sim* s, char* base) {
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
   s->red_counter = c.take<unsigned int>(64);
+  {
+    // compact ILU block copies: 2 colours x 54 values per colour slot
+    int kind = s->opts.ilu_store;
+    if (kind < 0) kind = s->g.n >= 1000000 ? (s->mixed ? 2 : 1) : 0;  // automatic: the copy pays off on large grids
+    if (s->opts.stage1 != PF_S1_ILU0) kind = 0;
+    const size_t es = kind == 2 ? 2 : dts;
+    const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
+    s->cpr.ilu_cp.kind = kind;
+    for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
+  }
   s->w_perf_of = c.take<int>(n);
   s->w_pwell = c.take<int>(std::max(1LL, s->npf));
   s->d_sat = s->ph.n_sat > 0 ? c.take<double>((size_t)7 * s->ph.n_sat) : nullptr;
@@ -450,14 +462,14 @@ pf_status precond_setup(pf_sim* s) {
   if (s->mixed) {
     if (ilu)
       launch_ilu_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
-                                     (float*)s->Dwinv, s->opts.ilu_guard, s->stream);
+                                     (float*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream);
     else
       launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
                                          (float*)s->Dwinv, s->stream);
   } else {
     if (ilu)
       launch_ilu_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
-                                       (double*)s->Dwinv, s->opts.ilu_guard, s->stream);
+                                       (double*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream);
     else
       launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
                                            (double*)s->Dwinv, s->stream);
@@ -485,10 +497,12 @@ pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullp
     int nl;
     if (s->mixed)
       nl = launch_ilu_apply<float, float, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
-                                                  (const float*)s->Dwinv, v, z, s->tune.ilu_fused, s->stream);
+                                                  (const float*)s->Dwinv, v, z, s->tune.ilu_fused, s->cpr.ilu_cp,
+                                                  s->stream);
     else
       nl = launch_ilu_apply<double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
-                                                    (const double*)s->Dwinv, v, z, s->tune.ilu_fused, s->stream);
+                                                    (const double*)s->Dwinv, v, z, s->tune.ilu_fused, s->cpr.ilu_cp,
+                                                    s->stream);
     PF_LAUNCHED(nl);
   } else {
     if (s->mixed)
@@ -768,6 +782,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->reorth_eta = 0.70710678118654752;
   o->ilu_guard = 0.1;
   o->newton_div = 1e6;
+  o->ilu_store = -1;
   return PF_OK;
 }
 

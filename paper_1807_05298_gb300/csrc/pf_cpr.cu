@@ -700,7 +700,8 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
              const void* Dwinv, const double* v, double* z, cudaStream_t st, int& k) {
   // stage 1: y = D^{-1} f, or the red-black block ILU(0) solve (cells; wells by their diagonal)
   if (c.ilu) {
-    k += launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, c.ilu_fused, st);
+    k += launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, c.ilu_fused,
+                                        c.ilu_cp, st);
   } else {
     launch_bjacobi_apply<T>(g, w.nw, (const T*)Dinv, (const T*)Dwinv, v, z, st);
     k += 1;
@@ -809,7 +810,7 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
     const int gb = grid_for(g.n + w.nw, 256);
     if (c.ilu) {
       k += launch_ilu_apply<float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv, (const float*)Dwinv, v,
-                                                 zf, c.ilu_fused, st);
+                                                 zf, c.ilu_fused, c.ilu_cp, st);
     } else {
       launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
       k += 1;

@@ -134,12 +134,18 @@ void launch_spmv(const Grid& g, const Wells& w, const DT* J, const DT* Bw, const
 template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
                           PT* Dwinv, cudaStream_t st);
+// Compact per-colour copies of the off-diagonal blocks for the ILU(0) sweeps:
+// kind 0 none (the sweeps read J), 1 in the Jacobian's precision, 2 BF16.
+struct IluCompact {
+  int kind = 0;
+  void* c[2] = {nullptr, nullptr};  // red, black: [6 slots][9 entries][colour slots]
+};
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, double guard,
-                      cudaStream_t st);
+                      const IluCompact& cp, cudaStream_t st);
 template <typename DT, typename PT, typename OT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
-                     int fused, cudaStream_t st);  // returns the number of launches
+                     int fused, const IluCompact& cp, cudaStream_t st);  // returns the number of launches
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);

@@ -2,6 +2,7 @@
 // ordering): 7-point 3x3-block SpMV on the structured grid with the bordered
 // well rows and columns, block-Jacobi, and the FP64 vector kernels of the
 // restarted Krylov solver (deterministic two-stage reductions).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "pf_internal.cuh"
@@ -412,8 +413,18 @@ __global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, const PT* __restri
 // diagonal-only red sweep folded in), else read from y where k_ilu_red_diag
 // left it; red sweep (colour 0): t_j = y_j of the black neighbours, and the
 // threads past the cells take the well rows y_w = f_w / D_w.
-template <typename DT, typename PT, typename OT>
-__global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, int fused, int nw, const DT* __restrict__ J,
+__device__ __forceinline__ float as_pt(float v, float) { return v; }
+__device__ __forceinline__ float as_pt(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ double as_pt(double v, double) { return v; }
+__device__ __forceinline__ double as_pt(float v, double) { return (double)v; }
+__device__ __forceinline__ double as_pt(__nv_bfloat16 v, double) { return (double)__bfloat162float(v); }
+
+// With COMPACT the off-diagonal blocks come from this colour's compact copy
+// (k_ilu_compact: slot-major, indexed by the colour slot q, so a sweep reads
+// only its own rows); otherwise from J itself, whose lines also carry the
+// other colour's rows.
+template <typename BT, typename PT, typename OT, bool COMPACT>
+__global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int colour, int fused, int nw, const BT* __restrict__ J,
                                                    const PT* __restrict__ Dinv, const PT* __restrict__ Dwinv,
                                                    const double* __restrict__ f, OT* __restrict__ y) {
   PF_PDL_ENTRY();
@@ -446,10 +457,12 @@ __global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, int fused
         t1 = (PT)y[3 * c + 1];
         t2 = (PT)y[3 * c + 2];
       }
-      const DT* B = J + (size_t)s * 9 * n + i;
-      r0 -= (PT)B[0] * t0 + (PT)B[n] * t1 + (PT)B[2 * n] * t2;
-      r1 -= (PT)B[3 * n] * t0 + (PT)B[4 * n] * t1 + (PT)B[5 * n] * t2;
-      r2 -= (PT)B[6 * n] * t0 + (PT)B[7 * n] * t1 + (PT)B[8 * n] * t2;
+      const BT* B = COMPACT ? J + (size_t)(s - 1) * 9 * nq + q : J + (size_t)s * 9 * n + i;
+      const long long m = COMPACT ? nq : n;
+      const PT pz{};
+      r0 -= as_pt(B[0], pz) * t0 + as_pt(B[m], pz) * t1 + as_pt(B[2 * m], pz) * t2;
+      r1 -= as_pt(B[3 * m], pz) * t0 + as_pt(B[4 * m], pz) * t1 + as_pt(B[5 * m], pz) * t2;
+      r2 -= as_pt(B[6 * m], pz) * t0 + as_pt(B[7 * m], pz) * t1 + as_pt(B[8 * m], pz) * t2;
     }
     const PT* D = Dinv + i;
     y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
@@ -458,20 +471,63 @@ __global__ void __launch_bounds__(256) k_ilu_sweep(Grid g, int colour, int fused
   }
 }
 
+// compact per-colour copy of the six off-diagonal blocks of every row, in the
+// storage type CT (the Jacobian's own, or BF16)
+__device__ __forceinline__ float to_ct(float v, float) { return v; }
+__device__ __forceinline__ double to_ct(double v, double) { return v; }
+__device__ __forceinline__ __nv_bfloat16 to_ct(float v, __nv_bfloat16) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return __float2bfloat16_rn((float)v); }
+
+template <typename DT, typename CT>
+__global__ void __launch_bounds__(256) k_ilu_compact(Grid g, const DT* __restrict__ J, CT* __restrict__ c0,
+                                                     CT* __restrict__ c1) {
+  PF_PDL_ENTRY();
+  const long long n = g.n, nq = colour_slots(g);
+  const unsigned int hx = ((unsigned int)g.nx + 1u) >> 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned int ui = (unsigned int)i, nxu = (unsigned int)g.nx;
+    const unsigned int row = ui / nxu, x = ui - row * nxu;
+    const unsigned int y = row % (unsigned int)g.ny, z = row / (unsigned int)g.ny;
+    CT* dst = ((x + y + z) & 1u) ? c1 : c0;
+    const long long q = (long long)row * hx + (x >> 1);
+    const CT zc{};
+#pragma unroll
+    for (int s = 1; s < SL_COUNT; ++s)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) dst[(size_t)((s - 1) * 9 + e) * nq + q] = to_ct(J[(size_t)(s * 9 + e) * n + i], zc);
+  }
+}
+
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
-                      double guard, cudaStream_t st) {
+                      double guard, const IluCompact& cp, cudaStream_t st) {
   launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
   launch(k_ilu_setup_black<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv, (PT)guard);
+  if (cp.kind == 1)
+    launch(k_ilu_compact<DT, DT>, grid_for(g.n, 256), 256, 0, st, g, J, (DT*)cp.c[0], (DT*)cp.c[1]);
+  else if (cp.kind == 2)
+    launch(k_ilu_compact<DT, __nv_bfloat16>, grid_for(g.n, 256), 256, 0, st, g, J, (__nv_bfloat16*)cp.c[0],
+           (__nv_bfloat16*)cp.c[1]);
 }
 
 template <typename DT, typename PT, typename OT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
-                     int fused, cudaStream_t st) {
+                     int fused, const IluCompact& cp, cudaStream_t st) {
   const long long nq = colour_slots_host(g);
   if (!fused) launch(k_ilu_red_diag<PT, OT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
-  launch(k_ilu_sweep<DT, PT, OT>, grid_for(nq, 256), 256, 0, st, g, 1, fused, nw, J, Dinv, Dwinv, f, y);
-  launch(k_ilu_sweep<DT, PT, OT>, grid_for(nq + nw, 256), 256, 0, st, g, 0, fused, nw, J, Dinv, Dwinv, f, y);
+  for (int colour = 1; colour >= 0; --colour) {
+    const long long nt = colour == 0 ? nq + nw : nq;
+    if (cp.kind == 1)
+      launch(k_ilu_sweep<DT, PT, OT, true>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw,
+             (const DT*)cp.c[colour], Dinv, Dwinv, f, y);
+    else if (cp.kind == 2)
+      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw,
+             (const __nv_bfloat16*)cp.c[colour], Dinv, Dwinv, f, y);
+    else
+      launch(k_ilu_sweep<DT, PT, OT, false>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw, J, Dinv, Dwinv, f,
+             y);
+  }
   return fused ? 2 : 3;
 }
 
@@ -732,15 +788,16 @@ template void launch_bjacobi_setup<double, double>(const Grid&, const Wells&, co
 template void launch_bjacobi_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                                  cudaStream_t);
 template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const double*, const double*, double*,
-                                               double*, double, cudaStream_t);
+                                               double*, double, const IluCompact&, cudaStream_t);
 template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
-                                             double, cudaStream_t);
+                                             double, const IluCompact&, cudaStream_t);
 template int launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
-                                                      const double*, const double*, double*, int, cudaStream_t);
+                                                      const double*, const double*, double*, int, const IluCompact&,
+                                                      cudaStream_t);
 template int launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,
-                                                   const double*, float*, int, cudaStream_t);
+                                                   const double*, float*, int, const IluCompact&, cudaStream_t);
 template int launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
-                                                    const double*, double*, int, cudaStream_t);
+                                                    const double*, double*, int, const IluCompact&, cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,
