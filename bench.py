@@ -610,7 +610,7 @@ def main():
     ap.add_argument("--amg-pre", type=int, default=2)
     ap.add_argument("--amg-post", type=int, default=2)
     ap.add_argument("--amg-cycle", type=int, default=1)
-    ap.add_argument("--reorth-eta", type=float, default=0.70710678118654752,
+    ap.add_argument("--reorth-eta", type=float, default=0.2,
                     help="second Gram-Schmidt pass when the first leaves less than this fraction of |w|")
     ap.add_argument("--amg-coarse", type=int, default=-1,
                     help="smoothing sweeps on the levels below the finest (-1: as on the finest)")

@@ -158,7 +158,8 @@ typedef struct pf_solver_opts {
   int amg_coarse_sweeps;  /* pre- and post-smoothing sweeps on the levels below the finest;
                              -1: the finest level's counts (default -1) */
   double reorth_eta;    /* classical Gram-Schmidt takes its second pass when the first one left less
-                           than reorth_eta of |w| (default 1/sqrt(2); 0: never, 1: always) */
+                           than reorth_eta of |w| (default 0.2: a single pass leaves the new vector
+                           orthogonal to within about eps |w| / |w'| <= 5 eps; 0: never, 1: always) */
   double ilu_guard;     /* ILU(0) pivot guard: a black cell whose Schur-updated diagonal block has
                            det(D') / det(D) <= ilu_guard keeps D (default 0.1; a large negative
                            value disables the guard) */

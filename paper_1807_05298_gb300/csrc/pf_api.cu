@@ -779,7 +779,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->forcing_form = 3;
   o->stage1 = PF_S1_ILU0;
   o->amg_coarse_sweeps = -1;
-  o->reorth_eta = 0.70710678118654752;
+  o->reorth_eta = 0.2;
   o->ilu_guard = 0.1;
   o->newton_div = 1e6;
   o->ilu_store = -1;

@@ -702,10 +702,9 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
 }
 
 // w -= sum_{j<k} V_j h[j], then out[0] = |w|^2 and out[1] = 1 / |w|.  With
-// norm0 and decide: *decide = 1 when |w_new|^2 < eta2 |w_old|^2 (eta2 =
-// norm0-relative threshold, 1/2 by default: the update removed more than half
-// of |w|^2), i.e. when a second Gram-Schmidt pass is needed ("twice is
-// enough").  run_if as in k_multidot.
+// norm0 and decide: *decide = 1 when |w_new|^2 < eta2 |w_old|^2, i.e. when
+// the first pass cancelled so much of w that a second Gram-Schmidt pass is
+// needed ("twice is enough").  run_if as in k_multidot.
 __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const double* __restrict__ V, long long ld,
                                                    const double* __restrict__ h, double* __restrict__ w,
                                                    double* __restrict__ partial, int stride, double* __restrict__ out,
