@@ -607,12 +607,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
     ap.add_argument("--autotune", type=int, default=1, help="tune the per-cell kernels' block sizes at set-up")
-    ap.add_argument("--amg-pre", type=int, default=2)
-    ap.add_argument("--amg-post", type=int, default=2)
+    ap.add_argument("--amg-pre", type=int, default=1)
+    ap.add_argument("--amg-post", type=int, default=1)
     ap.add_argument("--amg-cycle", type=int, default=1)
     ap.add_argument("--reorth-eta", type=float, default=0.2,
                     help="second Gram-Schmidt pass when the first leaves less than this fraction of |w|")
-    ap.add_argument("--amg-coarse", type=int, default=-1,
+    ap.add_argument("--amg-coarse", type=int, default=2,
                     help="smoothing sweeps on the levels below the finest (-1: as on the finest)")
     ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the kernels")
     ap.add_argument("--stage1", default="ilu0", choices=["bjacobi", "ilu0"],

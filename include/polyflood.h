@@ -141,7 +141,7 @@ typedef struct pf_solver_opts {
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
   double dc_frac;       /* per-iteration concentration change limit as a fraction of c_ref (default 0.5) */
-  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps on the finest level (default 2, 2) */
+  int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps on the finest level (default 1, 1) */
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
   int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
@@ -156,7 +156,7 @@ typedef struct pf_solver_opts {
   int stage1;           /* PF_S1_BJACOBI or PF_S1_ILU0: the local solve, alone (PF_PC_BJACOBI)
                            or as the first stage of CPR (default PF_S1_ILU0) */
   int amg_coarse_sweeps;  /* pre- and post-smoothing sweeps on the levels below the finest;
-                             -1: the finest level's counts (default -1) */
+                             -1: the finest level's counts (default 2) */
   double reorth_eta;    /* classical Gram-Schmidt takes its second pass when the first one left less
                            than reorth_eta of |w| (default 0.2: a single pass leaves the new vector
                            orthogonal to within about eps |w| / |w'| <= 5 eps; 0: never, 1: always) */

@@ -771,14 +771,14 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->newton_tol = 1e-10;
   o->ds_max = 0.2;
   o->dc_frac = 0.5;
-  o->amg_pre_sweeps = 2;
-  o->amg_post_sweeps = 2;
+  o->amg_pre_sweeps = 1;
+  o->amg_post_sweeps = 1;
   o->amg_coarse_size = 8;
   o->amg_cycle = 1;
   o->autotune = 0;
   o->forcing_form = 3;
   o->stage1 = PF_S1_ILU0;
-  o->amg_coarse_sweeps = -1;
+  o->amg_coarse_sweeps = 2;
   o->reorth_eta = 0.2;
   o->ilu_guard = 0.1;
   o->newton_div = 1e6;
