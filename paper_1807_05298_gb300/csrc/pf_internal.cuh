@@ -85,6 +85,26 @@ struct Tuning {
   int ilu_fused = 1;    // ILU(0) solve: diagonal red sweep folded into the black sweep (1) or separate (0)
 };
 
+// One row of a 3x3 block times a 3-vector, accumulated as three fused
+// multiply-adds: acc + b0 x0 + b1 x1 + b2 x2 (fma3) and acc - b0 x0 - b1 x1
+// - b2 x2 (fnms3), in that order.  Written out so that an FP64 block product
+// costs one FP64-pipe instruction per product, with no separate multiply and
+// add around a partial sum.
+__device__ __forceinline__ double fma3(double b0, double b1, double b2, double x0, double x1, double x2,
+                                       double acc) {
+  return __fma_rn(b2, x2, __fma_rn(b1, x1, __fma_rn(b0, x0, acc)));
+}
+__device__ __forceinline__ float fma3(float b0, float b1, float b2, float x0, float x1, float x2, float acc) {
+  return __fmaf_rn(b2, x2, __fmaf_rn(b1, x1, __fmaf_rn(b0, x0, acc)));
+}
+__device__ __forceinline__ double fnms3(double b0, double b1, double b2, double x0, double x1, double x2,
+                                        double acc) {
+  return __fma_rn(-b2, x2, __fma_rn(-b1, x1, __fma_rn(-b0, x0, acc)));
+}
+__device__ __forceinline__ float fnms3(float b0, float b1, float b2, float x0, float x1, float x2, float acc) {
+  return __fmaf_rn(-b2, x2, __fmaf_rn(-b1, x1, __fmaf_rn(-b0, x0, acc)));
+}
+
 // Launch helpers ------------------------------------------------------------
 // slots of one colour of the red-black ordering: ceil(nx / 2) per (j, k) row
 inline long long colour_slots_host(const Grid& g) { return (long long)((g.nx + 1) / 2) * g.ny * g.nz; }

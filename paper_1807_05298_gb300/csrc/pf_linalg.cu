@@ -35,8 +35,8 @@ __device__ __forceinline__ void spmv_well_rows(const Grid& g, const Wells& w, co
     double acc = 0.0;
     for (int m = w.ptr[wi] + lane; m < w.ptr[wi + 1]; m += 32) {
       const long long c = w.cell[m];
-      acc += (double)Cw[m] * (double)x[3 * c] + (double)Cw[npf + m] * (double)x[3 * c + 1] +
-             (double)Cw[2 * npf + m] * (double)x[3 * c + 2];
+      acc = fma3((double)Cw[m], (double)Cw[npf + m], (double)Cw[2 * npf + m], (double)x[3 * c],
+                 (double)x[3 * c + 1], (double)x[3 * c + 2], acc);
     }
     acc = wsum(acc);
     if (lane == 0) y[3 * n + wi] = acc + (double)Dw[wi] * (double)x[3 * n + wi];
@@ -86,9 +86,9 @@ __global__ void __launch_bounds__(256, 4) k_spmv_cells(Grid g, Wells w, const DT
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + (size_t)s * 9 * n + i;
       const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc0 += (double)B[0] * x0 + (double)B[n] * x1 + (double)B[2 * n] * x2;
-      acc1 += (double)B[3 * n] * x0 + (double)B[4 * n] * x1 + (double)B[5 * n] * x2;
-      acc2 += (double)B[6 * n] * x0 + (double)B[7 * n] * x1 + (double)B[8 * n] * x2;
+      acc0 = fma3((double)B[0], (double)B[n], (double)B[2 * n], x0, x1, x2, acc0);
+      acc1 = fma3((double)B[3 * n], (double)B[4 * n], (double)B[5 * n], x0, x1, x2, acc1);
+      acc2 = fma3((double)B[6 * n], (double)B[7 * n], (double)B[8 * n], x0, x1, x2, acc2);
     }
     if (w.nw > 0) {
       const int m = w.perf_of[i];
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(384, 2) k_spmv_rows(Grid g, Wells w, const DT*
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + ((size_t)s * 9 + 3 * r) * n + i;
       const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc += (double)B[0] * x0 + (double)B[n] * x1 + (double)B[2 * n] * x2;
+      acc = fma3((double)B[0], (double)B[n], (double)B[2 * n], x0, x1, x2, acc);
     }
     if (w.nw > 0) {
       const int m = w.perf_of[i];
@@ -169,9 +169,9 @@ __global__ void __launch_bounds__(256, 4) k_spmv_cells_f32(Grid g, Wells w, cons
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const float* B = J + (size_t)s * 9 * n + i;
       const float x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc0 += B[0] * x0 + B[n] * x1 + B[2 * n] * x2;
-      acc1 += B[3 * n] * x0 + B[4 * n] * x1 + B[5 * n] * x2;
-      acc2 += B[6 * n] * x0 + B[7 * n] * x1 + B[8 * n] * x2;
+      acc0 = fma3(B[0], B[n], B[2 * n], x0, x1, x2, acc0);
+      acc1 = fma3(B[3 * n], B[4 * n], B[5 * n], x0, x1, x2, acc1);
+      acc2 = fma3(B[6 * n], B[7 * n], B[8 * n], x0, x1, x2, acc2);
     }
     double y0 = (double)acc0, y1 = (double)acc1, y2 = (double)acc2;
     if (w.nw > 0) {
@@ -460,9 +460,9 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int colour, int fu
       const BT* B = COMPACT ? J + (size_t)(s - 1) * 9 * nq + q : J + (size_t)s * 9 * n + i;
       const long long m = COMPACT ? nq : n;
       const PT pz{};
-      r0 -= as_pt(B[0], pz) * t0 + as_pt(B[m], pz) * t1 + as_pt(B[2 * m], pz) * t2;
-      r1 -= as_pt(B[3 * m], pz) * t0 + as_pt(B[4 * m], pz) * t1 + as_pt(B[5 * m], pz) * t2;
-      r2 -= as_pt(B[6 * m], pz) * t0 + as_pt(B[7 * m], pz) * t1 + as_pt(B[8 * m], pz) * t2;
+      r0 = fnms3(as_pt(B[0], pz), as_pt(B[m], pz), as_pt(B[2 * m], pz), t0, t1, t2, r0);
+      r1 = fnms3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), t0, t1, t2, r1);
+      r2 = fnms3(as_pt(B[6 * m], pz), as_pt(B[7 * m], pz), as_pt(B[8 * m], pz), t0, t1, t2, r2);
     }
     const PT* D = Dinv + i;
     y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
