@@ -311,7 +311,7 @@ pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* tota
 typedef struct pf_tuning {
   int props, face, gather, spmv, stage2, rbgs;
   int block_cells;  /* CPR: multigrid levels of at most this many cells (and all coarser ones) run in
-                       one thread block (default 256 in FP64, 4096 in FP32; the tuner keeps it) */
+                       one thread block (default 512 in FP64, 4096 in FP32; the tuner keeps it) */
   int ilu_fused;    /* ILU(0) solve in two launches, the diagonal red sweep folded into the black
                        sweep (1), or three launches (0); the same arithmetic either way */
   int cluster_cells;  /* CPR: larger levels of at most this many cells (<= 16384) run in one

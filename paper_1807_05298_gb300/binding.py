@@ -397,7 +397,7 @@ class Simulator:
     def set_tuning(self, **shapes):
         t = pf_tuning()
         cur = dict(props=256, face=256, gather=256, spmv=256, stage2=256, rbgs=256,
-                   block_cells=4096 if self.opts.precision == PF_PREC_MIXED else 256, ilu_fused=1,
+                   block_cells=4096 if self.opts.precision == PF_PREC_MIXED else 512, ilu_fused=1,
                    cluster_cells=0)
         cur.update(shapes)
         for k, v in cur.items():

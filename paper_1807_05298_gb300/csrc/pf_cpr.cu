@@ -695,6 +695,19 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
   }
 }
 
+// stage 2 in the form that matches stage 1: after the ILU(0) solve only the
+// black rows need the product (k_stage2_ilu), after block-Jacobi every row
+template <typename T>
+void launch_stage2(const CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const T* y,
+                   const double* v, int block, cudaStream_t st) {
+  T* b0 = (T*)c.lev[0].b;
+  if (c.ilu)
+    launch_stage2_ilu<T>(g, w, (const T*)J, c.ilu_cp, (const T*)Bw, y, v, (T)c.w_o, (T)c.w_w, b0, block, st);
+  else
+    launch(k_stage2<T>, grid_for(g.n, block), block, 0, st, g, w, (const T*)J, (const T*)Bw, y, v, (T)c.w_o,
+           (T)c.w_w, b0);
+}
+
 template <typename T>
 void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const void* Dinv,
              const void* Dwinv, const double* v, double* z, cudaStream_t st, int& k) {
@@ -708,8 +721,7 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
   }
   // stage 2: r = f - J y restricted to the pressure equation (oil and water rows only)
   CprLevel& L0 = c.lev[0];
-  launch(k_stage2<T>, grid_for(g.n, c.block_stage2), c.block_stage2, 0, st, g, w, (const T*)J, (const T*)Bw,
-         (const T*)z, v, (T)c.w_o, (T)c.w_w, (T*)L0.b);
+  launch_stage2<T>(c, g, w, J, Bw, (const T*)z, v, c.block_stage2, st);
   k += 1;
   // stage 3: pressure multigrid cycle, then y += Pi_p x (in the cycle's last pass when it can)
   TopOut top;
@@ -736,12 +748,8 @@ void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
 
 void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
                      const double* v, double* tmp, int block, cudaStream_t st) {
-  if (mixed)
-    launch(k_stage2<float>, grid_for(g.n, block), block, 0, st, g, w, (const float*)J, (const float*)Bw,
-           reinterpret_cast<const float*>(tmp), v, (float)c.w_o, (float)c.w_w, (float*)c.lev[0].b);
-  else
-    launch(k_stage2<double>, grid_for(g.n, block), block, 0, st, g, w, (const double*)J, (const double*)Bw,
-           (const double*)tmp, v, c.w_o, c.w_w, (double*)c.lev[0].b);
+  if (mixed) launch_stage2<float>(c, g, w, J, Bw, reinterpret_cast<const float*>(tmp), v, block, st);
+  else launch_stage2<double>(c, g, w, J, Bw, (const double*)tmp, v, block, st);
 }
 
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
@@ -778,7 +786,7 @@ void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
 }
 
 pf_status cpr_init(CprData& c, const Grid&, bool mixed, const pf_solver_opts& o, cudaStream_t) {
-  c.block_cells = mixed ? 4096 : 256;
+  c.block_cells = mixed ? 4096 : 512;
   c.pre = std::max(0, o.amg_pre_sweeps);
   c.post = std::max(0, o.amg_post_sweeps);
   c.cpre = o.amg_coarse_sweeps >= 0 ? o.amg_coarse_sweeps : c.pre;
@@ -815,8 +823,7 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
       launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
       k += 1;
     }
-    launch(k_stage2<float>, grid_for(g.n, c.block_stage2), c.block_stage2, 0, st, g, w, (const float*)J,
-           (const float*)Bw, (const float*)zf, v, (float)c.w_o, (float)c.w_w, (float*)L0.b);
+    launch_stage2<float>(c, g, w, J, Bw, (const float*)zf, v, c.block_stage2, st);
     k += 1;
     TopOut top;
     top.mode = 2;

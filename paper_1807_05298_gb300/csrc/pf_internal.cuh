@@ -166,6 +166,11 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
 template <typename DT, typename PT, typename OT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
                      int fused, const IluCompact& cp, cudaStream_t st);  // returns the number of launches
+// CPR stage 2 after the ILU(0) first stage: black rows in full, red rows their
+// well column only (the red sweep solved their cell part exactly)
+template <typename T>
+void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
+                       const double* v, T w_o, T w_w, T* b0, int block, cudaStream_t st);
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);

@@ -531,6 +531,69 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
   return fused ? 2 : 3;
 }
 
+// CPR stage 2 after the red-black block ILU(0) first stage (Alg. 2):
+// b0 = w_o (v - J y)_oil + w_w (v - J y)_water.  The red sweep, the last one,
+// solved the red rows' cell part exactly, D_r y_r + sum_b J_rb y_b = v_r with
+// the off-diagonal blocks it read, so a red row's residual is its well column
+// alone, -B y_w (up to rounding).  The black rows are formed in full, the same
+// products in the same order as the plain stage 2, with the off-diagonal
+// blocks from the black compact copy when the sweeps read one (COMPACT; the
+// diagonal block always from J).  Threads [0, nq) take the black cells and
+// [nq, 2 nq) the red ones, so the black threads of a warp run together.
+template <typename T, typename BT, bool COMPACT>
+__global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T* __restrict__ J,
+                                                    const BT* __restrict__ Cb, const T* __restrict__ Bw,
+                                                    const T* __restrict__ y, const double* __restrict__ v, T w_o,
+                                                    T w_w, T* __restrict__ b0) {
+  PF_PDL_ENTRY();
+  const long long n = g.n, nq = colour_slots(g);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * nq;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int colour = t < nq ? 1 : 0;
+    const long long q = colour ? t : t - nq;
+    long long i;
+    int x, yy, z;
+    if (!colour_cell(g, colour, q, i, x, yy, z)) continue;
+    T r = 0;
+    if (colour == 1) {
+      const T* D = J + i;
+      const T d0 = y[3 * i], d1 = y[3 * i + 1], d2 = y[3 * i + 2];
+      T t0 = fma3(D[0], D[n], D[2 * n], d0, d1, d2, (T)0);
+      T t1 = fma3(D[3 * n], D[4 * n], D[5 * n], d0, d1, d2, (T)0);
+      const T pz{};
+#pragma unroll
+      for (int s = 1; s < SL_COUNT; ++s) {
+        long long c;
+        if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
+        const BT* B = COMPACT ? Cb + (size_t)(s - 1) * 9 * nq + q : (const BT*)J + (size_t)s * 9 * n + i;
+        const long long m = COMPACT ? nq : n;
+        const T x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
+        t0 = fma3(as_pt(B[0], pz), as_pt(B[m], pz), as_pt(B[2 * m], pz), x0, x1, x2, t0);
+        t1 = fma3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), x0, x1, x2, t1);
+      }
+      r = w_o * ((T)v[3 * i] - t0) + w_w * ((T)v[3 * i + 1] - t1);
+    }
+    if (w.nw > 0) {
+      const int m = w.perf_of[i];
+      if (m >= 0) r -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * y[3 * n + w.pwell[m]];
+    }
+    b0[i] = r;
+  }
+}
+
+template <typename T>
+void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
+                       const double* v, T w_o, T w_w, T* b0, int block, cudaStream_t st) {
+  const int grid = grid_for(2 * colour_slots_host(g), block);
+  if (cp.kind == 1)
+    launch(k_stage2_ilu<T, T, true>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0);
+  else if (cp.kind == 2)
+    launch(k_stage2_ilu<T, __nv_bfloat16, true>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.c[1], Bw, y,
+           v, w_o, w_w, b0);
+  else
+    launch(k_stage2_ilu<T, T, false>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0);
+}
+
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r, double* z,
                           cudaStream_t st) {
@@ -797,6 +860,10 @@ template int launch_ilu_apply<float, float, float>(const Grid&, int, const float
                                                    const double*, float*, int, const IluCompact&, cudaStream_t);
 template int launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
                                                     const double*, double*, int, const IluCompact&, cudaStream_t);
+template void launch_stage2_ilu<double>(const Grid&, const Wells&, const double*, const IluCompact&, const double*,
+                                        const double*, const double*, double, double, double*, int, cudaStream_t);
+template void launch_stage2_ilu<float>(const Grid&, const Wells&, const float*, const IluCompact&, const float*,
+                                       const float*, const double*, float, float, float*, int, cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,

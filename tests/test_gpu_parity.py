@@ -447,7 +447,8 @@ def test_block_ilu0_matches_its_definition(B, shape):
 def test_compact_ilu_copies(B):
     """ilu_store: the sweeps reading a compact per-colour copy of the
     off-diagonal blocks (J's precision) give the same preconditioner output
-    bit for bit; with a BF16 copy (mixed precision) the time steps still land
+    bit for bit, alone and inside CPR (whose stage 2 then reads the copy for
+    the black rows); with a BF16 copy (mixed precision) the time steps still land
     on the oracle's root."""
     sc, ctl = ragged_scenario(nx=9, ny=7, nz=4)
     st = M.Setup(sc)
@@ -455,13 +456,14 @@ def test_compact_ilu_copies(B):
     x0 = M.initial_state(st)
     x_old, x = random_state(st, rng, x0), random_state(st, rng, x0)
     v = rng.normal(size=st.nunk)
-    outs = []
-    for store in (0, 1):
-        _, sim, _, _, _, _ = assemble_both(B, sc, ctl, x_old, x, DAY, precond=B.PF_PC_BJACOBI, stage1=1,
-                                           ilu_store=store)
-        outs.append(sim.apply_preconditioner(v))
-        sim.close()
-    assert np.array_equal(outs[0], outs[1])
+    for precond in (B.PF_PC_BJACOBI, B.PF_PC_CPR):  # the ILU(0) solve alone; the CPR apply (stage 2 too)
+        outs = []
+        for store in (0, 1):
+            _, sim, _, _, _, _ = assemble_both(B, sc, ctl, x_old, x, DAY, precond=precond, stage1=1,
+                                               ilu_store=store)
+            outs.append(sim.apply_preconditioner(v))
+            sim.close()
+        assert np.array_equal(outs[0], outs[1])
     sc1 = G.scenario_c1(nx=12, ny=10, nz=3, n_steps=4)
     sim = B.Simulator(sc1, stream=B.current_stream_handle(), precision=B.PF_PREC_MIXED, precond=B.PF_PC_CPR,
                       use_forcing=1, ilu_store=2)
@@ -471,3 +473,33 @@ def test_compact_ilu_copies(B):
     st1, _, hist = M.run(sc1, n_steps=4)
     for k in range(4):
         assert max(field_errors(st1.n, states[k], hist[k]["x"])) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(9, 7, 4), (8, 1, 3)])
+def test_red_rows_of_the_ilu_residual_are_their_well_columns(B, shape):
+    """The reading behind the CPR stage 2 after ILU(0): the last (red) sweep
+    solves the red rows' cell part exactly, so v - J y on a red cell is its
+    well column -B y_w alone, and the stage forms only the black rows.  Checked
+    in FP64 with the GPU's own ILU(0) output and Jacobian."""
+    nx, ny, nz = shape
+    sc, ctl = ragged_scenario(nx=nx, ny=ny, nz=nz)
+    st = M.Setup(sc)
+    rng = np.random.default_rng(21)
+    x0 = M.initial_state(st)
+    x_old, x = random_state(st, rng, x0), random_state(st, rng, x0)
+    st, sim, _, _, _, J_g = assemble_both(B, sc, ctl, x_old, x, DAY, precond=B.PF_PC_BJACOBI, stage1=1)
+    v = rng.normal(size=st.nunk)
+    y = sim.apply_preconditioner(v)
+    sim.close()
+    n = st.n
+    J = J_g.tocsr()
+    cell_part = v[:3 * n] - J[:3 * n, :3 * n] @ y[:3 * n]
+    idx = np.arange(n)
+    red = ((idx % nx) + (idx // nx) % ny + idx // (nx * ny)) % 2 == 0
+    rows_red = (3 * idx[red][:, None] + np.arange(3)).ravel()
+    rows_black = (3 * idx[~red][:, None] + np.arange(3)).ravel()
+    scale = np.abs(J[:3 * n, :3 * n]) @ np.abs(y[:3 * n]) + np.abs(v[:3 * n])
+    assert np.all(np.abs(cell_part[rows_red]) <= 1e-12 * scale[rows_red])
+    # the black rows are where the ILU(0) error lives
+    assert np.max(np.abs(cell_part[rows_black]) / scale[rows_black]) > 1e-6
+    assert np.count_nonzero(J[:3 * n, 3 * n:][rows_red].toarray()) > 0  # a red cell is perforated: its well column counts

@@ -126,7 +126,7 @@ def test_autotuned_launch_shapes_give_identical_results(B, precision):
                if k not in ("spmv", "block_cells", "ilu_fused", "cluster_cells"))
     assert t["ilu_fused"] in (0, 1)
     assert t["spmv"] in ((64, 128, 256, -96, -192, -384) if precision == 0 else (64, 128, 256))
-    assert t["block_cells"] == (256 if precision == 0 else 4096)
+    assert t["block_cells"] == (512 if precision == 0 else 4096)
     B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
     x = sim.get_x()
     sim.close()
