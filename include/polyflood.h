@@ -171,6 +171,12 @@ typedef struct pf_solver_opts {
                            in J's precision, 2: the same copy in BF16 (mixed precision only);
                            made at each preconditioner set-up.  -1 (default): 2 in mixed and 1 in
                            FP64 precision from 1,000,000 cells on, else 0 */
+  int krylov_lookahead; /* 1 (default): while Arnoldi step j runs, enqueue step j + 1 before the host
+                           reads step j's Hessenberg column, unless the residual extrapolated from
+                           the previous steps says step j may meet the tolerance; 0: enqueue each
+                           step after the previous one is checked.  A step enqueued after the
+                           solve has converged runs but is not used: the result is the same
+                           either way, only the host round trip between steps differs */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
@@ -386,7 +392,10 @@ pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* 
 /* Batch engine: n scenarios, each a pf_sim with its own stream and CUDA
  * graphs on the current device; pf_batch_run drives them from n_threads host
  * threads so their kernels overlap on the GPU.  schedules[n], reports[n]
- * (may be NULL).  Returns the first failing member's status. */
+ * (may be NULL).  Returns the first failing member's status.  o may be NULL
+ * (defaults); its krylov_lookahead is ignored (members run with 0, since their
+ * overlapping work already fills the gaps it would hide; the same holds for
+ * pf_server). */
 typedef struct pf_batch pf_batch;
 pf_status pf_batch_create(const pf_model_desc* const* models, int n, const pf_solver_opts* o, int n_threads,
                           pf_batch** out);

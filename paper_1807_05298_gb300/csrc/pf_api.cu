@@ -106,6 +106,10 @@ struct pf_sim {
     int k_pre = 0, k_spmv = 0, k_ortho = 0;
   };
   std::vector<IterGraphs> graphs;
+  // completion of the Arnoldi steps in flight, by the parity of j (at most two:
+  // step j and the step enqueued ahead of it)
+  cudaEvent_t step_done[2] = {nullptr, nullptr};
+  double krylov_rate = 0.5;  // mean residual reduction per Arnoldi step of the last solve
   // step state
   double dt = 0.0;
   bool in_step = false;
@@ -135,6 +139,12 @@ cudaEvent_t kt_event(pf_sim* s) {
 }
 
 // Brackets one launch of kernel class `which` with events on the sim's stream.
+// Pinned host buffer: [0, 8) norms read by the host right away; two slots of
+// one Arnoldi step's Hessenberg data (h1, h2, |w|^2 and 1/|w|, second-pass
+// flag), by the parity of j, so the step enqueued ahead never overwrites the
+// one the host is reading; then the least-squares solution y of a cycle.
+constexpr int kPinStep = 8, kPinStepStride = 392, kPinY = kPinStep + 2 * kPinStepStride, kPinTotal = kPinY + 128;
+
 struct KtScope {
   pf_sim* s;
   int which;
@@ -322,6 +332,7 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (!(o->newton_div >= 0.0)) return fail(PF_EINVAL, "newton_div must be >= 0");
     if (o->ilu_store < -1 || o->ilu_store > 2 || (o->ilu_store == 2 && o->precision != PF_PREC_MIXED))
       return fail(PF_EINVAL, "ilu_store must be -1, 0, 1, or 2 (BF16, mixed precision only)");
+    if (o->krylov_lookahead != 0 && o->krylov_lookahead != 1) return fail(PF_EINVAL, "krylov_lookahead must be 0 or 1");
   }
   return PF_OK;
 }
@@ -571,7 +582,8 @@ pf_status piece_ortho(pf_sim* s, int j) {
                    nullptr, reorth, st);
   launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st);
   PF_LAUNCHED(5);
-  PF_CUDA(cudaMemcpyAsync(s->h_pinned, s->hbuf, (3 * 128 + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned + kPinStep + (j & 1) * kPinStepStride, s->hbuf, (3 * 128 + 1) * sizeof(double),
+                          cudaMemcpyDeviceToHost, st));
   return PF_OK;
 }
 
@@ -600,38 +612,44 @@ pf_status capture(pf_sim* s, pf_status (*piece)(pf_sim*, int), int j, cudaGraphE
   return PF_OK;
 }
 
-pf_status arnoldi_step(pf_sim* s, int j) {
+// Enqueues Arnoldi step j (no host synchronisation) and records its
+// completion event; arnoldi_wait blocks until its Hessenberg column is in
+// pinned memory.
+pf_status arnoldi_enqueue(pf_sim* s, int j) {
   cudaStream_t st = s->stream;
+  pf_status rc;
   if (!s->use_graphs) {
-    pf_status rc;
     if ((rc = piece_pre(s, j)) != PF_OK) return rc;
     if ((rc = piece_spmv(s, j)) != PF_OK) return rc;
     if ((rc = piece_ortho(s, j)) != PF_OK) return rc;
-    PF_CUDA(cudaStreamSynchronize(st));
-    return PF_OK;
+  } else {
+    if ((int)s->graphs.size() <= j) s->graphs.resize(j + 1);
+    pf_sim::IterGraphs& G = s->graphs[j];
+    if (!G.pre) {
+      if ((rc = capture(s, piece_pre, j, &G.pre, &G.k_pre)) != PF_OK) return rc;
+      if ((rc = capture(s, piece_spmv, j, &G.spmv, &G.k_spmv)) != PF_OK) return rc;
+      if ((rc = capture(s, piece_ortho, j, &G.ortho, &G.k_ortho)) != PF_OK) return rc;
+    }
+    {
+      KtScope t(s, PF_KT_PRECOND);
+      PF_CUDA(cudaGraphLaunch(G.pre, st));
+    }
+    {
+      KtScope t(s, PF_KT_SPMV);
+      PF_CUDA(cudaGraphLaunch(G.spmv, st));
+    }
+    {
+      KtScope t(s, PF_KT_ORTHO);
+      PF_CUDA(cudaGraphLaunch(G.ortho, st));
+    }
+    s->launches += G.k_pre + G.k_spmv + G.k_ortho;
   }
-  if ((int)s->graphs.size() <= j) s->graphs.resize(j + 1);
-  pf_sim::IterGraphs& G = s->graphs[j];
-  pf_status rc;
-  if (!G.pre) {
-    if ((rc = capture(s, piece_pre, j, &G.pre, &G.k_pre)) != PF_OK) return rc;
-    if ((rc = capture(s, piece_spmv, j, &G.spmv, &G.k_spmv)) != PF_OK) return rc;
-    if ((rc = capture(s, piece_ortho, j, &G.ortho, &G.k_ortho)) != PF_OK) return rc;
-  }
-  {
-    KtScope t(s, PF_KT_PRECOND);
-    PF_CUDA(cudaGraphLaunch(G.pre, st));
-  }
-  {
-    KtScope t(s, PF_KT_SPMV);
-    PF_CUDA(cudaGraphLaunch(G.spmv, st));
-  }
-  {
-    KtScope t(s, PF_KT_ORTHO);
-    PF_CUDA(cudaGraphLaunch(G.ortho, st));
-  }
-  s->launches += G.k_pre + G.k_spmv + G.k_ortho;
-  PF_CUDA(cudaStreamSynchronize(st));
+  PF_CUDA(cudaEventRecord(s->step_done[j & 1], st));
+  return PF_OK;
+}
+
+pf_status arnoldi_wait(pf_sim* s, int j) {
+  PF_CUDA(cudaEventSynchronize(s->step_done[j & 1]));
   return PF_OK;
 }
 
@@ -667,13 +685,23 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int jdone = 0;
+    bool queued = false;       // step j was enqueued ahead, while step j - 1 ran
+    double prev = beta;        // residual after the last step the host has read
+    double rate = s->krylov_rate;
     for (int j = 0; j < m && total < maxit; ++j) {
-      if ((rc = arnoldi_step(s, j)) != PF_OK) return rc;
+      if (!queued && (rc = arnoldi_enqueue(s, j)) != PF_OK) return rc;
+      // look ahead: put step j + 1 behind step j before reading step j, unless
+      // the residual extrapolated one step (prev * rate) is within 3x of the
+      // tolerance, where step j may be the last one
+      queued = s->opts.krylov_lookahead && j + 1 < m && total + 1 < maxit && prev * rate > 3.0 * rtol * bnorm;
+      if (queued && (rc = arnoldi_enqueue(s, j + 1)) != PF_OK) return rc;
+      if ((rc = arnoldi_wait(s, j)) != PF_OK) return rc;
       const int k = j + 1;
-      const double* h1 = s->h_pinned;
-      const double* h2 = s->h_pinned + 128;
-      const bool second_pass = reinterpret_cast<const int*>(s->h_pinned + 384)[0] != 0;
-      const double hn = sqrt(std::max(s->h_pinned[256], 0.0));
+      const double* hp = s->h_pinned + kPinStep + (j & 1) * kPinStepStride;
+      const double* h1 = hp;
+      const double* h2 = hp + 128;
+      const bool second_pass = reinterpret_cast<const int*>(hp + 384)[0] != 0;
+      const double hn = sqrt(std::max(hp[256], 0.0));
       double* col = &H[(size_t)j * (m + 1)];
       for (int i = 0; i < k; ++i) col[i] = h1[i] + (second_pass ? h2[i] : 0.0);
       col[k] = hn;
@@ -693,6 +721,8 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
       ++total;
       jdone = j + 1;
       if (!std::isfinite(res)) return fail(PF_ENOT_CONVERGED, "Krylov solve produced a non-finite residual");
+      if (prev > 0.0) rate = std::min(res / prev, 1.0);
+      prev = res;
       if (res <= rtol * bnorm || hn == 0.0) { converged = true; break; }
     }
     for (int i = jdone - 1; i >= 0; --i) {
@@ -700,8 +730,8 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
       for (int l = i + 1; l < jdone; ++l) t -= H[(size_t)l * (m + 1) + i] * y[l];
       y[i] = t / H[(size_t)i * (m + 1) + i];
     }
-    memcpy(s->h_pinned, y.data(), jdone * sizeof(double));
-    PF_CUDA(cudaMemcpyAsync(s->ydev, s->h_pinned, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
+    memcpy(s->h_pinned + kPinY, y.data(), jdone * sizeof(double));
+    PF_CUDA(cudaMemcpyAsync(s->ydev, s->h_pinned + kPinY, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_multi_axpy_add(n, jdone, s->Z, ld, s->ydev, xout, st);
     s->launches += 1;
     if (!converged && total < maxit) {
@@ -714,6 +744,7 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
     }
   }
   PF_CUDA(cudaStreamSynchronize(st));
+  if (total > 0 && res > 0.0) s->krylov_rate = std::min(pow(res / bnorm, 1.0 / total), 1.0);
   if (iters) *iters = total;
   if (relres) *relres = res / bnorm;
   return PF_OK;
@@ -783,6 +814,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->ilu_guard = 0.1;
   o->newton_div = 1e6;
   o->ilu_store = -1;
+  o->krylov_lookahead = 1;
   return PF_OK;
 }
 
@@ -891,7 +923,7 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
       delete s;
       return fail(PF_ENOMEM, "device arena of " + std::to_string(s->arena_bytes) + " bytes: " + cudaGetErrorString(e));
     }
-    e = cudaMallocHost((void**)&s->h_pinned, (4 * 128 + 8) * sizeof(double));
+    e = cudaMallocHost((void**)&s->h_pinned, kPinTotal * sizeof(double));
     if (e != cudaSuccess) {
       cudaFreeAsync(s->arena, s->stream);
       cudaStreamSynchronize(s->stream);
@@ -908,6 +940,17 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
       cudaFreeHost(s->h_pinned);
       delete s;
       return fail(PF_ECUDA, std::string("capture stream: ") + cudaGetErrorString(e));
+    }
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&s->step_done[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (cudaEvent_t ev : s->step_done)
+        if (ev) cudaEventDestroy(ev);
+      cudaStreamDestroy(s->cap_stream);
+      cudaFreeAsync(s->arena, s->stream);
+      cudaStreamSynchronize(s->stream);
+      cudaFreeHost(s->h_pinned);
+      delete s;
+      return fail(PF_ECUDA, std::string("step events: ") + cudaGetErrorString(e));
     }
   }
   // upload
@@ -1007,6 +1050,8 @@ pf_status pf_destroy(pf_sim* s) {
     if (G.ortho) cudaGraphExecDestroy(G.ortho);
   }
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (cudaEvent_t ev : s->step_done)
+    if (ev) cudaEventDestroy(ev);
   if (s->arena) {
     cudaFreeAsync(s->arena, s->stream);
     cudaStreamSynchronize(s->stream);

@@ -253,3 +253,23 @@ def test_runaway_step_fails_early_and_restores_the_state(B):
         its[div] = n
         sim.close()
     assert its[1e6] < its[0.0] and its[1e6] < 25
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_krylov_lookahead_gives_identical_results(B, precision):
+    """Arnoldi step j + 1 enqueued before the host reads step j (and left
+    unused when step j meets the tolerance) changes no result: the same
+    states, Newton and Krylov counts bit for bit, with a launch count at
+    least as large (the unused steps ran)."""
+    sc = G.scenario_c1(nx=17, ny=11, nz=3, n_steps=4)
+    out = []
+    for look in (0, 1):
+        sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision,
+                          krylov_lookahead=look)
+        l0 = sim.launch_count()
+        rep = B.run_schedule(sim, B.Schedule(sc["schedule"], 4))
+        out.append((sim.get_x(), (rep.newton_iters, rep.krylov_iters, rep.cuts), sim.launch_count() - l0))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert out[1][2] >= out[0][2]
