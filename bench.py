@@ -297,7 +297,7 @@ def run_ours(args, rank, world, dist):
                     "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s (FP64)",
                     "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4),
                     "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
-                    "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 4 FP64 FMA/clk), measured 1.20",
+                    "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 2 FP64 FMA = 4 flop per clock), measured 1.20",
                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
                     "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                     "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,

@@ -666,17 +666,21 @@ pf_status arnoldi_wait(pf_sim* s, int j) {
 }
 
 // Restarted flexible GMRES (right preconditioning) for J x = b, x0 = 0.
+// bnorm_known > 0 is |b| when the caller has it (the Newton right-hand side
+// -R, whose 2-norm the residual check just formed); otherwise it is computed.
+// Returns without synchronising the stream: x is ready in stream order.
 // Arnoldi with classical Gram-Schmidt applied twice; the second projection
 // reuses the pass that applies the first (fused kernel), and the
 // Hessenberg column crosses to the host once per iteration for the Givens
 // rotations.
-pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int maxit, int* iters, double* relres) {
+pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int maxit, int* iters, double* relres,
+                double bnorm_known = 0.0) {
   const long long n = s->nunk, ld = s->ld;
   const int m = s->opts.gmres_restart;
   cudaStream_t st = s->stream;
   pf_status rc;
-  double bnorm;
-  if ((rc = dev_norm2(s, bvec, &bnorm)) != PF_OK) return rc;
+  double bnorm = bnorm_known;
+  if (!(bnorm > 0.0) && (rc = dev_norm2(s, bvec, &bnorm)) != PF_OK) return rc;
   launch_fill(n, 0.0, xout, st);
   s->launches += 1;
   if (iters) *iters = 0;
@@ -689,11 +693,11 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
   int total = 0;
   double beta = bnorm;
   double res = bnorm;
-  launch_copy(n, bvec, s->r, st);
-  s->launches += 1;
   bool converged = false;
+  bool first = true;
   while (total < maxit && !converged) {
-    scale_vec(s, s->r, 1.0 / beta, s->V);
+    scale_vec(s, first ? bvec : s->r, 1.0 / beta, s->V);  // the first cycle's residual is b itself
+    first = false;
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int jdone = 0;
@@ -759,7 +763,6 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
       if (beta <= rtol * bnorm) converged = true;
     }
   }
-  PF_CUDA(cudaStreamSynchronize(st));
   if (total > 0 && res > 0.0) s->krylov_rate = std::min(pow(res / bnorm, 1.0 / total), 1.0);
   if (iters) *iters = total;
   if (relres) *relres = res / bnorm;
@@ -1283,7 +1286,7 @@ static pf_status newton_iteration(pf_sim* s, pf_iter_report* rep, bool allow_upd
   if ((rc = precond_setup(s)) != PF_OK) return rc;
   int its = 0;
   double rr = 0.0;
-  rc = gmres(s, s->b, s->dx, eta, s->opts.gmres_max_iter, &its, &rr);
+  rc = gmres(s, s->b, s->dx, eta, s->opts.gmres_max_iter, &its, &rr, nrm);  // |b| = |R|
   r.krylov_iters = its;
   r.lin_rel_res = rr;
   if (rc != PF_OK) {

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
         const PT u0 = (PT)J[((size_t)so * 9 + col) * n + c], u1 = (PT)J[((size_t)so * 9 + 3 + col) * n + c],
                  u2 = (PT)J[((size_t)so * 9 + 6 + col) * n + c];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) a[3 * r + col] -= T[3 * r] * u0 + T[3 * r + 1] * u1 + T[3 * r + 2] * u2;
+        for (int r = 0; r < 3; ++r) a[3 * r + col] = fnms3(T[3 * r], T[3 * r + 1], T[3 * r + 2], u0, u1, u2, a[3 * r + col]);
       }
     }
     // pivot guard: det(D'_b) / det(D_b) = det(I - D_b^-1 S) measures how much
