@@ -174,7 +174,7 @@ def run_ours(args, rank, world, dist):
                 gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
                 amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form,
                 stage1=STAGE1[args.stage1], amg_coarse_sweeps=args.amg_coarse, reorth_eta=args.reorth_eta,
-                krylov_lookahead=args.lookahead, ortho_fused=args.ortho_fused)
+                krylov_lookahead=args.lookahead)
     with torch.cuda.stream(stream):
         sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
     n = sim.n
@@ -327,7 +327,7 @@ def run_ours(args, rank, world, dist):
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
                        "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse], "reorth_eta": args.reorth_eta,
-                       "precond": args.precond, "stage1": args.stage1, "pdl": args.pdl, "krylov_lookahead": args.lookahead, "ortho_fused": args.ortho_fused, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
+                       "precond": args.precond, "stage1": args.stage1, "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
                        "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
                        "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
             "krylov_iters_per_newton": round(krylov / args.steps, 2),
@@ -616,8 +616,6 @@ def main():
     ap.add_argument("--amg-coarse", type=int, default=2,
                     help="smoothing sweeps on the levels below the finest (-1: as on the finest)")
     ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the kernels")
-    ap.add_argument("--ortho-fused", type=int, default=-1, choices=[-1, 0, 1],
-                    help="Gram-Schmidt as one cooperative launch (-1: by size)")
     ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
                     help="enqueue Arnoldi step j+1 before the host reads step j (krylov_lookahead)")
     ap.add_argument("--stage1", default="ilu0", choices=["bjacobi", "ilu0"],

@@ -177,11 +177,6 @@ typedef struct pf_solver_opts {
                            step after the previous one is checked.  A step enqueued after the
                            solve has converged runs but is not used: the result is the same
                            either way, only the host round trip between steps differs */
-  int ortho_fused;      /* Gram-Schmidt step of the Krylov iteration as one cooperative launch
-                           with grid-wide barriers (1) or as separate kernels (0); -1 (default):
-                           fused up to 16,000,000 unknowns, where launch latency rather than the
-                           FP64 arithmetic bounds it.  The two differ only in the order of the
-                           reduction sums (rounding) */
 } pf_solver_opts;
 
 typedef struct pf_well_control {
@@ -398,10 +393,9 @@ pf_status pf_footprint(const pf_model_desc* m, const pf_solver_opts* o, size_t* 
  * graphs on the current device; pf_batch_run drives them from n_threads host
  * threads so their kernels overlap on the GPU.  schedules[n], reports[n]
  * (may be NULL).  Returns the first failing member's status.  o may be NULL
- * (defaults); its krylov_lookahead and ortho_fused are ignored: members run
- * with 0 for both, since their overlapping work already fills the gaps these
- * hide, and concurrent cooperative launches are not guaranteed to be
- * co-resident (the same holds for pf_server). */
+ * (defaults); its krylov_lookahead is ignored (members run with 0, since their
+ * overlapping work already fills the gaps it would hide; the same holds for
+ * pf_server). */
 typedef struct pf_batch pf_batch;
 pf_status pf_batch_create(const pf_model_desc* const* models, int n, const pf_solver_opts* o, int n_threads,
                           pf_batch** out);

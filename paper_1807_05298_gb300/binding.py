@@ -67,7 +67,7 @@ class pf_solver_opts(C.Structure):
                 ("amg_cycle", C.c_int), ("autotune", C.c_int), ("forcing_form", C.c_int),
                 ("stage1", C.c_int), ("amg_coarse_sweeps", C.c_int), ("reorth_eta", C.c_double),
                 ("ilu_guard", C.c_double), ("newton_div", C.c_double), ("ilu_store", C.c_int),
-                ("krylov_lookahead", C.c_int), ("ortho_fused", C.c_int)]
+                ("krylov_lookahead", C.c_int)]
 
 
 class pf_tuning(C.Structure):

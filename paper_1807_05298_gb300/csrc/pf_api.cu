@@ -86,9 +86,6 @@ struct pf_sim {
   double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
   double* wtot = nullptr;  // [3 nw] well totals
   unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
-  unsigned int* coop_bar = nullptr;     // grid barrier of the fused Gram-Schmidt kernel (zeroed)
-  int ortho_blocks = 0;                 // its grid: co-resident blocks, at most nblocks
-  bool ortho_fused = false;             // one cooperative launch per Gram-Schmidt step
   double* h_pinned = nullptr;
   CprData cpr;
   Tuning tune;  // block sizes of the per-cell kernels
@@ -146,7 +143,6 @@ cudaEvent_t kt_event(pf_sim* s) {
 // one Arnoldi step's Hessenberg data (h1, h2, |w|^2 and 1/|w|, second-pass
 // flag), by the parity of j, so the step enqueued ahead never overwrites the
 // one the host is reading; then the least-squares solution y of a cycle.
-constexpr long long kOrthoFusedAuto = 16000000;
 constexpr int kPinStep = 8, kPinStepStride = 392, kPinY = kPinStep + 2 * kPinStepStride, kPinTotal = kPinY + 128;
 
 struct KtScope {
@@ -337,7 +333,6 @@ pf_status validate(const pf_model_desc* m, const pf_solver_opts* o) {
     if (o->ilu_store < -1 || o->ilu_store > 2 || (o->ilu_store == 2 && o->precision != PF_PREC_MIXED))
       return fail(PF_EINVAL, "ilu_store must be -1, 0, 1, or 2 (BF16, mixed precision only)");
     if (o->krylov_lookahead != 0 && o->krylov_lookahead != 1) return fail(PF_EINVAL, "krylov_lookahead must be 0 or 1");
-    if (o->ortho_fused < -1 || o->ortho_fused > 1) return fail(PF_EINVAL, "ortho_fused must be -1, 0 or 1");
   }
   return PF_OK;
 }
@@ -407,7 +402,6 @@ size_t carve(pf_sim* s, char* base) {
   s->ydev = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
   s->red_counter = c.take<unsigned int>(64);
-  s->coop_bar = c.take<unsigned int>(64);
   {
     // compact ILU block copies: 2 colours x 54 values per colour slot
     int kind = s->opts.ilu_store;
@@ -574,27 +568,21 @@ pf_status piece_ortho(pf_sim* s, int j) {
   double* w = s->V + (size_t)(j + 1) * ld;
   cudaStream_t st = s->stream;
   KtScope t(s, PF_KT_ORTHO);
+  // pass 1: hbuf[0..k) = V^T w and hbuf[k] = |w|^2; w -= V h1 with |w|^2 and
+  // 1/|w| at hbuf[256..257] and the reorthogonalisation flag at hbuf+384.
+  // pass 2 runs only if flagged: hbuf[128..128+k) = V^T w, w -= V h2, and it
+  // overwrites hbuf[256..257].
   const double eta2 = s->opts.reorth_eta * s->opts.reorth_eta;
-  if (s->ortho_fused) {
-    PF_CUDA(launch_ortho_fused(n, k, s->V, ld, w, s->partial, s->ortho_blocks, s->hbuf, eta2, s->coop_bar, st));
-    PF_LAUNCHED(1);
-  } else {
-    // pass 1: hbuf[0..k) = V^T w and hbuf[k] = |w|^2; w -= V h1 with |w|^2 and
-    // 1/|w| at hbuf[256..257] and the reorthogonalisation flag at hbuf+384.
-    // pass 2 runs only if flagged: hbuf[128..128+k) = V^T w, w -= V h2, and it
-    // overwrites hbuf[256..257].
-    int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
-    launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr);
-    launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter,
-                     s->hbuf + k, reorth, nullptr, st, eta2);
-    launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
-    launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter,
-                     nullptr, nullptr, reorth, st);
-    launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st);
-    PF_LAUNCHED(5);
-  }
-  // h1, h2, |w|^2 and 1/|w|, the second-pass flag and the barrier status
-  PF_CUDA(cudaMemcpyAsync(s->h_pinned + kPinStep + (j & 1) * kPinStepStride, s->hbuf, (3 * 128 + 2) * sizeof(double),
+  int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr);
+  launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, s->hbuf + k,
+                   reorth, nullptr, st, eta2);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
+  launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
+                   nullptr, reorth, st);
+  launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st);
+  PF_LAUNCHED(5);
+  PF_CUDA(cudaMemcpyAsync(s->h_pinned + kPinStep + (j & 1) * kPinStepStride, s->hbuf, (3 * 128 + 1) * sizeof(double),
                           cudaMemcpyDeviceToHost, st));
   return PF_OK;
 }
@@ -717,10 +705,6 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
       const double* h1 = hp;
       const double* h2 = hp + 128;
       const bool second_pass = reinterpret_cast<const int*>(hp + 384)[0] != 0;
-      if (reinterpret_cast<const int*>(hp + 385)[0] != 0) {
-        s->dead = true;
-        return fail(PF_ECUDA, "Gram-Schmidt grid barrier gave up waiting");
-      }
       const double hn = sqrt(std::max(hp[256], 0.0));
       double* col = &H[(size_t)j * (m + 1)];
       for (int i = 0; i < k; ++i) col[i] = h1[i] + (second_pass ? h2[i] : 0.0);
@@ -834,7 +818,6 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->newton_div = 1e6;
   o->ilu_store = -1;
   o->krylov_lookahead = 1;
-  o->ortho_fused = -1;
   return PF_OK;
 }
 
@@ -871,15 +854,9 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   s->ld = (long long)align_up((size_t)s->nunk, 64);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  s->nblocks = 4 * sms;  // reduction grids: 4 blocks of 256 per SM
-  // Gram-Schmidt as one cooperative launch where kernel boundaries, not the
-  // FP64 arithmetic, bound it: up to kOrthoFusedAuto unknowns by default
-  // (about 8 entries per thread, at least one block per SM: every block reads
-  // every other block's partial sums after each barrier)
-  s->ortho_blocks = (int)std::min<long long>(std::min(s->nblocks, ortho_fused_max_blocks()),
-                                             std::max<long long>(sms, (s->nunk + 2047) / 2048));
-  s->ortho_fused = s->ortho_blocks > 0 &&
-                   (s->opts.ortho_fused == 1 || (s->opts.ortho_fused < 0 && s->nunk <= kOrthoFusedAuto));
+  // reduction grids: about 8 entries per thread, from one to four blocks of
+  // 256 per SM (the last block of each reduction sums one row per block)
+  s->nblocks = (int)std::min<long long>(4LL * sms, std::max<long long>(sms, (s->nunk + 2047) / 2048));
   s->h_ctl.resize(s->nw);
   s->switched.assign(s->nw, 0);
   // host set-up: transmissibilities and well indices

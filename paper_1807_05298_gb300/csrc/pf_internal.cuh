@@ -198,17 +198,6 @@ void launch_axpy_norm(long long n, int k, const double* V, long long ld, const d
                       double* partial, int nblocks, double* out, unsigned int* counter, const double* norm0,
                       int* decide, const int* run_if, cudaStream_t st,
                       double eta2 = 0.5);
-// The whole classical Gram-Schmidt step in one cooperative launch (grid-wide
-// barriers instead of kernel boundaries): h = V^T w with |w|^2; w -= V h;
-// the second pass if |w'|^2 < eta2 |w|^2; w /= |w|.  Writes the same words of
-// hbuf as the separate kernels (h1 at 0, |w|^2 at k, h2 at 128, |w|^2 and
-// 1/|w| at 256, the second-pass flag as an int at hbuf + 384) and, as an int
-// at hbuf + 385, 1 if a barrier wait gave up (the results are then invalid).
-// bar: two zeroed device words owned by the caller's stream.  nblocks must not
-// exceed ortho_fused_max_blocks().
-cudaError_t launch_ortho_fused(long long n, int k, const double* V, long long ld, double* w, double* partial,
-                               int nblocks, double* hbuf, double eta2, unsigned int* bar, cudaStream_t st);
-int ortho_fused_max_blocks();  // co-resident blocks of 256 threads on this device
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
                      const float* Dw, const float* x, double* y, cudaStream_t st, int block = 256);
 // x += sum_j Z[j] y[j]

@@ -40,25 +40,6 @@ inline void launch(void (*kern)(KArgs...), unsigned int grid, unsigned int block
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-// A cooperative launch: every block of the grid is resident at once, so the
-// blocks may wait on one another (grid-wide barriers).  The grid must fit the
-// occupancy limit; the launch status is returned (no PDL attribute).
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_cooperative(void (*kern)(KArgs...), unsigned int grid, unsigned int block, cudaStream_t st,
-                                      Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 // One thread-block cluster of `cluster` blocks (<= 16; above 8 the kernel must
 // allow non-portable cluster sizes, which this sets once per kernel).
 template <typename... KArgs, typename... Args>

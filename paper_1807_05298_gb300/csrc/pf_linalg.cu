@@ -821,131 +821,6 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
   }
 }
 
-// Grid-wide barrier of a cooperative launch (every block resident).  Each
-// thread publishes its writes, thread 0 arrives on bar[0]; the last arrival
-// re-arms the count and advances the generation bar[1], which the others wait
-// for.  The wait is bounded (about a second): on giving up it sets *err and
-// the block returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err) {
-  __shared__ int ok;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned int spins = 0;
-      while (*gen == g) {
-        if (++spins > (1u << 24)) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// h[j] = sum over blocks of partial[b * stride + c0 + j], j < kk, in the fixed
-// order of last_block_reduce, computed by every block into shared memory
-__device__ __forceinline__ void all_blocks_sum(const double* partial, int stride, int c0, int kk, double* h) {
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = wid; j < kk; j += nw) {
-    double v = lane_sum_blocks(partial + c0 + j, stride, (int)gridDim.x, lane);
-    v = wsum(v);
-    if (lane == 0) h[j] = v;
-  }
-  __syncthreads();
-}
-
-// w -= sum_{j<k} V_j h[j] over this thread's entries; returns their |w|^2
-__device__ __forceinline__ double project_out(long long n, int k, const double* __restrict__ V, long long ld,
-                                              const double* h, double* __restrict__ w) {
-  double acc = 0.0;
-  GRID_STRIDE(i, n) {
-    double wi = w[i];
-    for (int j = 0; j < k; ++j) wi -= V[(size_t)j * ld + i] * h[j];
-    w[i] = wi;
-    acc += wi * wi;
-  }
-  return acc;
-}
-
-__global__ void __launch_bounds__(256) k_ortho_fused(long long n, int k, const double* __restrict__ V, long long ld,
-                                                     double* __restrict__ w, double* __restrict__ partial,
-                                                     int stride, double* __restrict__ hbuf, double eta2,
-                                                     unsigned int* bar) {
-  __shared__ double h[129];
-  __shared__ double scale;
-  int* err = reinterpret_cast<int*>(hbuf + 385);
-  double* row = partial + (size_t)blockIdx.x * stride;
-  // pass 1: V^T w and <w, w> into columns [0, k] (k <= 64); the norms use
-  // columns 66 and 67 of the 72-wide rows
-  int j0 = 0;
-  for (; j0 + 8 <= k; j0 += 8) md_dispatch<false>(8, n, V, ld, w, j0, row);
-  md_dispatch<true>(k - j0, n, V, ld, w, j0, row);
-  if (!grid_barrier(bar, err)) return;
-  all_blocks_sum(partial, stride, 0, k + 1, h);
-  if (blockIdx.x == 0)
-    for (int t = threadIdx.x; t <= k; t += blockDim.x) hbuf[t] = h[t];
-  const double norm0 = h[k];
-  double acc[1] = {project_out(n, k, V, ld, h, w)};
-  block_reduce_write<1>(acc, 1, row + 66);
-  if (!grid_barrier(bar, err)) return;
-  all_blocks_sum(partial, stride, 66, 1, h + 128);
-  double s = h[128];
-  const bool second = s < eta2 * norm0;  // the same in every block: the sums are bit-identical
-  if (second) {
-    // pass 2 against the projected w, into columns [0, k) (pass 1's rows were
-    // read by every block before it reached the last barrier)
-    for (j0 = 0; j0 + 8 < k; j0 += 8) md_dispatch<false>(8, n, V, ld, w, j0, row);
-    md_dispatch<false>(k - j0, n, V, ld, w, j0, row);
-    if (!grid_barrier(bar, err)) return;
-    all_blocks_sum(partial, stride, 0, k, h);
-    if (blockIdx.x == 0)
-      for (int t = threadIdx.x; t < k; t += blockDim.x) hbuf[128 + t] = h[t];
-    acc[0] = project_out(n, k, V, ld, h, w);
-    block_reduce_write<1>(acc, 1, row + 67);
-    if (!grid_barrier(bar, err)) return;
-    all_blocks_sum(partial, stride, 67, 1, h + 128);
-    s = h[128];
-  }
-  if (threadIdx.x == 0) {
-    scale = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-    if (blockIdx.x == 0) {
-      hbuf[256] = s;
-      hbuf[257] = scale;
-      reinterpret_cast<int*>(hbuf + 384)[0] = second ? 1 : 0;
-    }
-  }
-  __syncthreads();
-  const double f = scale;
-  GRID_STRIDE(i, n) w[i] *= f;  // this thread's own entries of the projection above
-}
-
-cudaError_t launch_ortho_fused(long long n, int k, const double* V, long long ld, double* w, double* partial,
-                               int nblocks, double* hbuf, double eta2, unsigned int* bar, cudaStream_t st) {
-  return launch_cooperative(k_ortho_fused, nblocks, 256, st, n, k, V, ld, w, partial, 72, hbuf, eta2, bar);
-}
-
-int ortho_fused_max_blocks() {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ortho_fused, 256, 0) != cudaSuccess) return 0;
-  return per_sm * sms;
-}
-
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
                      double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if) {
   launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if);

@@ -185,7 +185,6 @@ pf_status pf_batch_create(const pf_model_desc* const* models, int n, const pf_so
   if (o) mo = *o;
   else pf_default_opts(&mo);
   mo.krylov_lookahead = 0;
-  mo.ortho_fused = 0;  // concurrent cooperative launches need not be co-resident
   pf_batch* b = new pf_batch();
   cudaGetDevice(&b->device);
   b->n_threads = n_threads;
@@ -340,7 +339,6 @@ pf_status pf_server_create(size_t hbm_budget, int n_workers, const pf_solver_opt
   if (o) srv->opts = *o;
   else pf_default_opts(&srv->opts);
   srv->opts.krylov_lookahead = 0;  // requests overlap on the GPU, as in pf_batch
-  srv->opts.ortho_fused = 0;
   for (int i = 0; i < n_workers; ++i) srv->workers.emplace_back(server_worker, srv);
   *out = srv;
   return PF_OK;

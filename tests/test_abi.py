@@ -40,7 +40,7 @@ def test_version_and_defaults(B):
     o = B.default_opts()
     assert o.gmres_restart == 30 and o.newton_tol == 1e-10 and o.ds_max == 0.2
     assert o.precision == B.PF_PREC_FP64
-    assert o.ilu_store == -1 and o.krylov_lookahead == 1 and o.ortho_fused == -1
+    assert o.ilu_store == -1 and o.krylov_lookahead == 1
 
 
 def _model(**over):
@@ -73,6 +73,3 @@ def test_invalid_options_rejected(B):
     with pytest.raises(B.PfError) as e:
         B.Simulator(_model(), krylov_lookahead=2)
     assert e.value.status == B.PF_EINVAL and "krylov_lookahead" in str(e.value)
-    with pytest.raises(B.PfError) as e:
-        B.Simulator(_model(), ortho_fused=3)
-    assert e.value.status == B.PF_EINVAL and "ortho_fused" in str(e.value)

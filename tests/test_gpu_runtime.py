@@ -273,36 +273,3 @@ def test_krylov_lookahead_gives_identical_results(B, precision):
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
     assert out[1][2] >= out[0][2]
-
-
-@pytest.mark.parametrize("precision", [0, 1])
-def test_fused_gram_schmidt_matches_separate_kernels(B, precision):
-    """The Gram-Schmidt step as one cooperative launch (grid barriers) against
-    the separate kernels: only the reduction order differs, so the runs take
-    the same Newton and Krylov counts and land on the same states to rounding;
-    and a linear solve with a forced second pass (reorth_eta = 1) agrees too."""
-    sc = G.scenario_c1(nx=17, ny=11, nz=3, n_steps=4)
-    out = []
-    for fused in (0, 1):
-        sim = B.Simulator(sc, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision,
-                          ortho_fused=fused)
-        rep = B.run_schedule(sim, B.Schedule(sc["schedule"], 4))
-        out.append((sim.get_x(), (rep.newton_iters, rep.krylov_iters, rep.cuts)))
-        sim.close()
-    assert out[0][1] == out[1][1]
-    n = sc["nx"] * sc["ny"] * sc["nz"]
-    for a in range(3):
-        ref = out[0][0][a:3 * n:3]
-        assert np.max(np.abs(out[1][0][a:3 * n:3] - ref)) <= 1e-9 * max(np.max(np.abs(ref)), 1.0)
-    sols = []
-    for fused in (0, 1):
-        sim = B.Simulator(sc, precond=B.PF_PC_CPR, precision=precision, ortho_fused=fused, reorth_eta=1.0)
-        sim.set_controls(sc["schedule"][0]["controls"])
-        sim.begin_step(sc["schedule"][0]["dt"])
-        sim.assemble()
-        b = np.random.default_rng(5).standard_normal(sim.nunk)
-        x, its, rr = sim.solve_linear(b, 1e-10)
-        sols.append((x, its, rr))
-        sim.close()
-    assert sols[0][1] == sols[1][1] and sols[0][2] <= 1e-10 and sols[1][2] <= 1e-10
-    assert np.max(np.abs(sols[0][0] - sols[1][0])) <= 1e-8 * np.max(np.abs(sols[0][0]))
