@@ -129,8 +129,8 @@ class ClockSampler:
 # the ncu captures summarised in profiles/ (current kernels: the FP64 row-split
 # SpMV at 100k cells, the FP32 SpMV at 2M cells); the 27M-cell figure is the
 # 2M-cell capture scaled by the number of 3x3 blocks (traffic grows with them).
-SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 578.7e6,
-                ("c3", "mixed"): 578.7e6 * 188250000 / 14008500}
+SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 577.0e6,
+                ("c3", "mixed"): 577.0e6 * 188250000 / 14008500}
 
 
 def max_over_ranks(values, dist, device="cpu"):
