@@ -435,6 +435,10 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
         b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 0, zi[l] && sweep == 0);
         b_rbgs<T, CL>(tm, d, L.A[l], L.dinv[l], L.b[l], L.x[l], 1, false);
       }
+      if (npre == 0 && zi[l]) {  // no pre-smoothing: the iterate is the zero initial guess
+        for (long long i = tm.tid; i < d.n; i += tm.stride) L.x[l][i] = (T)0;
+        tm.sync();
+      }
       const Dims c = L.d[l + 1];
       const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
       const T* A = L.A[l];
@@ -569,6 +573,7 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
     launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 1, 0, (const T*)nullptr, Dims{}, none);
     k += 2;
   }
+  if (npre == 0 && zero_init) cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), st);  // the zero initial guess
   CprLevel& C = c.lev[l + 1];
   const Dims dc = dims_of(C);
   launch(k_residual_restrict<T>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b);

@@ -155,9 +155,12 @@ def test_assembly_degenerate_grids(B, shape):
     sim.close()
 
 
-@pytest.mark.parametrize("precond,cycle,stage1", [("bjacobi", 1, 0), ("cpr", 1, 0), ("cpr", 2, 0),
-                                                  ("bjacobi", 1, 1), ("cpr", 1, 1)])
-def test_linear_solve_matches_direct(B, precond, cycle, stage1):
+@pytest.mark.parametrize("precond,cycle,stage1,sweeps", [("bjacobi", 1, 0, 1), ("cpr", 1, 0, 1), ("cpr", 2, 0, 1),
+                                                          ("bjacobi", 1, 1, 1), ("cpr", 1, 1, 1), ("cpr", 1, 1, 0)])
+def test_linear_solve_matches_direct(B, precond, cycle, stage1, sweeps):
+    """GMRES with each preconditioner against a direct solve of the oracle's
+    system; sweeps = 0: no pre-smoothing on any multigrid level (the levels
+    start from the zero initial guess) and no post-smoothing below the finest."""
     sc, ctl = ragged_scenario(nx=17, ny=9, nz=4)
     st = M.Setup(sc)
     rng = np.random.default_rng(3)
@@ -167,8 +170,9 @@ def test_linear_solve_matches_direct(B, precond, cycle, stage1):
     x[0:3 * st.n:3] += rng.normal(0.0, 0.5 * BAR, st.n)
     dt = 0.5 * DAY
     pc = B.PF_PC_CPR if precond == "cpr" else B.PF_PC_BJACOBI
+    sw = {} if sweeps else dict(amg_pre_sweeps=0, amg_coarse_sweeps=0)
     st, sim, R_o, J_o, R_g, J_g = assemble_both(B, sc, ctl, x_old, x, dt, gmres_max_iter=2000, precond=pc,
-                                                amg_cycle=cycle, stage1=stage1)
+                                                amg_cycle=cycle, stage1=stage1, **sw)
     b = -R_o
     xg, its, rr = sim.solve_linear(b, 1e-12)
     xo = spla.spsolve(J_o.tocsc(), b)
