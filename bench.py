@@ -309,6 +309,19 @@ def run_ours(args, rank, world, dist):
                     "peak_kind": hbm_kind, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
     kernel_ms = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()}
+    # assembly (cell properties + faces + gather + wells) against the HBM roof: compulsory bytes per
+    # assembly = x, phi_r, M^n, the face transmissibilities and weights read (104 B per cell), R and
+    # the 7 Jacobian blocks written (24 B + 63 values per cell)
+    asm_calls = kt["props"][0]
+    asm = None
+    if asm_calls > 0:
+        asm_bytes = ncell * (104 + 24 + 63 * jbytes)
+        asm_s = sum(kt[k][1] for k in ("props", "face", "gather", "wells")) / 1000.0 / asm_calls
+        asm_gbs = asm_bytes / asm_s / 1e9
+        asm = {"kernels": "k_cell_props + k_face_flux + k_gather + k_wells", "algorithmic_bytes": asm_bytes,
+               "us_per_assembly": round(asm_s * 1e6, 2), "achieved_gbs": round(asm_gbs, 1),
+               "hbm_frac": round(asm_gbs / hbm_peak, 4), "hbm_peak": hbm_peak,
+               "bound": "FP64 ALU (the residual and flux values stay FP64)"}
     out = None
     if rank == 0:
         cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
@@ -337,6 +350,7 @@ def run_ours(args, rank, world, dist):
                     "steps": e2e_steps},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "assembly": asm,
             "kernels_ms": kernel_ms,
             "clocks": clk,
             "cpu_baseline": cpu,
