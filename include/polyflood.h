@@ -170,7 +170,9 @@ typedef struct pf_solver_opts {
                            colour's rows), 1: a compact copy of each colour's off-diagonal blocks
                            in J's precision, 2: the same copy in BF16 (mixed precision only);
                            made at each preconditioner set-up.  -1 (default): 2 in mixed and 1 in
-                           FP64 precision from 1,000,000 cells on, else 0 */
+                           FP64 precision from 1,000,000 cells on, else 0.  Any value but 0 also
+                           gives the finest multigrid smoother per-colour copies of its stencil
+                           and 1/diag (in the preconditioner's precision) */
   int krylov_lookahead; /* 1 (default): while Arnoldi step j runs, enqueue step j + 1 before the host
                            reads step j's Hessenberg column, unless the residual extrapolated from
                            the previous steps says step j may meet the tolerance; 0: enqueue each

@@ -410,6 +410,8 @@ size_t carve(pf_sim* s, char* base) {
     const size_t es = kind == 2 ? 2 : dts;
     const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
     s->cpr.ilu_cp.kind = kind;
+    // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
+    s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
     for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
   }
   s->w_perf_of = c.take<int>(n);

@@ -197,6 +197,89 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
   }
 }
 
+// Per-colour copies of the finest level's six off-diagonal stencil slots and
+// 1/diag, indexed by the colour slot q = (y + ny z) ceil(nx / 2) + x / 2: a
+// colour pass then reads only its own colour's coefficients (in the natural
+// layout every line also carries the other colour's).
+__device__ __forceinline__ long long rb_slots(const Dims& d) { return (long long)((d.nx + 1) / 2) * d.ny * d.nz; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_compact(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
+                                                    T* __restrict__ c0, T* __restrict__ c1) {
+  PF_PDL_ENTRY();
+  const long long nq = rb_slots(d);
+  const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
+  GSTRIDE(i, d.n) {
+    int cx, cy, cz;
+    coords(d, i, cx, cy, cz);
+    T* dst = ((cx + cy + cz) & 1) ? c1 : c0;
+    const long long q = ((long long)cy + (long long)d.ny * cz) * hx + (cx >> 1);
+#pragma unroll
+    for (int sl = 1; sl < SL_COUNT; ++sl) dst[(size_t)(sl - 1) * nq + q] = A[(size_t)sl * d.n + i];
+    dst[(size_t)6 * nq + q] = dinv[i];
+  }
+}
+
+// k_rbgs on the finest level reading this colour's copy cp (the same
+// arithmetic in the same order).  Without TOP the threads take the colour's
+// slots; with TOP every cell (and the well rows), as in k_rbgs.
+template <typename T, bool TOP>
+__global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ cp, const T* __restrict__ b,
+                                                 T* __restrict__ x, int color, int zero_init,
+                                                 const T* __restrict__ xc, Dims c, TopOut top) {
+  PF_PDL_ENTRY();
+  const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
+  const long long nq = rb_slots(d);
+  const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
+  auto relax = [&](long long i, long long q, int cx, int cy, int cz) {
+    T s = b[i];
+    if (!zero_init) {
+#pragma unroll
+      for (int sl = 1; sl < SL_COUNT; ++sl) {
+        long long j;
+        if (!nbr(d, cx, cy, cz, sl, j)) continue;
+        T xj = x[j];
+        if (xc) {
+          int jx, jy, jz;
+          coords(d, j, jx, jy, jz);
+          xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
+        }
+        s = fnms(cp[(size_t)(sl - 1) * nq + q], xj, s);
+      }
+    }
+    const T xi = s * cp[(size_t)6 * nq + q];
+    x[i] = xi;
+    return xi;
+  };
+  if (!TOP) {
+    GSTRIDE(q, nq) {
+      const unsigned int uq = (unsigned int)q, row = uq / hx, m = uq - row * hx;
+      const int cz = (int)(row / (unsigned int)d.ny), cy = (int)(row - (unsigned int)cz * (unsigned int)d.ny);
+      const int cx = (int)((((unsigned int)(cy + cz + color)) & 1u) + 2u * m);
+      if (cx >= d.nx) continue;
+      relax(cx + (long long)d.nx * row, q, cx, cy, cz);
+    }
+  } else {
+    GSTRIDE(i, d.n + (top.mode == 2 ? top.nw : 0)) {
+      if (i >= d.n) {  // well rows of the mixed output: stage-1 values
+        const long long wv = 3 * d.n + (i - d.n);
+        const float v = top.zf[wv];
+        top.z[wv] = (double)v;
+        if (top.zf_out) top.zf_out[wv] = v;
+        continue;
+      }
+      int cx, cy, cz;
+      coords(d, i, cx, cy, cz);
+      if (((cx + cy + cz) & 1) != color) {
+        top_write(top, i, x[i]);  // final value of the other colour
+        continue;
+      }
+      const long long q = ((long long)cy + (long long)d.ny * cz) * hx + (cx >> 1);
+      top_write(top, i, relax(i, q, cx, cy, cz));
+    }
+  }
+}
+
 // coarse right-hand side: sum over each aggregate of the fine residual b - A x
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const T* __restrict__ A,
@@ -565,12 +648,27 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
   }
   const int npre = l == 0 ? c.pre : c.cpre, npost = l == 0 ? c.post : c.cpost;
   const int bs = l == 0 ? c.block_rbgs0 : 256;
-  const int gs = grid_for(L.n, bs);
   const TopOut none;
+  // one colour pass; on the finest level with per-colour copies the threads
+  // take that colour's slots only (or every cell, for the output-writing pass)
+  const bool cp = l == 0 && c.rb_cp[0] != nullptr;
+  const long long nq = ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
+  auto pass = [&](int color, int zi, const T* xc, const Dims& dxc, const TopOut& to) {
+    const bool wtop = to.mode != 0;
+    const long long nt = wtop ? L.n + (to.mode == 2 ? to.nw : 0) : (cp ? nq : L.n);
+    const int grid = grid_for(nt, bs);
+    if (cp) {
+      const T* cc = (const T*)c.rb_cp[color];
+      if (wtop) launch(k_rbgs_cp<T, true>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
+      else launch(k_rbgs_cp<T, false>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
+    } else {
+      if (wtop) launch(k_rbgs<T, true>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
+      else launch(k_rbgs<T, false>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
+    }
+  };
   for (int sweep = 0; sweep < npre; ++sweep) {
-    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 0, (zero_init && sweep == 0) ? 1 : 0, (const T*)nullptr,
-           Dims{}, none);
-    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 1, 0, (const T*)nullptr, Dims{}, none);
+    pass(0, (zero_init && sweep == 0) ? 1 : 0, (const T*)nullptr, Dims{}, none);
+    pass(1, 0, (const T*)nullptr, Dims{}, none);
     k += 2;
   }
   if (npre == 0 && zero_init) cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), st);  // the zero initial guess
@@ -586,14 +684,9 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
   }
   for (int sweep = 0; sweep < npost; ++sweep) {
     // the first black pass applies the prolongation to the red neighbours it reads
-    launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 1, 0, sweep == 0 ? (const T*)C.x : (const T*)nullptr,
-           sweep == 0 ? dc : Dims{}, none);
+    pass(1, 0, sweep == 0 ? (const T*)C.x : (const T*)nullptr, sweep == 0 ? dc : Dims{}, none);
     const bool last = sweep + 1 == npost && top.mode != 0;
-    const int gs_last = last ? grid_for(L.n + (top.mode == 2 ? top.nw : 0), bs) : gs;
-    if (last)
-      launch(k_rbgs<T, true>, gs_last, bs, 0, st, d, A, dinv, b, x, 0, 0, (const T*)nullptr, Dims{}, top);
-    else
-      launch(k_rbgs<T, false>, gs, bs, 0, st, d, A, dinv, b, x, 0, 0, (const T*)nullptr, Dims{}, none);
+    pass(0, 0, (const T*)nullptr, Dims{}, last ? top : none);
     k += 2;
   }
   return top.mode != 0;
@@ -604,6 +697,11 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
   CprLevel& L0 = c.lev[0];
   launch(k_extract_pressure<T>, grid_for(L0.n, 256), 256, 0, st, L0.n, (const T*)J, (T*)L0.A, (T*)L0.dinv, c.w_o, c.w_w);
   k += 1;
+  if (c.rb_cp[0]) {
+    launch(k_rb_compact<T>, grid_for(L0.n, 256), 256, 0, st, dims_of(L0), (const T*)L0.A, (const T*)L0.dinv,
+           (T*)c.rb_cp[0], (T*)c.rb_cp[1]);
+    k += 1;
+  }
   for (int l = 0; l + 1 < c.nlev; ++l) {
     CprLevel& F = c.lev[l];
     CprLevel& C = c.lev[l + 1];
@@ -743,12 +841,22 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
 void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
   CprLevel& L = c.lev[0];
   const Dims d = dims_of(L);
-  if (mixed)
-    launch(k_rbgs<float, false>, grid_for(L.n, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
-                                                          (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
-  else
-    launch(k_rbgs<double, false>, grid_for(L.n, block), block, 0, st, d, (const double*)L.A, (const double*)L.dinv,
-                                                           (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
+  const long long nq = ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
+  if (mixed) {
+    if (c.rb_cp[0])
+      launch(k_rbgs_cp<float, false>, grid_for(nq, block), block, 0, st, d, (const float*)c.rb_cp[0],
+             (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
+    else
+      launch(k_rbgs<float, false>, grid_for(L.n, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
+             (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
+  } else {
+    if (c.rb_cp[0])
+      launch(k_rbgs_cp<double, false>, grid_for(nq, block), block, 0, st, d, (const double*)c.rb_cp[0],
+             (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
+    else
+      launch(k_rbgs<double, false>, grid_for(L.n, block), block, 0, st, d, (const double*)L.A,
+             (const double*)L.dinv, (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
+  }
 }
 
 void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
@@ -788,6 +896,8 @@ void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
   }
   c.coarse_inv = take((size_t)kMaxCoarse * kMaxCoarse * ts);
   c.coarse_status = (int*)take(sizeof(int));
+  const size_t nq = (size_t)((g.nx + 1) / 2) * g.ny * g.nz;
+  for (int q = 0; q < 2; ++q) c.rb_cp[q] = c.rb_copy ? take(7 * nq * ts) : nullptr;
 }
 
 pf_status cpr_init(CprData& c, const Grid&, bool mixed, const pf_solver_opts& o, cudaStream_t) {

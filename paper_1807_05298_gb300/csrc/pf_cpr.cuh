@@ -39,6 +39,8 @@ struct CprData {
   bool ilu = false;             // first stage: red-black block ILU(0) instead of block-Jacobi
   int ilu_fused = 1;            // ILU solve in two launches (1) or three (0); same results
   IluCompact ilu_cp;            // compact per-colour block copies read by the ILU sweeps
+  bool rb_copy = false;         // the finest smoother reads per-colour copies (rb_cp) of its stencil
+  void* rb_cp[2] = {nullptr, nullptr};  // red, black: [6 off-diagonal slots + 1/diag][colour slots]
   long long block_cells = 512;  // levels of at most this many cells run in one thread block
   long long cluster_cells = 0;  // larger levels up to this size run in one thread-block cluster (0: none)
   double w_o = 0.0, w_w = 0.0;
