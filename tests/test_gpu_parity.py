@@ -18,7 +18,7 @@ import scipy.sparse.linalg as spla
 
 from oracle import model as M
 from scenarios import generate as G
-from gpu_helpers import gpu_system_to_csr, rel_matrix_error
+from gpu_helpers import gpu_system_to_csr, rb_block_ilu0_apply, rel_matrix_error
 
 pytestmark = pytest.mark.gpu
 
@@ -380,54 +380,6 @@ def test_equilibrium_state_is_a_rest_state_on_the_gpu(B):
     assert rep.newton_iters == 0
     assert np.array_equal(sim.get_x(), x0)
     sim.close()
-
-
-def rb_block_ilu0_apply(sc, J_csr, v, guard=0.1):
-    """Reference red-black block ILU(0) solve, written from its definition:
-    red cells (i + j + k even) first; the factor keeps the red diagonal
-    blocks and replaces each black one by D_b - sum_j J_bj D_j^-1 J_jb
-    (unless det of the result over det(D_b) is not above `guard`, when the
-    cell keeps D_b); then forward and backward substitution.  Well rows:
-    v_w / D_w."""
-    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
-    n = nx * ny * nz
-    J = J_csr.tocsr()
-    idx = np.arange(n)
-    i_, j_, k_ = idx % nx, (idx // nx) % ny, idx // (nx * ny)
-    red = (i_ + j_ + k_) % 2 == 0
-    blk = lambda r, c: J[3 * r:3 * r + 3, 3 * c:3 * c + 3].toarray()
-
-    def nbrs(c):
-        out = []
-        for d, (coord, lim, st_) in enumerate(((i_[c], nx, 1), (j_[c], ny, nx), (k_[c], nz, nx * ny))):
-            if coord > 0:
-                out.append(c - st_)
-            if coord < lim - 1:
-                out.append(c + st_)
-        return out
-    Dinv = {c: np.linalg.inv(blk(c, c)) for c in idx[red]}
-    Dp = {}
-    for c in idx[~red]:
-        D0 = blk(c, c)
-        D = D0
-        for r in nbrs(c):
-            D = D - blk(c, r) @ Dinv[r] @ blk(r, c)
-        if not np.linalg.det(D) / np.linalg.det(D0) > guard:
-            D = D0
-        Dp[c] = np.linalg.inv(D)
-    f = v[:3 * n].reshape(n, 3)
-    y = np.zeros((n, 3))
-    for c in idx[red]:
-        y[c] = Dinv[c] @ f[c]
-    for c in idx[~red]:
-        y[c] = Dp[c] @ (f[c] - sum(blk(c, r) @ y[r] for r in nbrs(c)))
-    for c in idx[red]:
-        y[c] = Dinv[c] @ (f[c] - sum(blk(c, r) @ y[r] for r in nbrs(c)))
-    out = np.empty_like(v)
-    out[:3 * n] = y.ravel()
-    diag = J.diagonal()
-    out[3 * n:] = v[3 * n:] / diag[3 * n:]
-    return out
 
 
 @pytest.mark.parametrize("shape", [(7, 5, 4), (9, 1, 3), (3, 3, 5), (4, 3, 1)])
