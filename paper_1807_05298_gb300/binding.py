@@ -344,6 +344,12 @@ class Simulator:
         return R, Jc.reshape(7, 9, self.n), Bw[:3 * self.npf].reshape(3, self.npf), \
             Cw[:3 * self.npf].reshape(3, self.npf), Dw[:self.nw]
 
+    def export_residual(self):
+        """R alone (pf_export_system with the Jacobian outputs skipped)."""
+        R = np.empty(self.nunk)
+        _check(lib().pf_export_system(self.h, _ptr(R), None, None, None, None))
+        return R
+
     def apply_jacobian(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.empty(self.nunk)

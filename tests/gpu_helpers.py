@@ -123,3 +123,35 @@ def rb_block_ilu0_apply(sc, J_csr, v, guard=0.1):
     diag = J.diagonal()
     out[3 * n:] = v[3 * n:] / diag[3 * n:]
     return out
+
+
+def window_around(sc, c):
+    """The 3x3x3 block of cells centred on the interior cell c as a scenario
+    of its own (same cell sizes, depth, rock and physics; no wells), with the
+    natural indices of its 27 cells.  The centre (window cell 13) has the same
+    faces, neighbours and transmissibilities as in the full grid, so the
+    oracle's residual row and Jacobian row of the centre are those of cell c:
+    only the window's own border rows differ.  Lets the oracle check single
+    cells of grids too large for it to assemble whole."""
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    k, rem = divmod(int(c), nx * ny)
+    j, i = divmod(rem, nx)
+    assert 0 < i < nx - 1 and 0 < j < ny - 1 and 0 < k < nz - 1, "interior cells only"
+    ii, jj, kk = np.arange(i - 1, i + 2), np.arange(j - 1, j + 2), np.arange(k - 1, k + 2)
+    idx = (ii[None, None, :] + nx * (jj[None, :, None] + ny * kk[:, None, None])).ravel()
+    w = dict(sc)
+    w.update(nx=3, ny=3, nz=3, top=sc["top"] + (k - 1) * sc["dz"],
+             kx=sc["kx"][idx], ky=sc["ky"][idx], kz=sc["kz"][idx], phi=sc["phi"][idx],
+             P0=sc["P0"][idx], S0=sc["S0"][idx], C0=sc["C0"][idx], wells=[],
+             schedule=[dict(n_steps=1, dt=sc["schedule"][0]["dt"], controls=[])])
+    return w, idx
+
+
+def window_state(x, idx):
+    """Cell unknowns (P, S, C) of the window cells idx from a full state x."""
+    cols = (3 * idx[:, None] + np.arange(3)).ravel()
+    return x[cols]
+
+
+def perforated_cells(sc):
+    return set(int(c) for w in sc["wells"] for c in w["cells"])
