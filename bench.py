@@ -143,6 +143,20 @@ def max_over_ranks(values, dist, device="cpu"):
     return [float(v) for v in t.cpu()]
 
 
+def spmv_bytes(blocks, ncell, npf, nw, jbytes, xbytes):
+    """Algorithmic bytes of one SpMV launch: the 3x3 blocks of J (9 values of
+    jbytes each), the vector read (xbytes per unknown) and the FP64 result
+    written, the well border (B and C per perforation, D per well)."""
+    return blocks * 9 * jbytes + 3 * ncell * (xbytes + 8) + npf * 3 * 2 * jbytes + nw * jbytes
+
+
+def assembly_bytes(ncell, jbytes):
+    """Compulsory bytes of one assembly: x, phi_r, M^n, the three face
+    transmissibilities and weights read (104 B per cell); R (24 B) and the 7
+    Jacobian blocks (63 values of jbytes) written."""
+    return ncell * (104 + 24 + 63 * jbytes)
+
+
 def replica_throughput(world, cells, iters, seconds):
     """Whole-job cells x Newton iterations per second for ``world`` replicas
     that each ran ``iters`` iterations on ``cells`` cells in ``seconds``
@@ -280,16 +294,16 @@ def run_ours(args, rank, world, dist):
     jbytes = 4 if prec == B.PF_PREC_MIXED else 8
     # J blocks + x (FP64, or its FP32 copy in mixed precision) read + y (FP64) written + well border
     xbytes = 8 if prec == B.PF_PREC_FP64 else 4
-    spmv_bytes = blocks * 9 * jbytes + 3 * ncell * (xbytes + 8) + sim.npf * 3 * 2 * jbytes + sim.nw * jbytes
+    spmv_b = spmv_bytes(blocks, ncell, sim.npf, sim.nw, jbytes, xbytes)
     spmv_flops = blocks * 18 + sim.npf * 12 + sim.nw * 2
     cnt, ms = kt["spmv"]
     hbm_peak, hbm_kind = peaks()
     roof = None
     if cnt > 0:
         avg_s = ms / cnt / 1000.0
-        gbs = spmv_bytes / avg_s / 1e9
+        gbs = spmv_b / avg_s / 1e9
         tfl = spmv_flops / avg_s / 1e12
-        t_hbm = spmv_bytes / (hbm_peak * 1e9)
+        t_hbm = spmv_b / (hbm_peak * 1e9)
         # the FP64 operator is bound by the FP64 rate; the mixed one does FP32 arithmetic
         t_alu = spmv_flops / (FP64_PEAK_TFLOPS_NOMINAL * 1e12) if prec == B.PF_PREC_FP64 else 0.0
         if t_alu > t_hbm:
@@ -300,13 +314,13 @@ def run_ours(args, rank, world, dist):
                     "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 2 FP64 FMA = 4 flop per clock), measured 1.20",
                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
                     "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
-                    "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
+                    "algorithmic_bytes": spmv_b, "algorithmic_flops": spmv_flops,
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
         else:
             roof = {"kernel": SPMV_KERNEL[prec == B.PF_PREC_MIXED], "bound": "hbm", "achieved": round(gbs, 1),
                     "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                     "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
-                    "peak_kind": hbm_kind, "algorithmic_bytes": spmv_bytes, "algorithmic_flops": spmv_flops,
+                    "peak_kind": hbm_kind, "algorithmic_bytes": spmv_b, "algorithmic_flops": spmv_flops,
                     "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
     kernel_ms = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()}
     # assembly (cell properties + faces + gather + wells) against the HBM roof: compulsory bytes per
@@ -315,7 +329,7 @@ def run_ours(args, rank, world, dist):
     asm_calls = kt["props"][0]
     asm = None
     if asm_calls > 0:
-        asm_bytes = ncell * (104 + 24 + 63 * jbytes)
+        asm_bytes = assembly_bytes(ncell, jbytes)
         asm_s = sum(kt[k][1] for k in ("props", "face", "gather", "wells")) / 1000.0 / asm_calls
         asm_gbs = asm_bytes / asm_s / 1e9
         asm = {"kernels": "k_cell_props + k_face_flux + k_gather + k_wells", "algorithmic_bytes": asm_bytes,
