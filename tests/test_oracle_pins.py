@@ -167,6 +167,37 @@ def test_darcy_pressure_drop_series(mixing, omega):
 # gravity: hydrostatic rest and segregation (Sec. 2.2 gravity term)
 # ---------------------------------------------------------------------------
 
+def test_static_wellbore_in_a_water_column_does_not_flow():
+    """Sec. 2.4, eqs. (ssw:Q) and (ssw:dp): a producer perforated through a
+    water-filled column at rest, held at the static wellbore pressure of its
+    top perforation, draws nothing from any perforation: the wellbore gradient
+    gamma of a producer is the mobility-weighted mixture density (here water)
+    times g, and the perforation pressures shift by gamma (z_m - z_b).  The same
+    state with an oil-density gradient would flow (checked as the control)."""
+    ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=0.0, pc_e=0.0)
+    nx, ny, nz, dz, top = 3, 3, 6, 4.0, 1500.0
+    n = nx * ny * nz
+    k = np.full(n, 200.0 * MD)
+    col = [1 + nx * (1 + ny * kk) for kk in range(nz)]
+    sc = G.make_scenario(nx, ny, nz, 20.0, 20.0, dz, top, k, k, 0.1 * k, np.full(n, 0.2), ph,
+                         [dict(kind="prod", cells=col)], [dict(n_steps=1, dt=DAY, controls=[])], s0=1.0)
+    st = M.Setup(sc)
+    z = top + (np.arange(nz) + 0.5) * dz
+    p_top = 180.0 * BAR
+    P = np.repeat(p_top + ph["rho_w"] * ph["g"] * (z - z[0]), nx * ny)   # water hydrostatics
+    x = np.zeros(st.nunk)
+    x[0:3 * n:3], x[1:3 * n:3], x[2:3 * n:3] = P, 1.0, 0.0
+    x[3 * n] = P[col[0]]
+    ctl = [dict(ctrl="bhp", target=P[col[0]], limit=None, c_inj=0.0)]
+    gam = M.well_gamma(st, x, ctl)
+    assert gam[0] == pytest.approx(ph["g"] * ph["rho_w"], rel=1e-14)
+    R, _ = M.assemble(st, x, M.masses(st, x), DAY, ctl, gam, with_jacobian=False)
+    assert M.scaled_residual(st, R, DAY, ctl) < 1e-12
+    R_oil, _ = M.assemble(st, x, M.masses(st, x), DAY, ctl, np.array([ph["g"] * ph["rho_o"]]),
+                          with_jacobian=False)
+    assert M.scaled_residual(st, R_oil, DAY, ctl) > 1e-6
+
+
 def test_hydrostatic_rest_is_a_root():
     ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=0.0)
     nx, ny, nz = 3, 2, 6
