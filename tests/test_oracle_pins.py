@@ -198,6 +198,36 @@ def test_static_wellbore_in_a_water_column_does_not_flow():
     assert M.scaled_residual(st, R_oil, DAY, ctl) > 1e-6
 
 
+def test_rate_controls_deliver_their_reference_volumes():
+    """Sec. 2.4 rate constraints with B = 1: after a converged step, a water-
+    rate injector puts in its target water volume at reference conditions,
+    and producers on liquid-rate and oil-rate control take out their target
+    liquid (water + oil) and oil volumes, each phase's mass rate divided by its
+    own reference density."""
+    ph = G.default_physics()
+    nx, ny, nz = 7, 6, 2
+    n = nx * ny * nz
+    k = np.full(n, 150.0 * MD)
+    col = lambda i, j: [i + nx * (j + ny * kk) for kk in range(nz)]
+    wells = [dict(kind="inj", cells=col(0, 0)), dict(kind="prod", cells=col(nx - 1, ny - 1)),
+             dict(kind="prod", cells=col(nx - 1, 0))]
+    ctl = [dict(ctrl="wrate", target=60.0 / DAY, limit=None, c_inj=0.5),
+           dict(ctrl="lrate", target=25.0 / DAY, limit=None, c_inj=0.0),
+           dict(ctrl="orate", target=15.0 / DAY, limit=None, c_inj=0.0)]
+    sc = G.make_scenario(nx, ny, nz, 20.0, 20.0, 4.0, 1500.0, k, k, 0.1 * k, np.full(n, 0.2), ph, wells,
+                         [dict(n_steps=1, dt=DAY, controls=ctl)], s0=0.45)
+    st = M.Setup(sc)
+    x0 = M.initial_state(st)
+    x1, ok, _ = M.newton_step(st, x0, 2.0 * DAY, ctl, tol=1e-12)
+    assert ok
+    (qw0, qo0, _), (qw1, qo1, _), (qw2, qo2, _) = M.well_totals(st, x1, ctl, M.well_gamma(st, x0, ctl))
+    rw, ro = ph["rho_w"], ph["rho_o"]
+    assert qw0 / rw == pytest.approx(60.0 / DAY, rel=1e-9) and qo0 == 0.0
+    assert -(qw1 / rw + qo1 / ro) == pytest.approx(25.0 / DAY, rel=1e-9)
+    assert -qo2 / ro == pytest.approx(15.0 / DAY, rel=1e-9)
+    assert qw1 < 0.0 and qo1 < 0.0 and qw2 <= 0.0          # both phases flow out of the producers
+
+
 def test_hydrostatic_rest_is_a_root():
     ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=0.0)
     nx, ny, nz = 3, 2, 6
