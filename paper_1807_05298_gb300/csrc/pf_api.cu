@@ -927,8 +927,9 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
+      const size_t bytes = s->arena_bytes;
       delete s;
-      return fail(PF_ENOMEM, "device arena of " + std::to_string(s->arena_bytes) + " bytes: " + cudaGetErrorString(e));
+      return fail(PF_ENOMEM, "device arena of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
     }
     e = cudaMallocHost((void**)&s->h_pinned, kPinTotal * sizeof(double));
     if (e != cudaSuccess) {
