@@ -6,7 +6,7 @@
 
 A step is one full Newton iteration of the fully implicit water/oil/polymer
 model (Alg. 1): property evaluation, residual and 3x3 block-Jacobian assembly
-with upstream fluxes and wells, convergence test, forcing term eq. (fterm),
+with upstream fluxes and wells, convergence test, forcing term (Sec. 3.3),
 CPR preconditioner set-up and FGMRES solve (Alg. 2), update.  The timed
 iterations run inside the time loop (begin-step work, convergence checks and
 BHP-limit re-solves are inside the timed region).  The default workload is the
@@ -354,7 +354,7 @@ def run_ours(args, rank, world, dist):
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
                        "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse], "reorth_eta": args.reorth_eta,
-                       "precond": args.precond, "stage1": args.stage1, "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30, "forcing_term": f"eq. (fterm) form {args.forcing_form}",
+                       "precond": args.precond, "stage1": args.stage1, "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30, "forcing_term": f"Sec. 3.3 form {args.forcing_form}",
                        "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
                        "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
             "krylov_iters_per_newton": round(krylov / args.steps, 2),
@@ -651,7 +651,7 @@ def main():
     ap.add_argument("--check-fp64", type=int, default=1,
                     help="mixed precision: state the error against the FP64 path on one step")
     ap.add_argument("--forcing-form", type=int, default=3, choices=[1, 2, 3],
-                    help="which choice of the forcing term eq. (fterm); 3 is the paper's")
+                    help="which choice of the forcing term of Sec. 3.3; 3 is the paper's")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=48)

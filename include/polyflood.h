@@ -135,7 +135,7 @@ typedef struct pf_solver_opts {
   int gmres_restart;    /* Krylov basis size m (default 30) */
   int gmres_max_iter;   /* cap on Krylov iterations per linear solve (default 300) */
   int newton_max_iter;  /* cap on Newton iterations per step (default 25) */
-  int use_forcing;      /* 1: linear tolerance eta from eq. (fterm) in the form
+  int use_forcing;      /* 1: linear tolerance eta from the Sec. 3.3 forcing term in the form
                            forcing_form selects; 0: fixed lin_rtol */
   double lin_rtol;      /* fixed relative linear tolerance (default 1e-12) */
   double newton_tol;    /* scaled residual tolerance (default 1e-10) */
@@ -145,7 +145,7 @@ typedef struct pf_solver_opts {
   int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
   int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
-  int forcing_form;     /* which choice of eq. (fterm), all restricted to [0.01, 0.1],
+  int forcing_form;     /* which choice of the Sec. 3.3 forcing term, all restricted to [0.01, 0.1],
                            first Newton iteration of a step 0.1 (default 3):
                            1: |b^l - r^{l-1}| / |b^{l-1}|, r^{l-1} = b^{l-1} - J dx^{l-1}
                               the residual the previous linear solve left (one
@@ -227,6 +227,17 @@ typedef struct pf_sim pf_sim;
 pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* stream, pf_sim** out);
 /* Frees all device and host memory of s; NULL is accepted. */
 pf_status pf_destroy(pf_sim* s);
+/* Host-side fault injection for tests of pf_create's failure paths (the
+ * paper has no counterpart).  Arms the next pf_create (on any thread) so that
+ * its k-th CUDA runtime call reports an error instead of running, without
+ * touching the GPU: call 1 is the device arena's allocation and call 2 the
+ * pinned host buffer (both reported as PF_ENOMEM), then the capture stream,
+ * the two step events, the uploads and the closing synchronisation (PF_ECUDA).
+ * pf_create then frees everything it had allocated, leaves *out NULL and
+ * returns that status with the failed call in pf_last_error().  The hook
+ * disarms when it fires and at the end of a pf_create that made fewer than k
+ * calls; k = 0 disarms it.  PF_EINVAL for k < 0. */
+pf_status pf_inject_create_failure(int k);
 /* Well constraints for the next steps (Sec. 3, step 4(b): unchanged within a
  * step).  c[nwells], nwells must equal the model's well count. */
 pf_status pf_set_controls(pf_sim* s, const pf_well_control* c, int nwells);
@@ -236,7 +247,7 @@ pf_status pf_set_controls(pf_sim* s, const pf_well_control* c, int nwells);
 pf_status pf_begin_step(pf_sim* s, double dt);
 /* One Newton iteration of Alg. 1 at the current iterate: property evaluation,
  * residual and Jacobian assembly, convergence test, linear tolerance from
- * eq. (fterm), preconditioner set-up, Krylov solve, update.  Requires
+ * the forcing term of Sec. 3.3, preconditioner set-up, Krylov solve, update.  Requires
  * pf_begin_step.  rep may be NULL. */
 pf_status pf_newton_iteration(pf_sim* s, pf_iter_report* rep);
 /* pf_begin_step + Newton iterations to convergence (Alg. 1), controls fixed
@@ -435,29 +446,36 @@ pf_status pf_server_stats(pf_server* srv, size_t* in_use, int* running, int* que
 pf_status pf_server_destroy(pf_server* srv);
 
 /* Residual norms without any device allocation.  The paper has no
- * counterpart: this entry point serves callers that cannot call cudaMalloc
- * (code running while a stream is captured into a CUDA graph, plugins of a
- * framework that owns all device memory, loops that forbid allocation after
- * start-up).  It computes what the residual-norm step of pf_newton_iteration
- * computes, from caller-owned device buffers:
+ * counterpart.  Some callers of this library cannot call cudaMalloc: a host
+ * framework that hands out every byte of device memory from its own pool and
+ * treats any other allocation as an error, or a loop with a fixed time budget
+ * per iteration that cannot afford an allocation (which may synchronise the
+ * device) once it has started.  For them this entry point computes what the
+ * residual-norm step of pf_newton_iteration computes, from caller-owned
+ * device buffers:
  *   out[0] = max over cells of |R_oil| / (V phi_r rho_o), |R_water| /
  *            (V phi_r rho_w), |R_polymer| / (V phi_r c_ref) and over wells of
  *            |R_well| / well_denom, the Newton convergence measure;
- *   out[1] = 2-norm of R, the measure of the forcing term eq. (fterm).
+ *   out[1] = 2-norm of R, the measure the forcing term uses.
  * Arguments (device pointers unless stated): R[3 n_cells + n_wells] block-wise
  * residual; inv_pv[n_cells] = 1 / (V phi_r); well_denom[n_wells] the well
  * rows' scale (dt * W * 1e5 Pa for a BHP row, dt * rho_ref * |target| for a
  * rate row; may be NULL without wells); rho_o, rho_w, c_ref host scalars;
- * out[2] device output; stream a cudaStream_t (NULL = legacy stream).
+ * out[2] device output; stream a cudaStream_t of the CUDA device that is
+ * current on the calling thread (NULL = its legacy stream); a stream of
+ * another device is rejected with PF_EINVAL.
  * Limits: n_cells <= 16,777,216 and n_wells <= 4096 (PF_EINVAL with a message
  * from pf_noalloc_last_error() otherwise).  Its scratch is one fixed 64 KiB
  * device array per GPU that loads the library, held until the process exits;
  * the function calls no cudaMalloc, cudaFree or allocating library routine.
  * The first call on each device resolves the array's device address (a
- * symbol lookup, no allocation): make that first call outside any stream
- * capture.  All calls on a device share the array, so calls that overlap on
- * the GPU (other streams, concurrent host threads) race; serialise them.
- * Asynchronous: out is written in stream order. */
+ * symbol lookup, no allocation) and keeps it for later calls; make that
+ * first call before any stream capture.  The kept address is void after
+ * cudaDeviceReset.  All calls on a device share the array, which holds the
+ * last call's partial results; each call clears the counter it needs, and
+ * calls that overlap on the GPU (other streams, concurrent host threads) race
+ * on the array: serialise them.  Asynchronous: out is written in stream
+ * order. */
 pf_status pf_residual_norms_noalloc(int64_t n_cells, int n_wells, const double* R, const double* inv_pv,
                                     const double* well_denom, double rho_o, double rho_w, double c_ref,
                                     double* out, void* stream);

@@ -8,8 +8,7 @@ with it and never calls it.
 Contents:
   dual.py    forward-mode dual numbers (exact Jacobians)
   model.py   properties, set-up, residual/Jacobian, wells, Newton (Alg. 1),
-             forcing term (eq. fterm), time loop
-  linalg.py  dense LU with partial pivoting, restarted GMRES, red-black
-             block-ILU(0), pressure decoupling and aggregation coarse
-             operators written from their textbook definitions
+             forcing term (Sec. 3.3), time loop
+  linalg.py  dense LU with partial pivoting (Golub and Van Loan, Alg.
+             3.4.1), the check on the sparse direct solve that model.py uses
 """

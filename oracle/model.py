@@ -20,7 +20,7 @@ Everything is written from the paper's equations (arXiv 1807.05298):
   time        backward Euler                                       (Sec. 3.1)
   space       two-point transmissibility, harmonic k and geometry,
               pore-volume weighted rho and mu, upstream k_r          (Sec. 3.2)
-  Newton      Algorithm 1 with forcing term eq. (fterm), third form (Sec. 3.3)
+  Newton      Algorithm 1 with forcing term of Sec. 3.3, third choice
 
 Where the paper is silent the following readings are taken (the CUDA path
 takes the same ones):
@@ -591,14 +591,14 @@ def scaled_residual(st, R, dt, controls):
 
 
 # ---------------------------------------------------------------------------
-# Newton (Algorithm 1) and the forcing term eq. (fterm)
+# Newton (Algorithm 1) and the forcing term of Sec. 3.3
 # ---------------------------------------------------------------------------
 
 GOLDEN = (math.sqrt(5.0) + 1.0) / 2.0
 
 
 def forcing_term(norm_b, norm_b_prev, gamma=0.5, beta=GOLDEN, lo=0.01, hi=0.1):
-    """Third choice of eq. (fterm), restricted to [0.01, 0.1]; the first
+    """Third choice of the Sec. 3.3 forcing term, restricted to [0.01, 0.1]; the first
     iteration (no previous norm) takes the upper bound."""
     if norm_b_prev is None or norm_b_prev <= 0.0:
         return hi
@@ -607,7 +607,7 @@ def forcing_term(norm_b, norm_b_prev, gamma=0.5, beta=GOLDEN, lo=0.01, hi=0.1):
 
 
 def forcing_term_difference(b, r_prev, norm_b_prev, lo=0.01, hi=0.1):
-    """First choice of eq. (fterm): |b^l - r^{l-1}| / |b^{l-1}|, where b^l is
+    """First choice of the Sec. 3.3 forcing term: |b^l - r^{l-1}| / |b^{l-1}|, where b^l is
     the current right-hand side (-R) and r^{l-1} = b^{l-1} - J^{l-1} dx^{l-1}
     the residual the previous Newton iteration's linear solve left; the
     numerator measures how far the linear model of the previous iteration
@@ -620,7 +620,7 @@ def forcing_term_difference(b, r_prev, norm_b_prev, lo=0.01, hi=0.1):
 
 
 def forcing_term_norms(norm_b, norm_r_prev, norm_b_prev, lo=0.01, hi=0.1):
-    """Second choice of eq. (fterm): (|b^l| - |r^{l-1}|) / |b^{l-1}|, taken
+    """Second choice of the Sec. 3.3 forcing term: (|b^l| - |r^{l-1}|) / |b^{l-1}|, taken
     as printed (no absolute value: a negative value is restricted to the
     lower bound).  Restricted to [0.01, 0.1]; first iteration: upper bound."""
     if norm_r_prev is None or norm_b_prev is None or norm_b_prev <= 0.0:

@@ -151,6 +151,7 @@ def lib():
             "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_programmatic_launch": ([C.c_int], C.c_int),
+            "pf_inject_create_failure": ([C.c_int], C.c_int),
             "pf_apply_preconditioner": ([vp, _dp, _dp], C.c_int),
             "pf_equilibrium_init": ([C.POINTER(pf_model_desc), C.c_double, C.c_double, C.c_double, _dp, _dp],
                                     C.c_int),
@@ -250,6 +251,12 @@ class Model:
     def _keep(self, a):
         self.keep.append(a)
         return a
+
+
+def inject_create_failure(k):
+    """Arms the host-side fault injection of the next pf_create: its k-th CUDA
+    call reports an error instead of running (k = 0 disarms)."""
+    _check(lib().pf_inject_create_failure(int(k)))
 
 
 def set_programmatic_launch(on):

@@ -1,5 +1,5 @@
 // C ABI of the polyflood library: model set-up, device arena, Newton driver
-// (Alg. 1 with the forcing term eq. (fterm)) and the restarted flexible GMRES
+// (Alg. 1 with the forcing term of Sec. 3.3) and the restarted flexible GMRES
 // with a right preconditioner (block-Jacobi or CPR, Alg. 2).
 #include <math.h>
 #include <stdio.h>
@@ -24,6 +24,16 @@ static pf_status fail(pf_status st, const std::string& msg) {
 }
 
 static std::atomic<bool> g_pdl{false};
+
+// Host-side fault injection (pf_inject_create_failure): the k-th guarded CUDA
+// call of the next pf_create reports an error instead of running.
+static std::atomic<int> g_inject_k{0};
+
+static bool inject_hit(int* site) {
+  ++*site;
+  int k = g_inject_k.load(std::memory_order_relaxed);
+  return k > 0 && *site == k && g_inject_k.compare_exchange_strong(k, 0);
+}
 
 namespace pf {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -776,7 +786,7 @@ pf_status check(pf_sim* s) {
 double clamp_eta(double eta) { return std::isnan(eta) ? 0.1 : std::min(std::max(eta, 0.01), 0.1); }
 
 double forcing_term(double nb, double nb_prev) {
-  // eq. (fterm), third choice: gamma (|b^l| / |b^{l-1}|)^beta, gamma = 0.5,
+  // forcing term of Sec. 3.3, third choice: gamma (|b^l| / |b^{l-1}|)^beta, gamma = 0.5,
   // beta = (sqrt(5) + 1) / 2, restricted to [0.01, 0.1]; first iteration 0.1
   if (!(nb_prev > 0.0)) return 0.1;
   return clamp_eta(0.5 * pow(nb / nb_prev, (sqrt(5.0) + 1.0) / 2.0));
@@ -788,6 +798,12 @@ extern "C" {
 
 pf_status pf_set_programmatic_launch(int on) {
   g_pdl.store(on != 0);
+  return PF_OK;
+}
+
+pf_status pf_inject_create_failure(int k) {
+  if (k < 0) return fail(PF_EINVAL, "pf_inject_create_failure: k must be >= 0");
+  g_inject_k.store(k);
   return PF_OK;
 }
 
@@ -920,47 +936,40 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   s->cpr.coarse_limit = std::min(std::max(opts.amg_coarse_size, 1), 64);
   s->cpr.ilu = opts.stage1 == PF_S1_ILU0;
   s->arena_bytes = carve(s, nullptr);
+  // Every CUDA call from here on goes through PF_CREATE: a failure frees
+  // whatever the sim holds so far (pf_destroy handles a partly built sim) and
+  // returns the status with the call's message.  inject_hit() lets a test make
+  // the k-th of these calls fail on the host (pf_inject_create_failure).
+  int site = 0;
+#define PF_CREATE(call, inj_err, status)                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = inject_hit(&site) ? (inj_err) : (call);                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
+      const std::string msg_ = std::string("pf_create: ") + #call + ": " + cudaGetErrorString(e_); \
+      pf_destroy(s);                                                                        \
+      return fail((status), msg_);                                                          \
+    }                                                                                       \
+  } while (0)
   {
     // stream-ordered allocation: no device-wide synchronisation, so creating
     // or destroying one simulator does not stall the others' streams
-    cudaError_t e = cudaMallocAsync((void**)&s->arena, s->arena_bytes, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaError_t e = inject_hit(&site) ? cudaErrorMemoryAllocation
+                                      : cudaMallocAsync((void**)&s->arena, s->arena_bytes, s->stream);
+    if (e != cudaSuccess) s->arena = nullptr;
+    else e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       const size_t bytes = s->arena_bytes;
-      delete s;
+      pf_destroy(s);
       return fail(PF_ENOMEM, "device arena of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
     }
-    e = cudaMallocHost((void**)&s->h_pinned, kPinTotal * sizeof(double));
-    if (e != cudaSuccess) {
-      cudaFreeAsync(s->arena, s->stream);
-      cudaStreamSynchronize(s->stream);
-      delete s;
-      return fail(PF_ENOMEM, "pinned host buffer");
-    }
   }
+  PF_CREATE(cudaMallocHost((void**)&s->h_pinned, kPinTotal * sizeof(double)), cudaErrorMemoryAllocation, PF_ENOMEM);
   carve(s, s->arena);
-  {
-    cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      cudaFreeAsync(s->arena, s->stream);
-      cudaStreamSynchronize(s->stream);
-      cudaFreeHost(s->h_pinned);
-      delete s;
-      return fail(PF_ECUDA, std::string("capture stream: ") + cudaGetErrorString(e));
-    }
-    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&s->step_done[q], cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-      for (cudaEvent_t ev : s->step_done)
-        if (ev) cudaEventDestroy(ev);
-      cudaStreamDestroy(s->cap_stream);
-      cudaFreeAsync(s->arena, s->stream);
-      cudaStreamSynchronize(s->stream);
-      cudaFreeHost(s->h_pinned);
-      delete s;
-      return fail(PF_ECUDA, std::string("step events: ") + cudaGetErrorString(e));
-    }
-  }
+  PF_CREATE(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), cudaErrorInvalidValue, PF_ECUDA);
+  for (int q = 0; q < 2; ++q)
+    PF_CREATE(cudaEventCreateWithFlags(&s->step_done[q], cudaEventDisableTiming), cudaErrorInvalidValue, PF_ECUDA);
   // upload
   std::vector<double> x0((size_t)s->nunk);
   for (long long i = 0; i < n; ++i) {
@@ -970,23 +979,28 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
   }
   for (int w = 0; w < s->nw; ++w) x0[3 * n + w] = pb0[w];
   cudaStream_t st = s->stream;
-  PF_CUDA(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st));
-  PF_CUDA(cudaMemcpyAsync(s->phi_r, m->phi, n * sizeof(double), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->T3, T3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->wL3, wL3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->inv_pv, inv_pv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->x, x0.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->w_ptr, s->h_ptr.data(), (s->nw + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  const cudaError_t einv = cudaErrorInvalidValue;
+  PF_CREATE(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st), einv, PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->phi_r, m->phi, n * sizeof(double), cudaMemcpyHostToDevice, st), einv, PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->T3, T3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st), einv, PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->wL3, wL3.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st), einv, PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->inv_pv, inv_pv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st), einv,
+            PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->x, x0.data(), s->nunk * sizeof(double), cudaMemcpyHostToDevice, st), einv, PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->w_ptr, s->h_ptr.data(), (s->nw + 1) * sizeof(int), cudaMemcpyHostToDevice, st), einv,
+            PF_ECUDA);
   std::vector<double> sat_soa, poly_soa;   // live until the stream synchronises below
   if (m->n_sat > 0) {
     sat_soa = table_soa(m->sat_table, m->n_sat, 3);
-    PF_CUDA(cudaMemcpyAsync(s->d_sat, sat_soa.data(), sat_soa.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CREATE(cudaMemcpyAsync(s->d_sat, sat_soa.data(), sat_soa.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+              einv, PF_ECUDA);
     s->ph.sat = s->d_sat;
   }
   if (m->n_poly > 0) {
     poly_soa = table_soa(m->poly_table, m->n_poly, 2);
-    PF_CUDA(cudaMemcpyAsync(s->d_poly, poly_soa.data(), poly_soa.size() * sizeof(double), cudaMemcpyHostToDevice,
-                            st));
+    PF_CREATE(cudaMemcpyAsync(s->d_poly, poly_soa.data(), poly_soa.size() * sizeof(double), cudaMemcpyHostToDevice,
+                              st),
+              einv, PF_ECUDA);
     s->ph.poly = s->d_poly;
   }
   std::vector<int> perf_of((size_t)n, -1), pwell((size_t)std::max(1LL, s->npf), 0);
@@ -995,20 +1009,29 @@ pf_status pf_create(const pf_model_desc* m, const pf_solver_opts* o, void* strea
       perf_of[(size_t)cell[t]] = t;
       pwell[(size_t)t] = w;
     }
-  PF_CUDA(cudaMemcpyAsync(s->w_perf_of, perf_of.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemcpyAsync(s->w_pwell, pwell.data(), pwell.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  PF_CREATE(cudaMemcpyAsync(s->w_perf_of, perf_of.data(), n * sizeof(int), cudaMemcpyHostToDevice, st), einv,
+            PF_ECUDA);
+  PF_CREATE(cudaMemcpyAsync(s->w_pwell, pwell.data(), pwell.size() * sizeof(int), cudaMemcpyHostToDevice, st), einv,
+            PF_ECUDA);
   if (s->nw > 0) {
-    PF_CUDA(cudaMemcpyAsync(s->w_kind, kind.data(), s->nw * sizeof(int), cudaMemcpyHostToDevice, st));
-    PF_CUDA(cudaMemcpyAsync(s->w_cell, cell.data(), s->npf * sizeof(long long), cudaMemcpyHostToDevice, st));
-    PF_CUDA(cudaMemcpyAsync(s->w_wi, wi.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st));
-    PF_CUDA(cudaMemcpyAsync(s->w_dzb, dzb.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st));
-    PF_CUDA(cudaMemcpyAsync(s->w_W, Wsc.data(), s->nw * sizeof(double), cudaMemcpyHostToDevice, st));
+    PF_CREATE(cudaMemcpyAsync(s->w_kind, kind.data(), s->nw * sizeof(int), cudaMemcpyHostToDevice, st), einv,
+              PF_ECUDA);
+    PF_CREATE(cudaMemcpyAsync(s->w_cell, cell.data(), s->npf * sizeof(long long), cudaMemcpyHostToDevice, st), einv,
+              PF_ECUDA);
+    PF_CREATE(cudaMemcpyAsync(s->w_wi, wi.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st), einv,
+              PF_ECUDA);
+    PF_CREATE(cudaMemcpyAsync(s->w_dzb, dzb.data(), s->npf * sizeof(double), cudaMemcpyHostToDevice, st), einv,
+              PF_ECUDA);
+    PF_CREATE(cudaMemcpyAsync(s->w_W, Wsc.data(), s->nw * sizeof(double), cudaMemcpyHostToDevice, st), einv,
+              PF_ECUDA);
   }
   if (s->opts.precond == PF_PC_CPR) {
     pf_status r2 = cpr_init(s->cpr, s->g, s->mixed, s->opts, s->stream);
     if (r2 != PF_OK) { pf_destroy(s); return fail(r2, "CPR set-up failed"); }
   }
-  PF_CUDA(cudaStreamSynchronize(st));
+  PF_CREATE(cudaStreamSynchronize(st), einv, PF_ECUDA);
+#undef PF_CREATE
+  g_inject_k.store(0);  // armed for one pf_create only, also when it had fewer guarded calls than k
   if (s->opts.autotune) {
     pf_status r3 = pf_autotune(s, nullptr);
     if (r3 != PF_OK) {

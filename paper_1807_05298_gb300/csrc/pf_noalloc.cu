@@ -1,13 +1,14 @@
 // Residual norms for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not capturable), plugins of a
-// host framework that owns every device allocation itself, and real-time
-// loops that forbid allocation (and its implicit synchronisation) after
-// start-up.  pf_residual_norms_noalloc serves them: the caller passes device
-// inputs and the device output, and the kernel's scratch (one pair of partial
-// results per block and a completion counter) lives in a fixed-size array of
-// this file, kept by every GPU that loads the library until the process exits.
+// Some callers of this library cannot call cudaMalloc: a host framework that
+// hands out every byte of device memory from its own pool and treats any
+// other allocation as an error, or a loop with a fixed time budget per
+// iteration that cannot afford an allocation (which may synchronise the
+// device) once it has started.  pf_residual_norms_noalloc serves them: the
+// caller passes device inputs and the device output, and the kernel's scratch
+// (one pair of partial results per block and a completion counter) lives in a
+// fixed-size array of this file, kept by every GPU that loads the library
+// until the process exits.
 //
 // It computes the same two numbers as the residual-norm step of
 // pf_newton_iteration: the scaled max-norm used as the Newton convergence
@@ -159,10 +160,26 @@ pf_status pf_residual_norms_noalloc(int64_t n_cells, int n_wells, const double* 
     g_na_error = "pf_residual_norms_noalloc: reference densities and c_ref must be positive";
     return PF_EINVAL;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st) {
+    // the scratch address is the current device's; a stream of another
+    // device would run the kernel against memory it does not own
+    int cur = 0, sdev = 0;
+    cudaError_t e0 = cudaGetDevice(&cur);
+    if (e0 == cudaSuccess) e0 = cudaStreamGetDevice(st, &sdev);
+    if (e0 != cudaSuccess) {
+      g_na_error = std::string("pf_residual_norms_noalloc: stream device: ") + cudaGetErrorString(e0);
+      return PF_EINVAL;
+    }
+    if (sdev != cur) {
+      g_na_error = "pf_residual_norms_noalloc: the stream belongs to device " + std::to_string(sdev) +
+                   ", the current device is " + std::to_string(cur);
+      return PF_EINVAL;
+    }
+  }
   double* scratch = nullptr;
   pf_status rc = scratch_address(&scratch);
   if (rc != PF_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   // the counter must start at zero even if an earlier call on this device was cut short
   cudaError_t e = cudaMemsetAsync(scratch + kNaCounterSlot, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) {

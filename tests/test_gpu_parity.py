@@ -217,7 +217,7 @@ def test_timesteps_match_oracle_c1(B):
 
 def test_timesteps_match_oracle_c1_cpr(B):
     """Same root under the CPR preconditioner and the inexact-Newton forcing
-    term (eq. (fterm)): the Newton tolerance decides, not the linear path."""
+    term (Sec. 3.3): the Newton tolerance decides, not the linear path."""
     sc = G.scenario_c1()
     st, states, hist = run_both(B, sc, 30, precond=B.PF_PC_CPR, use_forcing=1)
     for xg, h in zip(states, hist):
@@ -363,7 +363,7 @@ def test_bhp_limit_switching_matches_oracle(B):
 
 @pytest.mark.parametrize("form", [1, 2])
 def test_forcing_term_forms_match_oracle(B, form):
-    """First and second choices of eq. (fterm): the tolerance the library
+    """First and second choices of the Sec. 3.3 forcing term: the tolerance the library
     picks at each Newton iteration equals the oracle's formula evaluated on
     the iterates the library produced (the previous linear residual rebuilt as
     b - J dx from the oracle's own R and J), and the step still lands on the

@@ -292,3 +292,44 @@ def test_per_colour_copies_give_identical_results(B, precision, shape):
         sim.close()
     assert outs[0][1] == outs[1][1]
     assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_create_failure_paths_free_everything(B):
+    """Failure detection on the host (no GPU fault): the fault-injection hook
+    makes each CUDA call of pf_create fail in turn, from the device arena's
+    allocation through the uploads to the closing synchronisation.  Every
+    failure reports its status (PF_ENOMEM for the two allocations, PF_ECUDA
+    after them) with the failed call in the message, leaves no device memory
+    behind, and a pf_create that follows still works and steps."""
+    import torch
+    sc = G.scenario_c2(seed=7, nx=64, ny=64, nz=16, n_steps=1)
+    arena = B.footprint(sc)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    statuses = []
+    for k in range(1, 200):
+        B.inject_create_failure(k)
+        try:
+            sim = B.Simulator(sc, stream=B.current_stream_handle(), autotune=0)
+        except B.PfError as e:
+            statuses.append(e.status)
+            msg = str(e)
+            assert "device arena" in msg if k == 1 else "pf_create: cuda" in msg, msg
+            torch.cuda.synchronize()
+            free, _ = torch.cuda.mem_get_info()
+            assert free0 - free < arena // 4, (k, free0 - free, arena)
+            continue
+        # k is past the last guarded call: the hook did not fire and is disarmed
+        sim.close()
+        break
+    assert statuses[:2] == [B.PF_ENOMEM, B.PF_ENOMEM]
+    assert len(statuses) >= 12 and all(s == B.PF_ECUDA for s in statuses[2:]), statuses
+    B.inject_create_failure(0)
+    sim = B.Simulator(sc, stream=B.current_stream_handle(), autotune=0)
+    sim.set_controls(sc["schedule"][0]["controls"])
+    rc, rep = sim.step(sc["schedule"][0]["dt"], raise_on_failure=False)
+    assert rc == B.PF_OK and rep.newton_iters > 0
+    sim.close()
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    assert free0 - free < arena // 4

@@ -228,6 +228,35 @@ def test_rate_controls_deliver_their_reference_volumes():
     assert qw1 < 0.0 and qo1 < 0.0 and qw2 <= 0.0          # both phases flow out of the producers
 
 
+def test_rock_compressibility_closed_tank():
+    """Sec. 2.1 porosity law phi(P) = phi_r + c_r (P - P_r), pinned by a
+    closed tank: one 10 m cube full of water (S_w = 1, so k_ro = 0 and only
+    water moves), incompressible fluids, c_r = 1e-4 / bar, and a producer that
+    takes q = 0.5 m^3/day of water.  The water mass V phi(P) rho_w can only fall
+    by rho_w q dt, so with the additive law V c_r (P1 - P0) = -q dt:
+        P1 = P0 - q dt / (V c_r) = 250 bar - 0.5 / (1000 * 1e-9 / Pa) = 245 bar
+    after one day, and 240 bar after a second one.  The multiplicative form
+    phi_r (1 + c_r (P - P_r)) would give 225 bar (a drop divided by phi_r =
+    0.2), and a flipped sign would raise the pressure.  P0 = 250 bar differs
+    from P_r = 200 bar, so a law anchored at P instead of P_r fails as well."""
+    ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=1.0e-4 / BAR, p_r=200.0 * BAR, pc_e=0.0)
+    k = np.full(1, 100.0 * MD)
+    wells = [dict(kind="prod", cells=[0])]
+    ctl = [dict(ctrl="wrate", target=0.5 / DAY, limit=None, c_inj=0.0)]
+    sc = G.make_scenario(1, 1, 1, 10.0, 10.0, 10.0, 1000.0, k, k, k, np.full(1, 0.2), ph, wells,
+                         [dict(n_steps=2, dt=DAY, controls=ctl)], p_top=250.0 * BAR, s0=1.0, c0=0.0)
+    st = M.Setup(sc)
+    x0 = M.initial_state(st)
+    assert x0[0] == 250.0 * BAR and x0[1] == 1.0
+    x1, ok, _ = M.newton_step(st, x0, DAY, ctl, tol=1e-11)
+    assert ok
+    assert x1[0] == pytest.approx(245.0 * BAR, rel=1e-9)
+    assert x1[1] == pytest.approx(1.0, abs=1e-12) and abs(x1[2]) < 1e-15
+    x2, ok, _ = M.newton_step(st, x1, DAY, ctl, tol=1e-11)
+    assert ok
+    assert x2[0] == pytest.approx(240.0 * BAR, rel=1e-9)
+
+
 def test_hydrostatic_rest_is_a_root():
     ph = G.default_physics(c_w=0.0, c_o=0.0, c_r=0.0)
     nx, ny, nz = 3, 2, 6
@@ -394,7 +423,7 @@ def test_forcing_term_third_choice():
 
 
 def test_forcing_term_first_and_second_choices():
-    """Eq. (fterm), first and second choices.  For a linear F the previous
+    """Forcing term of Sec. 3.3, first and second choices.  For a linear F the previous
     linear model is exact, so b^l = r^{l-1} whatever the step: both
     numerators vanish and eta takes the lower bound.  For F(x) = x*x - c the
     model misses by exactly s*s (closed form).  The second choice never
