@@ -1,8 +1,9 @@
 """Benchmark of the polymer-flooding Newton step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c2|c3|c3s|c1|paper] [--precision fp64|mixed]
-                    [--precond cpr|bjacobi] [--mode single|batch|serve]
+                    [--workload c3|c2|c3s|c1|paper] [--precision fp64|mixed]
+                    [--subs mixed,batch,serve|none] [--mode single|batch|serve]
+                    [--profile-iters N]
 
 A step is one full Newton iteration of the fully implicit water/oil/polymer
 model (Alg. 1): property evaluation, residual and 3x3 block-Jacobian assembly
@@ -10,14 +11,32 @@ with upstream fluxes and wells, convergence test, forcing term (Sec. 3.3),
 CPR preconditioner set-up and FGMRES solve (Alg. 2), update.  The timed
 iterations run inside the time loop (begin-step work, convergence checks and
 BHP-limit re-solves are inside the timed region).  The default workload is the
-100x100x10 grid (100,000 cells, seeded layered lognormal permeability, 5-spot,
-0.3 PV polymer slug) in FP64; the metric is cells x Newton iterations / s.
+600x450x100 grid (27,000,000 cells, seeded channelised permeability, 40
+injectors and 80 producers) in FP64; the metric is cells x Newton iterations
+per second.
+
+The default run (one GPU) prints one JSON line:
+  * the headline: K timed Newton iterations, no instrumentation inside the
+    timed region;
+  * ``roofline``: the CPR-FP preconditioner apply (the largest share of the
+    step) and the SpMV, per-launch times from a separate instrumented pass of
+    the same workload (CUDA events around each launch);
+  * ``e2e``: the same iterations through the C ABI with the state copied in
+    from and out to pinned host memory every iteration (L2 flushed as in the
+    device-timed loop);
+  * ``mixed``, ``batch``, ``serve``: the mixed-precision form on the same
+    grid (with its error against the FP64 path), the batched ensemble and the
+    serving loop, each a shorter run whose size is stated in its entry;
+  * ``cpu_baseline``: the FP64 oracle on all host cores (one process per
+    core, each on a bounded sample of the workload) and on one core.
 
 Multi-GPU: the path does not shard (one scenario per GPU), so N ranks run N
 independent replicas; value is the total over ranks, time the max over ranks.
 
-``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (rank 0 only).
+``--impl reference`` times the FP64 CPU oracle on the host cores (one process
+per core) on a bounded sample of the same workload (rank 0 only).
+``--profile-iters N`` runs N Newton iterations between cudaProfilerStart and
+cudaProfilerStop after the warm-up and exits (for ncu --profile-from-start off).
 """
 
 import argparse
@@ -36,9 +55,18 @@ import numpy as np  # noqa: E402
 
 from scenarios import generate as G  # noqa: E402
 
-FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate
+# GB300 FP64 (non-tensor) peak from unit counts and clocks: 152 SMs x 2070 MHz x
+# 4 flop per clock per SM (2 FP64 FMA; 1.25 TFLOP/s nominal)
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12
 HBM_FALLBACK_GBS = 6800.0         # profiling recipe fallback when no measured peak exists
 L2_BYTES = 129 * 1024 * 1024
+# Algorithmic bytes and FP64 flops per cell of one CPR-FP preconditioner apply
+# (Alg. 2): block-ILU(0) apply + stage-2 SpMV + pressure multigrid V-cycle, the
+# per-cell figures of the survey's measurement table (FP64: 600 + 584 + 350 B;
+# mixed, BF16/FP32 storage: 190 + 330 + 180 B; 126 + 126 + 60 flop).
+PRECOND_BYTES_PER_CELL = {"fp64": 600 + 584 + 350, "mixed": 190 + 330 + 180}
+PRECOND_FLOPS_PER_CELL = 126 + 126 + 60
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 STAGE1 = {"bjacobi": 0, "ilu0": 1}
 SPMV_KERNEL = {False: "k_spmv_cells / k_spmv_rows (FP64, well border fused)",
                True: "k_spmv_cells_f32 (FP32 J and vector, well border fused)"}
@@ -131,6 +159,10 @@ class ClockSampler:
 # 2M-cell capture scaled by the number of 3x3 blocks (traffic grows with them).
 SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 577.0e6,
                 ("c3", "mixed"): 577.0e6 * 188250000 / 14008500}
+# DRAM traffic per CPR-FP preconditioner apply (summed over the apply's
+# kernels) from the ncu captures summarised in profiles/; None where no
+# capture of the current kernels exists.
+PRECOND_TRAFFIC = {}
 
 
 def max_over_ranks(values, dist, device="cpu"):
@@ -173,172 +205,275 @@ def spmv_algorithmic(sc, nwell_perf):
     return blocks, n, faces
 
 
-def run_ours(args, rank, world, dist):
-    import torch
-    from paper_1807_05298_gb300 import binding as B
-
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    sc, desc = workload(args.workload)
-    B.set_programmatic_launch(bool(args.pdl))
-    prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
+def solver_opts(args, B, precision):
+    prec = B.PF_PREC_MIXED if precision == "mixed" else B.PF_PREC_FP64
     pc = B.PF_PC_CPR if args.precond == "cpr" else B.PF_PC_BJACOBI
-    stream = torch.cuda.Stream()
-    opts = dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
+    return dict(precision=prec, precond=pc, use_forcing=1, newton_tol=args.newton_tol, gmres_restart=30,
                 gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
                 amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form,
                 stage1=STAGE1[args.stage1], amg_coarse_sweeps=args.amg_coarse, reorth_eta=args.reorth_eta,
                 krylov_lookahead=args.lookahead)
-    with torch.cuda.stream(stream):
-        sim = B.Simulator(sc, stream=B.current_stream_handle(), **opts)
-    n = sim.n
-    sched = sc["schedule"]
-    period = sched[0]
-    dt = period["dt"]
-    # start-up (untimed): past the initial transient with the library's own step loop
-    sim.run_schedule(n_steps=args.startup_steps)
 
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    state = dict(in_step=False, dt=dt, its=0)
 
-    def newton_iteration():
-        """One full Newton iteration (assemble -> solve -> update) inside the
-        time loop; begin/end-of-step work that falls on the way is included."""
+class NewtonDriver:
+    """Newton iterations inside the time loop (Sec. 3 step 4): a converged
+    iteration ends the step (with the BHP-limit check; a switch re-solves the
+    step), a diverged or capped step is cut in half; each ``iteration()``
+    returns after one full assemble -> solve -> update."""
+
+    def __init__(self, B, sim, dt):
+        self.B, self.sim, self.dt0 = B, sim, dt
+        self.dt = dt
+        self.in_step = False
+        self.its = 0
+
+    def iteration(self):
+        B, sim = self.B, self.sim
         while True:
-            if not state["in_step"]:
-                sim.begin_step(state["dt"])
-                state["in_step"] = True
-                state["its"] = 0
+            if not self.in_step:
+                sim.begin_step(self.dt)
+                self.in_step = True
+                self.its = 0
             try:
                 r = sim.newton_iteration()
             except B.PfError as e:        # diverged iterate: cut the step (Sec. 3, step 4(a))
                 if e.status != B.PF_ENOT_CONVERGED:
                     raise
                 sim.abort_step()
-                state["in_step"] = False
-                state["dt"] *= 0.5
+                self.in_step = False
+                self.dt *= 0.5
                 continue
             if r.converged:
-                state["in_step"] = False
+                self.in_step = False
                 if sim.end_step():
                     continue          # BHP-limit switch: re-solve the step
-                state["dt"] = dt
+                self.dt = self.dt0
                 continue
-            state["its"] += 1
-            if state["its"] >= 25:    # cut the step (Sec. 3, step 4(a))
+            self.its += 1
+            if self.its >= 25:        # cut the step (Sec. 3, step 4(a))
                 sim.abort_step()
-                state["in_step"] = False
-                state["dt"] *= 0.5
+                self.in_step = False
+                self.dt *= 0.5
             return r
 
-    for _ in range(args.warmup):
-        newton_iteration()
-    torch.cuda.synchronize()
 
-    clocks = ClockSampler(dev)
-    if rank == 0:
-        clocks.start()
-    sim.kernel_timing_enable(True)
-    launches0 = sim.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+def timed_iterations(sim, drv, steps, stream, flush, dist):
+    """``steps`` Newton iterations, each bracketed by CUDA events on the
+    library's stream, L2 flushed before each; returns device seconds, host
+    wall seconds, Krylov iterations and kernel launches of the region."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     krylov = 0
+    launches0 = sim.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))                  # evict L2 between timed iterations (same stream)
         ev[k][0].record(stream)
-        r = newton_iteration()
+        r = drv.iteration()
         ev[k][1].record(stream)
         krylov += r.krylov_iters
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    launches = sim.launch_count() - launches0
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    return dev_s, wall, krylov, sim.launch_count() - launches0
+
+
+def instrumented_pass(B, sim, drv, steps):
+    """Per-kernel-class launches and device time over ``steps`` further Newton
+    iterations (CUDA events around every launch or graph launch); this pass
+    is separate from the timed region."""
+    import torch
+    torch.cuda.synchronize()
+    sim.kernel_timing_enable(True)
+    for _ in range(steps):
+        drv.iteration()
+    torch.cuda.synchronize()
     kt = {name: sim.kernel_timing(name) for name in B.PF_KT}
     sim.kernel_timing_enable(False)
-    clk = clocks.stop() if rank == 0 else None
+    return kt
 
-    # end-to-end through the C ABI with host buffers: state in from pinned host
-    # memory, one Newton iteration, state out to pinned host memory
+
+def e2e_iterations(sim, drv, steps, stream, flush, dist):
+    """The metric end to end through the C ABI with host buffers: each
+    iteration takes the state from pinned host memory, runs one Newton
+    iteration and returns the state to pinned host memory (two buffers
+    alternate); L2 is flushed before each iteration as in the device loop."""
+    import torch
     nunk = sim.nunk
     h_in = torch.empty(nunk, dtype=torch.float64, pin_memory=True)
     h_out = torch.empty(nunk, dtype=torch.float64, pin_memory=True)
     sim.get_x_ptr(h_in.data_ptr())
-    e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    bufs = (h_in, h_out)
+    krylov = 0
     t0 = time.perf_counter()
-    bufs = (h_in, h_out)  # the state leaves through one pinned buffer and comes back from it next time
-    for k in range(e2e_steps):
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
         sim.set_x_ptr(bufs[k % 2].data_ptr())
-        newton_iteration()
+        krylov += drv.iteration().krylov_iters
         sim.get_x_ptr(bufs[(k + 1) % 2].data_ptr())
     torch.cuda.synchronize()
-    e2e_wall = time.perf_counter() - t0
+    return time.perf_counter() - t0, nunk * 8, krylov
+
+
+def precond_roofline(kt, ncell, precision, hbm_peak, hbm_kind, traffic=None):
+    """Roofline of one CPR-FP preconditioner apply (a CUDA graph of the
+    first-stage sweeps, stage 2 and the multigrid cycle) from its live
+    per-apply time: algorithmic bytes and flops per cell times the cells.
+    FP64 takes the binding one of the FP64 rate and HBM; the mixed form does
+    FP32/BF16 arithmetic and is bound by HBM."""
+    cnt, ms = kt["precond"]
+    if cnt == 0:
+        return None
+    t = ms / cnt / 1000.0
+    nbytes = PRECOND_BYTES_PER_CELL[precision] * ncell
+    flops = PRECOND_FLOPS_PER_CELL * ncell
+    gbs = nbytes / t / 1e9
+    tfl = flops / t / 1e12
+    out = {"kernel": "CPR-FP preconditioner apply (Alg. 2; one CUDA graph: ILU(0) sweeps, stage 2, multigrid)",
+           "algorithmic_bytes": nbytes, "algorithmic_flops": flops, "avg_launch_us": round(t * 1e6, 2),
+           "launches": cnt, "traffic": traffic, "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+           "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind}
+    t_alu = flops / (FP64_PEAK_TFLOPS * 1e12) if precision == "fp64" else 0.0
+    if t_alu > nbytes / (hbm_peak * 1e9):
+        out.update(bound="alu", achieved=round(tfl, 4), peak=round(FP64_PEAK_TFLOPS, 4), unit="TFLOP/s (FP64)",
+                   frac=round(tfl / FP64_PEAK_TFLOPS, 4),
+                   peak_kind="FP64 rate from unit counts and clocks: 152 SMs x 2070 MHz x 4 flop/clk")
+    else:
+        out.update(bound="hbm", achieved=round(gbs, 1), peak=hbm_peak, unit="GB/s", frac=round(gbs / hbm_peak, 4),
+                   peak_kind=hbm_kind)
+    return out
+
+
+def spmv_roofline(kt, sc, sim, precision, hbm_peak, hbm_kind, workload):
+    blocks, ncell, faces = spmv_algorithmic(sc, sim.npf)
+    mixed = precision == "mixed"
+    jbytes = 4 if mixed else 8
+    xbytes = 4 if mixed else 8      # J x with the FP64 vector, or its FP32 copy in mixed precision
+    nbytes = spmv_bytes(blocks, ncell, sim.npf, sim.nw, jbytes, xbytes)
+    flops = blocks * 18 + sim.npf * 12 + sim.nw * 2
+    cnt, ms = kt["spmv"]
+    if cnt == 0:
+        return None
+    t = ms / cnt / 1000.0
+    gbs = nbytes / t / 1e9
+    tfl = flops / t / 1e12
+    out = {"kernel": SPMV_KERNEL[mixed], "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+           "avg_launch_us": round(t * 1e6, 2), "launches": cnt,
+           "traffic": SPMV_TRAFFIC.get((workload, precision)), "hbm_gbs": round(gbs, 1),
+           "hbm_frac": round(gbs / hbm_peak, 4), "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind}
+    t_alu = flops / (FP64_PEAK_TFLOPS * 1e12) if not mixed else 0.0
+    if t_alu > nbytes / (hbm_peak * 1e9):
+        out.update(bound="alu", achieved=round(tfl, 4), peak=round(FP64_PEAK_TFLOPS, 4), unit="TFLOP/s (FP64)",
+                   frac=round(tfl / FP64_PEAK_TFLOPS, 4),
+                   peak_kind="FP64 rate from unit counts and clocks: 152 SMs x 2070 MHz x 4 flop/clk")
+    else:
+        out.update(bound="hbm", achieved=round(gbs, 1), peak=hbm_peak, unit="GB/s", frac=round(gbs / hbm_peak, 4),
+                   peak_kind=hbm_kind)
+    return out
+
+
+def assembly_roofline(kt, ncell, precision, hbm_peak):
+    asm_calls = kt["props"][0]
+    if asm_calls == 0:
+        return None
+    nbytes = assembly_bytes(ncell, 4 if precision == "mixed" else 8)
+    t = sum(kt[k][1] for k in ("props", "face", "gather", "wells")) / 1000.0 / asm_calls
+    gbs = nbytes / t / 1e9
+    return {"kernels": "k_cell_props + k_face_flux + k_gather + k_wells", "algorithmic_bytes": nbytes,
+            "us_per_assembly": round(t * 1e6, 2), "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+            "hbm_peak": hbm_peak, "bound": "FP64 ALU (the residual and flux values stay FP64)"}
+
+
+def start_sim(args, B, sc, precision, stream):
+    """Simulator of ``sc`` on ``stream``, past its start-up steps (untimed,
+    the library's own step loop) and ``args.warmup`` warm-up iterations."""
+    import torch
+    with torch.cuda.stream(stream):
+        sim = B.Simulator(sc, stream=B.current_stream_handle(), **solver_opts(args, B, precision))
+    sim.run_schedule(n_steps=args.startup_steps)
+    drv = NewtonDriver(B, sim, sc["schedule"][0]["dt"])
+    for _ in range(args.warmup):
+        drv.iteration()
+    torch.cuda.synchronize()
+    return sim, drv
+
+
+def run_profile_window(args, B):
+    """--profile-iters: after the start-up and warm-up, N Newton iterations
+    between cudaProfilerStart and cudaProfilerStop (what an ncu run with
+    --profile-from-start off captures), then exit."""
+    import torch
+    sc, desc = workload(args.workload)
+    stream = torch.cuda.Stream()
+    sim, drv = start_sim(args, B, sc, args.precision, stream)
+    l0 = sim.launch_count()
+    torch.cuda.profiler.start()
+    krylov = 0
+    for _ in range(args.profile_iters):
+        krylov += drv.iteration().krylov_iters
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    out = {"profile_window": desc, "precision": args.precision, "newton_iters": args.profile_iters,
+           "krylov_iters": krylov, "kernel_launches": sim.launch_count() - l0}
+    sim.close()
+    return out
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1807_05298_gb300 import binding as B
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    B.set_programmatic_launch(bool(args.pdl))
+    if args.profile_iters:
+        return run_profile_window(args, B)
+    sc, desc = workload(args.workload)
+    stream = torch.cuda.Stream()
+    sim, drv = start_sim(args, B, sc, args.precision, stream)
+    n = sim.n
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # headline: no instrumentation inside the timed region
+    clocks = ClockSampler(dev)
+    if rank == 0:
+        clocks.start()
+    dev_s, wall, krylov, launches = timed_iterations(sim, drv, args.steps, stream, flush, dist)
+    clk = clocks.stop() if rank == 0 else None
+    # per-kernel-class times, in a separate pass
+    kt = instrumented_pass(B, sim, drv, args.prof_steps)
+    # end to end with host buffers
+    e2e_steps = args.e2e_steps or max(3, args.steps // 2)
+    e2e_wall, state_bytes, e2e_krylov = e2e_iterations(sim, drv, e2e_steps, stream, flush, dist)
 
     prec_check = None
-    if prec == B.PF_PREC_MIXED and args.check_fp64 and rank == 0:
+    if args.precision == "mixed" and args.check_fp64 and rank == 0:
         with torch.cuda.stream(stream):
-            prec_check = precision_check(B, sim, sc, opts, dt, state["in_step"], B.current_stream_handle())
+            prec_check = precision_check(B, sim, sc, solver_opts(args, B, "mixed"), drv.dt0, drv.in_step,
+                                         B.current_stream_handle())
+    nw, npf = sim.nw, sim.npf
+    spmv_roof = spmv_roofline(kt, sc, sim, args.precision, *peaks(), args.workload)
+    sim.close()
 
-    t_dev, e2e_wall, wall = max_over_ranks([dev_ms / 1000.0, e2e_wall, wall], dist, device="cuda")
+    t_dev, e2e_wall, wall = max_over_ranks([dev_s, e2e_wall, wall], dist, device="cuda")
     value = replica_throughput(world, n, args.steps, t_dev)
     e2e_value = replica_throughput(world, n, e2e_steps, e2e_wall)
-
-    # roofline of the SpMV (the Krylov operator; the metric names SpMV GB/s)
-    blocks, ncell, faces = spmv_algorithmic(sc, sim.npf)
-    jbytes = 4 if prec == B.PF_PREC_MIXED else 8
-    # J blocks + x (FP64, or its FP32 copy in mixed precision) read + y (FP64) written + well border
-    xbytes = 8 if prec == B.PF_PREC_FP64 else 4
-    spmv_b = spmv_bytes(blocks, ncell, sim.npf, sim.nw, jbytes, xbytes)
-    spmv_flops = blocks * 18 + sim.npf * 12 + sim.nw * 2
-    cnt, ms = kt["spmv"]
     hbm_peak, hbm_kind = peaks()
-    roof = None
-    if cnt > 0:
-        avg_s = ms / cnt / 1000.0
-        gbs = spmv_b / avg_s / 1e9
-        tfl = spmv_flops / avg_s / 1e12
-        t_hbm = spmv_b / (hbm_peak * 1e9)
-        # the FP64 operator is bound by the FP64 rate; the mixed one does FP32 arithmetic
-        t_alu = spmv_flops / (FP64_PEAK_TFLOPS_NOMINAL * 1e12) if prec == B.PF_PREC_FP64 else 0.0
-        if t_alu > t_hbm:
-            roof = {"kernel": SPMV_KERNEL[prec == B.PF_PREC_MIXED], "bound": "alu", "achieved": round(tfl, 4),
-                    "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s (FP64)",
-                    "frac": round(tfl / FP64_PEAK_TFLOPS_NOMINAL, 4),
-                    "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
-                    "peak_kind": "nominal FP64 rate (152 SMs x 2070 MHz x 2 FP64 FMA = 4 flop per clock), measured 1.20",
-                    "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
-                    "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
-                    "algorithmic_bytes": spmv_b, "algorithmic_flops": spmv_flops,
-                    "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
-        else:
-            roof = {"kernel": SPMV_KERNEL[prec == B.PF_PREC_MIXED], "bound": "hbm", "achieved": round(gbs, 1),
-                    "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
-                    "traffic": SPMV_TRAFFIC.get((args.workload, args.precision)),
-                    "peak_kind": hbm_kind, "algorithmic_bytes": spmv_b, "algorithmic_flops": spmv_flops,
-                    "avg_launch_us": round(avg_s * 1e6, 2), "launches": cnt}
-    kernel_ms = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()}
-    # assembly (cell properties + faces + gather + wells) against the HBM roof: compulsory bytes per
-    # assembly = x, phi_r, M^n, the face transmissibilities and weights read (104 B per cell), R and
-    # the 7 Jacobian blocks written (24 B + 63 values per cell)
-    asm_calls = kt["props"][0]
-    asm = None
-    if asm_calls > 0:
-        asm_bytes = assembly_bytes(ncell, jbytes)
-        asm_s = sum(kt[k][1] for k in ("props", "face", "gather", "wells")) / 1000.0 / asm_calls
-        asm_gbs = asm_bytes / asm_s / 1e9
-        asm = {"kernels": "k_cell_props + k_face_flux + k_gather + k_wells", "algorithmic_bytes": asm_bytes,
-               "us_per_assembly": round(asm_s * 1e6, 2), "achieved_gbs": round(asm_gbs, 1),
-               "hbm_frac": round(asm_gbs / hbm_peak, 4), "hbm_peak": hbm_peak,
-               "bound": "FP64 ALU (the residual and flux values stay FP64)"}
+    pre_roof = precond_roofline(kt, n, args.precision, hbm_peak, hbm_kind,
+                                PRECOND_TRAFFIC.get((args.workload, args.precision)))
+    roof = dict(pre_roof) if pre_roof else spmv_roof
+    if pre_roof:
+        roof["spmv"] = spmv_roof
     out = None
     if rank == 0:
-        cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
         out = {
             "metric": "cells*Newton-iters/s",
             "value": round(value, 1),
@@ -350,29 +485,75 @@ def run_ours(args, rank, world, dist):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if prec == B.PF_PREC_FP64 else "f64-residual/f32-jacobian",
+            "dtype": "f64" if args.precision == "fp64" else "f64-residual/f32-jacobian",
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
-            "config": {"workload": desc, "cells": n, "wells": sim.nw, "precision": args.precision,
-                       "autotune": args.autotune, "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse], "reorth_eta": args.reorth_eta,
-                       "precond": args.precond, "stage1": args.stage1, "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30, "forcing_term": f"Sec. 3.3 form {args.forcing_form}",
-                       "newton_tol": args.newton_tol, "startup_steps": args.startup_steps,
-                       "l2": "flushed between timed iterations (256 MiB write)", "parallelism": "replicas"},
+            "config": {"workload": desc, "cells": n, "wells": nw, "perforations": npf, "precision": args.precision,
+                       "autotune": args.autotune,
+                       "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse],
+                       "reorth_eta": args.reorth_eta, "precond": args.precond, "stage1": args.stage1,
+                       "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30,
+                       "forcing_term": f"Sec. 3.3 form {args.forcing_form}", "newton_tol": args.newton_tol,
+                       "startup_steps": args.startup_steps,
+                       "l2": "flushed between timed iterations (256 MiB write); the working set also exceeds L2"
+                             if n >= 1_000_000 else "flushed between timed iterations (256 MiB write)",
+                       "timing": "CUDA events on the library's stream around each timed iteration, no "
+                                 "per-kernel instrumentation; kernel shares and the roofline from a separate "
+                                 "pass of %d iterations" % args.prof_steps,
+                       "parallelism": "replicas"},
             "krylov_iters_per_newton": round(krylov / args.steps, 2),
             "wall_s": round(wall, 4),
             "e2e": {"value": round(e2e_value, 1), "unit": "cells*Newton-iters/s",
-                    "h2d_bytes_per_step": nunk * 8, "d2h_bytes_per_step": nunk * 8,
-                    "steps": e2e_steps},
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                    "steps": e2e_steps, "krylov_iters_per_newton": round(e2e_krylov / e2e_steps, 2),
+                    "timing": "host wall clock over later Newton iterations of the same run (the Krylov count "
+                              "per iteration differs from the timed region's)"},
             "gpu_launches": int(launches),
             "roofline": roof,
-            "assembly": asm,
-            "kernels_ms": kernel_ms,
+            "assembly": assembly_roofline(kt, n, args.precision, hbm_peak),
+            "kernels_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items()},
+            "kernels_ms_iters": args.prof_steps,
             "clocks": clk,
-            "cpu_baseline": cpu,
         }
         if prec_check is not None:
             out["precision_check"] = prec_check
-    sim.close()
+        if world == 1:
+            subs = [x for x in args.subs.split(",") if x and x != "none"]
+            if "mixed" in subs and args.precision == "fp64":
+                out["mixed"] = sub_mixed(args, B, sc, desc, value)
+            if "batch" in subs:
+                out["batch"] = run_batch(args, headline=value)
+            if "serve" in subs:
+                out["serve"] = run_serve(args, headline=value)
+            out["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(args)
     return out
+
+
+def sub_mixed(args, B, sc, desc, fp64_value):
+    """The mixed-precision form on the headline's grid: FP32 assembly
+    derivatives and Jacobian, FP32/BF16 preconditioner, FP64 residual, norms
+    and Krylov orthogonalisation; timed like the headline over fewer
+    iterations, with its error against the FP64 path on one step."""
+    import torch
+    stream = torch.cuda.Stream()
+    sim, drv = start_sim(args, B, sc, "mixed", stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    dev_s, wall, krylov, launches = timed_iterations(sim, drv, args.sub_steps, stream, flush, None)
+    kt = instrumented_pass(B, sim, drv, max(2, args.prof_steps // 2))
+    hbm_peak, hbm_kind = peaks()
+    with torch.cuda.stream(stream):
+        chk = precision_check(B, sim, sc, solver_opts(args, B, "mixed"), drv.dt0, drv.in_step,
+                              B.current_stream_handle()) if args.check_fp64 else None
+    n = sim.n
+    sim.close()
+    value = n * args.sub_steps / dev_s
+    return {"value": round(value, 1), "unit": "cells*Newton-iters/s", "steps": args.sub_steps,
+            "ms_per_step": round(1000.0 * dev_s / args.sub_steps, 4), "workload": desc,
+            "dtype": "f64-residual/f32-jacobian/bf16-f32-preconditioner",
+            "krylov_iters_per_newton": round(krylov / args.sub_steps, 2), "gpu_launches": int(launches),
+            "vs_fp64_headline": round(value / fp64_value, 4),
+            "roofline": precond_roofline(kt, n, "mixed", hbm_peak, hbm_kind,
+                                         PRECOND_TRAFFIC.get((args.workload, "mixed"))),
+            "precision_check": chk}
 
 
 def oracle_sample(args):
@@ -447,6 +628,84 @@ def time_oracle(sc, budget_s, max_iters):
     return its, time.perf_counter() - t0, r.n
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(conn, workload):
+    """One host core's oracle: the workload's bounded sample in its own time
+    loop; answers ("iter", k) with the seconds k Newton iterations took and
+    ("budget", seconds, cap) with the iterations that fit and their seconds."""
+    import types
+    sc, _ = oracle_sample(types.SimpleNamespace(workload=workload))
+    r = OracleRunner(sc)
+    conn.send(r.n)
+    while True:
+        msg = conn.recv()
+        if msg[0] == "iter":
+            t0 = time.perf_counter()
+            for _ in range(msg[1]):
+                r.iteration()
+            conn.send(time.perf_counter() - t0)
+        elif msg[0] == "budget":
+            its, t0 = 0, time.perf_counter()
+            while its < msg[2] and time.perf_counter() - t0 < msg[1]:
+                r.iteration()
+                its += 1
+            conn.send((its, time.perf_counter() - t0))
+        else:
+            return
+
+
+class OraclePool:
+    """One oracle process per host core (spawned, one BLAS thread each), each
+    on its own copy of the workload's sample; no GPU work in any of them."""
+
+    def __init__(self, workload, procs):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in THREAD_VARS}
+        for k in THREAD_VARS:
+            os.environ[k] = "1"
+        self.conns, self.procs = [], []
+        try:
+            for _ in range(procs):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_worker, args=(b, workload), daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.cells = [c.recv() for c in self.conns]
+
+    def iterate(self, k=1):
+        for c in self.conns:
+            c.send(("iter", k))
+        return [c.recv() for c in self.conns]
+
+    def budget(self, seconds, cap=1000):
+        for c in self.conns:
+            c.send(("budget", seconds, cap))
+        return [c.recv() for c in self.conns]
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
 def precision_check(B, sim, sc, opts, dt, in_step, stream):
     """Error of the mixed-precision result against the FP64 path: both take
     one time step from the same state under the same controls (switched rate
@@ -495,56 +754,83 @@ def precision_check(B, sim, sc, opts, dt, in_step, stream):
 
 
 def cpu_baseline(args):
+    """The FP64 oracle as it stands on the host cores: one process per core,
+    each on its own copy of the bounded sample, for about cpu_budget seconds;
+    and the same sample on one core for comparison."""
     sc, sample = oracle_sample(args)
-    its, secs, n = time_oracle(sc, args.cpu_budget, 1000)
-    return {"value": round(n * its / secs, 1), "unit": "cells*Newton-iters/s", "cores": 1, "kind": "oracle",
-            "sample": "%s: %d Newton iterations (numpy dual-number assembly + scipy sparse LU, one thread) "
-                      "in %.1f s" % (sample, its, secs),
+    procs = host_cores()
+    pool = OraclePool(args.workload, procs)
+    try:
+        res = pool.budget(args.cpu_budget)
+    finally:
+        pool.close()
+    work = sum(n * its for n, (its, _) in zip(pool.cells, res))
+    secs = max(t for _, t in res)
+    its1, secs1, n1 = time_oracle(sc, args.cpu_budget / 2.0, 1000)
+    return {"value": round(work / secs, 1), "unit": "cells*Newton-iters/s", "cores": procs, "kind": "oracle",
+            "sample": "%s, one copy per core in %d processes (numpy dual-number assembly + scipy sparse LU, one "
+                      "thread each): %d Newton iterations in %.1f s" % (sample, procs, sum(i for i, _ in res), secs),
+            "one_core": {"value": round(n1 * its1 / secs1, 1), "cores": 1,
+                         "sample": "%s: %d Newton iterations in %.1f s" % (sample, its1, secs1)},
             "host_cpus": os.cpu_count()}
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle on every host core, one process
+    per core on its own copy of the bounded sample; a step is one Newton
+    iteration on every core."""
     if rank != 0:
         return None
     sc, sample = oracle_sample(args)
-    r = OracleRunner(sc)
-    for _ in range(args.warmup):
-        r.iteration()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r.iteration()
-    secs = time.perf_counter() - t0
-    n = r.n
-    value = n * args.steps / secs
+    procs = host_cores()
+    pool = OraclePool(args.workload, procs)
+    try:
+        for _ in range(args.warmup):
+            pool.iterate(1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.iterate(1)
+        secs = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = sum(pool.cells) * args.steps / secs
+    desc = "%s, one copy per host core (%d processes)" % (sample, procs)
     return {"impl": "reference", "metric": "cells*Newton-iters/s", "value": round(value, 1),
             "unit": "cells*Newton-iters/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000.0 * secs / args.steps, 2), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": sample},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": round(value, 1),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": desc},
+            "cpu_baseline": {"kind": "oracle", "cores": procs, "sample": desc, "value": round(value, 1),
                              "unit": "cells*Newton-iters/s"},
             "e2e": {"value": round(value, 1), "unit": "cells*Newton-iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
-def run_batch(args):
+def run_batch(args, headline=None):
     """64 uneven scenarios (20k-400k cells, the C2 recipe with seeded slug
     concentration and RRF) resident at once, driven concurrently (pf_batch),
-    against the same members run one after another on one host thread."""
+    against the same members run one after another on one host thread, in the
+    batched form's precision and in plain FP64."""
     import torch
     from paper_1807_05298_gb300 import binding as B
     torch.cuda.set_device(0)
-    prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
-    opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
-               autotune=args.autotune, stage1=STAGE1[args.stage1])
     members = [G.scenario_member(i) for i in range(args.members)]
     cells = [sc["nx"] * sc["ny"] * sc["nz"] for sc in members]
+    steps = args.batch_steps
+
+    def opts(precision):
+        return dict(precision=B.PF_PREC_MIXED if precision == "mixed" else B.PF_PREC_FP64, precond=B.PF_PC_CPR,
+                    use_forcing=1, newton_tol=args.newton_tol, autotune=args.autotune, stage1=STAGE1[args.stage1])
+
+    runs = [("batched", args.batch_precision, args.threads), ("one_at_a_time", args.batch_precision, 1)]
+    if args.batch_precision != "fp64":
+        runs.append(("one_at_a_time_fp64", "fp64", 1))
     out = {}
-    for label, threads in (("batched", args.threads), ("one_at_a_time", 1)):
-        batch = B.Batch(members, n_threads=threads, **opt)
+    for label, precision, threads in runs:
+        batch = B.Batch(members, n_threads=threads, **opts(precision))
         batch.run(n_steps=args.startup_steps, raise_on_failure=False)   # start-up + graph capture, untimed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps = batch.run(n_steps=args.steps, raise_on_failure=False)
+        reps = batch.run(n_steps=steps, raise_on_failure=False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         batch.close()
@@ -552,18 +838,25 @@ def run_batch(args):
         work = sum(n * k for n, k in zip(cells, newton))
         out[label] = {"value": round(work / wall, 1), "wall_s": round(wall, 3), "newton_iters": sum(newton),
                       "failed_members": sum(1 for r in reps if r.status != 0),
-                      "krylov_iters": sum(r.krylov_iters for r in reps), "threads": threads}
-    return {"metric": "cells*Newton-iters/s", "value": out["batched"]["value"], "unit": "cells*Newton-iters/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.startup_steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": "batched ensemble: %d scenarios of 20k-400k cells (C2 recipe, seeds 100+)"
-                                   % args.members, "total_cells": sum(cells), "precision": args.precision,
-                       "precond": "cpr", "steps_per_member": args.steps},
-            "batched": out["batched"], "one_at_a_time": out["one_at_a_time"],
-            "speedup_vs_one_at_a_time": round(out["batched"]["value"] / out["one_at_a_time"]["value"], 3)}
+                      "krylov_iters": sum(r.krylov_iters for r in reps), "threads": threads, "precision": precision}
+    res = {"metric": "cells*Newton-iters/s", "value": out["batched"]["value"], "unit": "cells*Newton-iters/s",
+           "n_gpus": 1, "steps": steps, "warmup": args.startup_steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.batch_precision, "data": "synthetic",
+           "config": {"workload": "batched ensemble: %d scenarios of 20k-400k cells (100x100x10 recipe, seeds "
+                                  "100+), %d steps each after %d start-up steps" % (args.members, steps,
+                                                                                   args.startup_steps),
+                      "total_cells": sum(cells), "precision": args.batch_precision, "precond": "cpr",
+                      "timing": "host wall clock around pf_batch_run (all members resident)"},
+           "speedup_vs_one_at_a_time": round(out["batched"]["value"] / out["one_at_a_time"]["value"], 3)}
+    res.update(out)
+    if "one_at_a_time_fp64" in out:
+        res["speedup_vs_one_at_a_time_fp64"] = round(out["batched"]["value"] / out["one_at_a_time_fp64"]["value"], 3)
+    if headline is not None:
+        res["vs_fp64_headline"] = round(out["batched"]["value"] / headline, 4)
+    return res
 
 
-def run_serve(args):
+def run_serve(args, headline=None):
     """Poisson arrivals of scenarios of 10k-2M cells (mixed precision), admitted
     by device footprint into a continuous-batching server; latency p50/p99 and
     aggregate throughput."""
@@ -571,7 +864,7 @@ def run_serve(args):
     from paper_1807_05298_gb300 import binding as B
     from scenarios.generate import uniform01
     torch.cuda.set_device(0)
-    prec = B.PF_PREC_MIXED if args.precision == "mixed" else B.PF_PREC_FP64
+    prec = B.PF_PREC_MIXED if args.serve_precision == "mixed" else B.PF_PREC_FP64
     opt = dict(precision=prec, precond=B.PF_PC_CPR, use_forcing=1, newton_tol=args.newton_tol,
                autotune=args.autotune, stage1=STAGE1[args.stage1])
     u = uniform01(5, 9, 2 * args.requests)
@@ -579,8 +872,8 @@ def run_serve(args):
     for r in range(args.requests):
         n = math.exp(math.log(1e4) + (math.log(2e6) - math.log(1e4)) * u[r])
         nx, ny, nz = G.scenario_size(500 + r, n, 10)
-        reqs.append(G.scenario_c2(seed=500 + r, nx=nx, ny=ny, nz=nz, n_steps=args.steps, slug_steps=args.steps,
-                                  dt_days=args.dt_days))
+        reqs.append(G.scenario_c2(seed=500 + r, nx=nx, ny=ny, nz=nz, n_steps=args.serve_steps,
+                                  slug_steps=args.serve_steps, dt_days=args.dt_days))
     cells = [sc["nx"] * sc["ny"] * sc["nz"] for sc in reqs]
     budget = int(args.hbm_budget_gb * 2 ** 30)
     srv = B.Server(budget, n_workers=args.threads, **opt)
@@ -590,8 +883,8 @@ def run_serve(args):
     tk = [srv.submit(sc) for sc in calib]
     res = [srv.wait(t) for t in tk]
     cap_wall = time.perf_counter() - t0
-    cap_cells_s = sum(c * args.steps for c in cells[:args.calib]) / cap_wall   # cells*steps per second
-    mean_work = float(np.mean([c * args.steps for c in cells]))
+    cap_cells_s = sum(c * args.serve_steps for c in cells[:args.calib]) / cap_wall   # cells*steps per second
+    mean_work = float(np.mean([c * args.serve_steps for c in cells]))
     lam = args.load * cap_cells_s / mean_work                                 # requests per second
     gaps = -np.log(uniform01(6, 9, args.requests)) / lam
     arrivals = np.cumsum(gaps)
@@ -608,17 +901,20 @@ def run_serve(args):
     ok = [r.state == B.PF_REQ_DONE for r in res]
     span = max(r.t_end for r in res) - min(r.t_submit for r in res)
     work = sum(c * r.report.newton_iters for c, r in zip(cells, res))
-    return {"metric": "scenario latency p50/p99 and cells*Newton-iters/s", "value": round(work / span, 1),
-            "unit": "cells*Newton-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.calib,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+    res = {"metric": "scenario latency p50/p99 and cells*Newton-iters/s", "value": round(work / span, 1),
+            "unit": "cells*Newton-iters/s", "n_gpus": 1, "steps": args.serve_steps, "warmup": args.calib,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.serve_precision,
             "data": "synthetic", "config": {"workload": "serving: %d Poisson arrivals, 10k-2M cells, %d steps of "
-                                                      "%g d each" % (args.requests, args.steps, args.dt_days),
+                                                      "%g d each" % (args.requests, args.serve_steps, args.dt_days),
                                             "load": args.load, "arrival_rate_per_s": round(lam, 4),
                                             "hbm_budget_gb": args.hbm_budget_gb, "workers": args.threads},
             "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
                           "p99": round(float(np.percentile(lat, 99)), 4), "max": round(float(lat.max()), 4)},
             "completed": int(sum(ok)), "requests": args.requests, "total_cells": int(sum(cells)),
             "capacity_cells_steps_per_s": round(cap_cells_s, 1)}
+    if headline is not None:
+        res["vs_fp64_headline"] = round(res["value"] / headline, 4)
+    return res
 
 
 def main():
@@ -627,14 +923,22 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c3s", "paper"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3s", "paper"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", default="cpr", choices=["cpr", "bjacobi"])
     ap.add_argument("--newton-tol", type=float, default=1e-8)
     ap.add_argument("--startup-steps", type=int, default=2)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--subs", default="mixed,batch,serve",
+                    help="sub-results in the default line (one GPU): mixed, batch, serve or none")
+    ap.add_argument("--sub-steps", type=int, default=10, help="timed Newton iterations of the mixed sub-run")
+    ap.add_argument("--prof-steps", type=int, default=4,
+                    help="Newton iterations of the instrumented pass (kernel shares, roofline)")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (0: max(3, steps / 2))")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="run this many Newton iterations between cudaProfilerStart/Stop and exit")
     ap.add_argument("--autotune", type=int, default=1, help="tune the per-cell kernels' block sizes at set-up")
     ap.add_argument("--amg-pre", type=int, default=1)
     ap.add_argument("--amg-post", type=int, default=1)
@@ -651,10 +955,14 @@ def main():
     ap.add_argument("--check-fp64", type=int, default=1,
                     help="mixed precision: state the error against the FP64 path on one step")
     ap.add_argument("--forcing-form", type=int, default=3, choices=[1, 2, 3],
-                    help="which choice of the forcing term of Sec. 3.3; 3 is the paper's")
+                    help="which choice of the Sec. 3.3 forcing term; 3 is the paper's")
     ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--threads", type=int, default=16)
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--serve-steps", type=int, default=10)
+    ap.add_argument("--serve-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--calib", type=int, default=8)
     ap.add_argument("--load", type=float, default=0.7)
     ap.add_argument("--dt-days", type=float, default=2.0)

@@ -361,14 +361,16 @@ def test_bhp_limit_switching_matches_oracle(B):
     sim.close()
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 def test_forcing_term_forms_match_oracle(B, form):
-    """First and second choices of the Sec. 3.3 forcing term: the tolerance the library
-    picks at each Newton iteration equals the oracle's formula evaluated on
-    the iterates the library produced (the previous linear residual rebuilt as
-    b - J dx from the oracle's own R and J), and the step still lands on the
-    oracle's root.  Polymer is present everywhere at the start so no update
-    is clipped and dx is the difference of consecutive iterates."""
+    """All three choices of the Sec. 3.3 forcing term (the third is the
+    paper's and the library's default): the tolerance the library picks at
+    each Newton iteration equals the oracle's formula evaluated on the
+    iterates the library produced (for the first two, the previous linear
+    residual rebuilt as b - J dx from the oracle's own R and J), and the step
+    still lands on the oracle's root.  Polymer is present everywhere at the
+    start so no update is clipped and dx is the difference of consecutive
+    iterates."""
     sc = G.scenario_c1(nx=9, ny=7, nz=3)
     sc["C0"] = np.full(sc["C0"].shape, 0.5)
     dt = 2.0 * DAY
@@ -402,8 +404,10 @@ def test_forcing_term_forms_match_oracle(B, form):
         nb_prev = np.linalg.norm(R_a)
         if form == 1:
             want = M.forcing_term_difference(-R_b, r_prev, nb_prev)
-        else:
+        elif form == 2:
             want = M.forcing_term_norms(np.linalg.norm(R_b), np.linalg.norm(r_prev), nb_prev)
+        else:
+            want = M.forcing_term(np.linalg.norm(R_b), nb_prev)
         assert etas[l] == pytest.approx(want, rel=1e-6, abs=1e-12)
     x_o, ok, _ = M.newton_step(st, x_old, dt, ctl)
     assert ok
