@@ -281,16 +281,14 @@ def test_full_size_100k_root_is_oracle_root(B):
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
-    """600x450x100 (27M cells, 120 wells), in mixed precision as the benchmark
-    runs it and in FP64: one GPU assembly at a perturbed state.  At 48 sampled
-    interior cells away from the wells, the FP64 residual and the action of the
-    Jacobian (FP32 in mixed precision) on a random vector match the oracle,
-    which assembles the 3x3x3 window around each cell (the window reproduces
-    the full grid's rows of its centre: tests/test_window_oracle.py)."""
+def sampled_window_check(B, sc, precision, seed, n_sample=48, layer_cells=0):
+    """One GPU assembly of the full grid at a perturbed state; at n_sample
+    seeded interior cells away from the wells (layer_cells of them next to a
+    change of rock properties between layers), the FP64 residual and the
+    action of the Jacobian (FP32 in mixed precision) on a random vector match
+    the oracle, which assembles the 3x3x3 window around each cell (the window
+    reproduces the full grid's rows of its centre: tests/test_window_oracle.py)."""
     import scipy.sparse as sp
-    sc = G.scenario_c3(n_steps=3)
     ctl = sc["schedule"][0]["controls"]
     dt = sc["schedule"][0]["dt"]
     nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
@@ -298,7 +296,7 @@ def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
     x_old = np.empty(3 * n + len(sc["wells"]))
     x_old[0:3 * n:3], x_old[1:3 * n:3], x_old[2:3 * n:3] = sc["P0"], sc["S0"], sc["C0"]
     x_old[3 * n:] = [w["Pb0"] for w in sc["wells"]]
-    rng = np.random.default_rng(27)
+    rng = np.random.default_rng(seed)
     x = x_old.copy()
     x[0:3 * n:3] += rng.normal(0.0, 2.0 * BAR, n)
     x[1:3 * n:3] = rng.uniform(0.22, 0.78, n)
@@ -316,10 +314,15 @@ def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
     y_g = sim.apply_jacobian(v)
     sim.close()
     perf = perforated_cells(sc)
+    kz = sc["kz"]
     cells = []
-    while len(cells) < 48:
+    while len(cells) < n_sample:
         i, j, k = int(rng.integers(1, nx - 1)), int(rng.integers(1, ny - 1)), int(rng.integers(1, nz - 1))
         c = i + nx * (j + ny * k)
+        if len(cells) < layer_cells:       # a layer interface above or below c
+            nxy = nx * ny
+            if kz[c] == kz[c - nxy] and kz[c] == kz[c + nxy]:
+                continue
         if c not in perf and c not in cells:
             cells.append(c)
     ph = sc["physics"]
@@ -338,6 +341,25 @@ def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
             yo = row @ vw
             mag = abs(row) @ np.abs(vw)
             assert abs(y_g[3 * c + a] - yo[0]) <= jv_tol * mag[0]
+    return cells
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
+    """600x450x100 (27M cells, 120 wells), in mixed precision and in FP64 as
+    the benchmark runs them: 48 sampled cells against the oracle's windows."""
+    sampled_window_check(B, G.scenario_c3(n_steps=3), precision, 27)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_paper_scale_sampled_cells_match_the_oracle(B, precision):
+    """The paper's high-resolution grid, 951x1920x15 (27,388,800 cells, Sec.
+    4.2.2) over the Table 4 layers each split in three (the benchmark's paper
+    workload), in mixed precision and FP64: 48 sampled cells against the
+    oracle's windows, 16 of them next to a change of layer properties."""
+    sc = G.scenario_layered_table4(nx=951, ny=1920, refine_z=3, dt_days=1.0)
+    cells = sampled_window_check(B, sc, precision, 44, layer_cells=16)
+    assert len(cells) == 48
 
 
 def test_bhp_limit_switching_matches_oracle(B):
