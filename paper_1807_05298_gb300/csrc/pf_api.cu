@@ -93,6 +93,7 @@ struct pf_sim {
   double *w_wi = nullptr, *w_dzb = nullptr, *w_target = nullptr, *w_cinj = nullptr, *w_W = nullptr;
   double *w_sw = nullptr, *w_so = nullptr, *w_scale = nullptr, *w_gamma = nullptr;
   float* Zf = nullptr;  // mixed precision: FP32 copies of the preconditioned vectors
+  float* Vf = nullptr;  // mixed precision: FP32 copy of the Krylov vector the preconditioner takes next
   double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
   double* wtot = nullptr;  // [3 nw] well totals
   unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
@@ -406,6 +407,7 @@ size_t carve(pf_sim* s, char* base) {
   s->V = c.take<double>((size_t)(m + 1) * s->ld);
   s->Z = c.take<double>((size_t)m * s->ld);
   s->Zf = s->mixed ? c.take<float>((size_t)m * s->ld) : nullptr;
+  s->Vf = s->mixed ? c.take<float>((size_t)s->ld) : nullptr;
   s->hbuf = c.take<double>(4 * 128 + 8);
   s->partial = c.take<double>((size_t)s->nblocks * 72);
   s->norms = c.take<double>(4);
@@ -506,26 +508,35 @@ pf_status precond_setup(pf_sim* s) {
   return PF_OK;
 }
 
-// z = M^{-1} v (and, in mixed precision, an FP32 copy zf of z when zf != null)
-pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullptr) {
+// z = M^{-1} v (and, in mixed precision, an FP32 copy zf of z when zf != null).
+// vf: the FP32 copy of v when the caller has it (the Arnoldi steps: the
+// normalisation that wrote v wrote it too); otherwise the mixed CPR form makes
+// it first.
+pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullptr, const float* vf = nullptr) {
   if (s->opts.precond == PF_PC_CPR) {
     int k = 0;
     KtScope t(s, PF_KT_PRECOND);
-    cpr_apply(s->cpr, s->g, wells_view(s), s->mixed, s->J, s->Bw, s->Cw, s->Dw, s->Dinv, s->Dwinv, v, z, s->tmp,
-              zf, s->stream, &k);
-    PF_LAUNCHED(k);
+    if (s->mixed && !vf) {
+      launch_to_f32(s->nunk, v, s->Vf, s->stream);
+      k += 1;
+      vf = s->Vf;
+    }
+    int k2 = 0;
+    cpr_apply(s->cpr, s->g, wells_view(s), s->mixed, s->J, s->Bw, s->Cw, s->Dw, s->Dinv, s->Dwinv, v, vf, z, s->tmp,
+              zf, s->stream, &k2);
+    PF_LAUNCHED(k + k2);
     return PF_OK;
   }
   if (s->opts.stage1 == PF_S1_ILU0) {
     int nl;
     if (s->mixed)
-      nl = launch_ilu_apply<float, float, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
-                                                  (const float*)s->Dwinv, v, z, s->tune.ilu_fused, s->cpr.ilu_cp,
-                                                  s->stream);
+      nl = launch_ilu_apply<float, float, double, double>(s->g, s->nw, (const float*)s->J, (const float*)s->Dinv,
+                                                          (const float*)s->Dwinv, v, z, s->tune.ilu_fused,
+                                                          s->cpr.ilu_cp, s->stream);
     else
-      nl = launch_ilu_apply<double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
-                                                    (const double*)s->Dwinv, v, z, s->tune.ilu_fused, s->cpr.ilu_cp,
-                                                    s->stream);
+      nl = launch_ilu_apply<double, double, double, double>(s->g, s->nw, (const double*)s->J, (const double*)s->Dinv,
+                                                            (const double*)s->Dwinv, v, z, s->tune.ilu_fused,
+                                                            s->cpr.ilu_cp, s->stream);
     PF_LAUNCHED(nl);
   } else {
     if (s->mixed)
@@ -541,6 +552,9 @@ pf_status precond_apply(pf_sim* s, const double* v, double* z, float* zf = nullp
   return PF_OK;
 }
 
+// FP32 copy of the Krylov vectors for the mixed CPR preconditioner (null otherwise)
+float* precond_vf(pf_sim* s) { return s->mixed && s->opts.precond == PF_PC_CPR ? s->Vf : nullptr; }
+
 pf_status dev_norm2(pf_sim* s, const double* a, double* out_host) {
   launch_dot(s->nunk, a, a, s->partial, s->nblocks, s->norms, s->red_counter, s->stream);
   PF_LAUNCHED(1);
@@ -550,9 +564,11 @@ pf_status dev_norm2(pf_sim* s, const double* a, double* out_host) {
   return PF_OK;
 }
 
+// b = f a; in mixed precision with CPR also the FP32 copy the preconditioner
+// takes (b is the first vector of a Krylov cycle)
 void scale_vec(pf_sim* s, const double* a, double f, double* b) {
   launch_fill(1, f, s->norms + 3, s->stream);
-  launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, b, s->stream);
+  launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, b, s->stream, precond_vf(s));
   s->launches += 2;
 }
 
@@ -562,7 +578,7 @@ void scale_vec(pf_sim* s, const double* a, double f, double* b) {
 // Hessenberg column to pinned host memory.
 pf_status piece_pre(pf_sim* s, int j) {
   return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld,
-                       s->mixed ? s->Zf + (size_t)j * s->ld : nullptr);
+                       s->mixed ? s->Zf + (size_t)j * s->ld : nullptr, precond_vf(s));
 }
 pf_status piece_spmv(pf_sim* s, int j) {
   if (!s->mixed) return spmv(s, s->Z + (size_t)j * s->ld, s->V + (size_t)(j + 1) * s->ld);
@@ -592,7 +608,7 @@ pf_status piece_ortho(pf_sim* s, int j) {
   launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
   launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
                    nullptr, reorth, st);
-  launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st);
+  launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st, precond_vf(s));  // v_{j+1} (and its FP32 copy)
   PF_LAUNCHED(5);
   PF_CUDA(cudaMemcpyAsync(s->h_pinned + kPinStep + (j & 1) * kPinStepStride, s->hbuf, (3 * 128 + 1) * sizeof(double),
                           cudaMemcpyDeviceToHost, st));

@@ -150,50 +150,94 @@ __device__ __forceinline__ void top_write(const TopOut& t, long long i, T xi) {
   }
 }
 
-// one colour of a red-black Gauss-Seidel sweep; zero_init: x holds no valid
-// values yet (first half-sweep), so neighbours count as zero.  With xc (the
-// coarse correction of dims c): the neighbours are read as x_j + xc[agg(j)],
-// i.e. the prolongation x += P xc is applied on the fly.  A colour pass
-// overwrites every cell of its colour, so only the other colour's values
-// (the neighbours) need the correction; the next pass overwrites those.
+// Slots of one colour: ceil(nx / 2) per (y, z) row.
+__device__ __forceinline__ long long rb_slots(const Dims& d) { return (long long)((d.nx + 1) / 2) * d.ny * d.nz; }
+
+// Cell of colour `color` in colour slot q = (y + ny z) ceil(nx / 2) + x / 2
+// (false past the row's end when nx is odd).
+__device__ __forceinline__ bool slot_cell(const Dims& d, unsigned int hx, int color, long long q, int& cx, int& cy,
+                                          int& cz) {
+  const unsigned int uq = (unsigned int)q, row = uq / hx, m = uq - row * hx;
+  cz = (int)(row / (unsigned int)d.ny);
+  cy = (int)(row - (unsigned int)cz * (unsigned int)d.ny);
+  cx = (int)((((unsigned int)(cy + cz + color)) & 1u) + 2u * m);
+  return cx < d.nx;
+}
+
+// One Gauss-Seidel relaxation of cell i at (cx, cy, cz): x_i = (b_i - sum over
+// neighbours a_ij x_j) / a_ii with the neighbours in slot order; zero_init:
+// x holds no valid values yet (first half-sweep), so neighbours count as zero.
+// With xc (the coarse correction of dims c) the neighbours are read as
+// x_j + xc[agg(j)], i.e. the prolongation x += P xc is applied on the fly: a
+// colour pass overwrites every cell of its colour, so only the other colour's
+// values (the neighbours) need the correction; the next pass overwrites those.
+// off(sl) gives the coefficient of slot sl (1..6), inv_diag 1 / a_ii.
+template <typename T, typename Coef>
+__device__ __forceinline__ T relax_cell(const Dims& d, long long i, int cx, int cy, int cz, const T* __restrict__ b,
+                                        T* __restrict__ x, int zero_init, const T* __restrict__ xc, const Dims& c,
+                                        int fx, int fy, int fz, Coef off, T inv_diag) {
+  T s = b[i];
+  if (!zero_init) {
+#pragma unroll
+    for (int sl = 1; sl < SL_COUNT; ++sl) {
+      long long j;
+      if (!nbr(d, cx, cy, cz, sl, j)) continue;
+      T xj = x[j];
+      if (xc) {
+        int jx, jy, jz;
+        coords(d, j, jx, jy, jz);
+        xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
+      }
+      s = fnms(off(sl), xj, s);
+    }
+  }
+  const T xi = s * inv_diag;
+  x[i] = xi;
+  return xi;
+}
+
+// One colour of a red-black Gauss-Seidel sweep on a level in the natural
+// layout (A[slot][cell], dinv[cell]).  Without TOP the threads take the
+// colour's slots (every lane relaxes a cell).  With TOP (the last pass on the
+// finest level, which also writes the preconditioner's output) each thread
+// takes a pair of cells along x, one of each colour: it relaxes the one of
+// this colour and writes the output of both (the other colour's value is
+// final), so no lane of a warp idles on the other colour; threads past the
+// pairs write the well rows of the mixed output.
 template <typename T, bool TOP>
 __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
                                               const T* __restrict__ b, T* __restrict__ x, int color, int zero_init,
                                               const T* __restrict__ xc, Dims c, TopOut top) {
   PF_PDL_ENTRY();
   const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
-  GSTRIDE(i, d.n + (TOP && top.mode == 2 ? top.nw : 0)) {
-    if (TOP && i >= d.n) {  // well rows of the mixed output: stage-1 values
-      const long long wv = 3 * d.n + (i - d.n);
-      const float v = top.zf[wv];
-      top.z[wv] = (double)v;
-      if (top.zf_out) top.zf_out[wv] = v;
-      continue;
+  const long long nq = rb_slots(d);
+  const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
+  if (!TOP) {
+    GSTRIDE(q, nq) {
+      int cx, cy, cz;
+      if (!slot_cell(d, hx, color, q, cx, cy, cz)) continue;
+      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
+      relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                    [&](int sl) { return A[(size_t)sl * d.n + i]; }, dinv[i]);
     }
-    int cx, cy, cz;
-    coords(d, i, cx, cy, cz);
-    if (((cx + cy + cz) & 1) != color) {
-      if (TOP) top_write(top, i, x[i]);  // final value of the other colour
-      continue;
-    }
-    T s = b[i];
-    if (!zero_init) {
-#pragma unroll
-      for (int sl = 1; sl < SL_COUNT; ++sl) {
-        long long j;
-        if (!nbr(d, cx, cy, cz, sl, j)) continue;
-        T xj = x[j];
-        if (xc) {
-          int jx, jy, jz;
-          coords(d, j, jx, jy, jz);
-          xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
-        }
-        s = fnms(A[(size_t)sl * d.n + i], xj, s);
+  } else {
+    GSTRIDE(p, nq + (top.mode == 2 ? top.nw : 0)) {
+      if (p >= nq) {  // well rows of the mixed output: stage-1 values
+        const long long wv = 3 * d.n + (p - nq);
+        const float v = top.zf[wv];
+        top.z[wv] = (double)v;
+        if (top.zf_out) top.zf_out[wv] = v;
+        continue;
       }
+      int cx, cy, cz;
+      const bool own = slot_cell(d, hx, color, p, cx, cy, cz);
+      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
+      const int ox = cx ^ 1;  // the pair's cell of the other colour: final value
+      if (ox < d.nx) top_write(top, i - cx + ox, x[i - cx + ox]);
+      if (own)
+        top_write(top, i, relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                                        [&](int sl) { return A[(size_t)sl * d.n + i]; }, dinv[i]));
     }
-    const T xi = s * dinv[i];
-    x[i] = xi;
-    if (TOP) top_write(top, i, xi);
   }
 }
 
@@ -201,8 +245,6 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
 // 1/diag, indexed by the colour slot q = (y + ny z) ceil(nx / 2) + x / 2: a
 // colour pass then reads only its own colour's coefficients (in the natural
 // layout every line also carries the other colour's).
-__device__ __forceinline__ long long rb_slots(const Dims& d) { return (long long)((d.nx + 1) / 2) * d.ny * d.nz; }
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_rb_compact(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
                                                     T* __restrict__ c0, T* __restrict__ c1) {
@@ -221,8 +263,8 @@ __global__ void __launch_bounds__(256) k_rb_compact(Dims d, const T* __restrict_
 }
 
 // k_rbgs on the finest level reading this colour's copy cp (the same
-// arithmetic in the same order).  Without TOP the threads take the colour's
-// slots; with TOP every cell (and the well rows), as in k_rbgs.
+// arithmetic in the same order); the same thread mappings as k_rbgs.  In the
+// TOP pass the pair's cell of this colour has the pair's index as its slot.
 template <typename T, bool TOP>
 __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ cp, const T* __restrict__ b,
                                                  T* __restrict__ x, int color, int zero_init,
@@ -231,51 +273,32 @@ __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ c
   const int fx = c.nx < d.nx ? 2 : 1, fy = c.ny < d.ny ? 2 : 1, fz = c.nz < d.nz ? 2 : 1;
   const long long nq = rb_slots(d);
   const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
-  auto relax = [&](long long i, long long q, int cx, int cy, int cz) {
-    T s = b[i];
-    if (!zero_init) {
-#pragma unroll
-      for (int sl = 1; sl < SL_COUNT; ++sl) {
-        long long j;
-        if (!nbr(d, cx, cy, cz, sl, j)) continue;
-        T xj = x[j];
-        if (xc) {
-          int jx, jy, jz;
-          coords(d, j, jx, jy, jz);
-          xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
-        }
-        s = fnms(cp[(size_t)(sl - 1) * nq + q], xj, s);
-      }
-    }
-    const T xi = s * cp[(size_t)6 * nq + q];
-    x[i] = xi;
-    return xi;
-  };
   if (!TOP) {
     GSTRIDE(q, nq) {
-      const unsigned int uq = (unsigned int)q, row = uq / hx, m = uq - row * hx;
-      const int cz = (int)(row / (unsigned int)d.ny), cy = (int)(row - (unsigned int)cz * (unsigned int)d.ny);
-      const int cx = (int)((((unsigned int)(cy + cz + color)) & 1u) + 2u * m);
-      if (cx >= d.nx) continue;
-      relax(cx + (long long)d.nx * row, q, cx, cy, cz);
+      int cx, cy, cz;
+      if (!slot_cell(d, hx, color, q, cx, cy, cz)) continue;
+      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
+      relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                    [&](int sl) { return cp[(size_t)(sl - 1) * nq + q]; }, cp[(size_t)6 * nq + q]);
     }
   } else {
-    GSTRIDE(i, d.n + (top.mode == 2 ? top.nw : 0)) {
-      if (i >= d.n) {  // well rows of the mixed output: stage-1 values
-        const long long wv = 3 * d.n + (i - d.n);
+    GSTRIDE(p, nq + (top.mode == 2 ? top.nw : 0)) {
+      if (p >= nq) {  // well rows of the mixed output: stage-1 values
+        const long long wv = 3 * d.n + (p - nq);
         const float v = top.zf[wv];
         top.z[wv] = (double)v;
         if (top.zf_out) top.zf_out[wv] = v;
         continue;
       }
       int cx, cy, cz;
-      coords(d, i, cx, cy, cz);
-      if (((cx + cy + cz) & 1) != color) {
-        top_write(top, i, x[i]);  // final value of the other colour
-        continue;
-      }
-      const long long q = ((long long)cy + (long long)d.ny * cz) * hx + (cx >> 1);
-      top_write(top, i, relax(i, q, cx, cy, cz));
+      const bool own = slot_cell(d, hx, color, p, cx, cy, cz);
+      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
+      const int ox = cx ^ 1;  // the pair's cell of the other colour: final value
+      if (ox < d.nx) top_write(top, i - cx + ox, x[i - cx + ox]);
+      if (own)
+        top_write(top, i, relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                                        [&](int sl) { return cp[(size_t)(sl - 1) * nq + p]; },
+                                        cp[(size_t)6 * nq + p]));
     }
   }
 }
@@ -655,7 +678,8 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
   const long long nq = ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
   auto pass = [&](int color, int zi, const T* xc, const Dims& dxc, const TopOut& to) {
     const bool wtop = to.mode != 0;
-    const long long nt = wtop ? L.n + (to.mode == 2 ? to.nw : 0) : (cp ? nq : L.n);
+    // every pass takes the colour slots (the output-writing pass: cell pairs, then the well rows)
+    const long long nt = nq + (wtop && to.mode == 2 ? to.nw : 0);
     const int grid = grid_for(nt, bs);
     if (cp) {
       const T* cc = (const T*)c.rb_cp[color];
@@ -720,12 +744,12 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
 
 // stage 1 in FP32: zf = D^{-1} (float) v, cells and wells
 __global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const float* __restrict__ Dinv,
-                                                    const float* __restrict__ Dwinv, const double* __restrict__ v,
+                                                    const float* __restrict__ Dwinv, const float* __restrict__ v,
                                                     float* __restrict__ zf) {
   PF_PDL_ENTRY();
   GSTRIDE(i, n + nw) {
-    if (i >= n) { zf[3 * n + (i - n)] = Dwinv[i - n] * (float)v[3 * n + (i - n)]; continue; }
-    const float r0 = (float)v[3 * i], r1 = (float)v[3 * i + 1], r2 = (float)v[3 * i + 2];
+    if (i >= n) { zf[3 * n + (i - n)] = Dwinv[i - n] * v[3 * n + (i - n)]; continue; }
+    const float r0 = v[3 * i], r1 = v[3 * i + 1], r2 = v[3 * i + 2];
     const float* D = Dinv + i;
     zf[3 * i] = D[0] * r0 + D[n] * r1 + D[2 * n] * r2;
     zf[3 * i + 1] = D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2;
@@ -736,10 +760,10 @@ __global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const f
 // stage 2, restricted on the fly: b0 = w_o (v - J y)_oil + w_w (v - J y)_water in
 // the preconditioner's precision T (only the oil and water rows of J are read;
 // a perforated cell also takes its well column B y_w)
-template <typename T>
+template <typename T, typename VT>
 __global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __restrict__ J,
                                                 const T* __restrict__ Bw, const T* __restrict__ y,
-                                                const double* __restrict__ v, T w_o, T w_w, T* __restrict__ b0) {
+                                                const VT* __restrict__ v, T w_o, T w_w, T* __restrict__ b0) {
   PF_PDL_ENTRY();
   const long long n = g.n;
   GSTRIDE(i, n) {
@@ -800,14 +824,14 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
 
 // stage 2 in the form that matches stage 1: after the ILU(0) solve only the
 // black rows need the product (k_stage2_ilu), after block-Jacobi every row
-template <typename T>
+template <typename T, typename VT>
 void launch_stage2(const CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const T* y,
-                   const double* v, int block, cudaStream_t st) {
+                   const VT* v, int block, cudaStream_t st) {
   T* b0 = (T*)c.lev[0].b;
   if (c.ilu)
-    launch_stage2_ilu<T>(g, w, (const T*)J, c.ilu_cp, (const T*)Bw, y, v, (T)c.w_o, (T)c.w_w, b0, block, st);
+    launch_stage2_ilu<T, VT>(g, w, (const T*)J, c.ilu_cp, (const T*)Bw, y, v, (T)c.w_o, (T)c.w_w, b0, block, st);
   else
-    launch(k_stage2<T>, grid_for(g.n, block), block, 0, st, g, w, (const T*)J, (const T*)Bw, y, v, (T)c.w_o,
+    launch(k_stage2<T, VT>, grid_for(g.n, block), block, 0, st, g, w, (const T*)J, (const T*)Bw, y, v, (T)c.w_o,
            (T)c.w_w, b0);
 }
 
@@ -816,15 +840,15 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
              const void* Dwinv, const double* v, double* z, cudaStream_t st, int& k) {
   // stage 1: y = D^{-1} f, or the red-black block ILU(0) solve (cells; wells by their diagonal)
   if (c.ilu) {
-    k += launch_ilu_apply<T, T, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z, c.ilu_fused,
-                                        c.ilu_cp, st);
+    k += launch_ilu_apply<T, T, double, double>(g, w.nw, (const T*)J, (const T*)Dinv, (const T*)Dwinv, v, z,
+                                                c.ilu_fused, c.ilu_cp, st);
   } else {
     launch_bjacobi_apply<T>(g, w.nw, (const T*)Dinv, (const T*)Dwinv, v, z, st);
     k += 1;
   }
   // stage 2: r = f - J y restricted to the pressure equation (oil and water rows only)
   CprLevel& L0 = c.lev[0];
-  launch_stage2<T>(c, g, w, J, Bw, (const T*)z, v, c.block_stage2, st);
+  launch_stage2<T, double>(c, g, w, J, Bw, (const T*)z, v, c.block_stage2, st);
   k += 1;
   // stage 3: pressure multigrid cycle, then y += Pi_p x (in the cycle's last pass when it can)
   TopOut top;
@@ -847,22 +871,25 @@ void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
       launch(k_rbgs_cp<float, false>, grid_for(nq, block), block, 0, st, d, (const float*)c.rb_cp[0],
              (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
     else
-      launch(k_rbgs<float, false>, grid_for(L.n, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
+      launch(k_rbgs<float, false>, grid_for(nq, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
              (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
   } else {
     if (c.rb_cp[0])
       launch(k_rbgs_cp<double, false>, grid_for(nq, block), block, 0, st, d, (const double*)c.rb_cp[0],
              (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
     else
-      launch(k_rbgs<double, false>, grid_for(L.n, block), block, 0, st, d, (const double*)L.A,
+      launch(k_rbgs<double, false>, grid_for(nq, block), block, 0, st, d, (const double*)L.A,
              (const double*)L.dinv, (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
   }
 }
 
 void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
                      const double* v, double* tmp, int block, cudaStream_t st) {
-  if (mixed) launch_stage2<float>(c, g, w, J, Bw, reinterpret_cast<const float*>(tmp), v, block, st);
-  else launch_stage2<double>(c, g, w, J, Bw, (const double*)tmp, v, block, st);
+  // the mixed form reads the FP32 copy of its input; any float values serve for timing
+  if (mixed)
+    launch_stage2<float, float>(c, g, w, J, Bw, reinterpret_cast<const float*>(tmp), reinterpret_cast<const float*>(v),
+                                block, st);
+  else launch_stage2<double, double>(c, g, w, J, Bw, (const double*)tmp, v, block, st);
 }
 
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base) {
@@ -923,22 +950,24 @@ void cpr_setup(CprData& c, const Grid&, const Phys& ph, const double*, const Wel
 }
 
 void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw, const void* Cw,
-               const void* Dw, const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp,
-               float* zf_out, cudaStream_t st, int* launches) {
+               const void* Dw, const void* Dinv, const void* Dwinv, const double* v, const float* vf, double* z,
+               double* tmp, float* zf_out, cudaStream_t st, int* launches) {
   int k = 0;
   if (mixed) {
+    // the FP32 stages read vf, the FP32 copy of v (the same values they
+    // would round v to)
     // every stage in FP32; tmp serves as the FP32 stage-1 vector
     float* zf = reinterpret_cast<float*>(tmp);
     CprLevel& L0 = c.lev[0];
     const int gb = grid_for(g.n + w.nw, 256);
     if (c.ilu) {
-      k += launch_ilu_apply<float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv, (const float*)Dwinv, v,
-                                                 zf, c.ilu_fused, c.ilu_cp, st);
+      k += launch_ilu_apply<float, float, float, float>(g, w.nw, (const float*)J, (const float*)Dinv,
+                                                        (const float*)Dwinv, vf, zf, c.ilu_fused, c.ilu_cp, st);
     } else {
-      launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, v, zf);
+      launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, vf, zf);
       k += 1;
     }
-    launch_stage2<float>(c, g, w, J, Bw, (const float*)zf, v, c.block_stage2, st);
+    launch_stage2<float, float>(c, g, w, J, Bw, (const float*)zf, vf, c.block_stage2, st);
     k += 1;
     TopOut top;
     top.mode = 2;

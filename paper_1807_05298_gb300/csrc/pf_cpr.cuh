@@ -61,10 +61,11 @@ void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base);
 pf_status cpr_init(CprData& c, const Grid& g, bool mixed, const pf_solver_opts& o, cudaStream_t st);
 void cpr_setup(CprData& c, const Grid& g, const Phys& ph, const double* phi_r, const Wells& w, bool mixed,
                const void* J, const void* Bw, const void* Dw, cudaStream_t st, int* launches);
-// z = M^{-1} v.  Mixed precision runs every stage in FP32 (tmp then holds an
-// FP32 vector) and also writes an FP32 copy of z to zf_out (may be null).
+// z = M^{-1} v.  Mixed precision runs every stage in FP32 from vf, the FP32
+// copy of v (tmp then holds an FP32 vector), and also writes an FP32 copy of z
+// to zf_out (may be null); the FP64 form reads v (vf unused).
 void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw, const void* Cw,
-               const void* Dw, const void* Dinv, const void* Dwinv, const double* v, double* z, double* tmp,
-               float* zf_out, cudaStream_t st, int* launches);
+               const void* Dw, const void* Dinv, const void* Dwinv, const double* v, const float* vf, double* z,
+               double* tmp, float* zf_out, cudaStream_t st, int* launches);
 
 }  // namespace pf

@@ -163,14 +163,15 @@ struct IluCompact {
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, double guard,
                       const IluCompact& cp, cudaStream_t st);
-template <typename DT, typename PT, typename OT>
-int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+// f: the right-hand side, FP64 or (mixed-precision CPR) its FP32 copy
+template <typename DT, typename PT, typename OT, typename VT>
+int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const VT* f, OT* y,
                      int fused, const IluCompact& cp, cudaStream_t st);  // returns the number of launches
 // CPR stage 2 after the ILU(0) first stage: black rows in full, red rows their
 // well column only (the red sweep solved their cell part exactly)
-template <typename T>
+template <typename T, typename VT>
 void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
-                       const double* v, T w_o, T w_w, T* b0, int block, cudaStream_t st);
+                       const VT* v, T w_o, T w_w, T* b0, int block, cudaStream_t st);
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);
@@ -179,8 +180,9 @@ void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv
 void launch_copy(long long n, const double* a, double* b, cudaStream_t st);
 void launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
 void launch_fill(long long n, double v, double* a, cudaStream_t st);
+// b = a * s[0] or a / sqrt(s[0]); with bf also bf = (float) b
 void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b,
-                         cudaStream_t st);  // b = a * s[0] or a / sqrt(s[0])
+                         cudaStream_t st, float* bf = nullptr);
 void launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t st);
 void launch_xpay(long long n, const double* x, double beta, double* y, cudaStream_t st); // y = x + beta y
 void launch_sub(long long n, const double* a, const double* b, double* c, cudaStream_t st); // c = a - b

@@ -389,9 +389,9 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
 }
 
 // diagonal-only first sweep: t_r = D_r^-1 f_r on the red cells, into y
-template <typename PT, typename OT>
+template <typename PT, typename OT, typename VT>
 __global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, const PT* __restrict__ Dinv,
-                                                      const double* __restrict__ f, OT* __restrict__ y) {
+                                                      const VT* __restrict__ f, OT* __restrict__ y) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -422,17 +422,22 @@ __device__ __forceinline__ double as_pt(__nv_bfloat16 v, double) { return (doubl
 // With COMPACT the off-diagonal blocks come from this colour's compact copy
 // (k_ilu_compact: slot-major, indexed by the colour slot q, so a sweep reads
 // only its own rows); otherwise from J itself, whose lines also carry the
-// other colour's rows.
-template <typename BT, typename PT, typename OT, bool COMPACT>
-__global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int colour, int fused, int nw, const BT* __restrict__ J,
+// other colour's rows.  MODE: 0 the red sweep (t_j = y_j of the black
+// neighbours, then the well rows), 1 the black sweep after k_ilu_red_diag
+// (t_j = y_j of the red neighbours), 2 the black sweep with the red diagonal
+// folded in (t_j = D_j^-1 f_j formed on the fly).  One instantiation per mode
+// keeps each launch's code (and registers) to its own path.
+template <typename BT, typename PT, typename OT, bool COMPACT, typename VT, int MODE>
+__global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* __restrict__ J,
                                                    const PT* __restrict__ Dinv, const PT* __restrict__ Dwinv,
-                                                   const double* __restrict__ f, OT* __restrict__ y) {
+                                                   const VT* __restrict__ f, OT* __restrict__ y) {
   PF_PDL_ENTRY();
+  constexpr int colour = MODE == 0 ? 0 : 1;
   const long long n = g.n, nq = colour_slots(g);
   const long long nt = nq + (colour == 0 ? nw : 0);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nt;
        q += (long long)gridDim.x * blockDim.x) {
-    if (q >= nq) {
+    if (colour == 0 && q >= nq) {
       const long long w = q - nq;
       y[3 * n + w] = (OT)((PT)Dwinv[w] * (PT)f[3 * n + w]);
       continue;
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int colour, int fu
       long long c;
       if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
       PT t0, t1, t2;
-      if (colour == 1 && fused) {
+      if (MODE == 2) {
         const PT f0 = (PT)f[3 * c], f1 = (PT)f[3 * c + 1], f2 = (PT)f[3 * c + 2];
         const PT* Dc = Dinv + c;
         t0 = Dc[0] * f0 + Dc[n] * f1 + Dc[2 * n] * f2;
@@ -511,22 +516,27 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
            (__nv_bfloat16*)cp.c[1]);
 }
 
-template <typename DT, typename PT, typename OT>
-int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const double* f, OT* y,
+template <typename DT, typename PT, typename OT, typename VT>
+int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const VT* f, OT* y,
                      int fused, const IluCompact& cp, cudaStream_t st) {
   const long long nq = colour_slots_host(g);
-  if (!fused) launch(k_ilu_red_diag<PT, OT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
-  for (int colour = 1; colour >= 0; --colour) {
-    const long long nt = colour == 0 ? nq + nw : nq;
-    if (cp.kind == 1)
-      launch(k_ilu_sweep<DT, PT, OT, true>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw,
-             (const DT*)cp.c[colour], Dinv, Dwinv, f, y);
-    else if (cp.kind == 2)
-      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw,
-             (const __nv_bfloat16*)cp.c[colour], Dinv, Dwinv, f, y);
-    else
-      launch(k_ilu_sweep<DT, PT, OT, false>, grid_for(nt, 256), 256, 0, st, g, colour, fused, nw, J, Dinv, Dwinv, f,
-             y);
+  if (!fused) launch(k_ilu_red_diag<PT, OT, VT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
+  // the black sweep, then the red one (with the well rows)
+  const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
+  if (cp.kind == 1) {
+    const DT *c0 = (const DT*)cp.c[0], *c1 = (const DT*)cp.c[1];
+    if (fused) launch(k_ilu_sweep<DT, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
+    else launch(k_ilu_sweep<DT, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
+    launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dwinv, f, y);
+  } else if (cp.kind == 2) {
+    const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
+    if (fused) launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
+    else launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
+    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dwinv, f, y);
+  } else {
+    if (fused) launch(k_ilu_sweep<DT, PT, OT, false, VT, 2>, grid1, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
+    else launch(k_ilu_sweep<DT, PT, OT, false, VT, 1>, grid1, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
+    launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
   }
   return fused ? 2 : 3;
 }
@@ -540,10 +550,10 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
 // blocks from the black compact copy when the sweeps read one (COMPACT; the
 // diagonal block always from J).  Threads [0, nq) take the black cells and
 // [nq, 2 nq) the red ones, so the black threads of a warp run together.
-template <typename T, typename BT, bool COMPACT>
+template <typename T, typename BT, bool COMPACT, typename VT>
 __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T* __restrict__ J,
                                                     const BT* __restrict__ Cb, const T* __restrict__ Bw,
-                                                    const T* __restrict__ y, const double* __restrict__ v, T w_o,
+                                                    const T* __restrict__ y, const VT* __restrict__ v, T w_o,
                                                     T w_w, T* __restrict__ b0) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
@@ -581,17 +591,17 @@ __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T*
   }
 }
 
-template <typename T>
+template <typename T, typename VT>
 void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
-                       const double* v, T w_o, T w_w, T* b0, int block, cudaStream_t st) {
+                       const VT* v, T w_o, T w_w, T* b0, int block, cudaStream_t st) {
   const int grid = grid_for(2 * colour_slots_host(g), block);
   if (cp.kind == 1)
-    launch(k_stage2_ilu<T, T, true>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0);
+    launch(k_stage2_ilu<T, T, true, VT>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0);
   else if (cp.kind == 2)
-    launch(k_stage2_ilu<T, __nv_bfloat16, true>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.c[1], Bw, y,
-           v, w_o, w_w, b0);
+    launch(k_stage2_ilu<T, __nv_bfloat16, true, VT>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.c[1], Bw,
+           y, v, w_o, w_w, b0);
   else
-    launch(k_stage2_ilu<T, T, false>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0);
+    launch(k_stage2_ilu<T, T, false, VT>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0);
 }
 
 template <typename PT>
@@ -616,6 +626,18 @@ __global__ void k_scale_dev(long long n, const double* a, const double* __restri
   PF_PDL_ENTRY();
   const double f = inv_sqrt ? 1.0 / sqrt(s[0]) : s[0];
   GRID_STRIDE(i, n) b[i] = a[i] * f;
+}
+
+// the same, and an FP32 copy of b (the mixed-precision preconditioner's input)
+__global__ void k_scale_dev_f32(long long n, const double* a, const double* __restrict__ s, int inv_sqrt, double* b,
+                                float* __restrict__ bf) {
+  PF_PDL_ENTRY();
+  const double f = inv_sqrt ? 1.0 / sqrt(s[0]) : s[0];
+  GRID_STRIDE(i, n) {
+    const double v = a[i] * f;
+    b[i] = v;
+    bf[i] = (float)v;
+  }
 }
 __global__ void k_axpy(long long n, double al, const double* __restrict__ x, double* __restrict__ y) {
   PF_PDL_ENTRY();
@@ -642,8 +664,10 @@ void launch_copy(long long n, const double* a, double* b, cudaStream_t st) {
   launch(k_copy, grid_for(n, 256), 256, 0, st, n, a, b);
 }
 void launch_fill(long long n, double v, double* a, cudaStream_t st) { launch(k_fill, grid_for(n, 256), 256, 0, st, n, v, a); }
-void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b, cudaStream_t st) {
-  launch(k_scale_dev, grid_for(n, 256), 256, 0, st, n, a, s, inv_sqrt, b);
+void launch_scale_by_dev(long long n, const double* a, const double* s, int inv_sqrt, double* b, cudaStream_t st,
+                         float* bf) {
+  if (bf) launch(k_scale_dev_f32, grid_for(n, 256), 256, 0, st, n, a, s, inv_sqrt, b, bf);
+  else launch(k_scale_dev, grid_for(n, 256), 256, 0, st, n, a, s, inv_sqrt, b);
 }
 void launch_axpy(long long n, double al, const double* x, double* y, cudaStream_t st) {
   launch(k_axpy, grid_for(n, 256), 256, 0, st, n, al, x, y);
@@ -868,17 +892,20 @@ template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const 
                                                double*, double, const IluCompact&, cudaStream_t);
 template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                              double, const IluCompact&, cudaStream_t);
-template int launch_ilu_apply<double, double, double>(const Grid&, int, const double*, const double*,
-                                                      const double*, const double*, double*, int, const IluCompact&,
-                                                      cudaStream_t);
-template int launch_ilu_apply<float, float, float>(const Grid&, int, const float*, const float*, const float*,
-                                                   const double*, float*, int, const IluCompact&, cudaStream_t);
-template int launch_ilu_apply<float, float, double>(const Grid&, int, const float*, const float*, const float*,
-                                                    const double*, double*, int, const IluCompact&, cudaStream_t);
-template void launch_stage2_ilu<double>(const Grid&, const Wells&, const double*, const IluCompact&, const double*,
-                                        const double*, const double*, double, double, double*, int, cudaStream_t);
-template void launch_stage2_ilu<float>(const Grid&, const Wells&, const float*, const IluCompact&, const float*,
-                                       const float*, const double*, float, float, float*, int, cudaStream_t);
+template int launch_ilu_apply<double, double, double, double>(const Grid&, int, const double*, const double*,
+                                                              const double*, const double*, double*, int,
+                                                              const IluCompact&, cudaStream_t);
+template int launch_ilu_apply<float, float, float, float>(const Grid&, int, const float*, const float*, const float*,
+                                                          const float*, float*, int, const IluCompact&, cudaStream_t);
+template int launch_ilu_apply<float, float, double, double>(const Grid&, int, const float*, const float*,
+                                                            const float*, const double*, double*, int,
+                                                            const IluCompact&, cudaStream_t);
+template void launch_stage2_ilu<double, double>(const Grid&, const Wells&, const double*, const IluCompact&,
+                                                const double*, const double*, const double*, double, double, double*,
+                                                int, cudaStream_t);
+template void launch_stage2_ilu<float, float>(const Grid&, const Wells&, const float*, const IluCompact&,
+                                              const float*, const float*, const float*, float, float, float*, int,
+                                              cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,
