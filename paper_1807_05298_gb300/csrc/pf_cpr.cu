@@ -304,10 +304,15 @@ __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ c
 }
 
 // coarse right-hand side: sum over each aggregate of the fine residual b - A x
+// With xc (the coarse level's iterate) the first red pass of the coarse
+// level's cycle from a zero initial guess is done here too: a red coarse cell
+// gets xc = bc / a_cc (bc as stored, times the stored 1 / diagonal: the value
+// that pass would compute), so the coarse cycle starts with its black pass.
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const T* __restrict__ A,
                                                            const T* __restrict__ b, const T* __restrict__ x,
-                                                           T* __restrict__ bc) {
+                                                           T* __restrict__ bc, T* __restrict__ xc,
+                                                           const T* __restrict__ dinv_c) {
   PF_PDL_ENTRY();
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
   const long long total = 8 * c.n;
@@ -334,7 +339,15 @@ __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const
       }
     }
     r = grp8_sum(r);
-    if (t < total && child == 0) bc[I] = (T)r;
+    if (t < total && child == 0) {
+      const T bI = (T)r;
+      bc[I] = bI;
+      if (xc) {
+        int cx, cy, cz;
+        coords(c, I, cx, cy, cz);
+        if (((cx + cy + cz) & 1) == 0) xc[I] = bI * dinv_c[I];
+      }
+    }
   }
 }
 
@@ -632,12 +645,26 @@ __global__ void __launch_bounds__(256) k_prolong_top(long long n, const T* __res
 
 size_t aup(size_t v) { return (v + 255) / 256 * 256; }
 
+// Whether the cycle on level l starts (from a zero initial guess) with a
+// per-level red pass that the producer of its right-hand side can do instead:
+// the level runs per-level kernels (not the coarsest direct solve, the single
+// block or the cluster) and pre-smooths.
+bool folds_first_red(const CprData& c, int l) {
+  const CprLevel& L = c.lev[l];
+  if (l == c.nlev - 1 || L.n <= c.block_cells || L.n <= c.cluster_cells) return false;
+  return (l == 0 ? c.pre : c.cpre) >= 1;
+}
+
 // One cycle on level l (and below).  With top.mode set (only at l = 0), the
 // last post-smoothing pass also writes the preconditioner's output; returns
 // whether it did (not when the level runs in the single block or has no
 // post-smoothing).
 template <typename T>
-bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const TopOut& top = TopOut{}) {
+// first_red_done: the producer of this level's right-hand side also did the
+// first (zero initial guess) red pass (only for a level with per-level passes
+// and pre-smoothing; see folds_first_red).
+bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const TopOut& top = TopOut{},
+           bool first_red_done = false) {
   CprLevel& L = c.lev[l];
   const Dims d = dims_of(L);
   const int gb = grid_for(L.n, 256);
@@ -691,16 +718,21 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
     }
   };
   for (int sweep = 0; sweep < npre; ++sweep) {
-    pass(0, (zero_init && sweep == 0) ? 1 : 0, (const T*)nullptr, Dims{}, none);
+    if (!(sweep == 0 && zero_init && first_red_done)) {
+      pass(0, (zero_init && sweep == 0) ? 1 : 0, (const T*)nullptr, Dims{}, none);
+      k += 1;
+    }
     pass(1, 0, (const T*)nullptr, Dims{}, none);
-    k += 2;
+    k += 1;
   }
   if (npre == 0 && zero_init) cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), st);  // the zero initial guess
   CprLevel& C = c.lev[l + 1];
   const Dims dc = dims_of(C);
-  launch(k_residual_restrict<T>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b);
+  const bool fold = folds_first_red(c, l + 1);
+  launch(k_residual_restrict<T>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b,
+         fold ? (T*)C.x : (T*)nullptr, (const T*)C.dinv);
   k += 1;
-  for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k);
+  for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k, TopOut{}, g == 0 && fold);
   if (npost == 0) {
     launch(k_prolong_add<T>, gb, 256, 0, st, d, dc, (const T*)C.x, x);
     k += 1;
@@ -763,7 +795,8 @@ __global__ void __launch_bounds__(256) k_stage1_f32(long long n, int nw, const f
 template <typename T, typename VT>
 __global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __restrict__ J,
                                                 const T* __restrict__ Bw, const T* __restrict__ y,
-                                                const VT* __restrict__ v, T w_o, T w_w, T* __restrict__ b0) {
+                                                const VT* __restrict__ v, T w_o, T w_w, T* __restrict__ b0,
+                                                T* __restrict__ x0, const T* __restrict__ d0, int d0_slot) {
   PF_PDL_ENTRY();
   const long long n = g.n;
   GSTRIDE(i, n) {
@@ -798,6 +831,11 @@ __global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __r
       if (m >= 0) r -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * y[3 * n + w.pwell[m]];
     }
     b0[i] = r;
+    // the multigrid's first red pass from a zero guess (as in k_stage2_ilu)
+    if (x0 && ((ii + j + k) & 1) == 0) {
+      const long long q = (j + (long long)g.ny * k) * ((g.nx + 1) / 2) + ii / 2;
+      x0[i] = r * d0[d0_slot ? q : i];
+    }
   }
 }
 
@@ -824,15 +862,24 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
 
 // stage 2 in the form that matches stage 1: after the ILU(0) solve only the
 // black rows need the product (k_stage2_ilu), after block-Jacobi every row
+// fold: also the multigrid's first red pass from a zero guess on the finest
+// level (folds_first_red(c, 0)), reading 1 / diagonal from the red per-colour
+// copy when the smoother uses one
 template <typename T, typename VT>
 void launch_stage2(const CprData& c, const Grid& g, const Wells& w, const void* J, const void* Bw, const T* y,
-                   const VT* v, int block, cudaStream_t st) {
-  T* b0 = (T*)c.lev[0].b;
+                   const VT* v, int block, cudaStream_t st, bool fold = false) {
+  const CprLevel& L0 = c.lev[0];
+  T* b0 = (T*)L0.b;
+  T* x0 = fold ? (T*)L0.x : nullptr;
+  const long long nq = ((long long)(L0.nx + 1) / 2) * L0.ny * L0.nz;
+  const bool slot = c.rb_cp[0] != nullptr;
+  const T* d0 = slot ? (const T*)c.rb_cp[0] + 6 * nq : (const T*)L0.dinv;
   if (c.ilu)
-    launch_stage2_ilu<T, VT>(g, w, (const T*)J, c.ilu_cp, (const T*)Bw, y, v, (T)c.w_o, (T)c.w_w, b0, block, st);
+    launch_stage2_ilu<T, VT>(g, w, (const T*)J, c.ilu_cp, (const T*)Bw, y, v, (T)c.w_o, (T)c.w_w, b0, x0, d0,
+                             slot ? 1 : 0, block, st);
   else
     launch(k_stage2<T, VT>, grid_for(g.n, block), block, 0, st, g, w, (const T*)J, (const T*)Bw, y, v, (T)c.w_o,
-           (T)c.w_w, b0);
+           (T)c.w_w, b0, x0, d0, slot ? 1 : 0);
 }
 
 template <typename T>
@@ -848,13 +895,14 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
   }
   // stage 2: r = f - J y restricted to the pressure equation (oil and water rows only)
   CprLevel& L0 = c.lev[0];
-  launch_stage2<T, double>(c, g, w, J, Bw, (const T*)z, v, c.block_stage2, st);
+  const bool fold = folds_first_red(c, 0);
+  launch_stage2<T, double>(c, g, w, J, Bw, (const T*)z, v, c.block_stage2, st, fold);
   k += 1;
   // stage 3: pressure multigrid cycle, then y += Pi_p x (in the cycle's last pass when it can)
   TopOut top;
   top.mode = 1;
   top.z = z;
-  if (!cycle<T>(c, 0, true, st, k, top)) {
+  if (!cycle<T>(c, 0, true, st, k, top, fold)) {
     launch(k_prolong_top<T>, grid_for(g.n, 256), 256, 0, st, g.n, (const T*)L0.x, z);
     k += 1;
   }
@@ -967,7 +1015,8 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
       launch(k_stage1_f32, gb, 256, 0, st, g.n, w.nw, (const float*)Dinv, (const float*)Dwinv, vf, zf);
       k += 1;
     }
-    launch_stage2<float, float>(c, g, w, J, Bw, (const float*)zf, vf, c.block_stage2, st);
+    const bool fold = folds_first_red(c, 0);
+    launch_stage2<float, float>(c, g, w, J, Bw, (const float*)zf, vf, c.block_stage2, st, fold);
     k += 1;
     TopOut top;
     top.mode = 2;
@@ -975,7 +1024,7 @@ void cpr_apply(CprData& c, const Grid& g, const Wells& w, bool mixed, const void
     top.z = z;
     top.zf = zf;
     top.zf_out = zf_out;
-    if (!cycle<float>(c, 0, true, st, k, top)) {
+    if (!cycle<float>(c, 0, true, st, k, top, fold)) {
       launch(k_out_f32, gb, 256, 0, st, g.n, w.nw, zf, (const float*)L0.x, z, zf_out);
       k += 1;
     }

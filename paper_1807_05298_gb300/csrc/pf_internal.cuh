@@ -168,10 +168,13 @@ template <typename DT, typename PT, typename OT, typename VT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const VT* f, OT* y,
                      int fused, const IluCompact& cp, cudaStream_t st);  // returns the number of launches
 // CPR stage 2 after the ILU(0) first stage: black rows in full, red rows their
-// well column only (the red sweep solved their cell part exactly)
+// well column only (the red sweep solved their cell part exactly).  x0 (may be
+// null): also the multigrid's first red pass from a zero guess, x0 = b0 * d0
+// (d0 indexed by the red colour slot when d0_slot, else by the cell).
 template <typename T, typename VT>
 void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
-                       const VT* v, T w_o, T w_w, T* b0, int block, cudaStream_t st);
+                       const VT* v, T w_o, T w_w, T* b0, T* x0, const T* d0, int d0_slot, int block,
+                       cudaStream_t st);
 template <typename PT>
 void launch_bjacobi_apply(const Grid& g, int nw, const PT* Dinv, const PT* Dwinv, const double* r,
                           double* z, cudaStream_t st);

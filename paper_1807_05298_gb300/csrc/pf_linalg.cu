@@ -550,11 +550,16 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
 // blocks from the black compact copy when the sweeps read one (COMPACT; the
 // diagonal block always from J).  Threads [0, nq) take the black cells and
 // [nq, 2 nq) the red ones, so the black threads of a warp run together.
+// With x0 the red threads also do the multigrid cycle's first pass on the
+// finest pressure level, from its zero initial guess: x0 = b0 / a_ii (b0 times
+// the stored 1 / diagonal, d0[q] of the red per-colour copy when d0_slot,
+// else d0[i]).
 template <typename T, typename BT, bool COMPACT, typename VT>
 __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T* __restrict__ J,
                                                     const BT* __restrict__ Cb, const T* __restrict__ Bw,
                                                     const T* __restrict__ y, const VT* __restrict__ v, T w_o,
-                                                    T w_w, T* __restrict__ b0) {
+                                                    T w_w, T* __restrict__ b0, T* __restrict__ x0,
+                                                    const T* __restrict__ d0, int d0_slot) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * nq;
@@ -588,20 +593,24 @@ __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T*
       if (m >= 0) r -= (w_o * Bw[m] + w_w * Bw[w.npf + m]) * y[3 * n + w.pwell[m]];
     }
     b0[i] = r;
+    if (colour == 0 && x0) x0[i] = r * d0[d0_slot ? q : i];
   }
 }
 
 template <typename T, typename VT>
 void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompact& cp, const T* Bw, const T* y,
-                       const VT* v, T w_o, T w_w, T* b0, int block, cudaStream_t st) {
+                       const VT* v, T w_o, T w_w, T* b0, T* x0, const T* d0, int d0_slot, int block,
+                       cudaStream_t st) {
   const int grid = grid_for(2 * colour_slots_host(g), block);
   if (cp.kind == 1)
-    launch(k_stage2_ilu<T, T, true, VT>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0);
+    launch(k_stage2_ilu<T, T, true, VT>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0, x0,
+           d0, d0_slot);
   else if (cp.kind == 2)
     launch(k_stage2_ilu<T, __nv_bfloat16, true, VT>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.c[1], Bw,
-           y, v, w_o, w_w, b0);
+           y, v, w_o, w_w, b0, x0, d0, d0_slot);
   else
-    launch(k_stage2_ilu<T, T, false, VT>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0);
+    launch(k_stage2_ilu<T, T, false, VT>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0, x0,
+           d0, d0_slot);
 }
 
 template <typename PT>
@@ -902,10 +911,10 @@ template int launch_ilu_apply<float, float, double, double>(const Grid&, int, co
                                                             const IluCompact&, cudaStream_t);
 template void launch_stage2_ilu<double, double>(const Grid&, const Wells&, const double*, const IluCompact&,
                                                 const double*, const double*, const double*, double, double, double*,
-                                                int, cudaStream_t);
+                                                double*, const double*, int, int, cudaStream_t);
 template void launch_stage2_ilu<float, float>(const Grid&, const Wells&, const float*, const IluCompact&,
-                                              const float*, const float*, const float*, float, float, float*, int,
-                                              cudaStream_t);
+                                              const float*, const float*, const float*, float, float, float*, float*,
+                                              const float*, int, int, cudaStream_t);
 template void launch_bjacobi_apply<double>(const Grid&, int, const double*, const double*, const double*, double*,
                                            cudaStream_t);
 template void launch_bjacobi_apply<float>(const Grid&, int, const float*, const float*, const double*, double*,
