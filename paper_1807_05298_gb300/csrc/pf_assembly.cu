@@ -31,15 +31,24 @@ namespace pf {
 // cell properties and accumulation
 // ---------------------------------------------------------------------------
 
+// Values in FP64 (they build the residual); derivatives in the Jacobian's
+// type DT (FP64, or FP32 in mixed precision, where the derivative arithmetic
+// runs in FP32 from the FP64 values rounded once).
+template <typename DT>
 struct CellEval {
   double phi, rho_o, rho_w, Pw, krw, kro, Rk, mu_we, mu_pe, ads;
-  double dphi, drho_o, drho_wP, drho_wS, dPw_S, dkrw, dkro, dRk, dmu_we, dmu_pe, dads;
+  DT dphi, drho_o, drho_wP, drho_wS, dPw_S, dkrw, dkro, dRk, dmu_we, dmu_pe, dads;
 };
 
 __device__ __forceinline__ double powi_or_pow(double b, double e) {
   if (e == 2.0) return b * b;
   if (e == 1.0) return b;
   return pow(b, e);
+}
+__device__ __forceinline__ float powi_or_pow(float b, float e) {
+  if (e == 2.0f) return b * b;
+  if (e == 1.0f) return b;
+  return powf(b, e);
 }
 
 // Segment of a strictly increasing abscissa table: k with x[k] <= u < x[k+1],
@@ -69,18 +78,24 @@ __device__ __forceinline__ void table_eval(const double* __restrict__ T, int K, 
   d = sl;
 }
 
+template <typename DT>
 __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P, double S, double C,
-                                          CellEval& c) {
+                                          CellEval<DT>& c) {
   c.phi = phi_r + ph.c_r * (P - ph.p_r);
-  c.dphi = ph.c_r;
+  c.dphi = (DT)ph.c_r;
   c.rho_o = ph.rho_o * (1.0 + ph.c_o * (P - ph.p_ref));
-  c.drho_o = ph.rho_o * ph.c_o;
-  double pc = 0.0, dpc = 0.0;
+  c.drho_o = (DT)ph.rho_o * (DT)ph.c_o;
+  double pc = 0.0;
+  DT dpc = 0;
   if (ph.n_sat > 0) {  // tabulated k_rw, k_ro, P_c of S_w
     const int k = table_segment(ph.sat, ph.n_sat, S);
-    table_eval(ph.sat, ph.n_sat, 3, 1, k, S, c.krw, c.dkrw);
-    table_eval(ph.sat, ph.n_sat, 3, 2, k, S, c.kro, c.dkro);
-    table_eval(ph.sat, ph.n_sat, 3, 3, k, S, pc, dpc);
+    double d1, d2, d3;
+    table_eval(ph.sat, ph.n_sat, 3, 1, k, S, c.krw, d1);
+    table_eval(ph.sat, ph.n_sat, 3, 2, k, S, c.kro, d2);
+    table_eval(ph.sat, ph.n_sat, 3, 3, k, S, pc, d3);
+    c.dkrw = (DT)d1;
+    c.dkro = (DT)d2;
+    dpc = (DT)d3;
   } else {
     // normalised saturation, clipped; derivative of the interior formula on [0, 1]
     double sn = (S - ph.swc) * ph.inv_den, dsn = ph.inv_den;
@@ -88,70 +103,81 @@ __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P
     if (sn > 1.0) { sn = 1.0; dsn = 0.0; }
     const double so = 1.0 - sn;
     c.krw = ph.krw_max * powi_or_pow(sn, ph.nw);
-    c.dkrw = (sn == 0.0 && ph.nw > 1.0) ? 0.0 : ph.krw_max * ph.nw * powi_or_pow(sn, ph.nw - 1.0) * dsn;
+    c.dkrw = (sn == 0.0 && ph.nw > 1.0)
+                 ? (DT)0
+                 : (DT)ph.krw_max * (DT)ph.nw * powi_or_pow((DT)sn, (DT)(ph.nw - 1.0)) * (DT)dsn;
     c.kro = ph.kro_max * powi_or_pow(so, ph.no);
-    c.dkro = (so == 0.0 && ph.no > 1.0) ? 0.0 : -ph.kro_max * ph.no * powi_or_pow(so, ph.no - 1.0) * dsn;
+    c.dkro = (so == 0.0 && ph.no > 1.0)
+                 ? (DT)0
+                 : -(DT)ph.kro_max * (DT)ph.no * powi_or_pow((DT)so, (DT)(ph.no - 1.0)) * (DT)dsn;
     if (ph.pc_e != 0.0) {
       pc = ph.pc_e * powi_or_pow(so, ph.pc_n);
-      dpc = (so == 0.0 && ph.pc_n > 1.0) ? 0.0 : -ph.pc_e * ph.pc_n * powi_or_pow(so, ph.pc_n - 1.0) * dsn;
+      dpc = (so == 0.0 && ph.pc_n > 1.0)
+                ? (DT)0
+                : -(DT)ph.pc_e * (DT)ph.pc_n * powi_or_pow((DT)so, (DT)(ph.pc_n - 1.0)) * (DT)dsn;
     }
   }
   c.Pw = P - pc;
   c.dPw_S = -dpc;
   c.rho_w = ph.rho_w * (1.0 + ph.c_w * (c.Pw - ph.p_ref));
-  c.drho_wP = ph.rho_w * ph.c_w;
-  c.drho_wS = ph.rho_w * ph.c_w * c.dPw_S;
+  c.drho_wP = (DT)ph.rho_w * (DT)ph.c_w;
+  c.drho_wS = (DT)ph.rho_w * (DT)ph.c_w * c.dPw_S;
   const double beta = C * ph.inv_c_ref;
-  double mu_m, dmu_m;
+  double mu_m;
+  DT dmu_m;
   if (ph.n_poly > 0) {  // tabulated A_d(C) and water viscosity multiplier
     const int k = table_segment(ph.poly, ph.n_poly, C);
-    double mult, dmult;
+    double mult, dmult, dads;
     table_eval(ph.poly, ph.n_poly, 2, 1, k, C, mult, dmult);
-    table_eval(ph.poly, ph.n_poly, 2, 2, k, C, c.ads, c.dads);
+    table_eval(ph.poly, ph.n_poly, 2, 2, k, C, c.ads, dads);
+    c.dads = (DT)dads;
     mu_m = mult * ph.mu_w;
-    dmu_m = dmult * ph.mu_w;
+    dmu_m = (DT)dmult * (DT)ph.mu_w;
   } else {
     // Langmuir adsorption (one reciprocal: FP64 division is costly on this part)
     const double rden = 1.0 / (1.0 + ph.ads_b * C);
     c.ads = ph.ads_a * C * rden;
-    c.dads = ph.ads_a * rden * rden;
+    c.dads = (DT)ph.ads_a * (DT)rden * (DT)rden;
   }
   // permeability reduction
   c.Rk = 1.0 + ph.rk_coef * c.ads;
-  c.dRk = ph.rk_coef * c.dads;
+  c.dRk = (DT)ph.rk_coef * c.dads;
   // mixing rule (the table already gave mu_m)
   if (ph.n_poly > 0) {
     // mu_m, dmu_m from the viscosity multiplier above
   } else if (ph.mixing == PF_MIX_NONLINEAR) {
     mu_m = exp(ph.ln_mu_w + beta * ph.ln_mu_ratio);
-    dmu_m = mu_m * ph.ln_mu_ratio * ph.inv_c_ref;
+    dmu_m = (DT)mu_m * (DT)ph.ln_mu_ratio * (DT)ph.inv_c_ref;
   } else {
     mu_m = ph.mu_w + beta * (ph.mu_p0 - ph.mu_w);
-    dmu_m = (ph.mu_p0 - ph.mu_w) * ph.inv_c_ref;
+    dmu_m = (DT)(ph.mu_p0 - ph.mu_w) * (DT)ph.inv_c_ref;
   }
   // Todd-Longstaff effective viscosities
-  double alpha = beta, dalpha = ph.inv_c_ref;
-  if (alpha < 0.0) { alpha = 0.0; dalpha = 0.0; }
-  if (alpha > 1.0) { alpha = 1.0; dalpha = 0.0; }
+  double alpha = beta;
+  DT dalpha = (DT)ph.inv_c_ref;
+  if (alpha < 0.0) { alpha = 0.0; dalpha = 0; }
+  if (alpha > 1.0) { alpha = 1.0; dalpha = 0; }
   // 1/mu_w,e = alpha/mu_p,e + (1-alpha)/mu_w,partial, with one reciprocal per
   // viscosity (both are mu_m when omega = 1)
-  double mu_pe, dmu_pe, mu_wp, dmu_wp, rpe, rwp;
+  double mu_pe, mu_wp, rpe, rwp;
+  DT dmu_pe, dmu_wp;
   if (ph.omega == 1.0) {
     mu_pe = mu_m; dmu_pe = dmu_m; mu_wp = mu_m; dmu_wp = dmu_m;
     rpe = 1.0 / mu_m;
     rwp = rpe;
   } else {
     const double mo = pow(mu_m, ph.omega);
-    const double dmo = ph.omega * mo / mu_m * dmu_m;
-    mu_pe = mo * ph.mu_p0_pow; dmu_pe = dmo * ph.mu_p0_pow;
-    mu_wp = mo * ph.mu_w_pow; dmu_wp = dmo * ph.mu_w_pow;
+    const DT dmo = (DT)ph.omega * (DT)mo / (DT)mu_m * dmu_m;
+    mu_pe = mo * ph.mu_p0_pow; dmu_pe = dmo * (DT)ph.mu_p0_pow;
+    mu_wp = mo * ph.mu_w_pow; dmu_wp = dmo * (DT)ph.mu_w_pow;
     rpe = 1.0 / mu_pe;
     rwp = 1.0 / mu_wp;
   }
   const double inv = alpha * rpe + (1.0 - alpha) * rwp;
-  const double dinv = dalpha * rpe - alpha * dmu_pe * rpe * rpe - dalpha * rwp - (1.0 - alpha) * dmu_wp * rwp * rwp;
+  const DT a = (DT)alpha, p = (DT)rpe, w = (DT)rwp;
+  const DT dinv = dalpha * p - a * dmu_pe * p * p - dalpha * w - ((DT)1 - a) * dmu_wp * w * w;
   c.mu_we = 1.0 / inv;
-  c.dmu_we = -dinv * c.mu_we * c.mu_we;
+  c.dmu_we = -dinv * (DT)c.mu_we * (DT)c.mu_we;
   c.mu_pe = mu_pe;
   c.dmu_pe = dmu_pe;
 }
@@ -167,8 +193,8 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double P = x[3 * i], S = x[3 * i + 1], C = x[3 * i + 2];
-    CellEval c;
-    eval_cell(ph, phi_r[i], P, S, C, c);
+    CellEval<DT> c;
+    eval_cell<DT>(ph, phi_r[i], P, S, C, c);
     const double V = g.V;
     // accumulation masses (oil, water, polymer)
     const double Mo = V * c.phi * c.rho_o * (1.0 - S);
@@ -206,36 +232,39 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
     pv[PV_RK * n + i] = c.Rk;
     pv[PV_MUWE * n + i] = c.mu_we;
     pv[PV_MUPE * n + i] = c.mu_pe;
-    pd[PD_RHO_O * n + i] = (DT)c.drho_o;
-    pd[PD_RHO_WP * n + i] = (DT)c.drho_wP;
-    pd[PD_RHO_WS * n + i] = (DT)c.drho_wS;
-    pd[PD_PW_S * n + i] = (DT)c.dPw_S;
-    pd[PD_KRW * n + i] = (DT)c.dkrw;
-    pd[PD_KRO * n + i] = (DT)c.dkro;
-    pd[PD_RK * n + i] = (DT)c.dRk;
-    pd[PD_MUWE * n + i] = (DT)c.dmu_we;
-    pd[PD_MUPE * n + i] = (DT)c.dmu_pe;
+    pd[PD_RHO_O * n + i] = c.drho_o;
+    pd[PD_RHO_WP * n + i] = c.drho_wP;
+    pd[PD_RHO_WS * n + i] = c.drho_wS;
+    pd[PD_PW_S * n + i] = c.dPw_S;
+    pd[PD_KRW * n + i] = c.dkrw;
+    pd[PD_KRO * n + i] = c.dkro;
+    pd[PD_RK * n + i] = c.dRk;
+    pd[PD_MUWE * n + i] = c.dmu_we;
+    pd[PD_MUPE * n + i] = c.dmu_pe;
     R[3 * i] = Mo - Mold[3 * i];
     R[3 * i + 1] = Mw - Mold[3 * i + 1];
     R[3 * i + 2] = Mp - Mold[3 * i + 2];
     // d(M)/d(P, S, C): rows oil, water, polymer
     DT* Jd = J + (size_t)SL_D * 9 * n;
-    const double dMoP = V * (c.dphi * c.rho_o + c.phi * c.drho_o) * (1.0 - S);
-    const double dMoS = -V * c.phi * c.rho_o;
-    const double dMwP = V * (c.dphi * c.rho_w + c.phi * c.drho_wP) * S;
-    const double dMwS = V * c.phi * (c.drho_wS * S + c.rho_w);
-    const double dMpP = k1 * S * C * (c.dphi * c.rho_w + c.phi * c.drho_wP) - V * c.dphi * c.ads;
-    const double dMpS = k1 * C * c.phi * (c.rho_w + S * c.drho_wS);
-    const double dMpC = k1 * c.phi * S * c.rho_w + V * (1.0 - c.phi) * c.dads;
-    Jd[0 * n + i] = (DT)dMoP;
-    Jd[1 * n + i] = (DT)dMoS;
-    Jd[2 * n + i] = (DT)0.0;
-    Jd[3 * n + i] = (DT)dMwP;
-    Jd[4 * n + i] = (DT)dMwS;
-    Jd[5 * n + i] = (DT)0.0;
-    Jd[6 * n + i] = (DT)dMpP;
-    Jd[7 * n + i] = (DT)dMpS;
-    Jd[8 * n + i] = (DT)dMpC;
+    // in DT: the FP64 values rounded once, then the derivative arithmetic
+    const DT Vd = (DT)V, k1d = (DT)k1, Sd = (DT)S, Cd = (DT)C, phid = (DT)c.phi;
+    const DT rho_od = (DT)c.rho_o, rho_wd = (DT)c.rho_w, adsd = (DT)c.ads;
+    const DT dMoP = Vd * (c.dphi * rho_od + phid * c.drho_o) * ((DT)1 - Sd);
+    const DT dMoS = -Vd * phid * rho_od;
+    const DT dMwP = Vd * (c.dphi * rho_wd + phid * c.drho_wP) * Sd;
+    const DT dMwS = Vd * phid * (c.drho_wS * Sd + rho_wd);
+    const DT dMpP = k1d * Sd * Cd * (c.dphi * rho_wd + phid * c.drho_wP) - Vd * c.dphi * adsd;
+    const DT dMpS = k1d * Cd * phid * (rho_wd + Sd * c.drho_wS);
+    const DT dMpC = k1d * phid * Sd * rho_wd + Vd * ((DT)1 - phid) * c.dads;
+    Jd[0 * n + i] = dMoP;
+    Jd[1 * n + i] = dMoS;
+    Jd[2 * n + i] = (DT)0;
+    Jd[3 * n + i] = dMwP;
+    Jd[4 * n + i] = dMwS;
+    Jd[5 * n + i] = (DT)0;
+    Jd[6 * n + i] = dMpP;
+    Jd[7 * n + i] = dMpS;
+    Jd[8 * n + i] = dMpC;
   }
 }
 

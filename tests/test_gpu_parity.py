@@ -351,6 +351,58 @@ def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
     sampled_window_check(B, G.scenario_c3(n_steps=3), precision, 27)
 
 
+def test_full_size_27m_time_step_lands_on_the_oracle_root(B):
+    """600x450x100 (27M cells, 120 wells): one half-day time step from the
+    initial state under the benchmark's solver settings (CPR, forcing term,
+    Newton tolerance 1e-8 on the scaled residual), in mixed precision and in
+    FP64.  At 48 sampled interior cells away from the wells the oracle's
+    residual of the end state (assembled on the cell's 3x3x3 window, with the
+    initial state as x^n) is within the Newton tolerance in the oracle's own
+    scaled units, in both precisions; and the two end states agree to 1e-6 of
+    each field's max-norm."""
+    sc = G.scenario_c3(n_steps=1)
+    ctl = sc["schedule"][0]["controls"]
+    dt = 0.5 * DAY
+    tol = 1e-8
+    ends = {}
+    for precision in ("mixed", "fp64"):
+        prec = B.PF_PREC_MIXED if precision == "mixed" else B.PF_PREC_FP64
+        sim = B.Simulator(sc, stream=B.current_stream_handle(), precision=prec, precond=B.PF_PC_CPR, use_forcing=1,
+                          newton_tol=tol)
+        sim.set_controls(ctl)
+        x_old = sim.get_x()
+        rc, rep = sim.step(dt)
+        assert rc == B.PF_OK and rep.converged
+        ends[precision] = sim.get_x()
+        sim.close()
+    nx, ny, nz = sc["nx"], sc["ny"], sc["nz"]
+    n = nx * ny * nz
+    for a in range(3):
+        ref = np.abs(ends["fp64"][a:3 * n:3]).max()
+        assert np.abs(ends["mixed"][a:3 * n:3] - ends["fp64"][a:3 * n:3]).max() <= 1e-6 * ref
+    perf = perforated_cells(sc)
+    rng = np.random.default_rng(2727)
+    cells = []
+    while len(cells) < 48:
+        i, j, k = int(rng.integers(1, nx - 1)), int(rng.integers(1, ny - 1)), int(rng.integers(1, nz - 1))
+        c = i + nx * (j + ny * k)
+        if c not in perf and c not in cells:
+            cells.append(c)
+    ph = sc["physics"]
+    V = sc["dx"] * sc["dy"] * sc["dz"]
+    for precision, x in ends.items():
+        worst = 0.0
+        for c in cells:
+            w, idx = window_around(sc, c)
+            stw = M.Setup(w)
+            xw, xw_old = window_state(x, idx), window_state(x_old, idx)
+            Rw, _ = M.assemble(stw, xw, M.masses(stw, xw_old), dt, [], M.well_gamma(stw, xw_old, []),
+                               with_jacobian=False)
+            for a, ref in enumerate((ph["rho_o"], ph["rho_w"], ph["c_ref"])):
+                worst = max(worst, abs(Rw[3 * 13 + a]) / (V * sc["phi"][c] * ref))
+        assert worst <= 1.01 * tol, (precision, worst)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_paper_scale_sampled_cells_match_the_oracle(B, precision):
     """The paper's high-resolution grid, 951x1920x15 (27,388,800 cells, Sec.
