@@ -15,6 +15,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kMaxCoarse = 64;
+constexpr long long kTwoSlotCells = 1 << 20;  // levels from this size relax two cells per thread
 
 struct Dims {
   int nx, ny, nz;
@@ -183,9 +184,10 @@ __device__ __forceinline__ T relax_cell(const Dims& d, long long i, int cx, int 
       long long j;
       if (!nbr(d, cx, cy, cz, sl, j)) continue;
       T xj = x[j];
-      if (xc) {
-        int jx, jy, jz;
-        coords(d, j, jx, jy, jz);
+      if (xc) {  // the neighbour's coordinates follow from the slot (no division)
+        const int jx = cx + (sl == SL_XM ? -1 : sl == SL_XP ? 1 : 0);
+        const int jy = cy + (sl == SL_YM ? -1 : sl == SL_YP ? 1 : 0);
+        const int jz = cz + (sl == SL_ZM ? -1 : sl == SL_ZP ? 1 : 0);
         xj += xc[jx / fx + c.nx * (jy / fy + (long long)c.ny * (jz / fz))];
       }
       s = fnms(off(sl), xj, s);
@@ -204,7 +206,7 @@ __device__ __forceinline__ T relax_cell(const Dims& d, long long i, int cx, int 
 // this colour and writes the output of both (the other colour's value is
 // final), so no lane of a warp idles on the other colour; threads past the
 // pairs write the well rows of the mixed output.
-template <typename T, bool TOP>
+template <typename T, bool TOP, int CPT = 1>
 __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, const T* __restrict__ dinv,
                                               const T* __restrict__ b, T* __restrict__ x, int color, int zero_init,
                                               const T* __restrict__ xc, Dims c, TopOut top) {
@@ -213,12 +215,21 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
   const long long nq = rb_slots(d);
   const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
   if (!TOP) {
-    GSTRIDE(q, nq) {
-      int cx, cy, cz;
-      if (!slot_cell(d, hx, color, q, cx, cy, cz)) continue;
-      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
-      relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
-                    [&](int sl) { return A[(size_t)sl * d.n + i]; }, dinv[i]);
+    // CPT consecutive slots of a row per thread: one coordinate computation
+    const unsigned int hp = (hx + CPT - 1u) / CPT;  // slot groups per row
+    GSTRIDE(t, (long long)hp * d.ny * d.nz) {
+      const unsigned int ut = (unsigned int)t, row = ut / hp, m0 = CPT * (ut - row * hp);
+      const int cz = (int)(row / (unsigned int)d.ny), cy = (int)(row - (unsigned int)cz * (unsigned int)d.ny);
+      const int par = (int)(((unsigned int)(cy + cz + color)) & 1u);
+      const long long base = (long long)d.nx * row;
+#pragma unroll
+      for (int e = 0; e < CPT; ++e) {
+        const int cx = par + 2 * (int)(m0 + e);
+        if (m0 + e >= hx || cx >= d.nx) break;
+        const long long i = base + cx;
+        relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                      [&](int sl) { return A[(size_t)sl * d.n + i]; }, dinv[i]);
+      }
     }
   } else {
     GSTRIDE(p, nq + (top.mode == 2 ? top.nw : 0)) {
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(256) k_rb_compact(Dims d, const T* __restrict_
 // k_rbgs on the finest level reading this colour's copy cp (the same
 // arithmetic in the same order); the same thread mappings as k_rbgs.  In the
 // TOP pass the pair's cell of this colour has the pair's index as its slot.
-template <typename T, bool TOP>
+template <typename T, bool TOP, int CPT = 1>
 __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ cp, const T* __restrict__ b,
                                                  T* __restrict__ x, int color, int zero_init,
                                                  const T* __restrict__ xc, Dims c, TopOut top) {
@@ -274,12 +285,21 @@ __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ c
   const long long nq = rb_slots(d);
   const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
   if (!TOP) {
-    GSTRIDE(q, nq) {
-      int cx, cy, cz;
-      if (!slot_cell(d, hx, color, q, cx, cy, cz)) continue;
-      const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
-      relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
-                    [&](int sl) { return cp[(size_t)(sl - 1) * nq + q]; }, cp[(size_t)6 * nq + q]);
+    // CPT consecutive slots of a row per thread: one coordinate computation
+    const unsigned int hp = (hx + CPT - 1u) / CPT;  // slot groups per row
+    GSTRIDE(t, (long long)hp * d.ny * d.nz) {
+      const unsigned int ut = (unsigned int)t, row = ut / hp, m0 = CPT * (ut - row * hp);
+      const int cz = (int)(row / (unsigned int)d.ny), cy = (int)(row - (unsigned int)cz * (unsigned int)d.ny);
+      const int par = (int)(((unsigned int)(cy + cz + color)) & 1u);
+      const long long base = (long long)d.nx * row;
+#pragma unroll
+      for (int e = 0; e < CPT; ++e) {
+        const int cx = par + 2 * (int)(m0 + e);
+        if (m0 + e >= hx || cx >= d.nx) break;
+        const long long i = base + cx, q = (long long)row * hx + m0 + e;
+        relax_cell<T>(d, i, cx, cy, cz, b, x, zero_init, xc, c, fx, fy, fz,
+                      [&](int sl) { return cp[(size_t)(sl - 1) * nq + q]; }, cp[(size_t)6 * nq + q]);
+      }
     }
   } else {
     GSTRIDE(p, nq + (top.mode == 2 ? top.nw : 0)) {
@@ -705,16 +725,23 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
   const long long nq = ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
   auto pass = [&](int color, int zi, const T* xc, const Dims& dxc, const TopOut& to) {
     const bool wtop = to.mode != 0;
-    // every pass takes the colour slots (the output-writing pass: cell pairs, then the well rows)
-    const long long nt = nq + (wtop && to.mode == 2 ? to.nw : 0);
+    // the plain passes take one colour slot per thread, or from 1M cells two
+    // consecutive slots of a row (fewer coordinate computations; at smaller
+    // sizes the extra threads' parallelism counts for more: measured); the
+    // output-writing pass the colour slots (cell pairs), then the well rows
+    const bool two = L.n >= kTwoSlotCells;
+    const long long np = two ? (long long)((((L.nx + 1) / 2) + 1) / 2) * L.ny * L.nz : nq;
+    const long long nt = wtop ? nq + (to.mode == 2 ? to.nw : 0) : np;
     const int grid = grid_for(nt, bs);
     if (cp) {
       const T* cc = (const T*)c.rb_cp[color];
       if (wtop) launch(k_rbgs_cp<T, true>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
-      else launch(k_rbgs_cp<T, false>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
+      else if (two) launch(k_rbgs_cp<T, false, 2>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
+      else launch(k_rbgs_cp<T, false, 1>, grid, bs, 0, st, d, cc, b, x, color, zi, xc, dxc, to);
     } else {
       if (wtop) launch(k_rbgs<T, true>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
-      else launch(k_rbgs<T, false>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
+      else if (two) launch(k_rbgs<T, false, 2>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
+      else launch(k_rbgs<T, false, 1>, grid, bs, 0, st, d, A, dinv, b, x, color, zi, xc, dxc, to);
     }
   };
   for (int sweep = 0; sweep < npre; ++sweep) {
@@ -913,21 +940,28 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
 void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
   CprLevel& L = c.lev[0];
   const Dims d = dims_of(L);
-  const long long nq = ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
+  const bool two = L.n >= kTwoSlotCells;  // as in the cycle's plain passes
+  const long long np = two ? (long long)((((L.nx + 1) / 2) + 1) / 2) * L.ny * L.nz
+                           : ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
+  const int grid = grid_for(np, block);
   if (mixed) {
-    if (c.rb_cp[0])
-      launch(k_rbgs_cp<float, false>, grid_for(nq, block), block, 0, st, d, (const float*)c.rb_cp[0],
-             (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
-    else
-      launch(k_rbgs<float, false>, grid_for(nq, block), block, 0, st, d, (const float*)L.A, (const float*)L.dinv,
-             (const float*)L.b, (float*)L.x, 0, 0, (const float*)nullptr, Dims{}, TopOut{});
+    const float *cp = (const float*)c.rb_cp[0], *A = (const float*)L.A, *di = (const float*)L.dinv;
+    const float* b = (const float*)L.b;
+    float* x = (float*)L.x;
+    const float* none = nullptr;
+    if (cp) launch(two ? k_rbgs_cp<float, false, 2> : k_rbgs_cp<float, false, 1>, grid, block, 0, st, d, cp, b, x,
+                   0, 0, none, Dims{}, TopOut{});
+    else launch(two ? k_rbgs<float, false, 2> : k_rbgs<float, false, 1>, grid, block, 0, st, d, A, di, b, x, 0, 0,
+                none, Dims{}, TopOut{});
   } else {
-    if (c.rb_cp[0])
-      launch(k_rbgs_cp<double, false>, grid_for(nq, block), block, 0, st, d, (const double*)c.rb_cp[0],
-             (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
-    else
-      launch(k_rbgs<double, false>, grid_for(nq, block), block, 0, st, d, (const double*)L.A,
-             (const double*)L.dinv, (const double*)L.b, (double*)L.x, 0, 0, (const double*)nullptr, Dims{}, TopOut{});
+    const double *cp = (const double*)c.rb_cp[0], *A = (const double*)L.A, *di = (const double*)L.dinv;
+    const double* b = (const double*)L.b;
+    double* x = (double*)L.x;
+    const double* none = nullptr;
+    if (cp) launch(two ? k_rbgs_cp<double, false, 2> : k_rbgs_cp<double, false, 1>, grid, block, 0, st, d, cp, b,
+                   x, 0, 0, none, Dims{}, TopOut{});
+    else launch(two ? k_rbgs<double, false, 2> : k_rbgs<double, false, 1>, grid, block, 0, st, d, A, di, b, x, 0, 0,
+                none, Dims{}, TopOut{});
   }
 }
 
