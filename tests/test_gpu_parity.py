@@ -351,16 +351,14 @@ def test_full_size_27m_sampled_cells_match_the_oracle(B, precision):
     sampled_window_check(B, G.scenario_c3(n_steps=3), precision, 27)
 
 
-def test_full_size_27m_time_step_lands_on_the_oracle_root(B):
-    """600x450x100 (27M cells, 120 wells): one half-day time step from the
-    initial state under the benchmark's solver settings (CPR, forcing term,
-    Newton tolerance 1e-8 on the scaled residual), in mixed precision and in
-    FP64.  At 48 sampled interior cells away from the wells the oracle's
-    residual of the end state (assembled on the cell's 3x3x3 window, with the
-    initial state as x^n) is within the Newton tolerance in the oracle's own
-    scaled units, in both precisions; and the two end states agree to 1e-6 of
-    each field's max-norm."""
-    sc = G.scenario_c3(n_steps=1)
+def step_lands_on_oracle_root(B, sc, seed):
+    """One half-day time step from the initial state under the benchmark's
+    solver settings (CPR, forcing term, Newton tolerance 1e-8 on the scaled
+    residual), in mixed precision and in FP64.  At 48 sampled interior cells
+    away from the wells the oracle's residual of the end state (assembled on
+    the cell's 3x3x3 window, with the initial state as x^n) is within the
+    Newton tolerance in the oracle's own scaled units, in both precisions; and
+    the two end states agree to 1e-6 of each field's max-norm."""
     ctl = sc["schedule"][0]["controls"]
     dt = 0.5 * DAY
     tol = 1e-8
@@ -381,7 +379,7 @@ def test_full_size_27m_time_step_lands_on_the_oracle_root(B):
         ref = np.abs(ends["fp64"][a:3 * n:3]).max()
         assert np.abs(ends["mixed"][a:3 * n:3] - ends["fp64"][a:3 * n:3]).max() <= 1e-6 * ref
     perf = perforated_cells(sc)
-    rng = np.random.default_rng(2727)
+    rng = np.random.default_rng(seed)
     cells = []
     while len(cells) < 48:
         i, j, k = int(rng.integers(1, nx - 1)), int(rng.integers(1, ny - 1)), int(rng.integers(1, nz - 1))
@@ -401,6 +399,20 @@ def test_full_size_27m_time_step_lands_on_the_oracle_root(B):
             for a, ref in enumerate((ph["rho_o"], ph["rho_w"], ph["c_ref"])):
                 worst = max(worst, abs(Rw[3 * 13 + a]) / (V * sc["phi"][c] * ref))
         assert worst <= 1.01 * tol, (precision, worst)
+
+
+def test_full_size_27m_time_step_lands_on_the_oracle_root(B):
+    """600x450x100 (27M cells, 120 wells): see step_lands_on_oracle_root."""
+    step_lands_on_oracle_root(B, G.scenario_c3(n_steps=1), 2727)
+
+
+def test_odd_rows_1m_time_step_lands_on_the_oracle_root(B):
+    """201x105x50 (1,055,250 cells) of the channelised recipe: an odd number
+    of colour slots per row (101) on the levels from 1M cells, whose smoother
+    passes take two slots of a row per thread (the last thread of a row takes
+    one), and per-colour copies with ragged rows; see
+    step_lands_on_oracle_root."""
+    step_lands_on_oracle_root(B, G.scenario_c3(nx=201, ny=105, nz=50, n_steps=1), 1055)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
