@@ -164,7 +164,7 @@ SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 577.0e6,
 # 600x450x100 figures scale its bytes per cell by the cells); None where no
 # capture of the current kernels exists.
 PRECOND_TRAFFIC = {("c3", "fp64"): 1370.0 * 27_000_000, ("c3", "mixed"): 508.0 * 27_000_000,
-                   ("c3s", "fp64"): 2774.3e6, ("c3s", "mixed"): 1028.3e6}
+                   ("c3s", "fp64"): 2773.9e6, ("c3s", "mixed"): 1028.5e6}
 
 
 def max_over_ranks(values, dist, device="cpu"):

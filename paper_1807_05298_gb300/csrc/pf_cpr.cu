@@ -517,10 +517,13 @@ struct Team {
 template <typename T, bool CL>
 __device__ void b_rbgs(const Team<CL>& tm, const Dims& d, const T* A, const T* dinv, const T* b, T* x, int color,
                        bool zero_init) {
-  for (long long i = tm.tid; i < d.n; i += tm.stride) {
+  // the threads take the colour's slots, as in k_rbgs
+  const long long nq = rb_slots(d);
+  const unsigned int hx = ((unsigned int)d.nx + 1u) >> 1;
+  for (long long q = tm.tid; q < nq; q += tm.stride) {
     int cx, cy, cz;
-    coords(d, i, cx, cy, cz);
-    if (((cx + cy + cz) & 1) != color) continue;
+    if (!slot_cell(d, hx, color, q, cx, cy, cz)) continue;
+    const long long i = cx + (long long)d.nx * (cy + (long long)d.ny * cz);
     T s = b[i];
     if (!zero_init) {
       for (int sl = 1; sl < SL_COUNT; ++sl) {
