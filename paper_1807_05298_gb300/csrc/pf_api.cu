@@ -95,6 +95,7 @@ struct pf_sim {
   float* Zf = nullptr;  // mixed precision: FP32 copies of the preconditioned vectors
   float* Vf = nullptr;  // mixed precision: FP32 copy of the Krylov vector the preconditioner takes next
   double *V = nullptr, *Z = nullptr, *hbuf = nullptr, *partial = nullptr, *norms = nullptr, *ydev = nullptr;
+  double* vs = nullptr;  // [128] the Krylov basis vector j is vs[j] V_j (V_j is kept before normalisation)
   double* wtot = nullptr;  // [3 nw] well totals
   unsigned int* red_counter = nullptr;  // last-block reduction counter (zeroed)
   double* h_pinned = nullptr;
@@ -412,6 +413,7 @@ size_t carve(pf_sim* s, char* base) {
   s->partial = c.take<double>((size_t)s->nblocks * 72);
   s->norms = c.take<double>(4);
   s->ydev = c.take<double>(128);
+  s->vs = c.take<double>(128);
   s->wtot = c.take<double>(3 * (size_t)std::max(1, s->nw));
   s->red_counter = c.take<unsigned int>(64);
   {
@@ -564,18 +566,24 @@ pf_status dev_norm2(pf_sim* s, const double* a, double* out_host) {
   return PF_OK;
 }
 
-// b = f a; in mixed precision with CPR also the FP32 copy the preconditioner
-// takes (b is the first vector of a Krylov cycle)
-void scale_vec(pf_sim* s, const double* a, double f, double* b) {
-  launch_fill(1, f, s->norms + 3, s->stream);
-  launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, b, s->stream, precond_vf(s));
-  s->launches += 2;
+// The first basis vector of a Krylov cycle: V_0 = a (a copy; in mixed
+// precision with CPR also the FP32 copy the preconditioner takes) and its
+// normalisation vs[0] = 1 / |a|, given as inv_norm.
+void start_basis(pf_sim* s, const double* a, double inv_norm) {
+  launch_fill(1, 1.0, s->norms + 3, s->stream);
+  launch_scale_by_dev(s->nunk, a, s->norms + 3, 0, s->V, s->stream, precond_vf(s));
+  launch_fill(1, inv_norm, s->vs, s->stream);
+  s->launches += 3;
 }
 
-// Work of Arnoldi step j, in three pieces: z_j = M^{-1} v_j; w = J z_j into
-// v_{j+1}; two classical Gram-Schmidt passes against v_0..v_j (fused), the
-// normalisation of v_{j+1} by its device-side norm and the copy of the
-// Hessenberg column to pinned host memory.
+// Work of Arnoldi step j, in three pieces: z_j = M^{-1} V_j; w = J z_j into
+// V_{j+1}; two classical Gram-Schmidt passes against v_0..v_j (fused) and the
+// copy of the Hessenberg column to pinned host memory.  The basis is kept
+// before normalisation: V_j holds the orthogonalised vector and vs[j] = 1 /
+// |V_j|, so v_j = vs[j] V_j.  The dot products and the projection carry vs[j]
+// (one multiply per basis vector), and the preconditioner takes V_j itself:
+// with z_j = M^{-1} V_j the flexible Arnoldi relation J z_j = sum_i h_ij v_i
+// holds as before, and no pass over the vector normalises it.
 pf_status piece_pre(pf_sim* s, int j) {
   return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld,
                        s->mixed ? s->Zf + (size_t)j * s->ld : nullptr, precond_vf(s));
@@ -596,20 +604,21 @@ pf_status piece_ortho(pf_sim* s, int j) {
   double* w = s->V + (size_t)(j + 1) * ld;
   cudaStream_t st = s->stream;
   KtScope t(s, PF_KT_ORTHO);
-  // pass 1: hbuf[0..k) = V^T w and hbuf[k] = |w|^2; w -= V h1 with |w|^2 and
-  // 1/|w| at hbuf[256..257] and the reorthogonalisation flag at hbuf+384.
-  // pass 2 runs only if flagged: hbuf[128..128+k) = V^T w, w -= V h2, and it
-  // overwrites hbuf[256..257].
+  // pass 1: hbuf[0..k) = (vs[i] <V_i, w>) and hbuf[k] = |w|^2; w -= sum_i
+  // h1[i] vs[i] V_i with |w|^2 and 1/|w| at hbuf[256..257] (and 1/|w| into
+  // vs[j+1]) and the reorthogonalisation flag at hbuf+384.  pass 2 runs only
+  // if flagged: hbuf[128..128+k) the same dots, w -= the same projection, and
+  // it overwrites hbuf[256..257] and vs[j+1].
   const double eta2 = s->opts.reorth_eta * s->opts.reorth_eta;
   int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
-  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr);
+  float* wf = precond_vf(s);  // the FP32 copy of V_{j+1} for the next step's preconditioner (mixed CPR)
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr, s->vs);
   launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, s->hbuf + k,
-                   reorth, nullptr, st, eta2);
-  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth);
+                   reorth, nullptr, st, eta2, s->vs, wf, s->vs + j + 1);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth, s->vs);
   launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
-                   nullptr, reorth, st);
-  launch_scale_by_dev(n, w, s->hbuf + 257, 0, w, st, precond_vf(s));  // v_{j+1} (and its FP32 copy)
-  PF_LAUNCHED(5);
+                   nullptr, reorth, st, 0.5, s->vs, wf, s->vs + j + 1);
+  PF_LAUNCHED(4);
   PF_CUDA(cudaMemcpyAsync(s->h_pinned + kPinStep + (j & 1) * kPinStepStride, s->hbuf, (3 * 128 + 1) * sizeof(double),
                           cudaMemcpyDeviceToHost, st));
   return PF_OK;
@@ -712,7 +721,7 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
   bool converged = false;
   bool first = true;
   while (total < maxit && !converged) {
-    scale_vec(s, first ? bvec : s->r, 1.0 / beta, s->V);  // the first cycle's residual is b itself
+    start_basis(s, first ? bvec : s->r, 1.0 / beta);  // the first cycle's residual is b itself
     first = false;
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;

@@ -194,15 +194,20 @@ void launch_sub(long long n, const double* a, const double* b, double* c, cudaSt
 // reduces them in a fixed order (deterministic) and re-arms `counter` (a
 // zeroed device word shared by the reductions of one stream).  run_if (may
 // be null): skip the whole kernel unless *run_if.
+// vs (may be null): V_j holds the basis vector before its normalisation, the
+// basis vector is vs[j] V_j, and out[j] = vs[j] <V_j, w>.
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w,
                      double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st,
-                     int self_dot = 0, const int* run_if = nullptr);
+                     int self_dot = 0, const int* run_if = nullptr, const double* vs = nullptr);
 // w -= sum_j V[j] h[j]; out[0] = |w|^2, out[1] = 1/|w|; *decide = 1 if
 // |w|^2 < norm0[0] / 2 (a second Gram-Schmidt pass is needed)
+// vs as in launch_multidot; wf (may be null) gets an FP32 copy of the new w;
+// vs_next (may be null) gets 1 / |w|, the normalisation of w as the next
+// basis vector.
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w,
                       double* partial, int nblocks, double* out, unsigned int* counter, const double* norm0,
                       int* decide, const int* run_if, cudaStream_t st,
-                      double eta2 = 0.5);
+                      double eta2 = 0.5, const double* vs = nullptr, float* wf = nullptr, double* vs_next = nullptr);
 void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float* Bw, const float* Cw,
                      const float* Dw, const float* x, double* y, cudaStream_t st, int block = 256);
 // x += sum_j Z[j] y[j]

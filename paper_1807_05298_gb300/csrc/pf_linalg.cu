@@ -728,9 +728,11 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[KM], int k, dou
 // The last block to finish sums the per-block rows in a fixed order (one warp
 // per value, lanes over blocks, then a shuffle tree), so the result does not
 // depend on which block came last; it then re-arms the counter.
+// scale (may be null): out[j] *= scale[j] for the first nscaled values.
 __device__ __forceinline__ void last_block_reduce(const double* partial, int stride, int k, double* out,
                                                   unsigned int* counter, bool inv_norm = false,
-                                                  const double* norm0 = nullptr, int* decide = nullptr) {
+                                                  const double* norm0 = nullptr, int* decide = nullptr,
+                                                  const double* scale = nullptr, int nscaled = 0) {
   __shared__ bool last;
   __threadfence();  // every thread that wrote a partial publishes it before the count
   __syncthreads();
@@ -746,7 +748,7 @@ __device__ __forceinline__ void last_block_reduce(const double* partial, int str
     double s = lane_sum_blocks(partial + j, stride, (int)gridDim.x, lane);
     s = wsum(s);
     if (lane == 0) {
-      out[j] = s;
+      out[j] = (scale && j < nscaled) ? s * scale[j] : s;
       // out[k] = 1 / sqrt(last value): one FP64 sqrt and divide for the whole
       // vector instead of one per thread of the scaling kernel
       if (inv_norm && j == k - 1) out[k] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
@@ -795,13 +797,15 @@ __device__ __forceinline__ void md_dispatch(int nt, long long n, const double* V
   }
 }
 
-// out[j] = <V_j, w> for j < k and, with self_dot, out[k] = <w, w>; columns in
-// tiles of up to 8 (few registers, high occupancy), w re-read per tile.
-// run_if (may be null): the kernel returns at once unless *run_if is set.
+// out[j] = <V_j, w> for j < k (times vs[j] when vs is given: V_j then holds
+// the basis vector before its normalisation by vs[j]) and, with self_dot,
+// out[k] = <w, w>; columns in tiles of up to 8 (few registers, high
+// occupancy), w re-read per tile.  run_if (may be null): the kernel returns at
+// once unless *run_if is set.
 __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const double* __restrict__ V, long long ld,
                                                   const double* __restrict__ w, double* __restrict__ partial,
                                                   int stride, double* __restrict__ out, unsigned int* counter,
-                                                  int self_dot, const int* run_if) {
+                                                  int self_dot, const int* run_if, const double* __restrict__ vs) {
   PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   double* row = partial + (size_t)blockIdx.x * stride;
@@ -810,28 +814,33 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
   const int nt = k - j0;  // 0..8 columns left
   if (self_dot) md_dispatch<true>(nt, n, V, ld, w, j0, row);
   else if (nt > 0) md_dispatch<false>(nt, n, V, ld, w, j0, row);
-  last_block_reduce(partial, stride, k + (self_dot ? 1 : 0), out, counter);
+  last_block_reduce(partial, stride, k + (self_dot ? 1 : 0), out, counter, false, nullptr, nullptr, vs, k);
 }
 
-// w -= sum_{j<k} V_j h[j], then out[0] = |w|^2 and out[1] = 1 / |w|.  With
-// norm0 and decide: *decide = 1 when |w_new|^2 < eta2 |w_old|^2, i.e. when
-// the first pass cancelled so much of w that a second Gram-Schmidt pass is
-// needed ("twice is enough").  run_if as in k_multidot.
+// w -= sum_{j<k} v_j h[j] with v_j = vs[j] V_j (vs null: v_j = V_j), then
+// out[0] = |w|^2 and out[1] = 1 / |w| (also into *vs_next when given: w is
+// kept as the next basis vector before its normalisation).  wf (may be null):
+// an FP32 copy of the new w.  With norm0 and decide: *decide = 1 when
+// |w_new|^2 < eta2 |w_old|^2, i.e. when the first pass cancelled so much of w
+// that a second Gram-Schmidt pass is needed ("twice is enough").  run_if as in
+// k_multidot.
 __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const double* __restrict__ V, long long ld,
                                                    const double* __restrict__ h, double* __restrict__ w,
                                                    double* __restrict__ partial, int stride, double* __restrict__ out,
                                                    unsigned int* counter, const double* norm0, int* decide,
-                                                   const int* run_if, double eta2) {
+                                                   const int* run_if, double eta2, const double* __restrict__ vs,
+                                                   float* __restrict__ wf, double* __restrict__ vs_next) {
   PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   __shared__ double hs[128];
-  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = vs ? h[j] * vs[j] : h[j];
   __syncthreads();
   double acc[1] = {0.0};
   GRID_STRIDE(i, n) {
     double wi = w[i];
     for (int j = 0; j < k; ++j) wi -= V[(size_t)j * ld + i] * hs[j];
     w[i] = wi;
+    if (wf) wf[i] = (float)wi;
     acc[0] += wi * wi;
   }
   block_reduce_write<1>(acc, 1, partial + (size_t)blockIdx.x * stride);
@@ -848,6 +857,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
     if (threadIdx.x == 0) {
       out[0] = sum;
       out[1] = sum > 0.0 ? 1.0 / sqrt(sum) : 0.0;
+      if (vs_next) *vs_next = out[1];
       if (decide) *decide = (sum < eta2 * norm0[0]) ? 1 : 0;
       *counter = 0u;
     }
@@ -855,14 +865,17 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
 }
 
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
-                     double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if) {
-  launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if);
+                     double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if,
+                     const double* vs) {
+  launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if, vs);
 }
 
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w, double* partial,
                       int nblocks, double* out, unsigned int* counter, const double* norm0, int* decide,
-                      const int* run_if, cudaStream_t st, double eta2) {
-  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if, eta2);
+                      const int* run_if, cudaStream_t st, double eta2, const double* vs, float* wf,
+                      double* vs_next) {
+  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if, eta2,
+         vs, wf, vs_next);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
@@ -885,7 +898,8 @@ void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, co
 
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
                 unsigned int* counter, cudaStream_t st) {
-  launch(k_multidot, nblocks, 256, 0, st, n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr);
+  launch(k_multidot, nblocks, 256, 0, st, n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr,
+         (const double*)nullptr);
 }
 
 // explicit instantiations
