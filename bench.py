@@ -154,11 +154,9 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per SpMV launch from
-# the ncu captures summarised in profiles/ (current kernels: the FP64 row-split
-# SpMV at 100k cells, the FP32 SpMV at 2M cells); the 27M-cell figure is the
-# 2M-cell capture scaled by the number of 3x3 blocks (traffic grows with them).
-SPMV_TRAFFIC = {("c2", "fp64"): 51.67e6, ("c3s", "mixed"): 577.0e6,
-                ("c3", "mixed"): 577.0e6 * 188250000 / 14008500}
+# the ncu captures summarised in profiles/; the 27M-cell figures are the 2M-cell
+# captures scaled by the number of 3x3 blocks (traffic grows with them).
+SPMV_TRAFFIC = {}
 # DRAM traffic per CPR-FP preconditioner apply (summed over the apply's
 # kernels) from the ncu captures summarised in profiles/ (300x225x30; the
 # 600x450x100 figures scale its bytes per cell by the cells); None where no
@@ -177,11 +175,24 @@ def max_over_ranks(values, dist, device="cpu"):
     return [float(v) for v in t.cpu()]
 
 
+# Values of a 3x3 Jacobian block the SpMV needs: the oil row's polymer column is
+# zero by the model's structure (no oil term depends on C), so 8 of the 9.
+BLOCK_VALUES = 8
+
+
 def spmv_bytes(blocks, ncell, npf, nw, jbytes, xbytes):
-    """Algorithmic bytes of one SpMV launch: the 3x3 blocks of J (9 values of
-    jbytes each), the vector read (xbytes per unknown) and the FP64 result
-    written, the well border (B and C per perforation, D per well)."""
-    return blocks * 9 * jbytes + 3 * ncell * (xbytes + 8) + npf * 3 * 2 * jbytes + nw * jbytes
+    """Algorithmic bytes of one SpMV launch: the 3x3 blocks of J (the 8 values
+    that are not structurally zero, jbytes each), the vector read (xbytes per
+    unknown) and the FP64 result written, the well border (B and C per
+    perforation, D per well)."""
+    return blocks * BLOCK_VALUES * jbytes + 3 * ncell * (xbytes + 8) + npf * 3 * 2 * jbytes + nw * jbytes
+
+
+def spmv_flops(blocks, npf, nw):
+    """Algorithmic flops of one SpMV launch: one multiply-add (2 flops) per
+    nonzero block value, the well border's column (3 per perforation) and row
+    (3 per perforation) and its diagonal."""
+    return blocks * 2 * BLOCK_VALUES + npf * 12 + nw * 2
 
 
 def assembly_bytes(ncell, jbytes):
@@ -360,7 +371,7 @@ def spmv_roofline(kt, sc, sim, precision, hbm_peak, hbm_kind, workload):
     jbytes = 4 if mixed else 8
     xbytes = 4 if mixed else 8      # J x with the FP64 vector, or its FP32 copy in mixed precision
     nbytes = spmv_bytes(blocks, ncell, sim.npf, sim.nw, jbytes, xbytes)
-    flops = blocks * 18 + sim.npf * 12 + sim.nw * 2
+    flops = spmv_flops(blocks, sim.npf, sim.nw)
     cnt, ms = kt["spmv"]
     if cnt == 0:
         return None

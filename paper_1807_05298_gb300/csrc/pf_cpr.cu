@@ -852,7 +852,7 @@ __global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __r
       if (!has) continue;
       const T* B = J + (size_t)s * 9 * n + i;
       const T x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-      t0 = fma3(B[0], B[n], B[2 * n], x0, x1, x2, t0);
+      t0 = fma2(B[0], B[n], x0, x1, t0);  // oil row: no polymer column
       t1 = fma3(B[3 * n], B[4 * n], B[5 * n], x0, x1, x2, t1);
     }
     T r = w_o * ((T)v[3 * i] - t0) + w_w * ((T)v[3 * i + 1] - t1);

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 4) k_spmv_cells(Grid g, Wells w, const DT
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + (size_t)s * 9 * n + i;
       const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc0 = fma3((double)B[0], (double)B[n], (double)B[2 * n], x0, x1, x2, acc0);
+      acc0 = fma2((double)B[0], (double)B[n], x0, x1, acc0);  // oil row: no polymer column
       acc1 = fma3((double)B[3 * n], (double)B[4 * n], (double)B[5 * n], x0, x1, x2, acc1);
       acc2 = fma3((double)B[6 * n], (double)B[7 * n], (double)B[8 * n], x0, x1, x2, acc2);
     }
@@ -134,8 +134,12 @@ __global__ void __launch_bounds__(384, 2) k_spmv_rows(Grid g, Wells w, const DT*
       long long c;
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const DT* B = J + ((size_t)s * 9 + 3 * r) * n + i;
-      const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc = fma3((double)B[0], (double)B[n], (double)B[2 * n], x0, x1, x2, acc);
+      const double x0 = x[3 * c], x1 = x[3 * c + 1];
+      if (r == 0) {  // oil row: no polymer column (r is the same for the whole warp)
+        acc = fma2((double)B[0], (double)B[n], x0, x1, acc);
+      } else {
+        acc = fma3((double)B[0], (double)B[n], (double)B[2 * n], x0, x1, x[3 * c + 2], acc);
+      }
     }
     if (w.nw > 0) {
       const int m = w.perf_of[i];
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256, 4) k_spmv_cells_f32(Grid g, Wells w, cons
       if (!stencil_nbr(g, s, i, ii, j, k, c)) continue;
       const float* B = J + (size_t)s * 9 * n + i;
       const float x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      acc0 = fma3(B[0], B[n], B[2 * n], x0, x1, x2, acc0);
+      acc0 = fma2(B[0], B[n], x0, x1, acc0);  // oil row: no polymer column
       acc1 = fma3(B[3 * n], B[4 * n], B[5 * n], x0, x1, x2, acc1);
       acc2 = fma3(B[6 * n], B[7 * n], B[8 * n], x0, x1, x2, acc2);
     }
@@ -355,22 +359,34 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       long long c;
       if (!slot_nbr(g, s, i, x, y, z, c)) continue;
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
-      PT T[9];  // J_bj D_j^-1
+      PT T[9];  // J_bj D_j^-1 (the oil row of J_bj has no polymer column: fma2)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const PT b0 = (PT)J[((size_t)s * 9 + 3 * r) * n + i], b1 = (PT)J[((size_t)s * 9 + 3 * r + 1) * n + i],
-                 b2 = (PT)J[((size_t)s * 9 + 3 * r + 2) * n + i];
+        const PT b0 = (PT)J[((size_t)s * 9 + 3 * r) * n + i], b1 = (PT)J[((size_t)s * 9 + 3 * r + 1) * n + i];
 #pragma unroll
-        for (int col = 0; col < 3; ++col)
-          T[3 * r + col] = b0 * Dinv[(size_t)col * n + c] + b1 * Dinv[(size_t)(3 + col) * n + c] +
-                           b2 * Dinv[(size_t)(6 + col) * n + c];
+        for (int col = 0; col < 3; ++col) {
+          const PT d0 = Dinv[(size_t)col * n + c], d1 = Dinv[(size_t)(3 + col) * n + c];
+          if (r == 0) {
+            T[col] = fma2(b0, b1, d0, d1, (PT)0);
+          } else {
+            const PT b2 = (PT)J[((size_t)s * 9 + 3 * r + 2) * n + i];
+            T[3 * r + col] = fma3(b0, b1, b2, d0, d1, Dinv[(size_t)(6 + col) * n + c], (PT)0);
+          }
+        }
       }
 #pragma unroll
       for (int col = 0; col < 3; ++col) {
-        const PT u0 = (PT)J[((size_t)so * 9 + col) * n + c], u1 = (PT)J[((size_t)so * 9 + 3 + col) * n + c],
-                 u2 = (PT)J[((size_t)so * 9 + 6 + col) * n + c];
+        // column col of J_jb; its oil-row entry is zero in the polymer column
+        const PT u1 = (PT)J[((size_t)so * 9 + 3 + col) * n + c], u2 = (PT)J[((size_t)so * 9 + 6 + col) * n + c];
+        if (col == 2) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) a[3 * r + col] = fnms3(T[3 * r], T[3 * r + 1], T[3 * r + 2], u0, u1, u2, a[3 * r + col]);
+          for (int r = 0; r < 3; ++r) a[3 * r + col] = fnms2(T[3 * r + 1], T[3 * r + 2], u1, u2, a[3 * r + col]);
+        } else {
+          const PT u0 = (PT)J[((size_t)so * 9 + col) * n + c];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            a[3 * r + col] = fnms3(T[3 * r], T[3 * r + 1], T[3 * r + 2], u0, u1, u2, a[3 * r + col]);
+        }
       }
     }
     // pivot guard: det(D'_b) / det(D_b) = det(I - D_b^-1 S) measures how much
@@ -465,7 +481,7 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
       const BT* B = COMPACT ? J + (size_t)(s - 1) * 9 * nq + q : J + (size_t)s * 9 * n + i;
       const long long m = COMPACT ? nq : n;
       const PT pz{};
-      r0 = fnms3(as_pt(B[0], pz), as_pt(B[m], pz), as_pt(B[2 * m], pz), t0, t1, t2, r0);
+      r0 = fnms2(as_pt(B[0], pz), as_pt(B[m], pz), t0, t1, r0);  // oil row: no polymer column
       r1 = fnms3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), t0, t1, t2, r1);
       r2 = fnms3(as_pt(B[6 * m], pz), as_pt(B[7 * m], pz), as_pt(B[8 * m], pz), t0, t1, t2, r2);
     }
@@ -573,7 +589,7 @@ __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T*
     if (colour == 1) {
       const T* D = J + i;
       const T d0 = y[3 * i], d1 = y[3 * i + 1], d2 = y[3 * i + 2];
-      T t0 = fma3(D[0], D[n], D[2 * n], d0, d1, d2, (T)0);
+      T t0 = fma2(D[0], D[n], d0, d1, (T)0);  // oil row: no polymer column
       T t1 = fma3(D[3 * n], D[4 * n], D[5 * n], d0, d1, d2, (T)0);
       const T pz{};
 #pragma unroll
@@ -583,7 +599,7 @@ __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T*
         const BT* B = COMPACT ? Cb + (size_t)(s - 1) * 9 * nq + q : (const BT*)J + (size_t)s * 9 * n + i;
         const long long m = COMPACT ? nq : n;
         const T x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-        t0 = fma3(as_pt(B[0], pz), as_pt(B[m], pz), as_pt(B[2 * m], pz), x0, x1, x2, t0);
+        t0 = fma2(as_pt(B[0], pz), as_pt(B[m], pz), x0, x1, t0);
         t1 = fma3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), x0, x1, x2, t1);
       }
       r = w_o * ((T)v[3 * i] - t0) + w_w * ((T)v[3 * i + 1] - t1);

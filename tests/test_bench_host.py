@@ -23,11 +23,14 @@ def test_block_and_face_counts_of_the_benchmark_grids(bench):
 
 def test_algorithmic_bytes_of_the_benchmark_grids(bench):
     blocks, ncell, _ = bench.spmv_algorithmic({"nx": 100, "ny": 100, "nz": 10}, 50)
-    # FP64: 676,000 blocks x 72 B + 300,000 unknowns x (8 B read + 8 B written)
+    # FP64: 676,000 blocks x 8 values x 8 B (the oil row's polymer column is
+    # structurally zero) + 300,000 unknowns x (8 B read + 8 B written)
     # + 50 perforations x 3 x 2 x 8 B (B and C border) + 5 wells x 8 B (D)
-    assert bench.spmv_bytes(blocks, ncell, 50, 5, 8, 8) == 48_672_000 + 4_800_000 + 2_400 + 40
+    assert bench.spmv_bytes(blocks, ncell, 50, 5, 8, 8) == 43_264_000 + 4_800_000 + 2_400 + 40
     # mixed: FP32 blocks and FP32 vector copy, FP64 result
-    assert bench.spmv_bytes(blocks, ncell, 50, 5, 4, 4) == 24_336_000 + 3_600_000 + 1_200 + 20
+    assert bench.spmv_bytes(blocks, ncell, 50, 5, 4, 4) == 21_632_000 + 3_600_000 + 1_200 + 20
+    # 16 flops per block (8 multiply-adds) + 12 per perforation + 2 per well
+    assert bench.spmv_flops(blocks, 50, 5) == 10_816_000 + 600 + 10
     # assembly: 632 B per cell in FP64, 380 B in mixed precision
     assert bench.assembly_bytes(ncell, 8) == 63_200_000
     assert bench.assembly_bytes(27_000_000, 4) == 10_260_000_000

@@ -122,7 +122,11 @@ def test_assembly_matches_oracle(B, pi):
     st, sim, R_o, J_o, R_g, J_g = assemble_both(B, sc, ctl, x_old, x, dt)
     assert residual_error(st, R_g, R_o, dt, ctl) <= 1e-11
     assert rel_matrix_error(J_g, J_o) <= 1e-11
-    # SpMV with the assembled Jacobian (row 8a of the hot path)
+    # the oil row's polymer column of every block is exactly zero (the block
+    # products skip it; the oracle pins the same structure)
+    Jc = sim.export_system()[1]          # [slot][entry][cell]; entry 2 = oil row, polymer column
+    assert not np.any(Jc[:, 2, :])
+    # SpMV with the assembled Jacobian
     v = rng.normal(size=st.nunk) * np.tile([1e5, 0.1, 0.5], st.n + 1)[:st.nunk]
     y_g = sim.apply_jacobian(v)
     y_o = J_o @ v
