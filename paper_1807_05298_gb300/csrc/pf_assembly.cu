@@ -352,8 +352,10 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const double mu_we = wL * a.mu_we + wH * b.mu_we;
   const double mu_pe = wL * a.mu_pe + wH * b.mu_pe;
   const double A = rho_w * dPw;
-  // two FP64 divisions per face; 1/mu and 1/R_k follow by multiplication
-  const double irw = 1.0 / (Rk * mu_we), irp = 1.0 / (Rk * mu_pe);
+  // two FP64 divisions per face, one when the two effective viscosities are
+  // equal (omega = 1: mu_w,e = mu_p,e = mu_m); 1/mu and 1/R_k follow by
+  // multiplication
+  const double irw = 1.0 / (Rk * mu_we), irp = mu_pe == mu_we ? irw : 1.0 / (Rk * mu_pe);
   const double inv_mu_we = Rk * irw, inv_mu_pe = Rk * irp, inv_Rk = mu_we * irw;
   const double mw = krw * irw;
   const double mp = krw * irp;

@@ -338,11 +338,25 @@ __device__ __forceinline__ bool slot_nbr(const Grid& g, int s, long long i, int 
   }
 }
 
+// storage conversions of the compact per-colour block copies (CT: the
+// Jacobian's own type, or BF16)
+__device__ __forceinline__ float to_ct(float v, float) { return v; }
+__device__ __forceinline__ double to_ct(double v, double) { return v; }
+__device__ __forceinline__ __nv_bfloat16 to_ct(float v, __nv_bfloat16) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return __float2bfloat16_rn((float)v); }
+
 // black diagonal blocks: D'_b = D_b - sum_j J_bj D_j^-1 J_jb, then inverted;
-// the red blocks' inverses (from k_bjacobi_setup) are read, not written
-template <typename DT, typename PT>
+// the red blocks' inverses (from k_bjacobi_setup) are read, not written.
+// With cred and cblack (the compact per-colour copies of the off-diagonal
+// blocks; null for none) the kernel also writes the copies: a black cell's own
+// six blocks into cblack, and each red neighbour's block that points back at it
+// into cred (every red block points at exactly one black cell, so each is
+// written once; blocks that leave the grid are never read).  It reads all of
+// them for the Schur update anyway.  The oil row's polymer column is skipped
+// (structurally zero, never read).
+template <typename DT, typename PT, typename CT>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
-                                                          PT guard) {
+                                                          PT guard, CT* __restrict__ cred, CT* __restrict__ cblack) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -359,30 +373,53 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       long long c;
       if (!slot_nbr(g, s, i, x, y, z, c)) continue;
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
+      // the red neighbour's colour slot (for its compact copy)
+      const int cx = x + (s == SL_XM ? -1 : s == SL_XP ? 1 : 0), cy = y + (s == SL_YM ? -1 : s == SL_YP ? 1 : 0),
+                cz = z + (s == SL_ZM ? -1 : s == SL_ZP ? 1 : 0);
+      const long long qc = ((long long)cy + (long long)g.ny * cz) * ((g.nx + 1) / 2) + (cx >> 1);
+      CT* bl = cblack ? cblack + (size_t)(s - 1) * 9 * nq + q : nullptr;
+      CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
+      const CT zc{};
       PT T[9];  // J_bj D_j^-1 (the oil row of J_bj has no polymer column: fma2)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const PT b0 = (PT)J[((size_t)s * 9 + 3 * r) * n + i], b1 = (PT)J[((size_t)s * 9 + 3 * r + 1) * n + i];
+        const DT b0r = J[((size_t)s * 9 + 3 * r) * n + i], b1r = J[((size_t)s * 9 + 3 * r + 1) * n + i];
+        const PT b0 = (PT)b0r, b1 = (PT)b1r;
+        if (bl) {
+          bl[(size_t)(3 * r) * nq] = to_ct(b0r, zc);
+          bl[(size_t)(3 * r + 1) * nq] = to_ct(b1r, zc);
+        }
+        DT b2r = 0;
+        if (r != 0) {
+          b2r = J[((size_t)s * 9 + 3 * r + 2) * n + i];
+          if (bl) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
+        }
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
           const PT d0 = Dinv[(size_t)col * n + c], d1 = Dinv[(size_t)(3 + col) * n + c];
           if (r == 0) {
             T[col] = fma2(b0, b1, d0, d1, (PT)0);
           } else {
-            const PT b2 = (PT)J[((size_t)s * 9 + 3 * r + 2) * n + i];
-            T[3 * r + col] = fma3(b0, b1, b2, d0, d1, Dinv[(size_t)(6 + col) * n + c], (PT)0);
+            T[3 * r + col] = fma3(b0, b1, (PT)b2r, d0, d1, Dinv[(size_t)(6 + col) * n + c], (PT)0);
           }
         }
       }
 #pragma unroll
       for (int col = 0; col < 3; ++col) {
         // column col of J_jb; its oil-row entry is zero in the polymer column
-        const PT u1 = (PT)J[((size_t)so * 9 + 3 + col) * n + c], u2 = (PT)J[((size_t)so * 9 + 6 + col) * n + c];
+        const DT u1r = J[((size_t)so * 9 + 3 + col) * n + c], u2r = J[((size_t)so * 9 + 6 + col) * n + c];
+        const PT u1 = (PT)u1r, u2 = (PT)u2r;
+        if (rd) {
+          rd[(size_t)(3 + col) * nq] = to_ct(u1r, zc);
+          rd[(size_t)(6 + col) * nq] = to_ct(u2r, zc);
+        }
         if (col == 2) {
 #pragma unroll
           for (int r = 0; r < 3; ++r) a[3 * r + col] = fnms2(T[3 * r + 1], T[3 * r + 2], u1, u2, a[3 * r + col]);
         } else {
-          const PT u0 = (PT)J[((size_t)so * 9 + col) * n + c];
+          const DT u0r = J[((size_t)so * 9 + col) * n + c];
+          if (rd) rd[(size_t)col * nq] = to_ct(u0r, zc);
+          const PT u0 = (PT)u0r;
 #pragma unroll
           for (int r = 0; r < 3; ++r)
             a[3 * r + col] = fnms3(T[3 * r], T[3 * r + 1], T[3 * r + 2], u0, u1, u2, a[3 * r + col]);
@@ -436,7 +473,7 @@ __device__ __forceinline__ double as_pt(float v, double) { return (double)v; }
 __device__ __forceinline__ double as_pt(__nv_bfloat16 v, double) { return (double)__bfloat162float(v); }
 
 // With COMPACT the off-diagonal blocks come from this colour's compact copy
-// (k_ilu_compact: slot-major, indexed by the colour slot q, so a sweep reads
+// (written by k_ilu_setup_black: slot-major, indexed by the colour slot q, so a sweep reads
 // only its own rows); otherwise from J itself, whose lines also carry the
 // other colour's rows.  MODE: 0 the red sweep (t_j = y_j of the black
 // neighbours, then the well rows), 1 the black sweep after k_ilu_red_diag
@@ -492,44 +529,19 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
   }
 }
 
-// compact per-colour copy of the six off-diagonal blocks of every row, in the
-// storage type CT (the Jacobian's own, or BF16)
-__device__ __forceinline__ float to_ct(float v, float) { return v; }
-__device__ __forceinline__ double to_ct(double v, double) { return v; }
-__device__ __forceinline__ __nv_bfloat16 to_ct(float v, __nv_bfloat16) { return __float2bfloat16_rn(v); }
-__device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return __float2bfloat16_rn((float)v); }
-
-template <typename DT, typename CT>
-__global__ void __launch_bounds__(256) k_ilu_compact(Grid g, const DT* __restrict__ J, CT* __restrict__ c0,
-                                                     CT* __restrict__ c1) {
-  PF_PDL_ENTRY();
-  const long long n = g.n, nq = colour_slots(g);
-  const unsigned int hx = ((unsigned int)g.nx + 1u) >> 1;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const unsigned int ui = (unsigned int)i, nxu = (unsigned int)g.nx;
-    const unsigned int row = ui / nxu, x = ui - row * nxu;
-    const unsigned int y = row % (unsigned int)g.ny, z = row / (unsigned int)g.ny;
-    CT* dst = ((x + y + z) & 1u) ? c1 : c0;
-    const long long q = (long long)row * hx + (x >> 1);
-    const CT zc{};
-#pragma unroll
-    for (int s = 1; s < SL_COUNT; ++s)
-#pragma unroll
-      for (int e = 0; e < 9; ++e) dst[(size_t)((s - 1) * 9 + e) * nq + q] = to_ct(J[(size_t)(s * 9 + e) * n + i], zc);
-  }
-}
-
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
                       double guard, const IluCompact& cp, cudaStream_t st) {
   launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
-  launch(k_ilu_setup_black<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv, (PT)guard);
+  // the black set-up also writes the compact per-colour copies the sweeps read
+  const int grid = grid_for(colour_slots_host(g), 256);
   if (cp.kind == 1)
-    launch(k_ilu_compact<DT, DT>, grid_for(g.n, 256), 256, 0, st, g, J, (DT*)cp.c[0], (DT*)cp.c[1]);
+    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0], (DT*)cp.c[1]);
   else if (cp.kind == 2)
-    launch(k_ilu_compact<DT, __nv_bfloat16>, grid_for(g.n, 256), 256, 0, st, g, J, (__nv_bfloat16*)cp.c[0],
-           (__nv_bfloat16*)cp.c[1]);
+    launch(k_ilu_setup_black<DT, PT, __nv_bfloat16>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
+           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1]);
+  else
+    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr, (DT*)nullptr);
 }
 
 template <typename DT, typename PT, typename OT, typename VT>
