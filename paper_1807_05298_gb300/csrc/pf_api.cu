@@ -452,7 +452,7 @@ pf_status assemble_t(pf_sim* s) {
   }
   {
     KtScope t(s, PF_KT_GATHER);
-    launch_gather<DT>(s->g, s->Fbuf, s->dt, s->R, (DT*)s->J, st, s->tune.gather);
+    launch_gather<DT>(s->g, s->Fbuf, s->R, (DT*)s->J, st, s->tune.gather);
   }
   {
     KtScope t(s, PF_KT_WELLS);
@@ -604,17 +604,22 @@ pf_status piece_ortho(pf_sim* s, int j) {
   double* w = s->V + (size_t)(j + 1) * ld;
   cudaStream_t st = s->stream;
   KtScope t(s, PF_KT_ORTHO);
-  // pass 1: hbuf[0..k) = (vs[i] <V_i, w>) and hbuf[k] = |w|^2; w -= sum_i
-  // h1[i] vs[i] V_i with |w|^2 and 1/|w| at hbuf[256..257] (and 1/|w| into
-  // vs[j+1]) and the reorthogonalisation flag at hbuf+384.  pass 2 runs only
-  // if flagged: hbuf[128..128+k) the same dots, w -= the same projection, and
-  // it overwrites hbuf[256..257] and vs[j+1].
+  // pass 1: hbuf[0..k) = h_i = vs[i] <V_i, w> and hbuf[k] = |w|^2; the
+  // projected norm by Pythagoras, |w|^2 - sum_i h_i^2, and its 1/sqrt at
+  // hbuf[256..257] (and into vs[j+1]), with the reorthogonalisation flag at
+  // hbuf+384 when it falls below eta^2 |w|^2; then w -= sum_i h_i vs[i] V_i
+  // (no norm pass).  pass 2 runs only if flagged: hbuf[128..128+k) the same
+  // dots, w -= the same projection, and its measured |w|^2 and 1/|w|
+  // overwrite hbuf[256..257] and vs[j+1].  Without the flag the first pass
+  // kept more than eta^2 of |w|^2, so the Pythagorean value carries a relative
+  // error of at most about k eps / eta^2.
   const double eta2 = s->opts.reorth_eta * s->opts.reorth_eta;
   int* reorth = reinterpret_cast<int*>(s->hbuf + 384);
   float* wf = precond_vf(s);  // the FP32 copy of V_{j+1} for the next step's preconditioner (mixed CPR)
-  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr, s->vs);
-  launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, s->hbuf + k,
-                   reorth, nullptr, st, eta2, s->vs, wf, s->vs + j + 1);
+  launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf, s->red_counter, st, 1, nullptr, s->vs,
+                  s->hbuf + 256, s->vs + j + 1, reorth, eta2);
+  launch_axpy_norm(n, k, s->V, ld, s->hbuf, w, s->partial, s->nblocks, nullptr, s->red_counter, nullptr, nullptr,
+                   nullptr, st, eta2, s->vs, wf, nullptr);
   launch_multidot(n, k, s->V, ld, w, s->partial, s->nblocks, s->hbuf + 128, s->red_counter, st, 0, reorth, s->vs);
   launch_axpy_norm(n, k, s->V, ld, s->hbuf + 128, w, s->partial, s->nblocks, s->hbuf + 256, s->red_counter, nullptr,
                    nullptr, reorth, st, 0.5, s->vs, wf, s->vs + j + 1);
@@ -1661,7 +1666,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
                                                                  s->Mold, s->R, (float*)s->J, nullptr, 0, st, b); });
     t.face = pick_block(s, [&](int b) { launch_face_flux<float>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv,
                                                                (const float*)s->pd, dt, (float*)s->J, s->Fbuf, st, b); });
-    t.gather = pick_block(s, [&](int b) { launch_gather<float>(s->g, s->Fbuf, dt, s->R, (float*)s->J, st, b); });
+    t.gather = pick_block(s, [&](int b) { launch_gather<float>(s->g, s->Fbuf, s->R, (float*)s->J, st, b); });
     t.spmv = pick_block(s, [&](int b) {
       launch_spmv_f32(s->g, wells_view(s), (const float*)s->J, (const float*)s->Bw, (const float*)s->Cw,
                       (const float*)s->Dw, s->Zf, s->r, st, b);
@@ -1677,7 +1682,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     t.face = pick_block(s, [&](int b) { launch_face_flux<double>(s->g, s->ph, s->wL3, s->T3, s->x, s->pv,
                                                                 (const double*)s->pd, dt, (double*)s->J, s->Fbuf, st,
                                                                 b); });
-    t.gather = pick_block(s, [&](int b) { launch_gather<double>(s->g, s->Fbuf, dt, s->R, (double*)s->J, st, b); });
+    t.gather = pick_block(s, [&](int b) { launch_gather<double>(s->g, s->Fbuf, s->R, (double*)s->J, st, b); });
     // one thread per cell (64/128/256) or one per block row (-96/-192/-384)
     if (s->opts.precond == PF_PC_CPR)
       t.stage2 = pick_block(s, [&](int b) {

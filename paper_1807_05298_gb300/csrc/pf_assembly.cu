@@ -314,7 +314,9 @@ __device__ __forceinline__ void load_side(long long i, long long n, const double
 
 // Mass fluxes F (oil, water, polymer) from H into L across one face and their
 // derivatives dL = dF/d(P_L, S_L, C_L), dH = dF/d(P_H, S_H, C_H), row-major
-// 3x3 (rows oil, water, polymer).  gdz = g (Z_H - Z_L).
+// 3x3 (rows oil, water, polymer).  gdz = g (Z_H - Z_L).  Every output is
+// linear in the transmissibility T, so a caller that passes T dt gets the
+// time-step integrals dt F and dt dF directly.
 template <typename DT>
 __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, double wL,
                                           const SideV& a, const SideD<DT>& da, const SideV& b,
@@ -430,17 +432,18 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
       load_side<DT>(h, n, x, pv, pd, b, db);
       const double wL = wL3[(size_t)d * n + i];
       double F[3]; DT dL[9], dH[9];
-      face_flux<DT>(ph, T3[(size_t)d * n + i], gdz, wL, a, da, b, db, F, dL, dH);
+      // with T dt: F and its derivatives come out as dt F and dt dF (one
+      // multiply per face instead of one per Jacobian entry and flux)
+      face_flux<DT>(ph, T3[(size_t)d * n + i] * dt, gdz, wL, a, da, b, db, F, dL, dH);
       Fd[i] = F[0]; Fd[n + i] = F[1]; Fd[2 * n + i] = F[2];
       // row L, column H: -dt dF/dx_H  (slot +d of row i)
       DT* Jp = J + (size_t)(SL_XP + 2 * d) * 9 * n;
       // row H, column L: +dt dF/dx_L  (slot -d of row h)
       DT* Jm = J + (size_t)(SL_XM + 2 * d) * 9 * n;
-      const DT mdt = (DT)(-dt), pdt = (DT)dt;
 #pragma unroll
       for (int e = 0; e < 9; ++e) {
-        Jp[(size_t)e * n + i] = mdt * dH[e];
-        Jm[(size_t)e * n + h] = pdt * dL[e];
+        Jp[(size_t)e * n + i] = -dH[e];
+        Jm[(size_t)e * n + h] = dL[e];
       }
     }
     // slots that leave the grid on the minus side are zero
@@ -464,8 +467,8 @@ void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const do
 // ---------------------------------------------------------------------------
 
 template <typename DT>
-__global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict__ Fbuf, double dt,
-                                                double* __restrict__ R, DT* __restrict__ J) {
+__global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict__ Fbuf, double* __restrict__ R,
+                                                DT* __restrict__ J) {
   PF_PDL_ENTRY();
   const long long n = g.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -500,9 +503,9 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
         for (int e = 0; e < 9; ++e) dsum[e] += Jm[(size_t)e * n + h];
       }
     }
-    R[3 * i] -= dt * fs[0];
-    R[3 * i + 1] -= dt * fs[1];
-    R[3 * i + 2] -= dt * fs[2];
+    R[3 * i] -= fs[0];  // Fbuf holds dt F
+    R[3 * i + 1] -= fs[1];
+    R[3 * i + 2] -= fs[2];
     DT* Jd = J + (size_t)SL_D * 9 * n;
 #pragma unroll
     for (int e = 0; e < 9; ++e) Jd[(size_t)e * n + i] -= dsum[e];
@@ -510,8 +513,8 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
 }
 
 template <typename DT>
-void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st, int block) {
-  launch(k_gather<DT>, grid_for(g.n, block), block, 0, st, g, Fbuf, dt, R, J);
+void launch_gather(const Grid& g, const double* Fbuf, double* R, DT* J, cudaStream_t st, int block) {
+  launch(k_gather<DT>, grid_for(g.n, block), block, 0, st, g, Fbuf, R, J);
 }
 
 // ---------------------------------------------------------------------------
@@ -813,8 +816,8 @@ template void launch_face_flux<double>(const Grid&, const Phys&, const double*, 
                                        const double*, const double*, double, double*, double*, cudaStream_t, int);
 template void launch_face_flux<float>(const Grid&, const Phys&, const double*, const double*, const double*,
                                       const double*, const float*, double, float*, double*, cudaStream_t, int);
-template void launch_gather<double>(const Grid&, const double*, double, double*, double*, cudaStream_t, int);
-template void launch_gather<float>(const Grid&, const double*, double, double*, float*, cudaStream_t, int);
+template void launch_gather<double>(const Grid&, const double*, double*, double*, cudaStream_t, int);
+template void launch_gather<float>(const Grid&, const double*, double*, float*, cudaStream_t, int);
 template void launch_wells<double>(const Grid&, const Phys&, const Wells&, const double*, const double*,
                                    const double*, double, double*, double*, double*, double*, double*, cudaStream_t);
 template void launch_wells<float>(const Grid&, const Phys&, const Wells&, const double*, const double*,

@@ -146,9 +146,9 @@ template <typename DT>
 void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3,
                       const double* x, const double* pv, const DT* pd, double dt, DT* J,
                       double* Fbuf, cudaStream_t st, int block = 256);
+// Fbuf (written by launch_face_flux) holds dt F per face
 template <typename DT>
-void launch_gather(const Grid& g, const double* Fbuf, double dt, double* R, DT* J, cudaStream_t st,
-                   int block = 256);
+void launch_gather(const Grid& g, const double* Fbuf, double* R, DT* J, cudaStream_t st, int block = 256);
 template <typename DT>
 void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                   const DT* pd, double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st);
@@ -214,11 +214,17 @@ void launch_sub(long long n, const double* a, const double* b, double* c, cudaSt
 // be null): skip the whole kernel unless *run_if.
 // vs (may be null): V_j holds the basis vector before its normalisation, the
 // basis vector is vs[j] V_j, and out[j] = vs[j] <V_j, w>.
+// pyth (may be null, with self_dot): pyth[0] = |w|^2 - sum_j out[j]^2, the
+// squared norm of w after its projection on the orthonormal v_j, pyth[1] =
+// 1 / sqrt(pyth[0]) (also into *vs_next when given), and *decide = 1 when
+// pyth[0] < eta2 |w|^2.
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w,
                      double* partial, int nblocks, double* out, unsigned int* counter, cudaStream_t st,
-                     int self_dot = 0, const int* run_if = nullptr, const double* vs = nullptr);
+                     int self_dot = 0, const int* run_if = nullptr, const double* vs = nullptr,
+                     double* pyth = nullptr, double* vs_next = nullptr, int* decide = nullptr, double eta2 = 0.0);
 // w -= sum_j V[j] h[j]; out[0] = |w|^2, out[1] = 1/|w|; *decide = 1 if
-// |w|^2 < norm0[0] / 2 (a second Gram-Schmidt pass is needed)
+// |w|^2 < eta2 norm0[0] (a second Gram-Schmidt pass is needed); with out
+// null the projection alone (no norm, no reduction).
 // vs as in launch_multidot; wf (may be null) gets an FP32 copy of the new w;
 // vs_next (may be null) gets 1 / |w|, the normalisation of w as the next
 // basis vector.

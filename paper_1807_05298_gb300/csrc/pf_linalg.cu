@@ -757,7 +757,8 @@ __device__ __forceinline__ void block_reduce_write(double (&acc)[KM], int k, dou
 // per value, lanes over blocks, then a shuffle tree), so the result does not
 // depend on which block came last; it then re-arms the counter.
 // scale (may be null): out[j] *= scale[j] for the first nscaled values.
-__device__ __forceinline__ void last_block_reduce(const double* partial, int stride, int k, double* out,
+// Returns true in the last block (whose threads then all see out).
+__device__ __forceinline__ bool last_block_reduce(const double* partial, int stride, int k, double* out,
                                                   unsigned int* counter, bool inv_norm = false,
                                                   const double* norm0 = nullptr, int* decide = nullptr,
                                                   const double* scale = nullptr, int nscaled = 0) {
@@ -769,7 +770,7 @@ __device__ __forceinline__ void last_block_reduce(const double* partial, int str
     last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = wid; j < k; j += nw) {
@@ -786,6 +787,8 @@ __device__ __forceinline__ void last_block_reduce(const double* partial, int str
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
 }
 
 // One tile of the multi-dot: NT columns of V (and <w, w> when SELF), with a
@@ -830,10 +833,17 @@ __device__ __forceinline__ void md_dispatch(int nt, long long n, const double* V
 // out[k] = <w, w>; columns in tiles of up to 8 (few registers, high
 // occupancy), w re-read per tile.  run_if (may be null): the kernel returns at
 // once unless *run_if is set.
+// pyth (may be null; needs self_dot and orthonormal v_j): the squared norm of
+// w after the projection, by Pythagoras, |w - sum_j h_j v_j|^2 = |w|^2 -
+// sum_j h_j^2 with h_j = out[j], into pyth[0] and its 1/sqrt into pyth[1] and
+// *vs_next; *decide = 1 when it is below eta2 |w|^2 (a second Gram-Schmidt
+// pass will follow and measure the norm directly).
 __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const double* __restrict__ V, long long ld,
                                                   const double* __restrict__ w, double* __restrict__ partial,
                                                   int stride, double* __restrict__ out, unsigned int* counter,
-                                                  int self_dot, const int* run_if, const double* __restrict__ vs) {
+                                                  int self_dot, const int* run_if, const double* __restrict__ vs,
+                                                  double* __restrict__ pyth, double* __restrict__ vs_next,
+                                                  int* __restrict__ decide, double eta2) {
   PF_PDL_ENTRY();
   if (run_if && !*run_if) return;
   double* row = partial + (size_t)blockIdx.x * stride;
@@ -842,16 +852,31 @@ __global__ void __launch_bounds__(256) k_multidot(long long n, int k, const doub
   const int nt = k - j0;  // 0..8 columns left
   if (self_dot) md_dispatch<true>(nt, n, V, ld, w, j0, row);
   else if (nt > 0) md_dispatch<false>(nt, n, V, ld, w, j0, row);
-  last_block_reduce(partial, stride, k + (self_dot ? 1 : 0), out, counter, false, nullptr, nullptr, vs, k);
+  if (!last_block_reduce(partial, stride, k + (self_dot ? 1 : 0), out, counter, false, nullptr, nullptr, vs, k))
+    return;
+  if (pyth && threadIdx.x < 32) {
+    double q = 0.0;  // sum of h_j^2 in a fixed order (lanes over j, then a shuffle tree)
+    for (int j = threadIdx.x; j < k; j += 32) q += __ldcg(out + j) * __ldcg(out + j);
+    q = wsum(q);
+    if (threadIdx.x == 0) {
+      const double ww = __ldcg(out + k), e = ww - q;
+      pyth[0] = e;
+      pyth[1] = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
+      if (vs_next) *vs_next = pyth[1];
+      if (decide) *decide = (e < eta2 * ww) ? 1 : 0;
+    }
+  }
 }
 
 // w -= sum_{j<k} v_j h[j] with v_j = vs[j] V_j (vs null: v_j = V_j), then
-// out[0] = |w|^2 and out[1] = 1 / |w| (also into *vs_next when given: w is
-// kept as the next basis vector before its normalisation).  wf (may be null):
-// an FP32 copy of the new w.  With norm0 and decide: *decide = 1 when
+// (NORM) out[0] = |w|^2 and out[1] = 1 / |w| (also into *vs_next when given:
+// w is kept as the next basis vector before its normalisation).  wf (may be
+// null): an FP32 copy of the new w.  With norm0 and decide: *decide = 1 when
 // |w_new|^2 < eta2 |w_old|^2, i.e. when the first pass cancelled so much of w
 // that a second Gram-Schmidt pass is needed ("twice is enough").  run_if as in
-// k_multidot.
+// k_multidot.  Without NORM the kernel only projects (no sum of squares: no
+// FP64 multiply-add per element, no reduction).
+template <bool NORM>
 __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const double* __restrict__ V, long long ld,
                                                    const double* __restrict__ h, double* __restrict__ w,
                                                    double* __restrict__ partial, int stride, double* __restrict__ out,
@@ -869,8 +894,9 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
     for (int j = 0; j < k; ++j) wi -= V[(size_t)j * ld + i] * hs[j];
     w[i] = wi;
     if (wf) wf[i] = (float)wi;
-    acc[0] += wi * wi;
+    if (NORM) acc[0] += wi * wi;
   }
+  if (!NORM) return;
   block_reduce_write<1>(acc, 1, partial + (size_t)blockIdx.x * stride);
   __shared__ bool last;
   __threadfence();
@@ -894,16 +920,21 @@ __global__ void __launch_bounds__(256) k_axpy_norm(long long n, int k, const dou
 
 void launch_multidot(long long n, int k, const double* V, long long ld, const double* w, double* partial, int nblocks,
                      double* out, unsigned int* counter, cudaStream_t st, int self_dot, const int* run_if,
-                     const double* vs) {
-  launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if, vs);
+                     const double* vs, double* pyth, double* vs_next, int* decide, double eta2) {
+  launch(k_multidot, nblocks, 256, 0, st, n, k, V, ld, w, partial, 72, out, counter, self_dot, run_if, vs, pyth,
+         vs_next, decide, eta2);
 }
 
 void launch_axpy_norm(long long n, int k, const double* V, long long ld, const double* h, double* w, double* partial,
                       int nblocks, double* out, unsigned int* counter, const double* norm0, int* decide,
                       const int* run_if, cudaStream_t st, double eta2, const double* vs, float* wf,
                       double* vs_next) {
-  launch(k_axpy_norm, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if, eta2,
-         vs, wf, vs_next);
+  if (out)
+    launch(k_axpy_norm<true>, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide, run_if,
+           eta2, vs, wf, vs_next);
+  else
+    launch(k_axpy_norm<false>, nblocks, 256, 0, st, n, k, V, ld, h, w, partial, 72, out, counter, norm0, decide,
+           run_if, eta2, vs, wf, vs_next);
 }
 
 __global__ void __launch_bounds__(256) k_multi_axpy_add(long long n, int k, const double* __restrict__ Z, long long ld,
@@ -927,7 +958,7 @@ void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, co
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
                 unsigned int* counter, cudaStream_t st) {
   launch(k_multidot, nblocks, 256, 0, st, n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr,
-         (const double*)nullptr);
+         (const double*)nullptr, (double*)nullptr, (double*)nullptr, (int*)nullptr, 0.0);
 }
 
 // explicit instantiations

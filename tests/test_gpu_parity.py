@@ -190,6 +190,36 @@ def test_linear_solve_matches_direct(B, precond, cycle, stage1, sweeps):
     sim.close()
 
 
+@pytest.mark.parametrize("eta,restart", [(0.0, 30), (1.0, 30), (0.2, 5)])
+def test_gram_schmidt_variants_match_direct(B, eta, restart):
+    """The Arnoldi step's Gram-Schmidt under each reorthogonalisation rule:
+    eta = 0 keeps one classical pass (the second only where the projected
+    norm, taken by Pythagoras from the first pass's dots, is not positive),
+    eta = 1 always takes the second pass with its measured norm, and the
+    default 0.2 with a short restart (every cycle restarts from the true
+    residual).  Each solve must reach the direct solution of the oracle's
+    system (FP64: the mixed form solves with its FP32 operator)."""
+    sc, ctl = ragged_scenario(nx=17, ny=9, nz=4)
+    st = M.Setup(sc)
+    rng = np.random.default_rng(5)
+    x_old = random_state(st, rng, M.initial_state(st))
+    x = x_old + 0.0
+    x[0:3 * st.n:3] += rng.normal(0.0, 0.5 * BAR, st.n)
+    dt = 0.5 * DAY
+    st, sim, R_o, J_o, R_g, J_g = assemble_both(B, sc, ctl, x_old, x, dt, gmres_max_iter=2000, precond=B.PF_PC_CPR,
+                                                reorth_eta=eta, gmres_restart=restart)
+    b = -R_o
+    xg, its, rr = sim.solve_linear(b, 1e-12)
+    xo = spla.spsolve(J_o.tocsc(), b)
+    assert rr <= 1e-12
+    assert np.linalg.norm(J_o @ xg - b) <= 1e-10 * np.linalg.norm(b)
+    n = st.n
+    for a in range(3):
+        ref = np.abs(xo[a:3 * n:3]).max()
+        assert np.abs(xg[a:3 * n:3] - xo[a:3 * n:3]).max() <= 1e-6 * ref + 1e-300
+    sim.close()
+
+
 def field_errors(n, x_g, x_o):
     out = []
     for a in range(3):
@@ -283,6 +313,44 @@ def test_full_size_100k_root_is_oracle_root(B):
     assert residual_error(st, R_g, R_o, dt, ctl) <= 1e-11
     assert rel_matrix_error(J_g, J_o) <= 1e-11
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c2_trajectory_matches_the_oracle_run(B, precision):
+    """100x100x10 (100,000 cells, the 5-spot recipe with the polymer slug):
+    the first three time steps of 10 days from the initial state, under the
+    schedule's controls and BHP limits, against the oracle's own run of the
+    same steps (tests/golden/c2_trajectory.json, written by
+    make_c2_trajectory.py, which runs only oracle/): per step, P, S, C at the
+    sampled cells to 1e-6 of each field's max-norm, every bottom-hole
+    pressure to 1e-6 relative, the same number of step cuts and the same
+    wells switched onto their BHP limits.  In both precisions: the mixed
+    form's FP32 Jacobian and preconditioner change the Newton path, not the
+    root its FP64 residual defines."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_trajectory.json")))
+    sc = G.scenario_c2()
+    prec = B.PF_PREC_MIXED if precision == "mixed" else B.PF_PREC_FP64
+    sim = B.Simulator(sc, stream=B.current_stream_handle(), precond=B.PF_PC_CPR, use_forcing=0,
+                      newton_tol=g["newton_tol"], precision=prec)
+    states = []
+    hist = sim.run_schedule(n_steps=g["n_steps"],
+                            callback=lambda s, rec: states.append((s.get_x(), [bool(v) for v in s.switched()])))
+    sim.close()
+    cells = np.asarray(g["cells"])
+    n = sc["nx"] * sc["ny"] * sc["nz"]
+    assert len(states) == len(g["steps"])
+    for (x, sw), rec, want in zip(states, hist, g["steps"]):
+        for name, a in (("P", 0), ("S", 1), ("C", 2)):
+            got = x[a:3 * n:3][cells]
+            err = np.abs(got - np.asarray(want[name])).max() / want["max_abs"][name]
+            assert err <= 1e-6, (name, err)
+            assert abs(np.abs(x[a:3 * n:3]).max() - want["max_abs"][name]) <= 1e-6 * want["max_abs"][name]
+        pb = np.asarray(want["Pb"])
+        assert np.abs(x[3 * n:] - pb).max() <= 1e-6 * np.abs(pb).max()
+        assert rec["cuts"] == want["cuts"]
+        assert sw == want["switched"]
 
 
 def sampled_window_check(B, sc, precision, seed, n_sample=48, layer_cells=0):
