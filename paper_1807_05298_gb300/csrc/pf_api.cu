@@ -363,6 +363,10 @@ struct Carver {
   }
 };
 
+// Whether the preconditioned Krylov vectors are kept in FP32 only (mixed
+// precision with CPR, whose output is FP32 values).
+bool fp32_basis(const pf_sim* s) { return s->mixed && s->opts.precond == PF_PC_CPR; }
+
 // Lays out every device array in one arena; with base == nullptr only sizes it.
 size_t carve(pf_sim* s, char* base) {
   Carver c;
@@ -406,7 +410,9 @@ size_t carve(pf_sim* s, char* base) {
   s->tmp = c.take<double>(s->nunk);
   s->rlin = (s->opts.use_forcing && s->opts.forcing_form == 1) ? c.take<double>(s->nunk) : nullptr;
   s->V = c.take<double>((size_t)(m + 1) * s->ld);
-  s->Z = c.take<double>((size_t)m * s->ld);
+  // the mixed CPR preconditioner computes z in FP32: its vectors are kept in
+  // FP32 only (the FP64 copy would hold the same values)
+  s->Z = fp32_basis(s) ? nullptr : c.take<double>((size_t)m * s->ld);
   s->Zf = s->mixed ? c.take<float>((size_t)m * s->ld) : nullptr;
   s->Vf = s->mixed ? c.take<float>((size_t)s->ld) : nullptr;
   s->hbuf = c.take<double>(4 * 128 + 8);
@@ -585,7 +591,7 @@ void start_basis(pf_sim* s, const double* a, double inv_norm) {
 // with z_j = M^{-1} V_j the flexible Arnoldi relation J z_j = sum_i h_ij v_i
 // holds as before, and no pass over the vector normalises it.
 pf_status piece_pre(pf_sim* s, int j) {
-  return precond_apply(s, s->V + (size_t)j * s->ld, s->Z + (size_t)j * s->ld,
+  return precond_apply(s, s->V + (size_t)j * s->ld, fp32_basis(s) ? nullptr : s->Z + (size_t)j * s->ld,
                        s->mixed ? s->Zf + (size_t)j * s->ld : nullptr, precond_vf(s));
 }
 pf_status piece_spmv(pf_sim* s, int j) {
@@ -778,7 +784,8 @@ pf_status gmres(pf_sim* s, const double* bvec, double* xout, double rtol, int ma
     }
     memcpy(s->h_pinned + kPinY, y.data(), jdone * sizeof(double));
     PF_CUDA(cudaMemcpyAsync(s->ydev, s->h_pinned + kPinY, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
-    launch_multi_axpy_add(n, jdone, s->Z, ld, s->ydev, xout, st);
+    if (fp32_basis(s)) launch_multi_axpy_add_f32(n, jdone, s->Zf, ld, s->ydev, xout, st);
+    else launch_multi_axpy_add(n, jdone, s->Z, ld, s->ydev, xout, st);
     s->launches += 1;
     if (!converged && total < maxit) {
       if ((rc = spmv(s, xout, s->r)) != PF_OK) return rc;

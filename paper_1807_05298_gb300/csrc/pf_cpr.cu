@@ -128,8 +128,9 @@ __global__ void __launch_bounds__(256) k_galerkin(Dims f, Dims c, const T* __res
 
 // The preconditioner's output, written by the last post-smoothing pass on the
 // finest pressure level (saves a pass over the vector): mode 1 (FP64 path)
-// z[3i] += x_i on every cell; mode 2 (mixed) z = zf + Pi_p x in FP64 and its
-// FP32 copy zf_out (may be null), wells included.
+// z[3i] += x_i on every cell; mode 2 (mixed) z = zf + Pi_p x in FP64 (z may
+// be null: the Krylov solver then keeps only the FP32 copy, which holds the
+// same values) and its FP32 copy zf_out (may be null), wells included.
 struct TopOut {
   int mode = 0;
   int nw = 0;
@@ -144,9 +145,11 @@ __device__ __forceinline__ void top_write(const TopOut& t, long long i, T xi) {
     t.z[3 * i] += (double)xi;
   } else {
     const float p = t.zf[3 * i] + (float)xi, sv = t.zf[3 * i + 1], cv = t.zf[3 * i + 2];
-    t.z[3 * i] = (double)p;
-    t.z[3 * i + 1] = (double)sv;
-    t.z[3 * i + 2] = (double)cv;
+    if (t.z) {
+      t.z[3 * i] = (double)p;
+      t.z[3 * i + 1] = (double)sv;
+      t.z[3 * i + 2] = (double)cv;
+    }
     if (t.zf_out) { t.zf_out[3 * i] = p; t.zf_out[3 * i + 1] = sv; t.zf_out[3 * i + 2] = cv; }
   }
 }
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(256) k_rbgs(Dims d, const T* __restrict__ A, c
       if (p >= nq) {  // well rows of the mixed output: stage-1 values
         const long long wv = 3 * d.n + (p - nq);
         const float v = top.zf[wv];
-        top.z[wv] = (double)v;
+        if (top.z) top.z[wv] = (double)v;
         if (top.zf_out) top.zf_out[wv] = v;
         continue;
       }
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ c
       if (p >= nq) {  // well rows of the mixed output: stage-1 values
         const long long wv = 3 * d.n + (p - nq);
         const float v = top.zf[wv];
-        top.z[wv] = (double)v;
+        if (top.z) top.z[wv] = (double)v;
         if (top.zf_out) top.zf_out[wv] = v;
         continue;
       }
@@ -869,8 +872,9 @@ __global__ void __launch_bounds__(256, 4) k_stage2(Grid g, Wells w, const T* __r
   }
 }
 
-// z = zf + Pi_p x0, written as FP64 for the Krylov basis and as an FP32 copy
-// for the mixed-precision operator (the two hold the same float values)
+// z = zf + Pi_p x0, written as FP64 for the Krylov basis (z may be null) and
+// as an FP32 copy for the mixed-precision operator (the two hold the same float
+// values)
 __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const float* __restrict__ zf,
                                                  const float* __restrict__ x0, double* __restrict__ z,
                                                  float* __restrict__ zf_out) {
@@ -878,14 +882,16 @@ __global__ void __launch_bounds__(256) k_out_f32(long long n, int nw, const floa
   GSTRIDE(i, n + nw) {
     if (i >= n) {
       const float v = zf[3 * n + (i - n)];
-      z[3 * n + (i - n)] = (double)v;
+      if (z) z[3 * n + (i - n)] = (double)v;
       if (zf_out) zf_out[3 * n + (i - n)] = v;
       continue;
     }
     const float p = zf[3 * i] + x0[i], sv = zf[3 * i + 1], cv = zf[3 * i + 2];
-    z[3 * i] = (double)p;
-    z[3 * i + 1] = (double)sv;
-    z[3 * i + 2] = (double)cv;
+    if (z) {
+      z[3 * i] = (double)p;
+      z[3 * i + 1] = (double)sv;
+      z[3 * i + 2] = (double)cv;
+    }
     if (zf_out) { zf_out[3 * i] = p; zf_out[3 * i + 1] = sv; zf_out[3 * i + 2] = cv; }
   }
 }

@@ -237,6 +237,10 @@ void launch_spmv_f32(const Grid& g, const Wells& w, const float* J, const float*
 // x += sum_j Z[j] y[j]
 void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, const double* y,
                            double* x, cudaStream_t st);
+// the same with FP32 vectors Zf, summed in two-float arithmetic (about 47
+// significant bits) on the FP32 pipe
+void launch_multi_axpy_add_f32(long long n, int k, const float* Zf, long long ld, const double* y, double* x,
+                               cudaStream_t st);
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks,
                 double* out, unsigned int* counter, cudaStream_t st);
 

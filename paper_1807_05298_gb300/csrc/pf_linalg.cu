@@ -955,6 +955,77 @@ void launch_multi_axpy_add(long long n, int k, const double* Z, long long ld, co
   launch(k_multi_axpy_add, grid_for(n, 256), 256, 0, st, n, k, Z, ld, y, x);
 }
 
+// Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b), for any a, b
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// x += sum_{j<k} Zf[j] y[j] with the preconditioned vectors held in FP32 (the
+// mixed form computes them in FP32, so FP32 storage loses nothing).  The sum
+// runs in two-float arithmetic on the FP32 pipe: each y_j is split as
+// yh + yl (yh = y_j rounded to FP32, yl the FP32 rounding of the remainder);
+// the product z yh is made exact by the FMA-based error of the product
+// (p = z yh, e = fma(z, yh, -p)); the running sum (sh, sl) takes p by Knuth's
+// TwoSum and is renormalised by a second TwoSum after each term.  That keeps
+// about 47 significant bits (the FP64 sum keeps 53) and costs no FP64 unit
+// time per term; one conversion pair per element joins the result to x.
+// Where a split coefficient leaves the normal FP32 range the kernel sums in
+// FP64 instead (conversions per term).  The intrinsics (_rn) keep the compiler
+// from fusing the error-free steps into multiply-adds.
+__global__ void __launch_bounds__(256) k_multi_axpy_add_f32(long long n, int k, const float* __restrict__ Zf,
+                                                            long long ld, const double* __restrict__ y,
+                                                            double* __restrict__ x) {
+  PF_PDL_ENTRY();
+  __shared__ float yh[128], yl[128];
+  __shared__ double yd[128];
+  __shared__ int wide;
+  if (threadIdx.x == 0) wide = 0;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    const double v = y[threadIdx.x];
+    const float h = __double2float_rn(v);
+    const float l = __double2float_rn(v - (double)h);
+    yd[threadIdx.x] = v;
+    yh[threadIdx.x] = h;
+    yl[threadIdx.x] = l;
+    // the split is exact to the two-float precision only with yh and yl in
+    // the normal FP32 range (or both zero)
+    const float ah = fabsf(h), al = fabsf(l);
+    const bool ok = isfinite(h) && (h == 0.0f || (ah >= 1.0e-30f && ah <= 1.0e30f)) &&
+                    (l == 0.0f || al >= 1.17549435e-38f);
+    if (!ok) atomicOr(&wide, 1);
+  }
+  __syncthreads();
+  if (wide) {
+    GRID_STRIDE(i, n) {
+      double s = x[i];
+      for (int j = 0; j < k; ++j) s += (double)Zf[(size_t)j * ld + i] * yd[j];
+      x[i] = s;
+    }
+    return;
+  }
+  GRID_STRIDE(i, n) {
+    float sh = 0.0f, sl = 0.0f;
+    for (int j = 0; j < k; ++j) {
+      const float z = Zf[(size_t)j * ld + i];
+      const float ph = __fmul_rn(z, yh[j]);
+      const float pl = __fmaf_rn(z, yl[j], __fmaf_rn(z, yh[j], -ph));  // z yl + the error of z yh
+      float s, e;
+      two_sum_f(sh, ph, s, e);
+      const float t = __fadd_rn(sl, __fadd_rn(pl, e));
+      two_sum_f(s, t, sh, sl);  // renormalise (no ordering of |s| and |t| assumed)
+    }
+    x[i] = x[i] + ((double)sh + (double)sl);
+  }
+}
+
+void launch_multi_axpy_add_f32(long long n, int k, const float* Zf, long long ld, const double* y, double* x,
+                               cudaStream_t st) {
+  launch(k_multi_axpy_add_f32, grid_for(n, 256), 256, 0, st, n, k, Zf, ld, y, x);
+}
+
 void launch_dot(long long n, const double* a, const double* b, double* partial, int nblocks, double* out,
                 unsigned int* counter, cudaStream_t st) {
   launch(k_multidot, nblocks, 256, 0, st, n, 1, a, 0, b, partial, 72, out, counter, 0, nullptr,
