@@ -87,8 +87,8 @@ typedef struct pf_physics {
 } pf_physics;
 
 /* One well: perforated cells (natural indices, the first one is the datum of
- * the hydrostatic wellbore eq. (ssw:dp)), the direction of each perforation
- * for the Peaceman index eq. (wi)/(wi:re:k), and the index parameters.  A cell
+ * the hydrostatic wellbore, Sec. 2.4), the direction of each perforation for
+ * the Peaceman index (Sec. 2.4), and the index parameters.  A cell
  * may carry at most one perforation over all wells. */
 typedef struct pf_well_desc {
   int kind;                 /* PF_WELL_INJECTOR or PF_WELL_PRODUCER */
@@ -220,7 +220,7 @@ typedef struct pf_sim pf_sim;
 
 /* Model loading, grid set-up and initialisation (Sec. 3, steps 1-3): copies
  * the description, computes transmissibilities (Sec. 3.2, harmonic k and
- * geometry) and Peaceman well indices (eq. (wi), (wi:re:k)) on the host,
+ * geometry) and Peaceman well indices (Sec. 2.4) on the host,
  * uploads everything to device memory owned by the returned object.
  * stream: a cudaStream_t borrowed for the life of the object (NULL allowed).
  * Errors: PF_EINVAL (sizes, NaN, doubly perforated cell), PF_ENOMEM, PF_ECUDA. */
@@ -269,8 +269,8 @@ pf_status pf_step(pf_sim* s, double dt, pf_step_report* rep);
 pf_status pf_end_step(pf_sim* s, int* resolve);
 pf_status pf_abort_step(pf_sim* s);
 /* Per-well mass rates into the reservoir (positive for injection) [kg/s] of
- * water, oil and polymer, eq. (ssw:Q) at the current state with the wellbore
- * weight of the current step, and the reference BHP [Pa]; host arrays of the
+ * water, oil and polymer (the perforation rates of Sec. 2.4) at the current
+ * state with the wellbore weight of the current step, and the reference BHP [Pa]; host arrays of the
  * well count, any may be NULL. */
 pf_status pf_well_rates(pf_sim* s, double* q_w, double* q_o, double* q_p, double* pb);
 /* switched[w] = 1 if rate well w currently runs on its BHP limit. */
@@ -415,6 +415,24 @@ pf_status pf_batch_create(const pf_model_desc* const* models, int n, const pf_so
 pf_status pf_batch_run(pf_batch* b, const pf_schedule* const* schedules, int max_cuts, pf_run_report* reports);
 pf_status pf_batch_member(pf_batch* b, int i, pf_sim** out);
 pf_status pf_batch_destroy(pf_batch* b);
+
+/* Packed assembly for the batch (the paper has no counterpart: it runs one
+ * simulation at a time).  With on = 1 every member's assembly (cell
+ * properties, face fluxes, gather, wells) goes through a shared packer: the
+ * members that reach an assembly together are assembled by one launch per
+ * kernel over all their cells (up to 24 members per launch, several launches
+ * beyond that), on a stream of the batch that is ordered after each member's
+ * stream and before its next work.  The first member to arrive waits up to
+ * window_us microseconds for the others that are inside pf_batch_run (0: pack
+ * whoever is waiting now).  Results are bit-identical to the members' own
+ * launches.  on = 0 detaches the packer.  Call it only while no pf_batch_run
+ * is in progress; PF_EINVAL for a negative window, PF_ECUDA if the stream or
+ * events cannot be created.  The batch owns the packer until
+ * pf_batch_destroy. */
+pf_status pf_batch_set_packing(pf_batch* b, int on, double window_us);
+/* Packs launched and members assembled through them since packing was last
+ * turned on (their ratio is the mean pack size); either pointer may be NULL. */
+pf_status pf_batch_packing_stats(pf_batch* b, int64_t* packs, int64_t* members);
 
 /* Serving loop: requests (a model and a schedule, deep-copied at submit) are
  * queued in arrival order; n_workers host threads admit the first queued

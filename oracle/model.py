@@ -14,9 +14,9 @@ Everything is written from the paper's equations (arXiv 1807.05298):
   R_k         1 + (RRF - 1) A_d / A_d,max                          (Sec. 2.3)
   viscosity   Todd-Longstaff mu_p,e, mu_w,partial, mu_w,e; linear or
               nonlinear mixing rule in beta = C / C_ref             (Sec. 2.3)
-  wells       Peaceman index, eq. (wi), (wi:re:k); perforation rate
-              eq. (ssw:Q); hydrostatic wellbore eq. (ssw:dp); BHP and
-              rate constraints                                      (Sec. 2.4)
+  wells       Peaceman index with its equivalent radius and
+              permeability; perforation rate; hydrostatic wellbore;
+              BHP and rate constraints                              (Sec. 2.4)
   time        backward Euler                                       (Sec. 3.1)
   space       two-point transmissibility, harmonic k and geometry,
               pore-volume weighted rho and mu, upstream k_r          (Sec. 3.2)
@@ -101,7 +101,8 @@ def cell_depth(sc):
 
 
 def peaceman_wi(kx, ky, kz, dx, dy, dz, direction, rw, skin, gf=0.249, f=1.0, fh=1.0):
-    """Well index, eq. (wi) with r_e and k_a from eq. (wi:re:k).
+    """Peaceman well index (Sec. 2.4) with its equivalent radius r_e and
+    permeability k_a.
 
     The printed form is for a well along x (perpendicular directions y, z);
     a well along y or z uses the same expression with the two directions
@@ -112,7 +113,7 @@ def peaceman_wi(kx, ky, kz, dx, dy, dz, direction, rw, skin, gf=0.249, f=1.0, fh
         k1, k2, h1, h2, h = kx, kz, dx, dz, dy
     else:
         k1, k2, h1, h2, h = kx, ky, dx, dy, dz
-    # eq. (wi:re:k) with (y, z) -> (1, 2)
+    # r_e and k_a of Sec. 2.4 with (y, z) -> (1, 2)
     re = (2.0 * gf / math.sqrt(math.pi)) * math.sqrt(math.sqrt(k2 / k1) * h1 ** 2 + math.sqrt(k1 / k2) * h2 ** 2) \
         / ((k2 / k1) ** 0.25 + (k1 / k2) ** 0.25)
     ka = math.sqrt(k1 * k2)
@@ -451,7 +452,8 @@ def rate_coefficients(ph, ctrl, kind):
 
 def perforation_rates(st, pr, w, Pb_w, gamma_w, c_inj):
     """Phase mass rates (water, oil, polymer) into the perforated cells of
-    well w, eq. (ssw:Q) with eq. (ssw:dp); Duals in (x_cell, P_b): 4 columns."""
+    well w: the perforation rate of Sec. 2.4 with the hydrostatic wellbore
+    pressure of the same section; Duals in (x_cell, P_b): 4 columns."""
     ph = st.ph
     wl = st.wells[w]
     c = wl["cells"]
@@ -718,7 +720,8 @@ def controls_with_defaults(controls):
 
 def well_totals(st, x, controls, gamma):
     """Per well: summed water and oil mass rates into the reservoir (positive
-    for injection) at the state x, eq. (ssw:Q), and the reference BHP."""
+    for injection) at the state x (the perforation rate of Sec. 2.4), and the
+    reference BHP."""
     pr = cell_properties(st.ph, st.phi_r, *_cell_duals(st, x))
     out = []
     for w in range(st.nw):

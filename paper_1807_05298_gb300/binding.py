@@ -164,6 +164,8 @@ def lib():
             "pf_batch_run": ([vp, C.POINTER(C.POINTER(pf_schedule)), C.c_int, C.POINTER(pf_run_report)], C.c_int),
             "pf_batch_member": ([vp, C.c_int, C.POINTER(vp)], C.c_int),
             "pf_batch_destroy": ([vp], C.c_int),
+            "pf_batch_set_packing": ([vp, C.c_int, C.c_double], C.c_int),
+            "pf_batch_packing_stats": ([vp, _i64p, _i64p], C.c_int),
             "pf_server_create": ([C.c_size_t, C.c_int, C.POINTER(pf_solver_opts), C.c_int, C.POINTER(vp)],
                                  C.c_int),
             "pf_server_submit": ([vp, C.POINTER(pf_model_desc), C.POINTER(pf_schedule), C.POINTER(C.c_uint64)],
@@ -536,7 +538,7 @@ class Batch:
     """Many scenarios resident at once, each with its own stream; pf_batch_run
     drives them from ``n_threads`` host threads."""
 
-    def __init__(self, scenarios, n_threads=8, opts=None, **over):
+    def __init__(self, scenarios, n_threads=8, opts=None, packed=False, pack_window_us=0.0, **over):
         self.models = [Model(sc) for sc in scenarios]
         self.opts = opts if opts is not None else default_opts(**over)
         arr = (C.POINTER(pf_model_desc) * len(self.models))(*[C.pointer(m.desc) for m in self.models])
@@ -544,6 +546,19 @@ class Batch:
         _rt_check(lib().pf_batch_create(arr, len(self.models), C.byref(self.opts), n_threads, C.byref(h)))
         self.h = h
         self.scenarios = scenarios
+        if packed:
+            self.set_packing(True, pack_window_us)
+
+    def set_packing(self, on, window_us=0.0):
+        """Packed assembly (pf_batch_set_packing): one launch per assembly
+        kernel over the members that reach an assembly together."""
+        _rt_check(lib().pf_batch_set_packing(self.h, 1 if on else 0, float(window_us)))
+
+    def packing_stats(self):
+        """(packs launched, members assembled through them)."""
+        p = C.c_int64(); m = C.c_int64()
+        _rt_check(lib().pf_batch_packing_stats(self.h, C.byref(p), C.byref(m)))
+        return p.value, m.value
 
     def run(self, n_steps=None, max_cuts=6, raise_on_failure=True):
         scheds = [Schedule(sc["schedule"], n_steps) for sc in self.scenarios]

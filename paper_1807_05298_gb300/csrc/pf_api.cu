@@ -61,6 +61,10 @@ bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed); }
 
 struct pf_sim {
   cudaStream_t stream = nullptr;
+  // assembly through a packer (several simulators per launch, set by the
+  // batch engine); null: this simulator's own launches
+  pf_status (*packer)(void*, pf_sim*) = nullptr;
+  void* packer_ctx = nullptr;
   int device = 0;
   bool dead = false;
   bool mixed = false;
@@ -214,8 +218,9 @@ Wells wells_view(const pf_sim* s) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// Peaceman well index, eq. (wi) with eq. (wi:re:k); the printed form is for a
-// well along x, whose perpendicular directions are y and z.
+// Peaceman well index of Sec. 2.4 with its equivalent radius and permeability;
+// the printed form is for a well along x, whose perpendicular directions are y
+// and z.
 double well_index(double kx, double ky, double kz, double dx, double dy, double dz, int dir, double rw, double skin,
                   double gf, double f, double fh) {
   double k1, k2, h1, h2, h;
@@ -470,9 +475,57 @@ pf_status assemble_t(pf_sim* s) {
 }
 
 pf_status assemble(pf_sim* s) {
-  pf_status rc = s->mixed ? assemble_t<float>(s) : assemble_t<double>(s);
+  pf_status rc = s->packer ? s->packer(s->packer_ctx, s) : s->mixed ? assemble_t<float>(s) : assemble_t<double>(s);
   if (rc == PF_OK) s->assembled = true;
   return rc;
+}
+
+template <typename DT>
+void fill_asm_member(pf_sim* s, AsmMember<DT>& a) {
+  a.g = s->g;
+  a.ph = s->ph;
+  a.w = wells_view(s);
+  a.phi_r = s->phi_r;
+  a.x = s->x;
+  a.Mold = s->Mold;
+  a.wL3 = s->wL3;
+  a.T3 = s->T3;
+  a.pv = s->pv;
+  a.R = s->R;
+  a.Fbuf = s->Fbuf;
+  a.pd = (DT*)s->pd;
+  a.J = (DT*)s->J;
+  a.Bw = (DT*)s->Bw;
+  a.Cw = (DT*)s->Cw;
+  a.Dw = (DT*)s->Dw;
+  a.dt = s->dt;
+}
+
+template <typename DT>
+pf_status assemble_packed_t(pf_sim* const* sims, int n, cudaStream_t st, int* launches) {
+  AsmPack<DT> pk;
+  int kernels = 0;
+  for (int done = 0; done < n;) {
+    const int k = std::min(kPackMax, n - done);
+    pk.nm = k;
+    pk.cblock0[0] = 0;
+    pk.wblock0[0] = 0;
+    for (int q = 0; q < k; ++q) {
+      pf_sim* s = sims[done + q];
+      fill_asm_member<DT>(s, pk.m[q]);
+      pk.cblock0[q + 1] = pk.cblock0[q] + (int)((s->g.n + 255) / 256);
+      pk.wblock0[q + 1] = pk.wblock0[q] + s->nw;
+    }
+    kernels += launch_assemble_packed<DT>(pk, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      for (int q = 0; q < k; ++q) sims[done + q]->dead = true;
+      return fail(PF_ECUDA, std::string("packed assembly launch: ") + cudaGetErrorString(e));
+    }
+    done += k;
+  }
+  if (launches) *launches = kernels;
+  return PF_OK;
 }
 
 // y = J x on device vectors
@@ -830,6 +883,25 @@ double forcing_term(double nb, double nb_prev) {
 }
 
 }  // namespace
+
+namespace pf {
+
+pf_status assemble_packed(pf_sim* const* sims, int n, cudaStream_t st, int* launches) {
+  if (n < 1) return PF_OK;
+  for (int i = 0; i < n; ++i)
+    if (sims[i]->mixed != sims[0]->mixed) return fail(PF_EINVAL, "a pack mixes precisions");
+  return sims[0]->mixed ? assemble_packed_t<float>(sims, n, st, launches)
+                        : assemble_packed_t<double>(sims, n, st, launches);
+}
+
+void set_assembly_packer(pf_sim* s, pf_status (*fn)(void*, pf_sim*), void* ctx) {
+  s->packer = fn;
+  s->packer_ctx = ctx;
+}
+
+cudaStream_t sim_stream(const pf_sim* s) { return s->stream; }
+
+}  // namespace pf
 
 extern "C" {
 

@@ -4,8 +4,8 @@
 // conservation with Darcy flux and gravity Sec. 2.2; polymer conservation,
 // permeability reduction R_k, equilibrium adsorption, Todd-Longstaff
 // viscosities and mixing rules, inaccessible pore volume Sec. 2.3; wells
-// eq. (ssw:Q), (ssw:dp) and the BHP / rate constraints Sec. 2.4; backward
-// Euler Sec. 3.1; two-point transmissibility with harmonic geometry and
+// (perforation rate, hydrostatic wellbore, BHP / rate constraints) Sec. 2.4;
+// backward Euler Sec. 3.1; two-point transmissibility with harmonic geometry and
 // permeability, pore-volume weighted rho and mu, upstream k_r Sec. 3.2.
 //
 // Kernel sequence per assembly (all deterministic, no atomics):
@@ -182,16 +182,15 @@ __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P
   c.dmu_pe = dmu_pe;
 }
 
+// One cell of the property kernel (mode as in launch_cell_props).
 template <typename DT>
-__global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const double* __restrict__ phi_r,
-                                                    const double* __restrict__ x, double* __restrict__ pv,
-                                                    DT* __restrict__ pd, const double* __restrict__ Mold,
-                                                    double* __restrict__ R, DT* __restrict__ J,
-                                                    double* __restrict__ Mold_out, int mode) {
-  PF_PDL_ENTRY();
+__device__ __forceinline__ void cell_props_at(const Grid& g, const Phys& ph, const double* __restrict__ phi_r,
+                                              const double* __restrict__ x, double* __restrict__ pv,
+                                              DT* __restrict__ pd, const double* __restrict__ Mold,
+                                              double* __restrict__ R, DT* __restrict__ J,
+                                              double* __restrict__ Mold_out, int mode, long long i) {
   const long long n = g.n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  {
     const double P = x[3 * i], S = x[3 * i + 1], C = x[3 * i + 2];
     CellEval<DT> c;
     eval_cell<DT>(ph, phi_r[i], P, S, C, c);
@@ -210,7 +209,7 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
       pv[PV_RK * n + i] = c.Rk;
       pv[PV_MUWE * n + i] = c.mu_we;
       pv[PV_MUPE * n + i] = c.mu_pe;
-      continue;
+      return;
     }
     if (mode == 1) {
       Mold_out[3 * i] = Mo;
@@ -222,7 +221,7 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
       pv[PV_KRO * n + i] = c.kro;
       pv[PV_RK * n + i] = c.Rk;
       pv[PV_MUWE * n + i] = c.mu_we;
-      continue;
+      return;
     }
     pv[PV_RHO_O * n + i] = c.rho_o;
     pv[PV_RHO_W * n + i] = c.rho_w;
@@ -268,11 +267,18 @@ __global__ void __launch_bounds__(256) k_cell_props(Grid g, Phys ph, const doubl
   }
 }
 
+// modes 1 and 2 (the old masses at the start of a step, the property values
+// for the well totals); mode 0 runs in the assembly kernel k_cell_props
 template <typename DT>
-void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x, double* pv,
-                       DT* pd, const double* Mold, double* R, DT* J, double* Mold_out, int mode,
-                       cudaStream_t st, int block) {
-  launch(k_cell_props<DT>, grid_for(g.n, block), block, 0, st, g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode);
+__global__ void __launch_bounds__(256) k_cell_values(Grid g, Phys ph, const double* __restrict__ phi_r,
+                                                     const double* __restrict__ x, double* __restrict__ pv,
+                                                     DT* __restrict__ pd, const double* __restrict__ Mold,
+                                                     double* __restrict__ R, DT* __restrict__ J,
+                                                     double* __restrict__ Mold_out, int mode) {
+  PF_PDL_ENTRY();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n;
+       i += (long long)gridDim.x * blockDim.x)
+    cell_props_at<DT>(g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out, mode, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -398,15 +404,14 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   }
 }
 
+// The three faces of cell i towards +x, +y, +z (one thread per cell).
 template <typename DT>
-__global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double* __restrict__ wL3,
-                                                   const double* __restrict__ T3, const double* __restrict__ x,
-                                                   const double* __restrict__ pv, const DT* __restrict__ pd,
-                                                   double dt, DT* __restrict__ J, double* __restrict__ Fbuf) {
-  PF_PDL_ENTRY();
+__device__ __forceinline__ void face_flux_at(const Grid& g, const Phys& ph, const double* __restrict__ wL3,
+                                             const double* __restrict__ T3, const double* __restrict__ x,
+                                             const double* __restrict__ pv, const DT* __restrict__ pd, double dt,
+                                             DT* __restrict__ J, double* __restrict__ Fbuf, long long i) {
   const long long n = g.n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  {
     const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
     const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
     const unsigned int rem = ui - (unsigned int)k * nxy;
@@ -456,23 +461,17 @@ __global__ void __launch_bounds__(256) k_face_flux(Grid g, Phys ph, const double
   }
 }
 
-template <typename DT>
-void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3, const double* x,
-                      const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st, int block) {
-  launch(k_face_flux<DT>, grid_for(g.n, block), block, 0, st, g, ph, wL3, T3, x, pv, pd, dt, J, Fbuf);
-}
 
 // ---------------------------------------------------------------------------
 // gather: residual flux sums and the flux part of the diagonal block
 // ---------------------------------------------------------------------------
 
+// Row i of the gather.
 template <typename DT>
-__global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict__ Fbuf, double* __restrict__ R,
-                                                DT* __restrict__ J) {
-  PF_PDL_ENTRY();
+__device__ __forceinline__ void gather_at(const Grid& g, const double* __restrict__ Fbuf, double* __restrict__ R,
+                                          DT* __restrict__ J, long long i) {
   const long long n = g.n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  {
     const unsigned int ui = (unsigned int)i, nxy = (unsigned int)g.nxy, nxu = (unsigned int)g.nx;
     const long long k = ui / nxy;  // 32-bit division: fewer than 2^31 cells
     const unsigned int rem = ui - (unsigned int)k * nxy;
@@ -512,10 +511,7 @@ __global__ void __launch_bounds__(256) k_gather(Grid g, const double* __restrict
   }
 }
 
-template <typename DT>
-void launch_gather(const Grid& g, const double* Fbuf, double* R, DT* J, cudaStream_t st, int block) {
-  launch(k_gather<DT>, grid_for(g.n, block), block, 0, st, g, Fbuf, R, J);
-}
+
 
 // ---------------------------------------------------------------------------
 // wells: one warp per well
@@ -527,14 +523,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Well wi, one warp (lane 0..31).
 template <typename DT>
-__global__ void k_wells(Grid g, Phys ph, Wells w, const double* __restrict__ x, const double* __restrict__ pv,
-                        const DT* __restrict__ pd, double dt, double* __restrict__ R, DT* __restrict__ J,
-                        DT* __restrict__ Bw, DT* __restrict__ Cw, DT* __restrict__ Dw) {
-  PF_PDL_ENTRY();
-  const int wi = blockIdx.x;
-  if (wi >= w.nw) return;
-  const int lane = threadIdx.x;
+__device__ __forceinline__ void wells_at(const Grid& g, const Phys& ph, const Wells& w, const double* __restrict__ x,
+                                         const double* __restrict__ pv, const DT* __restrict__ pd, double dt,
+                                         double* __restrict__ R, DT* __restrict__ J, DT* __restrict__ Bw,
+                                         DT* __restrict__ Cw, DT* __restrict__ Dw, int wi, int lane) {
   const long long n = g.n;
   const long long npf = w.npf;
   const double Pb = x[3 * n + wi];
@@ -631,12 +625,7 @@ __global__ void k_wells(Grid g, Phys ph, Wells w, const double* __restrict__ x, 
   }
 }
 
-template <typename DT>
-void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv, const DT* pd,
-                  double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st) {
-  if (w.nw == 0) return;
-  launch(k_wells<DT>, w.nw, 32, 0, st, g, ph, w, x, pv, pd, dt, R, J, Bw, Cw, Dw);
-}
+
 
 // Lagged wellbore unit weight (frozen over a step): rho_w(P_b) g for an
 // injector, the mobility-weighted mixture density over the perforations
@@ -669,7 +658,8 @@ __global__ void k_well_gamma(Grid g, Phys ph, Wells w, const double* __restrict_
 }
 
 // Summed water, oil and polymer mass rates of each well at the current state
-// (values of eq. (ssw:Q) with the lagged gamma); needs pv from a mode-2 pass.
+// (the perforation rates of Sec. 2.4 with the lagged gamma); needs pv from a
+// mode-2 pass.
 __global__ void k_well_totals(Grid g, Phys ph, Wells w, const double* __restrict__ x,
                               const double* __restrict__ pv, double* __restrict__ out) {
   PF_PDL_ENTRY();
@@ -808,6 +798,158 @@ void launch_newton_update(const Grid& g, int nw, double* x, const double* dx, do
 }
 
 // explicit instantiations
+// ---------------------------------------------------------------------------
+// assembly kernels over a pack of simulators (one or up to kPackMax)
+// ---------------------------------------------------------------------------
+
+// The member that block b belongs to (b0 ascending, b0[0] = 0).
+__device__ __forceinline__ int pack_member(const int* b0, int nm, int b) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b0[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// the pack travels in the launch parameters (at most 32,764 bytes)
+static_assert(sizeof(AsmPack<double>) <= 32000 && sizeof(AsmPack<float>) <= 32000, "pack size");
+
+template <typename DT>
+struct PackWords {
+  static constexpr int n = (int)(sizeof(AsmMember<DT>) / sizeof(unsigned long long));
+  static_assert(sizeof(AsmMember<DT>) % sizeof(unsigned long long) == 0, "descriptor size");
+};
+
+// Copies member m's descriptor from the launch parameters into shared memory
+// (every thread of a block serves the same member), so that the per-cell
+// arithmetic reads it the same way in every pack size.
+template <typename DT, int CAP>
+__device__ __forceinline__ const AsmMember<DT>& pack_load(const AsmPack<DT, CAP>& pk, int m,
+                                                          unsigned long long* sm) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&pk.m[m]);
+  for (int w = threadIdx.x; w < PackWords<DT>::n; w += blockDim.x) sm[w] = src[w];
+  __syncthreads();
+  return *reinterpret_cast<const AsmMember<DT>*>(sm);
+}
+
+// cell index of this thread within its member (blockDim.x threads per block)
+template <typename DT, int CAP>
+__device__ __forceinline__ long long pack_cell(const AsmPack<DT, CAP>& pk, int m) {
+  return (long long)(blockIdx.x - pk.cblock0[m]) * blockDim.x + threadIdx.x;
+}
+
+template <typename DT, int CAP>
+__global__ void __launch_bounds__(256) k_cell_props(const __grid_constant__ AsmPack<DT, CAP> pk) {
+  PF_PDL_ENTRY();
+  __shared__ unsigned long long sm[PackWords<DT>::n];
+  const int m = CAP == 1 ? 0 : pack_member(pk.cblock0, pk.nm, blockIdx.x);
+  const AsmMember<DT>& a = pack_load(pk, m, sm);
+  const long long i = pack_cell(pk, m);
+  if (i < a.g.n) cell_props_at<DT>(a.g, a.ph, a.phi_r, a.x, a.pv, a.pd, a.Mold, a.R, a.J, nullptr, 0, i);
+}
+
+template <typename DT, int CAP>
+__global__ void __launch_bounds__(256) k_face_flux(const __grid_constant__ AsmPack<DT, CAP> pk) {
+  PF_PDL_ENTRY();
+  __shared__ unsigned long long sm[PackWords<DT>::n];
+  const int m = CAP == 1 ? 0 : pack_member(pk.cblock0, pk.nm, blockIdx.x);
+  const AsmMember<DT>& a = pack_load(pk, m, sm);
+  const long long i = pack_cell(pk, m);
+  if (i < a.g.n) face_flux_at<DT>(a.g, a.ph, a.wL3, a.T3, a.x, a.pv, a.pd, a.dt, a.J, a.Fbuf, i);
+}
+
+template <typename DT, int CAP>
+__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ AsmPack<DT, CAP> pk) {
+  PF_PDL_ENTRY();
+  __shared__ unsigned long long sm[PackWords<DT>::n];
+  const int m = CAP == 1 ? 0 : pack_member(pk.cblock0, pk.nm, blockIdx.x);
+  const AsmMember<DT>& a = pack_load(pk, m, sm);
+  const long long i = pack_cell(pk, m);
+  if (i < a.g.n) gather_at<DT>(a.g, a.Fbuf, a.R, a.J, i);
+}
+
+// one warp per well
+template <typename DT, int CAP>
+__global__ void k_wells(const __grid_constant__ AsmPack<DT, CAP> pk) {
+  PF_PDL_ENTRY();
+  __shared__ unsigned long long sm[PackWords<DT>::n];
+  const int m = CAP == 1 ? 0 : pack_member(pk.wblock0, pk.nm, blockIdx.x);
+  const AsmMember<DT>& a = pack_load(pk, m, sm);
+  wells_at<DT>(a.g, a.ph, a.w, a.x, a.pv, a.pd, a.dt, a.R, a.J, a.Bw, a.Cw, a.Dw, (int)(blockIdx.x - pk.wblock0[m]),
+               (int)threadIdx.x);
+}
+
+template <typename DT>
+int launch_assemble_packed(const AsmPack<DT>& pk, cudaStream_t st) {
+  const int cb = pk.cblock0[pk.nm], wb = pk.wblock0[pk.nm];
+  if (cb == 0) return 0;
+  launch(k_cell_props<DT, kPackMax>, cb, 256, 0, st, pk);
+  launch(k_face_flux<DT, kPackMax>, cb, 256, 0, st, pk);
+  launch(k_gather<DT, kPackMax>, cb, 256, 0, st, pk);
+  if (wb > 0) launch(k_wells<DT, kPackMax>, wb, 32, 0, st, pk);
+  return 3 + (wb > 0);
+}
+
+// A pack of one simulator for its own launches (fields a kernel does not read
+// stay null).
+template <typename DT>
+AsmPack<DT, 1> pack_of_one(const Grid& g, const Phys& ph) {
+  AsmPack<DT, 1> pk{};
+  pk.nm = 1;
+  pk.cblock0[0] = 0;
+  pk.wblock0[0] = 0;
+  pk.m[0].g = g;
+  pk.m[0].ph = ph;
+  return pk;
+}
+
+template <typename DT>
+void launch_cell_props(const Grid& g, const Phys& ph, const double* phi_r, const double* x, double* pv,
+                       DT* pd, const double* Mold, double* R, DT* J, double* Mold_out, int mode,
+                       cudaStream_t st, int block) {
+  if (mode != 0) {
+    launch(k_cell_values<DT>, grid_for(g.n, block), block, 0, st, g, ph, phi_r, x, pv, pd, Mold, R, J, Mold_out,
+           mode);
+    return;
+  }
+  AsmPack<DT, 1> pk = pack_of_one<DT>(g, ph);
+  AsmMember<DT>& a = pk.m[0];
+  a.phi_r = phi_r; a.x = x; a.pv = pv; a.pd = pd; a.Mold = Mold; a.R = R; a.J = J;
+  launch(k_cell_props<DT, 1>, grid_for(g.n, block), block, 0, st, pk);
+}
+
+template <typename DT>
+void launch_face_flux(const Grid& g, const Phys& ph, const double* wL3, const double* T3, const double* x,
+                      const double* pv, const DT* pd, double dt, DT* J, double* Fbuf, cudaStream_t st, int block) {
+  AsmPack<DT, 1> pk = pack_of_one<DT>(g, ph);
+  AsmMember<DT>& a = pk.m[0];
+  a.wL3 = wL3; a.T3 = T3; a.x = x; a.pv = const_cast<double*>(pv); a.pd = const_cast<DT*>(pd); a.dt = dt;
+  a.J = J; a.Fbuf = Fbuf;
+  launch(k_face_flux<DT, 1>, grid_for(g.n, block), block, 0, st, pk);
+}
+
+template <typename DT>
+void launch_gather(const Grid& g, const double* Fbuf, double* R, DT* J, cudaStream_t st, int block) {
+  AsmPack<DT, 1> pk = pack_of_one<DT>(g, Phys{});
+  AsmMember<DT>& a = pk.m[0];
+  a.Fbuf = const_cast<double*>(Fbuf); a.R = R; a.J = J;
+  launch(k_gather<DT, 1>, grid_for(g.n, block), block, 0, st, pk);
+}
+
+template <typename DT>
+void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv, const DT* pd,
+                  double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st) {
+  if (w.nw == 0) return;
+  AsmPack<DT, 1> pk = pack_of_one<DT>(g, ph);
+  AsmMember<DT>& a = pk.m[0];
+  a.w = w; a.x = x; a.pv = const_cast<double*>(pv); a.pd = const_cast<DT*>(pd); a.dt = dt; a.R = R; a.J = J;
+  a.Bw = Bw; a.Cw = Cw; a.Dw = Dw;
+  pk.wblock0[1] = w.nw;
+  launch(k_wells<DT, 1>, w.nw, 32, 0, st, pk);
+}
+
 template void launch_cell_props<double>(const Grid&, const Phys&, const double*, const double*, double*, double*,
                                         const double*, double*, double*, double*, int, cudaStream_t, int);
 template void launch_cell_props<float>(const Grid&, const Phys&, const double*, const double*, double*, float*,
@@ -822,5 +964,8 @@ template void launch_wells<double>(const Grid&, const Phys&, const Wells&, const
                                    const double*, double, double*, double*, double*, double*, double*, cudaStream_t);
 template void launch_wells<float>(const Grid&, const Phys&, const Wells&, const double*, const double*,
                                   const float*, double, double*, float*, float*, float*, float*, cudaStream_t);
+
+template int launch_assemble_packed<double>(const AsmPack<double>&, cudaStream_t);
+template int launch_assemble_packed<float>(const AsmPack<float>&, cudaStream_t);
 
 }  // namespace pf

@@ -152,6 +152,45 @@ void launch_gather(const Grid& g, const double* Fbuf, double* R, DT* J, cudaStre
 template <typename DT>
 void launch_wells(const Grid& g, const Phys& ph, const Wells& w, const double* x, const double* pv,
                   const DT* pd, double dt, double* R, DT* J, DT* Bw, DT* Cw, DT* Dw, cudaStream_t st);
+
+// Packed assembly: the four assembly kernels of several simulators in one
+// launch each, with every cell's arithmetic that of its own simulator's
+// kernels (results bit-identical).  The members travel in the launch
+// parameters; block b of a cell kernel belongs to the member m with
+// cblock0[m] <= b < cblock0[m + 1] (256 threads per block), block b of the well
+// kernel to the member with wblock0[m] <= b < wblock0[m + 1] (one warp per well).
+constexpr int kPackMax = 24;
+template <typename DT>
+struct AsmMember {
+  Grid g;
+  Phys ph;
+  Wells w;
+  const double *phi_r, *x, *Mold, *wL3, *T3;
+  double *pv, *R, *Fbuf;
+  DT *pd, *J, *Bw, *Cw, *Dw;
+  double dt;
+};
+template <typename DT, int CAP = kPackMax>
+struct AsmPack {
+  int nm;
+  int cblock0[CAP + 1];
+  int wblock0[CAP + 1];
+  AsmMember<DT> m[CAP];
+};
+// launches the pack on st (cblock0/wblock0 filled by the caller, 256 threads
+// per cell block); returns the kernel count.  A simulator's own assembly runs
+// the same kernels on a pack of one (launch_cell_props mode 0,
+// launch_face_flux, launch_gather, launch_wells), so packed and own results
+// are the same compiled arithmetic.
+template <typename DT>
+int launch_assemble_packed(const AsmPack<DT>& pk, cudaStream_t st);
+// The assembly of n simulators (one precision) in packs of up to kPackMax on
+// stream st; the caller orders st after each simulator's stream and each
+// simulator's stream after st.  *launches (may be null): kernels launched.
+pf_status assemble_packed(pf_sim* const* sims, int n, cudaStream_t st, int* launches);
+// Routes a simulator's assembly through fn(ctx, s) (null: its own launches).
+void set_assembly_packer(pf_sim* s, pf_status (*fn)(void*, pf_sim*), void* ctx);
+cudaStream_t sim_stream(const pf_sim* s);
 void launch_well_gamma(const Grid& g, const Phys& ph, const Wells& w, const double* x,
                        const double* pv, double* gamma, cudaStream_t st);
 // out[3w + {0,1,2}] = water, oil, polymer mass rate of well w (needs a mode-2 pv).

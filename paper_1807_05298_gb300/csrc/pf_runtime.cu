@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "polyflood.h"
+#include "pf_internal.cuh"
 
 namespace {
 
@@ -156,18 +157,124 @@ pf_status pf_run_schedule(pf_sim* s, const pf_schedule* sched, int max_cuts, pf_
 // batch engine
 // ---------------------------------------------------------------------------
 
+// Packed assembly for a batch.  A member that reaches an assembly records an
+// event on its stream and queues itself; the first one to find no pack in
+// flight becomes the packer: it waits (up to the window) until every member
+// inside pf_batch_run is queued, takes the queue, orders the packer stream
+// after the queued members' events, launches the packed kernels and records
+// one event that each member's stream then waits on.  Members that arrive
+// while a pack is in flight are taken by the next packer (one of them).
+namespace {
+
+struct EventRef {
+  cudaEvent_t e = nullptr;
+  ~EventRef() {
+    if (e) cudaEventDestroy(e);  // released once its stream work completes
+  }
+};
+
+struct AsmPacker {
+  struct Req {
+    pf_sim* s = nullptr;
+    cudaEvent_t ready = nullptr;
+    std::shared_ptr<EventRef> done;
+    pf_status rc = PF_OK;
+    bool served = false;
+  };
+  cudaStream_t st = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<Req*> waiting;
+  bool busy = false;
+  int running = 0;  // members inside pf_batch_run
+  std::chrono::microseconds window{0};
+  std::map<pf_sim*, cudaEvent_t> ready;
+  int64_t packs = 0, members = 0;
+};
+
+pf_status packer_assemble(void* ctx, pf_sim* s) {
+  AsmPacker* P = static_cast<AsmPacker*>(ctx);
+  AsmPacker::Req r;
+  r.s = s;
+  const cudaStream_t ms = pf::sim_stream(s);
+  std::unique_lock<std::mutex> lk(P->mu);
+  r.ready = P->ready.at(s);
+  if (cudaEventRecord(r.ready, ms) != cudaSuccess) return rt_fail(PF_ECUDA, "packed assembly: event record");
+  P->waiting.push_back(&r);
+  P->cv.notify_all();
+  while (!r.served) {
+    if (P->busy) {
+      P->cv.wait(lk);
+      continue;
+    }
+    P->busy = true;
+    P->cv.wait_until(lk, std::chrono::steady_clock::now() + P->window,
+                     [&] { return (int)P->waiting.size() >= P->running; });
+    std::vector<AsmPacker::Req*> pack;
+    pack.swap(P->waiting);
+    lk.unlock();
+    pf_status rc = PF_OK;
+    std::vector<pf_sim*> sims;
+    for (AsmPacker::Req* q : pack) {
+      sims.push_back(q->s);
+      if (cudaStreamWaitEvent(P->st, q->ready, 0) != cudaSuccess) rc = PF_ECUDA;
+    }
+    if (rc == PF_OK) rc = pf::assemble_packed(sims.data(), (int)sims.size(), P->st, nullptr);
+    auto ev = std::make_shared<EventRef>();
+    if (rc == PF_OK && (cudaEventCreateWithFlags(&ev->e, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventRecord(ev->e, P->st) != cudaSuccess))
+      rc = PF_ECUDA;
+    lk.lock();
+    for (AsmPacker::Req* q : pack) {
+      q->done = ev;
+      q->rc = rc;
+      q->served = true;
+    }
+    P->packs += 1;
+    P->members += (int64_t)pack.size();
+    P->busy = false;
+    P->cv.notify_all();
+  }
+  std::shared_ptr<EventRef> done = std::move(r.done);
+  const pf_status rc = r.rc;
+  lk.unlock();
+  if (rc != PF_OK) return rt_fail(rc, "packed assembly failed");
+  if (cudaStreamWaitEvent(ms, done->e, 0) != cudaSuccess) return rt_fail(PF_ECUDA, "packed assembly: stream wait");
+  return PF_OK;
+}
+
+}  // namespace
+
 struct pf_batch {
   int device = 0;
   int n_threads = 1;
   std::vector<pf_sim*> sims;
   std::vector<cudaStream_t> streams;
+  AsmPacker* packer = nullptr;
 };
+
+namespace {
+
+void packing_off(pf_batch* b) {
+  AsmPacker* P = b->packer;
+  if (!P) return;
+  for (pf_sim* s : b->sims) pf::set_assembly_packer(s, nullptr, nullptr);
+  if (P->st) cudaStreamSynchronize(P->st);
+  for (auto& kv : P->ready)
+    if (kv.second) cudaEventDestroy(kv.second);
+  if (P->st) cudaStreamDestroy(P->st);
+  delete P;
+  b->packer = nullptr;
+}
+
+}  // namespace
 
 extern "C" {
 
 pf_status pf_batch_destroy(pf_batch* b) {
   if (!b) return PF_OK;
   cudaSetDevice(b->device);
+  packing_off(b);
   for (pf_sim* s : b->sims) pf_destroy(s);
   for (cudaStream_t st : b->streams) if (st) cudaStreamDestroy(st);
   delete b;
@@ -219,12 +326,22 @@ pf_status pf_batch_run(pf_batch* b, const pf_schedule* const* schedules, int max
   const int n = (int)b->sims.size();
   std::atomic<int> next{0};
   std::vector<pf_run_report> rep(n);
+  AsmPacker* P = b->packer;
   auto worker = [&]() {
     cudaSetDevice(b->device);
     for (;;) {
       const int i = next.fetch_add(1);
       if (i >= n) break;
+      if (P) {
+        std::lock_guard<std::mutex> lk(P->mu);
+        P->running += 1;
+      }
       pf_run_schedule(b->sims[i], schedules[i], max_cuts, &rep[i]);
+      if (P) {
+        std::lock_guard<std::mutex> lk(P->mu);
+        P->running -= 1;
+        P->cv.notify_all();  // a packer waiting for this member stops waiting
+      }
     }
   };
   std::vector<std::thread> th;
@@ -238,6 +355,43 @@ pf_status pf_batch_run(pf_batch* b, const pf_schedule* const* schedules, int max
   }
   if (rc != PF_OK) g_rt_error = "at least one member failed (see its report status)";
   return rc;
+}
+
+pf_status pf_batch_set_packing(pf_batch* b, int on, double window_us) {
+  if (!b || !(window_us >= 0.0)) return rt_fail(PF_EINVAL, "invalid packing arguments");
+  cudaSetDevice(b->device);
+  packing_off(b);
+  if (!on) return PF_OK;
+  AsmPacker* P = new AsmPacker();
+  b->packer = P;
+  P->window = std::chrono::microseconds((long long)window_us);
+  if (cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking) != cudaSuccess) {
+    packing_off(b);
+    return rt_fail(PF_ECUDA, "packing: stream creation failed");
+  }
+  for (pf_sim* s : b->sims) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      packing_off(b);
+      return rt_fail(PF_ECUDA, "packing: event creation failed");
+    }
+    P->ready[s] = e;
+  }
+  for (pf_sim* s : b->sims) pf::set_assembly_packer(s, packer_assemble, P);
+  return PF_OK;
+}
+
+pf_status pf_batch_packing_stats(pf_batch* b, int64_t* packs, int64_t* members) {
+  if (!b) return rt_fail(PF_EINVAL, "batch is NULL");
+  int64_t p = 0, m = 0;
+  if (b->packer) {
+    std::lock_guard<std::mutex> lk(b->packer->mu);
+    p = b->packer->packs;
+    m = b->packer->members;
+  }
+  if (packs) *packs = p;
+  if (members) *members = m;
+  return PF_OK;
 }
 
 }  // extern "C"

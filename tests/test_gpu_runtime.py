@@ -79,6 +79,52 @@ def test_batch_members_equal_alone(B, precision):
         assert np.array_equal(xa, xb)
 
 
+@pytest.mark.parametrize("precision,window_us", [(0, 0.0), (1, 0.0), (1, 2000.0)])
+def test_packed_batch_members_equal_alone(B, precision, window_us):
+    """Packed assembly (one launch per assembly kernel over the members that
+    reach an assembly together): every member's final state is bit-identical
+    to its own run alone, with no waiting window and with a window long enough
+    that the members inside the run meet at their assemblies; the packs did
+    take several members at once."""
+    scs = small_members(5)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=precision)
+    batch = B.Batch(scs, n_threads=4, packed=True, pack_window_us=window_us, **opt)
+    reps = batch.run(n_steps=3)
+    assert all(r.status == 0 and r.steps == 3 for r in reps)
+    packs, members = batch.packing_stats()
+    xs = [batch.member_x(i) for i in range(len(scs))]
+    batch.close()
+    assert packs >= 1 and members >= packs
+    if window_us > 0.0:
+        assert members > packs          # some packs held more than one member
+    for sc, xb in zip(scs, xs):
+        xa = alone(B, sc, 3, **opt)
+        assert np.array_equal(xa, xb)
+
+
+def test_packing_turned_off_between_runs(B):
+    """Two batch runs, the first packed and the second with packing turned
+    off (the members' own launches again): each member ends where the same
+    two runs of it alone end, bit for bit, and the stats reset."""
+    scs = small_members(3)
+    opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=B.PF_PREC_MIXED)
+    batch = B.Batch(scs, n_threads=3, packed=True, pack_window_us=5000.0, **opt)
+    assert all(r.status == 0 for r in batch.run(n_steps=2))
+    assert batch.packing_stats()[0] >= 1
+    batch.set_packing(False)
+    assert batch.packing_stats() == (0, 0)
+    assert all(r.status == 0 for r in batch.run(n_steps=2))
+    xs = [batch.member_x(i) for i in range(len(scs))]
+    batch.close()
+    for sc, xb in zip(scs, xs):
+        sim = B.Simulator(sc, **opt)
+        for _ in range(2):
+            B.run_schedule(sim, B.Schedule(sc["schedule"], 2))
+        xa = sim.get_x()
+        sim.close()
+        assert np.array_equal(xa, xb)
+
+
 def test_server_same_alone_and_in_mix_and_admission(B):
     scs = small_members(6, n_steps=2)
     opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=B.PF_PREC_MIXED)

@@ -168,8 +168,8 @@ def test_darcy_pressure_drop_series(mixing, omega):
 # ---------------------------------------------------------------------------
 
 def test_static_wellbore_in_a_water_column_does_not_flow():
-    """Sec. 2.4, eqs. (ssw:Q) and (ssw:dp): a producer perforated through a
-    water-filled column at rest, held at the static wellbore pressure of its
+    """Sec. 2.4, the perforation rate and the hydrostatic wellbore: a producer
+    perforated through a water-filled column at rest, held at the static wellbore pressure of its
     top perforation, draws nothing from any perforation: the wellbore gradient
     gamma of a producer is the mobility-weighted mixture density (here water)
     times g, and the perforation pressures shift by gamma (z_m - z_b).  The same
