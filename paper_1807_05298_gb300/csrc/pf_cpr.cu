@@ -50,17 +50,19 @@ __device__ __forceinline__ bool nbr(const Dims& d, int x, int y, int z, int s, l
 #define GSTRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-// A_p from the P columns of the oil and water rows of J
+// A_p from the P columns of the oil and water rows of J, in the hierarchy's
+// precision (the FP32 form reads FP32 J: no FP64 unit time)
 template <typename T>
 __global__ void __launch_bounds__(256) k_extract_pressure(long long n, const T* __restrict__ J, T* __restrict__ A,
                                                           T* __restrict__ dinv, double w_o, double w_w) {
   PF_PDL_ENTRY();
+  const T wo = (T)w_o, ww = (T)w_w;
   GSTRIDE(i, n) {
 #pragma unroll
     for (int s = 0; s < SL_COUNT; ++s) {
-      const double a = w_o * (double)J[((size_t)s * 9 + 0) * n + i] + w_w * (double)J[((size_t)s * 9 + 3) * n + i];
-      A[(size_t)s * n + i] = (T)a;
-      if (s == SL_D) dinv[i] = (T)(1.0 / a);
+      const T a = wo * J[((size_t)s * 9 + 0) * n + i] + ww * J[((size_t)s * 9 + 3) * n + i];
+      A[(size_t)s * n + i] = a;
+      if (s == SL_D) dinv[i] = (T)1 / a;
     }
   }
 }
