@@ -337,11 +337,12 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const double To = T * ph.inv_mu_o;
   F[0] = To * kro * rho_o * dPo;
   {
+    // d(rho dPhi)/dP_L = wL rho'_L (dPhi - g dz rho) - rho, and the H side with
+    // +rho: the averaged density enters dPhi once more through g dz
     const DT Tk = (DT)(To * kro);
-    const DT ddPL = (DT)(-1.0) - (DT)gdz * (DT)wL * da.drho_o;
-    const DT ddPH = (DT)(1.0) - (DT)gdz * (DT)wH * db.drho_o;
-    dL[0] = Tk * ((DT)wL * da.drho_o * (DT)dPo + (DT)rho_o * ddPL);
-    dH[0] = Tk * ((DT)wH * db.drho_o * (DT)dPo + (DT)rho_o * ddPH);
+    const DT qo = (DT)dPo - (DT)gdz * (DT)rho_o;
+    dL[0] = Tk * ((DT)wL * da.drho_o * qo - (DT)rho_o);
+    dH[0] = Tk * ((DT)wH * db.drho_o * qo + (DT)rho_o);
     const DT dS = (DT)To * dkro * (DT)(rho_o * dPo);
     dL[1] = upHo ? (DT)0 : dS;
     dH[1] = upHo ? dS : (DT)0;
@@ -370,11 +371,13 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const double cf = Cu * ph.inv_rho_w;
   F[1] = T * mw * A;
   F[2] = T * mp * A * cf;
-  // dA/d(P_L, S_L, P_H, S_H)
-  const DT dA_PL = (DT)wL * da.drho_wP * (DT)dPw + (DT)rho_w * ((DT)(-1.0) - (DT)gdz * (DT)wL * da.drho_wP);
-  const DT dA_SL = (DT)wL * da.drho_wS * (DT)dPw + (DT)rho_w * (-da.dPw_S - (DT)gdz * (DT)wL * da.drho_wS);
-  const DT dA_PH = (DT)wH * db.drho_wP * (DT)dPw + (DT)rho_w * ((DT)(1.0) - (DT)gdz * (DT)wH * db.drho_wP);
-  const DT dA_SH = (DT)wH * db.drho_wS * (DT)dPw + (DT)rho_w * (db.dPw_S - (DT)gdz * (DT)wH * db.drho_wS);
+  // dA/d(P_L, S_L, P_H, S_H), A = rho_w dPhi_w, with qw = dPhi_w - g dz rho_w
+  // as for the oil phase
+  const DT qw = (DT)dPw - (DT)gdz * (DT)rho_w;
+  const DT dA_PL = (DT)wL * da.drho_wP * qw - (DT)rho_w;
+  const DT dA_SL = (DT)wL * da.drho_wS * qw - (DT)rho_w * da.dPw_S;
+  const DT dA_PH = (DT)wH * db.drho_wP * qw + (DT)rho_w;
+  const DT dA_SH = (DT)wH * db.drho_wS * qw + (DT)rho_w * db.dPw_S;
   const DT Tmw = (DT)(T * mw), Tmp = (DT)(T * mp * cf);
   // pressure and saturation columns through A
   dL[3] = Tmw * dA_PL;
