@@ -109,6 +109,9 @@ def test_packing_turned_off_between_runs(B):
     scs = small_members(3)
     opt = dict(precond=B.PF_PC_CPR, use_forcing=1, newton_tol=1e-8, precision=B.PF_PREC_MIXED)
     batch = B.Batch(scs, n_threads=3, packed=True, pack_window_us=5000.0, **opt)
+    with pytest.raises(B.PfError):
+        batch.set_packing(True, -1.0)             # a negative window is rejected (packing stays as it was)
+    batch.set_packing(True, 5000.0)               # turning it on again replaces the packer
     assert all(r.status == 0 for r in batch.run(n_steps=2))
     assert batch.packing_stats()[0] >= 1
     batch.set_packing(False)
