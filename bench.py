@@ -228,7 +228,7 @@ def solver_opts(args, B, precision):
                 gmres_max_iter=300, autotune=args.autotune, amg_pre_sweeps=args.amg_pre,
                 amg_post_sweeps=args.amg_post, amg_cycle=args.amg_cycle, forcing_form=args.forcing_form,
                 stage1=STAGE1[args.stage1], amg_coarse_sweeps=args.amg_coarse, reorth_eta=args.reorth_eta,
-                krylov_lookahead=args.lookahead)
+                krylov_lookahead=args.lookahead, amg_coarse_size=args.amg_coarse_size)
 
 
 class NewtonDriver:
@@ -506,6 +506,7 @@ def run_ours(args, rank, world, dist):
             "config": {"workload": desc, "cells": n, "wells": nw, "perforations": npf, "precision": args.precision,
                        "autotune": args.autotune,
                        "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse],
+                       "amg_coarse_size": args.amg_coarse_size,
                        "reorth_eta": args.reorth_eta, "precond": args.precond, "stage1": args.stage1,
                        "pdl": args.pdl, "krylov_lookahead": args.lookahead, "gmres_restart": 30,
                        "forcing_term": f"Sec. 3.3 form {args.forcing_form}", "newton_tol": args.newton_tol,
@@ -974,6 +975,8 @@ def main():
     ap.add_argument("--amg-cycle", type=int, default=1)
     ap.add_argument("--reorth-eta", type=float, default=0.2,
                     help="second Gram-Schmidt pass when the first leaves less than this fraction of |w|")
+    ap.add_argument("--amg-coarse-size", type=int, default=32,
+                    help="cells of the coarsest pressure level, solved by a dense inverse (at most 64)")
     ap.add_argument("--amg-coarse", type=int, default=2,
                     help="smoothing sweeps on the levels below the finest (-1: as on the finest)")
     ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the kernels")

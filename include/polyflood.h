@@ -142,7 +142,7 @@ typedef struct pf_solver_opts {
   double ds_max;        /* per-iteration saturation change limit (default 0.2) */
   double dc_frac;       /* per-iteration concentration change limit as a fraction of c_ref (default 0.5) */
   int amg_pre_sweeps, amg_post_sweeps;   /* CPR pressure smoother sweeps on the finest level (default 1, 1) */
-  int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 8) */
+  int amg_coarse_size;  /* coarsen until at most this many cells, <= 64 (default 32) */
   int amg_cycle;        /* 1: V-cycle, 2: W-cycle below the finest level (default 1) */
   int autotune;         /* 1: pf_create tunes the per-cell kernels' block sizes (pf_autotune) (default 0) */
   int forcing_form;     /* which choice of the Sec. 3.3 forcing term, all restricted to [0.01, 0.1],

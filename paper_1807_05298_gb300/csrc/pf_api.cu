@@ -934,7 +934,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->dc_frac = 0.5;
   o->amg_pre_sweeps = 1;
   o->amg_post_sweeps = 1;
-  o->amg_coarse_size = 8;
+  o->amg_coarse_size = 32;
   o->amg_cycle = 1;
   o->autotune = 0;
   o->forcing_form = 3;

@@ -387,26 +387,30 @@ __global__ void __launch_bounds__(256) k_prolong_add(Dims f, Dims c, const T* __
   }
 }
 
-// Dense inverse of the coarsest stencil matrix (n <= 64): LU with partial
-// pivoting in shared memory by one block, then one column of the inverse per
-// thread.  Storage is column-major (M[c * ld + r]) so that the threads of a
-// warp, one per row, touch consecutive words.  A zero pivot sets *status and
-// leaves that column zero.
+// Dense inverse of the coarsest stencil matrix (n <= 64) by Gauss-Jordan
+// elimination in place with partial pivoting (row swaps, undone as column
+// swaps of the inverse at the end), in shared memory by one block of 1024
+// threads: each step's n x n update is spread over the whole block, so the
+// SM's FP64 lanes stay full (one thread per row would leave them nearly all
+// idle, and FP64 on one SM is slow on this part).  Step k with pivot p:
+// row k is divided by p, every other row i takes row i - a_ik (row k), and
+// column k becomes a_kk = 1/p, a_ik = -a_ik / p.  A zero pivot sets *status
+// and skips its step.  Row-major storage: M[r * kLd + c].
 constexpr int kLd = kMaxCoarse + 1;
-constexpr size_t kCoarseSmem = sizeof(double) * (2 * kMaxCoarse * kLd) + sizeof(int) * (kMaxCoarse + 1);
+constexpr size_t kCoarseSmem = sizeof(double) * (kMaxCoarse * kLd + kMaxCoarse + 1) + sizeof(int) * (kMaxCoarse + 1);
 
 template <typename T>
-__global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__ inv, int* status) {
+__global__ void __launch_bounds__(1024) k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__ inv,
+                                                         int* status) {
   PF_PDL_ENTRY();
   extern __shared__ double sm[];
-  double* M = sm;                       // [n][kLd] column-major: M[c * kLd + r]
-  double* X = sm + kMaxCoarse * kLd;     // [n][kLd] column j of the inverse: X[j * kLd + r]
-  int* perm = reinterpret_cast<int*>(X + kMaxCoarse * kLd);
-  int* piv = perm + kMaxCoarse;
+  double* M = sm;                                              // [n][kLd]
+  double* fk = sm + kMaxCoarse * kLd;                          // column k before the step, then 1 / pivot
+  int* swp = reinterpret_cast<int*>(fk + kMaxCoarse + 1);      // pivot row of each step
+  int* pivok = swp + kMaxCoarse;                               // this step's pivot is non-zero
   const int n = (int)d.n;
-  const int t = threadIdx.x;
-  for (int e = t; e < kMaxCoarse * kLd; e += blockDim.x) M[e] = 0.0;
-  if (t < n) perm[t] = t;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < kMaxCoarse * kLd; e += nt) M[e] = 0.0;
   if (t == 0) *status = 0;
   __syncthreads();
   if (t < n) {
@@ -415,16 +419,16 @@ __global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__
     M[t * kLd + t] = (double)A[t];
     for (int s = 1; s < SL_COUNT; ++s) {
       long long j;
-      if (nbr(d, x, y, z, s, j)) M[(int)j * kLd + t] = (double)A[(size_t)s * n + t];
+      if (nbr(d, x, y, z, s, j)) M[t * kLd + (int)j] = (double)A[(size_t)s * n + t];
     }
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (t < 32) {  // pivot search by one warp
+    if (t < 32) {  // pivot search by one warp: largest |a_rk|, r >= k (ties: the lower row)
       int p = k;
       double best = -1.0;
       for (int r = k + t; r < n; r += 32) {
-        const double v = fabs(M[k * kLd + r]);
+        const double v = fabs(M[r * kLd + k]);
         if (v > best) { best = v; p = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -433,46 +437,51 @@ __global__ void k_coarse_factor(Dims d, const T* __restrict__ A, T* __restrict__
         if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
       }
       if (t == 0) {
-        *piv = p;
+        swp[k] = p;
+        *pivok = best > 0.0 ? 1 : 0;
         if (!(best > 0.0)) *status = 1;
       }
     }
     __syncthreads();
-    const int p = *piv;
+    const int p = swp[k];
     if (p != k) {
-      for (int c = t; c < n; c += blockDim.x) {
-        const double tmp = M[c * kLd + k]; M[c * kLd + k] = M[c * kLd + p]; M[c * kLd + p] = tmp;
+      for (int c = t; c < n; c += nt) {
+        const double tmp = M[k * kLd + c];
+        M[k * kLd + c] = M[p * kLd + c];
+        M[p * kLd + c] = tmp;
       }
-      if (t == 0) { const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp; }
     }
     __syncthreads();
-    const double pk = M[k * kLd + k];
-    if (t > k && t < n && pk != 0.0) {
-      const double m = M[k * kLd + t] / pk;
-      M[k * kLd + t] = m;
-      for (int c = k + 1; c < n; ++c) M[c * kLd + t] -= m * M[c * kLd + k];
+    if (!*pivok) continue;  // uniform over the block
+    // one FP64 division per step (by one thread: FP64 on one SM is scarce)
+    if (t == 0) fk[kMaxCoarse] = 1.0 / M[k * kLd + k];
+    for (int i = t; i < n; i += nt) fk[i] = M[i * kLd + k];
+    __syncthreads();
+    const double rp = fk[kMaxCoarse];
+    for (int c = t; c < n; c += nt) M[k * kLd + c] = c == k ? rp : M[k * kLd + c] * rp;
+    __syncthreads();
+    for (int e = t; e < n * n; e += nt) {
+      const int i = e / n, c = e - i * n;
+      if (i == k) continue;
+      M[i * kLd + c] = c == k ? -fk[i] * rp : fnms(fk[i], M[k * kLd + c], M[i * kLd + c]);
     }
     __syncthreads();
   }
-  // column j of the inverse solves L U x = P e_j; thread j owns X[j][*]
-  if (t < n) {
-    double* xc = X + t * kLd;
-    for (int r = 0; r < n; ++r) {
-      double v = (perm[r] == t) ? 1.0 : 0.0;
-      for (int c = 0; c < r; ++c) v -= M[c * kLd + r] * xc[c];
-      xc[r] = v;
+  // (P A)^{-1} = A^{-1} P^T: undo the row swaps as column swaps, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = swp[k];
+    if (p != k) {
+      for (int r = t; r < n; r += nt) {
+        const double tmp = M[r * kLd + k];
+        M[r * kLd + k] = M[r * kLd + p];
+        M[r * kLd + p] = tmp;
+      }
     }
-    for (int r = n - 1; r >= 0; --r) {
-      double v = xc[r];
-      for (int c = r + 1; c < n; ++c) v -= M[c * kLd + r] * xc[c];
-      const double dg = M[r * kLd + r];
-      xc[r] = dg != 0.0 ? v / dg : 0.0;
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = t; e < n * n; e += blockDim.x) {
-    const int r = e / n, c = e % n;
-    inv[e] = (T)X[c * kLd + r];
+  for (int e = t; e < n * n; e += nt) {
+    const int r = e / n, c = e - r * n;
+    inv[e] = (T)M[r * kLd + c];
   }
 }
 
@@ -802,7 +811,7 @@ void setup_t(CprData& c, const void* J, cudaStream_t st, int& k) {
   }
   CprLevel& Lc = c.lev[c.nlev - 1];
   cudaFuncSetAttribute(k_coarse_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
-  launch(k_coarse_factor<T>, 1, kMaxCoarse, kCoarseSmem, st, dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
+  launch(k_coarse_factor<T>, 1, 1024, kCoarseSmem, st, dims_of(Lc), (const T*)Lc.A, (T*)c.coarse_inv,
                                                          c.coarse_status);
   k += 1;
 }
