@@ -328,43 +328,68 @@ __global__ void __launch_bounds__(256) k_rbgs_cp(Dims d, const T* __restrict__ c
   }
 }
 
+// Residual b - A x of child `child` (bits dx, dy, dz) of coarse cell (cx, cy,
+// cz), in FP64; 0 for a child outside the aggregate or the grid, and with
+// red_only for a black child.  After a pre-smoothing whose last pass is black,
+// the black residuals are zero up to rounding (that pass solved the black rows
+// for the red values it read), so only the red children carry the coarse
+// right-hand side.
+template <typename T>
+__device__ __forceinline__ double child_residual(const Dims& f, const T* __restrict__ A, const T* __restrict__ b,
+                                                 const T* __restrict__ x, int cx, int cy, int cz, int fx, int fy,
+                                                 int fz, int child, bool red_only) {
+  const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
+  if (dx >= fx || dy >= fy || dz >= fz) return 0.0;
+  const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
+  if (X >= f.nx || Y >= f.ny || Z >= f.nz) return 0.0;
+  if (red_only && ((X + Y + Z) & 1)) return 0.0;
+  const long long i = X + f.nx * (Y + (long long)f.ny * Z);
+  T ri = fnms(A[i], x[i], b[i]);
+#pragma unroll
+  for (int sl = 1; sl < SL_COUNT; ++sl) {
+    long long j;
+    if (nbr(f, X, Y, Z, sl, j)) ri = fnms(A[(size_t)sl * f.n + i], x[j], ri);
+  }
+  return (double)ri;
+}
+
 // coarse right-hand side: sum over each aggregate of the fine residual b - A x
+// (RED: the red children only, see child_residual; four lanes per coarse
+// cell, lane q taking children q and q + 4, of which at most one is red in a
+// full aggregate; otherwise eight lanes, one per child).  The lanes' values
+// are summed by a fixed xor tree, which the single-block cycle reproduces.
 // With xc (the coarse level's iterate) the first red pass of the coarse
 // level's cycle from a zero initial guess is done here too: a red coarse cell
 // gets xc = bc / a_cc (bc as stored, times the stored 1 / diagonal: the value
 // that pass would compute), so the coarse cycle starts with its black pass.
-template <typename T>
+template <typename T, bool RED>
 __global__ void __launch_bounds__(256) k_residual_restrict(Dims f, Dims c, const T* __restrict__ A,
                                                            const T* __restrict__ b, const T* __restrict__ x,
                                                            T* __restrict__ bc, T* __restrict__ xc,
                                                            const T* __restrict__ dinv_c) {
   PF_PDL_ENTRY();
+  constexpr int kLanes = RED ? 4 : 8;
   const int fx = c.nx < f.nx ? 2 : 1, fy = c.ny < f.ny ? 2 : 1, fz = c.nz < f.nz ? 2 : 1;
-  const long long total = 8 * c.n;
+  const long long total = kLanes * c.n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
     const long long t = base + threadIdx.x;
-    const long long I = t >> 3;
-    const int child = (int)(t & 7);
-    const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
+    const long long I = t / kLanes;
+    const int lane = (int)(t % kLanes);
     double r = 0.0;
-    if (t < total && dx < fx && dy < fy && dz < fz) {
+    if (t < total) {
       int cx, cy, cz;
       coords(c, I, cx, cy, cz);
-      const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
-      if (X < f.nx && Y < f.ny && Z < f.nz) {
-        const long long i = X + f.nx * (Y + (long long)f.ny * Z);
-        T ri = fnms(A[i], x[i], b[i]);
-#pragma unroll
-        for (int sl = 1; sl < SL_COUNT; ++sl) {
-          long long j;
-          if (nbr(f, X, Y, Z, sl, j)) ri = fnms(A[(size_t)sl * f.n + i], x[j], ri);
-        }
-        r = (double)ri;
-      }
+      if (RED)
+        r = child_residual<T>(f, A, b, x, cx, cy, cz, fx, fy, fz, lane, true) +
+            child_residual<T>(f, A, b, x, cx, cy, cz, fx, fy, fz, lane + 4, true);
+      else
+        r = child_residual<T>(f, A, b, x, cx, cy, cz, fx, fy, fz, lane, false);
     }
-    r = grp8_sum(r);
-    if (t < total && child == 0) {
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    if (!RED) r += __shfl_xor_sync(0xffffffffu, r, 4);
+    if (t < total && lane == 0) {
       const T bI = (T)r;
       bc[I] = bI;
       if (xc) {
@@ -603,26 +628,26 @@ __global__ void __launch_bounds__(1024) k_block_cycle(BlockLevels<T> Lp, int zer
       for (long long I = tm.tid; I < c.n; I += tm.stride) {
         int cx, cy, cz;
         coords(c, I, cx, cy, cz);
-        // the children's residuals in FP64, summed in the pairing order of
-        // the per-level kernel's 8-lane reduction: ((0+1)+(2+3))+((4+5)+(6+7))
-        auto child_res = [&](int child) -> double {
-          const int dx = child & 1, dy = (child >> 1) & 1, dz = child >> 2;
-          if (dx >= fx || dy >= fy || dz >= fz) return 0.0;
-          const int X = cx * fx + dx, Y = cy * fy + dy, Z = cz * fz + dz;
-          if (X >= d.nx || Y >= d.ny || Z >= d.nz) return 0.0;
-          const long long i = X + d.nx * (Y + (long long)d.ny * Z);
-          T r = fnms(A[i], x[i], b[i]);
-          for (int sl = 1; sl < SL_COUNT; ++sl) {
-            long long j;
-            if (nbr(d, X, Y, Z, sl, j)) r = fnms(A[(size_t)sl * d.n + i], x[j], r);
-          }
-          return (double)r;
+        // the children's residuals in FP64, summed in the order of the
+        // per-level kernel's lanes and xor tree: with pre-smoothing (its last
+        // pass black) the red children, lane q holding children q and q + 4,
+        // ((v0 + v1) + (v2 + v3)); without, ((0+1)+(2+3))+((4+5)+(6+7))
+        auto child_res = [&](int child, bool red) -> double {
+          return child_residual<T>(d, A, b, x, cx, cy, cz, fx, fy, fz, child, red);
         };
-        double lo = child_res(0) + child_res(1);
-        lo = lo + (child_res(2) + child_res(3));
-        double hi = child_res(4) + child_res(5);
-        hi = hi + (child_res(6) + child_res(7));
-        L.b[l + 1][I] = (T)(lo + hi);
+        double v;
+        if (npre > 0) {
+          const double v0 = child_res(0, true) + child_res(4, true), v1 = child_res(1, true) + child_res(5, true);
+          const double v2 = child_res(2, true) + child_res(6, true), v3 = child_res(3, true) + child_res(7, true);
+          v = (v0 + v1) + (v2 + v3);
+        } else {
+          double lo = child_res(0, false) + child_res(1, false);
+          lo = lo + (child_res(2, false) + child_res(3, false));
+          double hi = child_res(4, false) + child_res(5, false);
+          hi = hi + (child_res(6, false) + child_res(7, false));
+          v = lo + hi;
+        }
+        L.b[l + 1][I] = (T)v;
       }
       if (threadIdx.x == 0) {
         cnt[l] = 0;
@@ -773,8 +798,13 @@ bool cycle(CprData& c, int l, bool zero_init, cudaStream_t st, int& k, const Top
   CprLevel& C = c.lev[l + 1];
   const Dims dc = dims_of(C);
   const bool fold = folds_first_red(c, l + 1);
-  launch(k_residual_restrict<T>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b,
-         fold ? (T*)C.x : (T*)nullptr, (const T*)C.dinv);
+  // after pre-smoothing (its last pass black) only the red residuals count
+  if (npre > 0)
+    launch(k_residual_restrict<T, true>, grid_for(4 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b,
+           fold ? (T*)C.x : (T*)nullptr, (const T*)C.dinv);
+  else
+    launch(k_residual_restrict<T, false>, grid_for(8 * C.n, 256), 256, 0, st, d, dc, A, b, x, (T*)C.b,
+           fold ? (T*)C.x : (T*)nullptr, (const T*)C.dinv);
   k += 1;
   for (int g = 0; g < (l == 0 ? 1 : c.cycle_gamma); ++g) cycle<T>(c, l + 1, g == 0, st, k, TopOut{}, g == 0 && fold);
   if (npost == 0) {
