@@ -157,15 +157,15 @@ class ClockSampler:
 # the ncu captures summarised in profiles/; the 27M-cell figures are the 2M-cell
 # captures scaled by the number of 3x3 blocks (traffic grows with them).
 _BLOCKS_C3, _BLOCKS_C3S = 188_250_000, 14_008_500     # 3x3 blocks of 600x450x100 and 300x225x30
-SPMV_TRAFFIC = {("c3s", "fp64"): 1000.14e6, ("c3s", "mixed"): 520.65e6,
-                ("c3", "fp64"): 1000.14e6 * _BLOCKS_C3 / _BLOCKS_C3S,
-                ("c3", "mixed"): 520.65e6 * _BLOCKS_C3 / _BLOCKS_C3S}
+SPMV_TRAFFIC = {("c3s", "fp64"): 1000.17e6, ("c3s", "mixed"): 520.75e6,
+                ("c3", "fp64"): 1000.17e6 * _BLOCKS_C3 / _BLOCKS_C3S,
+                ("c3", "mixed"): 520.75e6 * _BLOCKS_C3 / _BLOCKS_C3S}
 # DRAM traffic per CPR-FP preconditioner apply (summed over the apply's
 # kernels) from the ncu captures summarised in profiles/ (300x225x30; the
 # 600x450x100 figures scale its bytes per cell by the cells); None where no
 # capture of the current kernels exists.
-PRECOND_TRAFFIC = {("c3", "fp64"): 1284.4 * 27_000_000, ("c3", "mixed"): 466.4 * 27_000_000,
-                   ("c3s", "fp64"): 2600.9e6, ("c3s", "mixed"): 944.4e6}
+PRECOND_TRAFFIC = {("c3", "fp64"): 1359.8 * 27_000_000, ("c3", "mixed"): 466.4 * 27_000_000,
+                   ("c3s", "fp64"): 2753.6e6, ("c3s", "mixed"): 944.5e6}
 
 
 def max_over_ranks(values, dist, device="cpu"):
