@@ -158,14 +158,18 @@ __device__ __forceinline__ void eval_cell(const Phys& ph, double phi_r, double P
   if (alpha < 0.0) { alpha = 0.0; dalpha = 0; }
   if (alpha > 1.0) { alpha = 1.0; dalpha = 0; }
   // 1/mu_w,e = alpha/mu_p,e + (1-alpha)/mu_w,partial, with one reciprocal per
-  // viscosity (both are mu_m when omega = 1)
+  // viscosity.  With omega = 1 both are mu_m, so 1/mu_w,e = 1/mu_m: the
+  // effective viscosities are the mixture's, exactly (no reciprocal at all)
+  if (ph.omega == 1.0) {
+    c.mu_we = mu_m;
+    c.dmu_we = dmu_m;
+    c.mu_pe = mu_m;
+    c.dmu_pe = dmu_m;
+    return;
+  }
   double mu_pe, mu_wp, rpe, rwp;
   DT dmu_pe, dmu_wp;
-  if (ph.omega == 1.0) {
-    mu_pe = mu_m; dmu_pe = dmu_m; mu_wp = mu_m; dmu_wp = dmu_m;
-    rpe = 1.0 / mu_m;
-    rwp = rpe;
-  } else {
+  {
     const double mo = pow(mu_m, ph.omega);
     const DT dmo = (DT)ph.omega * (DT)mo / (DT)mu_m * dmu_m;
     mu_pe = mo * ph.mu_p0_pow; dmu_pe = dmo * (DT)ph.mu_p0_pow;
@@ -361,16 +365,18 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   const double mu_we = wL * a.mu_we + wH * b.mu_we;
   const double mu_pe = wL * a.mu_pe + wH * b.mu_pe;
   const double A = rho_w * dPw;
-  // two FP64 divisions per face, one when the two effective viscosities are
-  // equal (omega = 1: mu_w,e = mu_p,e = mu_m); 1/mu and 1/R_k follow by
-  // multiplication
-  const double irw = 1.0 / (Rk * mu_we), irp = mu_pe == mu_we ? irw : 1.0 / (Rk * mu_pe);
+  // two FP64 divisions per face; with omega = 1 (mu_p,e = mu_w,e = mu_m in
+  // every cell, so on every face) one, and the polymer flux and its
+  // derivatives are the water ones times c / rho_w,ref; 1/mu and 1/R_k follow
+  // by multiplication
+  const bool tl1 = ph.omega == 1.0;  // the same for every thread
+  const double irw = 1.0 / (Rk * mu_we), irp = tl1 ? irw : 1.0 / (Rk * mu_pe);
   const double inv_mu_we = Rk * irw, inv_mu_pe = Rk * irp, inv_Rk = mu_we * irw;
   const double mw = krw * irw;
   const double mp = krw * irp;
   const double cf = Cu * ph.inv_rho_w;
   F[1] = T * mw * A;
-  F[2] = T * mp * A * cf;
+  F[2] = tl1 ? F[1] * cf : T * mp * A * cf;
   // dA/d(P_L, S_L, P_H, S_H), A = rho_w dPhi_w, with qw = dPhi_w - g dz rho_w
   // as for the oil phase
   const DT qw = (DT)dPw - (DT)gdz * (DT)rho_w;
@@ -390,16 +396,26 @@ __device__ __forceinline__ void face_flux(const Phys& ph, double T, double gdz, 
   dH[7] = Tmp * dA_SH;
   // concentration columns through the averaged viscosities
   const DT TA = (DT)(T * A);
-  const DT cw = -TA * (DT)(mw * inv_mu_we), cp = -TA * (DT)(mp * cf * inv_mu_pe);
+  const DT cw = -TA * (DT)(mw * inv_mu_we);
   dL[5] = cw * (DT)wL * da.dmu_we;
   dH[5] = cw * (DT)wH * db.dmu_we;
-  dL[8] = cp * (DT)wL * da.dmu_pe;
-  dH[8] = cp * (DT)wH * db.dmu_pe;
   // upstream cell: k_rw (saturation), R_k and the carried concentration
   const DT dFw_S = TA * dkrw * (DT)irw;
-  const DT dFp_S = TA * (DT)cf * dkrw * (DT)irp;
   const DT dFw_C = -TA * (DT)(mw * inv_Rk) * dRk;
-  const DT dFp_C = TA * ((DT)(mp * cf * inv_Rk) * (-dRk) + (DT)(mp * ph.inv_rho_w));
+  DT dFp_S, dFp_C;
+  if (tl1) {
+    const DT cfd = (DT)cf;
+    dL[8] = dL[5] * cfd;
+    dH[8] = dH[5] * cfd;
+    dFp_S = dFw_S * cfd;
+    dFp_C = cfd * dFw_C + TA * (DT)(mw * ph.inv_rho_w);
+  } else {
+    const DT cp = -TA * (DT)(mp * cf * inv_mu_pe);
+    dL[8] = cp * (DT)wL * da.dmu_pe;
+    dH[8] = cp * (DT)wH * db.dmu_pe;
+    dFp_S = TA * (DT)cf * dkrw * (DT)irp;
+    dFp_C = TA * ((DT)(mp * cf * inv_Rk) * (-dRk) + (DT)(mp * ph.inv_rho_w));
+  }
   if (upHw) {
     dH[4] += dFw_S; dH[7] += dFp_S; dH[5] += dFw_C; dH[8] += dFp_C;
   } else {

@@ -757,3 +757,33 @@ def test_newton_gives_up_on_runaway_iterates():
     assert rec_on == rec_off[:len(rec_on)]
     _, _, hist = M.run(sc)
     assert hist[0]["cuts"] >= 1 and abs(sum(hist[0]["substeps"]) - 300.0 * DAY) <= 1e-6 * DAY
+
+
+@pytest.mark.parametrize("mixing", [0, 1])
+def test_todd_longstaff_limits(mixing):
+    """Sec. 2.3, the Todd-Longstaff limits of the effective viscosities, for
+    either mixing rule: full mixing (omega = 1) gives both phases the
+    mixture's viscosity, mu_p,e = mu_w,e = mu_m (so the GPU path may use mu_m
+    directly); no mixing (omega = 0) leaves the polymer solution at mu_p0 and
+    gives the water its own viscosity blended by the harmonic rule
+    1/mu_w,e = a/mu_p0 + (1 - a)/mu_w, a = C/C_ref clipped to [0, 1].  The
+    mixture viscosity is taken from the mixing rule written out here: mu_w at
+    C = 0 and mu_p0 at C = C_ref for both rules, the geometric or arithmetic
+    blend in between."""
+    mu_w, mu_p0, c_ref = 0.6 * CP, 7.0 * CP, 1.5
+    C = np.array([0.0, 0.3, 0.75, 1.2, 1.5, 1.9])
+    b = C / c_ref                      # the rules extrapolate above C_ref
+    mu_m = mu_w ** (1.0 - b) * mu_p0 ** b if mixing == 0 else b * mu_p0 + (1.0 - b) * mu_w
+    n = len(C)
+    P, S = np.full(n, 200.0 * BAR), np.full(n, 0.5)
+    ph1 = G.default_physics(mixing=mixing, omega=1.0, mu_w=mu_w, mu_p0=mu_p0, c_ref=c_ref)
+    pr = _props(ph1, P, S, C)
+    assert np.allclose(pr["mu_pe"].v, mu_m, rtol=1e-14, atol=0.0)
+    assert np.allclose(pr["mu_we"].v, mu_m, rtol=1e-14, atol=0.0)
+    # and their C-derivatives agree (the Jacobian's concentration column)
+    assert np.allclose(pr["mu_we"].d[2], pr["mu_pe"].d[2], rtol=1e-12, atol=0.0)
+    ph0 = G.default_physics(mixing=mixing, omega=0.0, mu_w=mu_w, mu_p0=mu_p0, c_ref=c_ref)
+    pr = _props(ph0, P, S, C)
+    a = np.clip(C / c_ref, 0.0, 1.0)
+    assert np.allclose(pr["mu_pe"].v, mu_p0, rtol=1e-14, atol=0.0)
+    assert np.allclose(pr["mu_we"].v, 1.0 / (a / mu_p0 + (1.0 - a) / mu_w), rtol=1e-14, atol=0.0)
