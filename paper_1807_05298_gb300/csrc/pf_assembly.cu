@@ -511,14 +511,16 @@ __device__ __forceinline__ void gather_at(const Grid& g, const double* __restric
         fs[0] -= Fd[l]; fs[1] -= Fd[n + l]; fs[2] -= Fd[2 * n + l];
         const DT* Jp = J + (size_t)(SL_XP + 2 * d) * 9 * n;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) dsum[e] += Jp[(size_t)e * n + l];
+        for (int e = 0; e < 9; ++e)
+          if (e != 2) dsum[e] += Jp[(size_t)e * n + l];  // (oil, C) is structurally zero
       }
       if (has_p) {  // face (i, i + s): i is L; R_L -= dt F; diag += -dt dF/dx_L = -J[i+s][-d]
         const long long h = i + s;
         fs[0] += Fd[i]; fs[1] += Fd[n + i]; fs[2] += Fd[2 * n + i];
         const DT* Jm = J + (size_t)(SL_XM + 2 * d) * 9 * n;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) dsum[e] += Jm[(size_t)e * n + h];
+        for (int e = 0; e < 9; ++e)
+          if (e != 2) dsum[e] += Jm[(size_t)e * n + h];
       }
     }
     R[3 * i] -= fs[0];  // Fbuf holds dt F

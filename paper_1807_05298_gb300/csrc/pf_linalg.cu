@@ -529,10 +529,32 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
   }
 }
 
+// the red cells' diagonal block inverses (the black ones come from the
+// Schur-updated blocks in k_ilu_setup_black)
+template <typename DT, typename PT>
+__global__ void __launch_bounds__(256) k_red_inverse(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+  PF_PDL_ENTRY();
+  const long long n = g.n, nq = colour_slots(g);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long i;
+    int x, y, z;
+    if (!colour_cell(g, 0, q, i, x, y, z)) continue;
+    PT a[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
+    PT inv[9];
+    inverse3(a, inv);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+  }
+}
+
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
                       double guard, const IluCompact& cp, cudaStream_t st) {
-  launch_bjacobi_setup<DT, PT>(g, w, J, Dw, Dinv, Dwinv, st);
+  launch(k_red_inverse<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv);
+  if (w.nw > 0) launch(k_bjacobi_wells<DT, PT>, grid_for(w.nw, 128), 128, 0, st, w.nw, Dw, Dwinv);
   // the black set-up also writes the compact per-colour copies the sweeps read
   const int grid = grid_for(colour_slots_host(g), 256);
   if (cp.kind == 1)
