@@ -438,6 +438,12 @@ size_t carve(pf_sim* s, char* base) {
     // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
     s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
     for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
+    // with CPR after ILU(0): the black rows' pressure combination for stage 2
+    // (18 values per black slot in the copy's type, or J's without a copy; 3
+    // for the diagonal block)
+    const bool cpr_p = s->opts.stage1 == PF_S1_ILU0 && s->opts.precond == PF_PC_CPR;
+    s->cpr.ilu_cp.p = cpr_p ? (void*)c.take<char>(18 * slots * es) : nullptr;
+    s->cpr.ilu_cp.pd = cpr_p ? (void*)c.take<char>(3 * slots * dts) : nullptr;
   }
   s->w_perf_of = c.take<int>(n);
   s->w_pwell = c.take<int>(std::max(1LL, s->npf));
@@ -545,17 +551,20 @@ pf_status spmv(pf_sim* s, const double* xin, double* y) {
 pf_status precond_setup(pf_sim* s) {
   const Wells w = wells_view(s);
   const bool ilu = s->opts.stage1 == PF_S1_ILU0;
+  if (s->opts.precond == PF_PC_CPR) cpr_weights(s->cpr, s->ph);  // read by the ILU(0) set-up below
   if (s->mixed) {
     if (ilu)
       launch_ilu_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
-                                     (float*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream);
+                                     (float*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream, s->cpr.w_o,
+                                     s->cpr.w_w);
     else
       launch_bjacobi_setup<float, float>(s->g, w, (const float*)s->J, (const float*)s->Dw, (float*)s->Dinv,
                                          (float*)s->Dwinv, s->stream);
   } else {
     if (ilu)
       launch_ilu_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
-                                       (double*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream);
+                                       (double*)s->Dwinv, s->opts.ilu_guard, s->cpr.ilu_cp, s->stream, s->cpr.w_o,
+                                       s->cpr.w_w);
     else
       launch_bjacobi_setup<double, double>(s->g, w, (const double*)s->J, (const double*)s->Dw, (double*)s->Dinv,
                                            (double*)s->Dwinv, s->stream);

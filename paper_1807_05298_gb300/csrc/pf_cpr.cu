@@ -1071,11 +1071,15 @@ pf_status cpr_init(CprData& c, const Grid&, bool mixed, const pf_solver_opts& o,
   return PF_OK;
 }
 
+void cpr_weights(CprData& c, const Phys& ph) {
+  c.w_o = 1.0 / ph.rho_o;
+  c.w_w = 1.0 / ph.rho_w;
+}
+
 void cpr_setup(CprData& c, const Grid&, const Phys& ph, const double*, const Wells&, bool mixed, const void* J,
                const void*, const void*, cudaStream_t st, int* launches) {
   int k = 0;
-  c.w_o = 1.0 / ph.rho_o;
-  c.w_w = 1.0 / ph.rho_w;
+  cpr_weights(c, ph);
   if (mixed) setup_t<float>(c, J, st, k);
   else setup_t<double>(c, J, st, k);
   *launches = k;

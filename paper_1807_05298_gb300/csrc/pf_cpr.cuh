@@ -59,6 +59,9 @@ void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, cons
 // Lays out the CPR arrays in the arena (base == nullptr: sizing only).
 void cpr_carve(CprData& c, const Grid& g, bool mixed, size_t& off, char* base);
 pf_status cpr_init(CprData& c, const Grid& g, bool mixed, const pf_solver_opts& o, cudaStream_t st);
+// the stage-2 weights w_o = 1 / rho_o,ref and w_w = 1 / rho_w,ref (the ILU(0)
+// set-up needs them before cpr_setup, for the pressure rows it precomputes)
+void cpr_weights(CprData& c, const Phys& ph);
 void cpr_setup(CprData& c, const Grid& g, const Phys& ph, const double* phi_r, const Wells& w, bool mixed,
                const void* J, const void* Bw, const void* Dw, cudaStream_t st, int* launches);
 // z = M^{-1} v.  Mixed precision runs every stage in FP32 from vf, the FP32

@@ -216,10 +216,17 @@ void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* 
 struct IluCompact {
   int kind = 0;
   void* c[2] = {nullptr, nullptr};  // red, black: [6 slots][9 entries][colour slots]
+  // the black rows' pressure combination w_o (oil row) + w_w (water row) of
+  // every block, for the CPR stage 2 (null without CPR): off-diagonal blocks
+  // [6 slots][3 columns][black slots] in the copy's type, the diagonal block
+  // [3 columns][black slots] in the preconditioner's type
+  void* p = nullptr;
+  void* pd = nullptr;
 };
+// w_o, w_w: the CPR stage-2 weights (used when cp.p is set)
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv, double guard,
-                      const IluCompact& cp, cudaStream_t st);
+                      const IluCompact& cp, cudaStream_t st, double w_o = 0.0, double w_w = 0.0);
 // f: the right-hand side, FP64 or (mixed-precision CPR) its FP32 copy
 template <typename DT, typename PT, typename OT, typename VT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const VT* f, OT* y,

@@ -353,10 +353,15 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // into cred (every red block points at exactly one black cell, so each is
 // written once; blocks that leave the grid are never read).  It reads all of
 // them for the Schur update anyway.  The oil row's polymer column is skipped
-// (structurally zero, never read).
+// (structurally zero, never read).  With pc (and pdg) it also writes the
+// black row's pressure combination w_o (oil row) + w_w (water row) of each of
+// its blocks for the CPR stage 2: pc [6 slots][3 columns][slots], pdg the
+// diagonal block's [3 columns][slots] (from J, before the Schur update).
 template <typename DT, typename PT, typename CT>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
-                                                          PT guard, CT* __restrict__ cred, CT* __restrict__ cblack) {
+                                                          PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
+                                                          CT* __restrict__ pc, PT* __restrict__ pdg, PT w_o,
+                                                          PT w_w) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -367,6 +372,11 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
     PT a[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
+    if (pdg) {  // the oil row's polymer column is zero
+      pdg[q] = w_o * a[0] + w_w * a[3];
+      pdg[nq + q] = w_o * a[1] + w_w * a[4];
+      pdg[2 * nq + q] = w_w * a[5];
+    }
     const PT det0 = det3(a);
 #pragma unroll
     for (int s = 1; s < SL_COUNT; ++s) {
@@ -381,6 +391,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
       const CT zc{};
       PT T[9];  // J_bj D_j^-1 (the oil row of J_bj has no polymer column: fma2)
+      PT po0 = 0, po1 = 0;  // the oil row (columns P, S) for the pressure combination
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const DT b0r = J[((size_t)s * 9 + 3 * r) * n + i], b1r = J[((size_t)s * 9 + 3 * r + 1) * n + i];
@@ -393,6 +404,14 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
         if (r != 0) {
           b2r = J[((size_t)s * 9 + 3 * r + 2) * n + i];
           if (bl) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
+        }
+        // the pressure combination w_o (oil row) + w_w (water row) of this block
+        if (pc && r == 0) { po0 = b0; po1 = b1; }
+        if (pc && r == 1) {
+          CT* P3 = pc + (size_t)(s - 1) * 3 * nq + q;
+          P3[0] = to_ct(w_o * po0 + w_w * b0, zc);
+          P3[nq] = to_ct(w_o * po1 + w_w * b1, zc);
+          P3[2 * nq] = to_ct(w_w * (PT)b2r, zc);
         }
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
@@ -552,18 +571,22 @@ __global__ void __launch_bounds__(256) k_red_inverse(Grid g, const DT* __restric
 
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
-                      double guard, const IluCompact& cp, cudaStream_t st) {
+                      double guard, const IluCompact& cp, cudaStream_t st, double w_o, double w_w) {
   launch(k_red_inverse<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv);
   if (w.nw > 0) launch(k_bjacobi_wells<DT, PT>, grid_for(w.nw, 128), 128, 0, st, w.nw, Dw, Dwinv);
   // the black set-up also writes the compact per-colour copies the sweeps read
+  // and the pressure combination stage 2 reads
   const int grid = grid_for(colour_slots_host(g), 256);
+  const PT wo = (PT)w_o, ww = (PT)w_w;
   if (cp.kind == 1)
-    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0], (DT*)cp.c[1]);
+    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0], (DT*)cp.c[1],
+           (DT*)cp.p, (PT*)cp.pd, wo, ww);
   else if (cp.kind == 2)
     launch(k_ilu_setup_black<DT, PT, __nv_bfloat16>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
-           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1]);
+           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww);
   else
-    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr, (DT*)nullptr);
+    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr, (DT*)nullptr,
+           (DT*)cp.p, (PT*)cp.pd, wo, ww);
 }
 
 template <typename DT, typename PT, typename OT, typename VT>
@@ -595,21 +618,23 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
 // b0 = w_o (v - J y)_oil + w_w (v - J y)_water.  The red sweep, the last one,
 // solved the red rows' cell part exactly, D_r y_r + sum_b J_rb y_b = v_r with
 // the off-diagonal blocks it read, so a red row's residual is its well column
-// alone, -B y_w (up to rounding).  The black rows are formed in full, the same
-// products in the same order as the plain stage 2, with the off-diagonal
-// blocks from the black compact copy when the sweeps read one (COMPACT; the
-// diagonal block always from J).  Threads [0, nq) take the black cells and
-// [nq, 2 nq) the red ones, so the black threads of a warp run together.
-// With x0 the red threads also do the multigrid cycle's first pass on the
-// finest pressure level, from its zero initial guess: x0 = b0 / a_ii (b0 times
-// the stored 1 / diagonal, d0[q] of the red per-colour copy when d0_slot,
-// else d0[i]).
+// alone, -B y_w (up to rounding).  The black rows are formed in full: with
+// COMPACT from the pressure combination w_o (oil row) + w_w (water row) of
+// each block, precomputed by the ILU(0) set-up per black colour slot (Pc, the
+// off-diagonal blocks in the copy's type or J's; Pd, the diagonal block), so
+// b0 = (w_o v_o + w_w v_w) - sum of the combined rows times y, three
+// multiply-adds per block instead of five; otherwise from J's oil and water
+// rows.  Threads [0, nq) take the black cells and [nq, 2 nq) the red ones, so
+// the black threads of a warp run together.  With x0 the red threads also do
+// the multigrid cycle's first pass on the finest pressure level, from its
+// zero initial guess: x0 = b0 / a_ii (b0 times the stored 1 / diagonal, d0[q]
+// of the red per-colour copy when d0_slot, else d0[i]).
 template <typename T, typename BT, bool COMPACT, typename VT>
 __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T* __restrict__ J,
-                                                    const BT* __restrict__ Cb, const T* __restrict__ Bw,
-                                                    const T* __restrict__ y, const VT* __restrict__ v, T w_o,
-                                                    T w_w, T* __restrict__ b0, T* __restrict__ x0,
-                                                    const T* __restrict__ d0, int d0_slot) {
+                                                    const BT* __restrict__ Pc, const T* __restrict__ Pd,
+                                                    const T* __restrict__ Bw, const T* __restrict__ y,
+                                                    const VT* __restrict__ v, T w_o, T w_w, T* __restrict__ b0,
+                                                    T* __restrict__ x0, const T* __restrict__ d0, int d0_slot) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * nq;
@@ -620,21 +645,31 @@ __global__ void __launch_bounds__(256, 4) k_stage2_ilu(Grid g, Wells w, const T*
     int x, yy, z;
     if (!colour_cell(g, colour, q, i, x, yy, z)) continue;
     T r = 0;
-    if (colour == 1) {
-      const T* D = J + i;
+    if (colour == 1 && COMPACT) {
       const T d0 = y[3 * i], d1 = y[3 * i + 1], d2 = y[3 * i + 2];
-      T t0 = fma2(D[0], D[n], d0, d1, (T)0);  // oil row: no polymer column
-      T t1 = fma3(D[3 * n], D[4 * n], D[5 * n], d0, d1, d2, (T)0);
+      T t = fma3(Pd[q], Pd[nq + q], Pd[2 * nq + q], d0, d1, d2, (T)0);
       const T pz{};
 #pragma unroll
       for (int s = 1; s < SL_COUNT; ++s) {
         long long c;
         if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
-        const BT* B = COMPACT ? Cb + (size_t)(s - 1) * 9 * nq + q : (const BT*)J + (size_t)s * 9 * n + i;
-        const long long m = COMPACT ? nq : n;
+        const BT* B = Pc + (size_t)(s - 1) * 3 * nq + q;
+        t = fma3(as_pt(B[0], pz), as_pt(B[nq], pz), as_pt(B[2 * nq], pz), y[3 * c], y[3 * c + 1], y[3 * c + 2], t);
+      }
+      r = (w_o * (T)v[3 * i] + w_w * (T)v[3 * i + 1]) - t;
+    } else if (colour == 1) {
+      const T* D = J + i;
+      const T d0 = y[3 * i], d1 = y[3 * i + 1], d2 = y[3 * i + 2];
+      T t0 = fma2(D[0], D[n], d0, d1, (T)0);  // oil row: no polymer column
+      T t1 = fma3(D[3 * n], D[4 * n], D[5 * n], d0, d1, d2, (T)0);
+#pragma unroll
+      for (int s = 1; s < SL_COUNT; ++s) {
+        long long c;
+        if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
+        const T* B = J + (size_t)s * 9 * n + i;
         const T x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-        t0 = fma2(as_pt(B[0], pz), as_pt(B[m], pz), x0, x1, t0);
-        t1 = fma3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), x0, x1, x2, t1);
+        t0 = fma2(B[0], B[n], x0, x1, t0);
+        t1 = fma3(B[3 * n], B[4 * n], B[5 * n], x0, x1, x2, t1);
       }
       r = w_o * ((T)v[3 * i] - t0) + w_w * ((T)v[3 * i + 1] - t1);
     }
@@ -652,15 +687,15 @@ void launch_stage2_ilu(const Grid& g, const Wells& w, const T* J, const IluCompa
                        const VT* v, T w_o, T w_w, T* b0, T* x0, const T* d0, int d0_slot, int block,
                        cudaStream_t st) {
   const int grid = grid_for(2 * colour_slots_host(g), block);
-  if (cp.kind == 1)
-    launch(k_stage2_ilu<T, T, true, VT>, grid, block, 0, st, g, w, J, (const T*)cp.c[1], Bw, y, v, w_o, w_w, b0, x0,
-           d0, d0_slot);
-  else if (cp.kind == 2)
-    launch(k_stage2_ilu<T, __nv_bfloat16, true, VT>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.c[1], Bw,
-           y, v, w_o, w_w, b0, x0, d0, d0_slot);
+  if (cp.kind != 2 && cp.p)
+    launch(k_stage2_ilu<T, T, true, VT>, grid, block, 0, st, g, w, J, (const T*)cp.p, (const T*)cp.pd, Bw, y, v, w_o,
+           w_w, b0, x0, d0, d0_slot);
+  else if (cp.kind == 2 && cp.p)
+    launch(k_stage2_ilu<T, __nv_bfloat16, true, VT>, grid, block, 0, st, g, w, J, (const __nv_bfloat16*)cp.p,
+           (const T*)cp.pd, Bw, y, v, w_o, w_w, b0, x0, d0, d0_slot);
   else
-    launch(k_stage2_ilu<T, T, false, VT>, grid, block, 0, st, g, w, J, (const T*)nullptr, Bw, y, v, w_o, w_w, b0, x0,
-           d0, d0_slot);
+    launch(k_stage2_ilu<T, T, false, VT>, grid, block, 0, st, g, w, J, (const T*)nullptr, (const T*)nullptr, Bw, y,
+           v, w_o, w_w, b0, x0, d0, d0_slot);
 }
 
 template <typename PT>
@@ -1064,9 +1099,9 @@ template void launch_bjacobi_setup<double, double>(const Grid&, const Wells&, co
 template void launch_bjacobi_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
                                                  cudaStream_t);
 template void launch_ilu_setup<double, double>(const Grid&, const Wells&, const double*, const double*, double*,
-                                               double*, double, const IluCompact&, cudaStream_t);
+                                               double*, double, const IluCompact&, cudaStream_t, double, double);
 template void launch_ilu_setup<float, float>(const Grid&, const Wells&, const float*, const float*, float*, float*,
-                                             double, const IluCompact&, cudaStream_t);
+                                             double, const IluCompact&, cudaStream_t, double, double);
 template int launch_ilu_apply<double, double, double, double>(const Grid&, int, const double*, const double*,
                                                               const double*, const double*, double*, int,
                                                               const IluCompact&, cudaStream_t);
