@@ -625,9 +625,9 @@ def test_block_ilu0_matches_its_definition(B, shape):
 def test_compact_ilu_copies(B):
     """ilu_store: the sweeps reading a compact per-colour copy of the
     off-diagonal blocks (J's precision) give the same preconditioner output
-    bit for bit, alone and inside CPR (whose stage 2 then reads the copy for
-    the black rows); with a BF16 copy (mixed precision) the time steps still land
-    on the oracle's root."""
+    bit for bit, alone and inside CPR (whose stage 2 reads the black rows'
+    pressure combination that the set-up writes in either case); with a BF16
+    copy (mixed precision) the time steps still land on the oracle's root."""
     sc, ctl = ragged_scenario(nx=9, ny=7, nz=4)
     st = M.Setup(sc)
     rng = np.random.default_rng(12)
