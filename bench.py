@@ -456,6 +456,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream()
     sim, drv = start_sim(args, B, sc, args.precision, stream)
     n = sim.n
+    tuning = sim.tuning()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     # headline: no instrumentation inside the timed region
@@ -504,7 +505,7 @@ def run_ours(args, rank, world, dist):
             "dtype": "f64" if args.precision == "fp64" else "f64-residual/f32-jacobian",
             "data": "synthetic (seeded SplitMix64/Box-Muller inputs shaped after the paper's workloads)",
             "config": {"workload": desc, "cells": n, "wells": nw, "perforations": npf, "precision": args.precision,
-                       "autotune": args.autotune,
+                       "autotune": args.autotune, "launch_shapes": tuning,
                        "amg": [args.amg_pre, args.amg_post, args.amg_cycle, args.amg_coarse],
                        "amg_coarse_size": args.amg_coarse_size,
                        "reorth_eta": args.reorth_eta, "precond": args.precond, "stage1": args.stage1,
@@ -553,6 +554,7 @@ def sub_mixed(args, B, sc, desc, fp64_value):
     import torch
     stream = torch.cuda.Stream()
     sim, drv = start_sim(args, B, sc, "mixed", stream)
+    tuning = sim.tuning()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     dev_s, wall, krylov, launches = timed_iterations(sim, drv, args.sub_steps, stream, flush, None)
     kt = instrumented_pass(B, sim, drv, max(2, args.prof_steps // 2))
@@ -567,7 +569,7 @@ def sub_mixed(args, B, sc, desc, fp64_value):
             "ms_per_step": round(1000.0 * dev_s / args.sub_steps, 4), "workload": desc,
             "dtype": "f64-residual/f32-jacobian/bf16-f32-preconditioner",
             "krylov_iters_per_newton": round(krylov / args.sub_steps, 2), "gpu_launches": int(launches),
-            "vs_fp64_headline": round(value / fp64_value, 4),
+            "vs_fp64_headline": round(value / fp64_value, 4), "launch_shapes": tuning,
             "roofline": precond_roofline(kt, n, "mixed", hbm_peak, hbm_kind,
                                          PRECOND_TRAFFIC.get((args.workload, "mixed"))),
             "precision_check": chk}

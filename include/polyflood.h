@@ -172,7 +172,9 @@ typedef struct pf_solver_opts {
                            made at each preconditioner set-up.  -1 (default): 2 in mixed and 1 in
                            FP64 precision from 1,000,000 cells on, else 0.  Any value but 0 also
                            gives the finest multigrid smoother per-colour copies of its stencil
-                           and 1/diag (in the preconditioner's precision) */
+                           and 1/diag (in the preconditioner's precision).  In FP64 precision the
+                           copies also keep the ILU(0) diagonal block inverses per colour slot, in
+                           place of the per-cell array */
   int krylov_lookahead; /* 1 (default): while Arnoldi step j runs, enqueue step j + 1 before the host
                            reads step j's Hessenberg column, unless the residual extrapolated from
                            the previous steps says step j may meet the tolerance; 0: enqueue each
@@ -321,7 +323,9 @@ pf_status pf_kernel_timing(pf_sim* s, int which, int64_t* launches, double* tota
 /* Launch-shape tuner (not in the paper: a GB300 launch detail).  Times block
  * sizes 64, 128 and 256 for the per-cell kernels (properties, face flux,
  * gather, SpMV, stage 2, finest-level smoother) and the two- or three-launch
- * ILU(0) solve on s's own data and keeps the fastest.  The FP64 SpMV also tries one thread per block row (reported
+ * ILU(0) solve on s's own data and keeps the fastest (the smoother's block
+ * sizes and the two ILU(0) forms, timed as whole preconditioner applications,
+ * take turns over five rounds and each keeps its fastest round).  The FP64 SpMV also tries one thread per block row (reported
  * as a negative spmv: -96, -192 or -384 threads per block).  Each row's
  * arithmetic does not depend on the launch shape, so results are
  * bit-identical whatever is chosen; reduction grids are never tuned for the
@@ -332,7 +336,9 @@ typedef struct pf_tuning {
   int block_cells;  /* CPR: multigrid levels of at most this many cells (and all coarser ones) run in
                        one thread block (default 512 in FP64, 4096 in FP32; the tuner keeps it) */
   int ilu_fused;    /* ILU(0) solve in two launches, the diagonal red sweep folded into the black
-                       sweep (1), or three launches (0); the same arithmetic either way */
+                       sweep (1), or three launches (0); the same arithmetic either way.  No
+                       effect in FP64 precision, whose solve is always two launches through the
+                       set-up's products J_bj D_j^-1 */
   int cluster_cells;  /* CPR: larger levels of at most this many cells (<= 16384) run in one
                          thread-block cluster of up to 16 blocks with cluster barriers between
                          phases; 0: none.  The same arithmetic as the per-level kernels. */
@@ -344,6 +350,9 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out);
  * in [1, 65536]; ilu_fused 0 or 1; cluster_cells in [0, 16384].  Results do not depend on the shapes.  PF_EINVAL for any
  * other value. */
 pf_status pf_set_tuning(pf_sim* s, const pf_tuning* t);
+/* The launch shapes s uses now (chosen by pf_autotune, given by pf_set_tuning,
+ * or the defaults); launches nothing.  PF_EINVAL for a NULL t. */
+pf_status pf_get_tuning(const pf_sim* s, pf_tuning* t);
 /* Kernel launches issued by s so far (monotone counter). */
 pf_status pf_launch_count(const pf_sim* s, int64_t* count);
 

@@ -150,6 +150,7 @@ def lib():
             "pf_kernel_timing": ([vp, C.c_int, _i64p, _dp], C.c_int),
             "pf_autotune": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
+            "pf_get_tuning": ([vp, C.POINTER(pf_tuning)], C.c_int),
             "pf_set_programmatic_launch": ([C.c_int], C.c_int),
             "pf_inject_create_failure": ([C.c_int], C.c_int),
             "pf_apply_preconditioner": ([vp, _dp, _dp], C.c_int),
@@ -408,6 +409,11 @@ class Simulator:
     def autotune(self):
         t = pf_tuning()
         _check(lib().pf_autotune(self.h, C.byref(t)))
+        return {n: getattr(t, n) for n, _ in pf_tuning._fields_}
+
+    def tuning(self):
+        t = pf_tuning()
+        _check(lib().pf_get_tuning(self.h, C.byref(t)))
         return {n: getattr(t, n) for n, _ in pf_tuning._fields_}
 
     def set_tuning(self, **shapes):

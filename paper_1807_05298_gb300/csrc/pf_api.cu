@@ -394,7 +394,16 @@ size_t carve(pf_sim* s, char* base) {
   s->Bw = c.take<char>(3 * (size_t)std::max(1LL, s->npf) * dts);
   s->Cw = c.take<char>(3 * (size_t)std::max(1LL, s->npf) * dts);
   s->Dw = c.take<char>((size_t)std::max(1, s->nw) * dts);
-  s->Dinv = c.take<char>(9 * (size_t)n * dts);
+  // the ILU(0) block copies' kind: 0 none, 1 J's type, 2 BF16
+  int ilu_kind = s->opts.ilu_store;
+  if (ilu_kind < 0) ilu_kind = s->g.n >= 1000000 ? (s->mixed ? 2 : 1) : 0;  // automatic: pays off on large grids
+  if (s->opts.stage1 != PF_S1_ILU0) ilu_kind = 0;
+  // the block inverses by cell; in FP64 with the copies they are kept per
+  // colour slot instead (measured at 27M cells: FP64 preconditioner apply
+  // 6.30 -> 6.07 ms; in mixed precision both the fused black sweep and the
+  // set-up ran slower reading them that way, so there they stay by cell)
+  const bool inv_by_slot = ilu_kind != 0 && !s->mixed;
+  s->Dinv = inv_by_slot ? nullptr : c.take<char>(9 * (size_t)n * dts);
   s->Dwinv = c.take<char>((size_t)std::max(1, s->nw) * dts);
   s->w_ptr = c.take<int>(s->nw + 1);
   s->w_kind = c.take<int>(std::max(1, s->nw));
@@ -429,21 +438,26 @@ size_t carve(pf_sim* s, char* base) {
   s->red_counter = c.take<unsigned int>(64);
   {
     // compact ILU block copies: 2 colours x 54 values per colour slot
-    int kind = s->opts.ilu_store;
-    if (kind < 0) kind = s->g.n >= 1000000 ? (s->mixed ? 2 : 1) : 0;  // automatic: the copy pays off on large grids
-    if (s->opts.stage1 != PF_S1_ILU0) kind = 0;
+    const int kind = ilu_kind;
     const size_t es = kind == 2 ? 2 : dts;
     const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
     s->cpr.ilu_cp.kind = kind;
+    // FP64 ILU(0): the black sweep reads the set-up's J_bj D_j^-1 by black
+    // slot, in the black copy's place (also without the copies)
+    const bool tform = s->opts.stage1 == PF_S1_ILU0 && !s->mixed;
+    s->cpr.ilu_cp.tform = tform ? 1 : 0;
     // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
     s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
-    for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
+    for (int q = 0; q < 2; ++q)
+      s->cpr.ilu_cp.c[q] = (kind || (q == 1 && tform)) ? (void*)c.take<char>(54 * slots * es) : nullptr;
     // with CPR after ILU(0): the black rows' pressure combination for stage 2
     // (18 values per black slot in the copy's type, or J's without a copy; 3
     // for the diagonal block)
     const bool cpr_p = s->opts.stage1 == PF_S1_ILU0 && s->opts.precond == PF_PC_CPR;
     s->cpr.ilu_cp.p = cpr_p ? (void*)c.take<char>(18 * slots * es) : nullptr;
     s->cpr.ilu_cp.pd = cpr_p ? (void*)c.take<char>(3 * slots * dts) : nullptr;
+    // FP64 with the copies: both colours' block inverses per colour slot (red, then black)
+    s->cpr.ilu_cp.dr = inv_by_slot ? (void*)c.take<char>(18 * slots * dts) : nullptr;
   }
   s->w_perf_of = c.take<int>(n);
   s->w_pwell = c.take<int>(std::max(1LL, s->npf));
@@ -1733,6 +1747,22 @@ static int pick_from(pf_sim* s, const int* cand, int nc, F fn_of_block) {
   return best;
 }
 
+// For candidates whose times differ by a few percent (whole preconditioner
+// applications): the candidates take turns over `rounds` rounds and each
+// keeps its fastest round, so a slow stretch of the device in one round does
+// not decide the choice.
+template <typename F>
+static int pick_interleaved(pf_sim* s, const int* cand, int nc, int rounds, F fn) {
+  float tmin[8];
+  for (int q = 0; q < nc; ++q) tmin[q] = 1e30f;
+  for (int r = 0; r < rounds; ++r)
+    for (int q = 0; q < nc; ++q) tmin[q] = std::min(tmin[q], time_launch(s, [&] { fn(cand[q]); }, 3));
+  int best = nc - 1;
+  for (int q = 0; q < nc; ++q)
+    if (tmin[q] < tmin[best]) best = q;
+  return cand[best];
+}
+
 template <typename F>
 static int pick_block(pf_sim* s, F fn_of_block) {
   static const int cand[3] = {64, 128, 256};
@@ -1783,13 +1813,16 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     });
   }
   if (s->opts.precond == PF_PC_CPR) {
-    t.rbgs = pick_block(s, [&](int b) { cpr_time_rbgs0(s->cpr, s->mixed, b, st); });
+    // the finest smoother pass is short (a few microseconds on small grids): turns over five rounds
+    static const int cand_rbgs[3] = {64, 128, 256};
+    t.rbgs = pick_interleaved(s, cand_rbgs, 3, 5, [&](int b) { cpr_time_rbgs0(s->cpr, s->mixed, b, st); });
     s->cpr.block_rbgs0 = t.rbgs;
     s->cpr.block_stage2 = t.stage2;
     // whole preconditioner applications: ILU(0) solve in two or three launches
-    if (s->opts.stage1 == PF_S1_ILU0) {
+    // (FP64 has one form, through the set-up's products J_bj D_j^-1)
+    if (s->opts.stage1 == PF_S1_ILU0 && !s->cpr.ilu_cp.tform) {
       static const int cand_fused[2] = {1, 0};
-      t.ilu_fused = pick_from(s, cand_fused, 2, [&](int f) {
+      t.ilu_fused = pick_interleaved(s, cand_fused, 2, 5, [&](int f) {
         s->cpr.ilu_fused = f;
         precond_apply(s, s->b, s->dx, s->mixed ? s->Zf : nullptr);
       });
@@ -1825,6 +1858,18 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     out->cluster_cells = (int)s->cpr.cluster_cells;
     out->ilu_fused = t.ilu_fused;
   }
+  return PF_OK;
+}
+
+pf_status pf_get_tuning(const pf_sim* s, pf_tuning* t) {
+  if (!s) return fail(PF_EINVAL, "pf_sim is NULL");
+  if (!t) return fail(PF_EINVAL, "tuning is NULL");
+  const Tuning& u = s->tune;
+  t->props = u.props; t->face = u.face; t->gather = u.gather;
+  t->spmv = u.spmv; t->stage2 = u.stage2; t->rbgs = u.rbgs;
+  t->block_cells = (int)s->cpr.block_cells;
+  t->cluster_cells = (int)s->cpr.cluster_cells;
+  t->ilu_fused = s->cpr.ilu_fused;
   return PF_OK;
 }
 

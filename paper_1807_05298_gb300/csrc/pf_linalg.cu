@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -338,6 +340,20 @@ __device__ __forceinline__ bool slot_nbr(const Grid& g, int s, long long i, int 
   }
 }
 
+// colour slot of the neighbour through slot s of the cell in colour slot q at
+// column x (the neighbour has the other colour; its column is x -+ 1, or x)
+__device__ __forceinline__ long long nbr_slot(const Grid& g, int s, long long q, int x) {
+  const long long hx = (g.nx + 1) / 2;
+  switch (s) {
+    case SL_XM: return q - ((x & 1) ? 0 : 1);
+    case SL_XP: return q + (x & 1);
+    case SL_YM: return q - hx;
+    case SL_YP: return q + hx;
+    case SL_ZM: return q - hx * g.ny;
+    default: return q + hx * g.ny;
+  }
+}
+
 // storage conversions of the compact per-colour block copies (CT: the
 // Jacobian's own type, or BF16)
 __device__ __forceinline__ float to_ct(float v, float) { return v; }
@@ -346,7 +362,10 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(float v, __nv_bfloat16) { return 
 __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return __float2bfloat16_rn((float)v); }
 
 // black diagonal blocks: D'_b = D_b - sum_j J_bj D_j^-1 J_jb, then inverted;
-// the red blocks' inverses (from k_bjacobi_setup) are read, not written.
+// the red blocks' inverses (from k_red_inverse) are read, not written.  With
+// Dc (the block inverses per colour slot, red then black; null for none) the
+// red inverses are read from it and the black ones written to it, else both
+// go through Dinv by cell.
 // With cred and cblack (the compact per-colour copies of the off-diagonal
 // blocks; null for none) the kernel also writes the copies: a black cell's own
 // six blocks into cblack, and each red neighbour's block that points back at it
@@ -357,11 +376,13 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // black row's pressure combination w_o (oil row) + w_w (water row) of each of
 // its blocks for the CPR stage 2: pc [6 slots][3 columns][slots], pdg the
 // diagonal block's [3 columns][slots] (from J, before the Schur update).
+// With tform, cblack receives T = J_bj D_j^-1 (all nine entries; the oil
+// row's polymer column of T is not zero) in place of J_bj.
 template <typename DT, typename PT, typename CT>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
                                                           PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
                                                           CT* __restrict__ pc, PT* __restrict__ pdg, PT w_o,
-                                                          PT w_w) {
+                                                          PT w_w, PT* __restrict__ Dc, int tform) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -383,10 +404,10 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       long long c;
       if (!slot_nbr(g, s, i, x, y, z, c)) continue;
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
-      // the red neighbour's colour slot (for its compact copy)
-      const int cx = x + (s == SL_XM ? -1 : s == SL_XP ? 1 : 0), cy = y + (s == SL_YM ? -1 : s == SL_YP ? 1 : 0),
-                cz = z + (s == SL_ZM ? -1 : s == SL_ZP ? 1 : 0);
-      const long long qc = ((long long)cy + (long long)g.ny * cz) * ((g.nx + 1) / 2) + (cx >> 1);
+      // the red neighbour's colour slot (for its compact copies)
+      const long long qc = nbr_slot(g, s, q, x);
+      const PT* Dj = Dc ? Dc + qc : Dinv + c;  // D_j^-1
+      const long long md = Dc ? nq : n;
       CT* bl = cblack ? cblack + (size_t)(s - 1) * 9 * nq + q : nullptr;
       CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
       const CT zc{};
@@ -396,14 +417,14 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       for (int r = 0; r < 3; ++r) {
         const DT b0r = J[((size_t)s * 9 + 3 * r) * n + i], b1r = J[((size_t)s * 9 + 3 * r + 1) * n + i];
         const PT b0 = (PT)b0r, b1 = (PT)b1r;
-        if (bl) {
+        if (bl && !tform) {
           bl[(size_t)(3 * r) * nq] = to_ct(b0r, zc);
           bl[(size_t)(3 * r + 1) * nq] = to_ct(b1r, zc);
         }
         DT b2r = 0;
         if (r != 0) {
           b2r = J[((size_t)s * 9 + 3 * r + 2) * n + i];
-          if (bl) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
+          if (bl && !tform) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
         }
         // the pressure combination w_o (oil row) + w_w (water row) of this block
         if (pc && r == 0) { po0 = b0; po1 = b1; }
@@ -415,13 +436,17 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
         }
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
-          const PT d0 = Dinv[(size_t)col * n + c], d1 = Dinv[(size_t)(3 + col) * n + c];
+          const PT d0 = Dj[col * md], d1 = Dj[(3 + col) * md];
           if (r == 0) {
             T[col] = fma2(b0, b1, d0, d1, (PT)0);
           } else {
-            T[3 * r + col] = fma3(b0, b1, (PT)b2r, d0, d1, Dinv[(size_t)(6 + col) * n + c], (PT)0);
+            T[3 * r + col] = fma3(b0, b1, (PT)b2r, d0, d1, Dj[(6 + col) * md], (PT)0);
           }
         }
+      }
+      if (bl && tform) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) bl[(size_t)e * nq] = to_ct(T[e], zc);
       }
 #pragma unroll
       for (int col = 0; col < 3; ++col) {
@@ -455,15 +480,20 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
     }
     PT inv[9];
     inverse3(a, inv);
+    if (Dc) {
 #pragma unroll
-    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+      for (int e = 0; e < 9; ++e) Dc[(size_t)(9 + e) * nq + q] = inv[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+    }
   }
 }
 
 // diagonal-only first sweep: t_r = D_r^-1 f_r on the red cells, into y
 template <typename PT, typename OT, typename VT>
-__global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, const PT* __restrict__ Dinv,
-                                                      const VT* __restrict__ f, OT* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_ilu_red_diag(Grid g, const PT* __restrict__ Dinv, const VT* __restrict__ f,
+                                                      OT* __restrict__ y) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -497,12 +527,17 @@ __device__ __forceinline__ double as_pt(__nv_bfloat16 v, double) { return (doubl
 // other colour's rows.  MODE: 0 the red sweep (t_j = y_j of the black
 // neighbours, then the well rows), 1 the black sweep after k_ilu_red_diag
 // (t_j = y_j of the red neighbours), 2 the black sweep with the red diagonal
-// folded in (t_j = D_j^-1 f_j formed on the fly).  One instantiation per mode
-// keeps each launch's code (and registers) to its own path.
+// folded in (t_j = D_j^-1 f_j formed on the fly), 3 the black sweep through
+// the set-up's products T = J_bj D_j^-1 (J_bj t_j = T f_j; J is then the
+// by-slot array of T).  One instantiation per mode
+// keeps each launch's code (and registers) to its own path.  The diagonal
+// block inverses come from Dc (both colours per colour slot, red then black)
+// when it is set (modes 0 and 3, the FP64 solve), else from Dinv by cell.
 template <typename BT, typename PT, typename OT, bool COMPACT, typename VT, int MODE>
 __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* __restrict__ J,
-                                                   const PT* __restrict__ Dinv, const PT* __restrict__ Dwinv,
-                                                   const VT* __restrict__ f, OT* __restrict__ y) {
+                                                   const PT* __restrict__ Dinv, const PT* __restrict__ Dc,
+                                                   const PT* __restrict__ Dwinv, const VT* __restrict__ f,
+                                                   OT* __restrict__ y) {
   PF_PDL_ENTRY();
   constexpr int colour = MODE == 0 ? 0 : 1;
   const long long n = g.n, nq = colour_slots(g);
@@ -523,12 +558,16 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
       long long c;
       if (!slot_nbr(g, s, i, x, yy, z, c)) continue;
       PT t0, t1, t2;
-      if (MODE == 2) {
+      if (MODE == 3) {
+        t0 = (PT)f[3 * c];
+        t1 = (PT)f[3 * c + 1];
+        t2 = (PT)f[3 * c + 2];
+      } else if (MODE == 2) {
         const PT f0 = (PT)f[3 * c], f1 = (PT)f[3 * c + 1], f2 = (PT)f[3 * c + 2];
-        const PT* Dc = Dinv + c;
-        t0 = Dc[0] * f0 + Dc[n] * f1 + Dc[2 * n] * f2;
-        t1 = Dc[3 * n] * f0 + Dc[4 * n] * f1 + Dc[5 * n] * f2;
-        t2 = Dc[6 * n] * f0 + Dc[7 * n] * f1 + Dc[8 * n] * f2;
+        const PT* Dj = Dinv + c;
+        t0 = Dj[0] * f0 + Dj[n] * f1 + Dj[2 * n] * f2;
+        t1 = Dj[3 * n] * f0 + Dj[4 * n] * f1 + Dj[5 * n] * f2;
+        t2 = Dj[6 * n] * f0 + Dj[7 * n] * f1 + Dj[8 * n] * f2;
       } else {
         t0 = (PT)y[3 * c];
         t1 = (PT)y[3 * c + 1];
@@ -537,21 +576,29 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
       const BT* B = COMPACT ? J + (size_t)(s - 1) * 9 * nq + q : J + (size_t)s * 9 * n + i;
       const long long m = COMPACT ? nq : n;
       const PT pz{};
-      r0 = fnms2(as_pt(B[0], pz), as_pt(B[m], pz), t0, t1, r0);  // oil row: no polymer column
+      if (MODE == 3)  // T = J_bj D_j^-1: a full oil row
+        r0 = fnms3(as_pt(B[0], pz), as_pt(B[m], pz), as_pt(B[2 * m], pz), t0, t1, t2, r0);
+      else
+        r0 = fnms2(as_pt(B[0], pz), as_pt(B[m], pz), t0, t1, r0);  // oil row: no polymer column
       r1 = fnms3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), t0, t1, t2, r1);
       r2 = fnms3(as_pt(B[6 * m], pz), as_pt(B[7 * m], pz), as_pt(B[8 * m], pz), t0, t1, t2, r2);
     }
-    const PT* D = Dinv + i;
-    y[3 * i] = (OT)(D[0] * r0 + D[n] * r1 + D[2 * n] * r2);
-    y[3 * i + 1] = (OT)(D[3 * n] * r0 + D[4 * n] * r1 + D[5 * n] * r2);
-    y[3 * i + 2] = (OT)(D[6 * n] * r0 + D[7 * n] * r1 + D[8 * n] * r2);
+    constexpr bool dslot = MODE == 0 || MODE == 3;  // the modes that run with the per-slot inverses
+    const PT* D = dslot && Dc ? Dc + (size_t)colour * 9 * nq + q : Dinv + i;
+    const long long md = dslot && Dc ? nq : n;
+    y[3 * i] = (OT)(D[0] * r0 + D[md] * r1 + D[2 * md] * r2);
+    y[3 * i + 1] = (OT)(D[3 * md] * r0 + D[4 * md] * r1 + D[5 * md] * r2);
+    y[3 * i + 2] = (OT)(D[6 * md] * r0 + D[7 * md] * r1 + D[8 * md] * r2);
   }
 }
 
 // the red cells' diagonal block inverses (the black ones come from the
-// Schur-updated blocks in k_ilu_setup_black)
+// Schur-updated blocks in k_ilu_setup_black), into Dinv by cell, or with the
+// per-colour copies into Dr by red colour slot instead (Dinv is then not
+// written: every reader takes the copy)
 template <typename DT, typename PT>
-__global__ void __launch_bounds__(256) k_red_inverse(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv) {
+__global__ void __launch_bounds__(256) k_red_inverse(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
+                                                     PT* __restrict__ Dr) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -564,15 +611,20 @@ __global__ void __launch_bounds__(256) k_red_inverse(Grid g, const DT* __restric
     for (int e = 0; e < 9; ++e) a[e] = (PT)J[(size_t)e * n + i];
     PT inv[9];
     inverse3(a, inv);
+    if (Dr) {
 #pragma unroll
-    for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+      for (int e = 0; e < 9; ++e) Dr[(size_t)e * nq + q] = inv[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) Dinv[(size_t)e * n + i] = inv[e];
+    }
   }
 }
 
 template <typename DT, typename PT>
 void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv, PT* Dwinv,
                       double guard, const IluCompact& cp, cudaStream_t st, double w_o, double w_w) {
-  launch(k_red_inverse<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv);
+  launch(k_red_inverse<DT, PT>, grid_for(colour_slots_host(g), 256), 256, 0, st, g, J, Dinv, (PT*)cp.dr);
   if (w.nw > 0) launch(k_bjacobi_wells<DT, PT>, grid_for(w.nw, 128), 128, 0, st, w.nw, Dw, Dwinv);
   // the black set-up also writes the compact per-colour copies the sweeps read
   // and the pressure combination stage 2 reads
@@ -580,36 +632,51 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
   const PT wo = (PT)w_o, ww = (PT)w_w;
   if (cp.kind == 1)
     launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0], (DT*)cp.c[1],
-           (DT*)cp.p, (PT*)cp.pd, wo, ww);
+           (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr, cp.tform);
   else if (cp.kind == 2)
     launch(k_ilu_setup_black<DT, PT, __nv_bfloat16>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
-           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww);
+           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr,
+           0);
   else
-    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr, (DT*)nullptr,
-           (DT*)cp.p, (PT*)cp.pd, wo, ww);
+    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr,
+           cp.tform ? (DT*)cp.c[1] : (DT*)nullptr, (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr, cp.tform);
 }
 
 template <typename DT, typename PT, typename OT, typename VT>
 int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const PT* Dwinv, const VT* f, OT* y,
                      int fused, const IluCompact& cp, cudaStream_t st) {
   const long long nq = colour_slots_host(g);
+  const PT* Dc = (const PT*)cp.dr;  // the block inverses per colour slot (with the copies)
+  const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
+  if constexpr (std::is_same<DT, double>::value) {
+    if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep
+      launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, (const DT*)cp.c[1], Dinv, Dc, Dwinv, f,
+             y);
+      if (cp.kind == 1)
+        launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, (const DT*)cp.c[0], Dinv, Dc, Dwinv,
+               f, y);
+      else
+        launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv,
+               f, y);
+      return 2;
+    }
+  }
   if (!fused) launch(k_ilu_red_diag<PT, OT, VT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
   // the black sweep, then the red one (with the well rows)
-  const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
   if (cp.kind == 1) {
     const DT *c0 = (const DT*)cp.c[0], *c1 = (const DT*)cp.c[1];
-    if (fused) launch(k_ilu_sweep<DT, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
-    else launch(k_ilu_sweep<DT, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
-    launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dwinv, f, y);
+    if (fused) launch(k_ilu_sweep<DT, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    else launch(k_ilu_sweep<DT, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
   } else if (cp.kind == 2) {
     const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
-    if (fused) launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
-    else launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dwinv, f, y);
-    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dwinv, f, y);
+    if (fused) launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    else launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
   } else {
-    if (fused) launch(k_ilu_sweep<DT, PT, OT, false, VT, 2>, grid1, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
-    else launch(k_ilu_sweep<DT, PT, OT, false, VT, 1>, grid1, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
-    launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, Dwinv, f, y);
+    if (fused) launch(k_ilu_sweep<DT, PT, OT, false, VT, 2>, grid1, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
+    else launch(k_ilu_sweep<DT, PT, OT, false, VT, 1>, grid1, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
+    launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
   }
   return fused ? 2 : 3;
 }

@@ -171,6 +171,7 @@ def test_autotuned_launch_shapes_give_identical_results(B, precision):
     base = alone(B, sc, 3, **opt)
     sim = B.Simulator(sc, autotune=1, **opt)
     t = sim.autotune()
+    assert sim.tuning() == t
     assert all(v in (64, 128, 256) for k, v in t.items()
                if k not in ("spmv", "block_cells", "ilu_fused", "cluster_cells"))
     assert t["ilu_fused"] in (0, 1)
