@@ -66,6 +66,12 @@ L2_BYTES = 129 * 1024 * 1024
 # mixed, BF16/FP32 storage: 190 + 330 + 180 B; 126 + 126 + 60 flop).
 PRECOND_BYTES_PER_CELL = {"fp64": 600 + 584 + 350, "mixed": 190 + 330 + 180}
 PRECOND_FLOPS_PER_CELL = 126 + 126 + 60
+# FP64 flops per cell the current apply kernels execute (interior cell): the
+# ILU(0) sweeps 117 (black 6 x 9 multiply-adds through J_bj D_j^-1 and a 3x3
+# product, red 6 x 8 and a 3x3 product, averaged over the colours), stage 2 on
+# the black rows 24, the multigrid cycle about 37 (finest level 1+1 sweeps and
+# the red-only restriction, the coarser levels 2+2 at 1/7 of the cells)
+PRECOND_KERNEL_FLOPS_PER_CELL = 117 + 24 + 37
 THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 STAGE1 = {"bjacobi": 0, "ilu0": 1}
 SPMV_KERNEL = {False: "k_spmv_cells / k_spmv_rows (FP64, well border fused)",
@@ -164,8 +170,8 @@ SPMV_TRAFFIC = {("c3s", "fp64"): 1000.17e6, ("c3s", "mixed"): 520.75e6,
 # kernels) from the ncu captures summarised in profiles/ (300x225x30; the
 # 600x450x100 figures scale its bytes per cell by the cells); None where no
 # capture of the current kernels exists.
-PRECOND_TRAFFIC = {("c3", "fp64"): 1359.8 * 27_000_000, ("c3", "mixed"): 466.4 * 27_000_000,
-                   ("c3s", "fp64"): 2753.6e6, ("c3s", "mixed"): 944.5e6}
+PRECOND_TRAFFIC = {("c3", "fp64"): 1091.9 * 27_000_000, ("c3", "mixed"): 438.0 * 27_000_000,
+                   ("c3s", "fp64"): 2211.2e6, ("c3s", "mixed"): 886.9e6}
 
 
 def max_over_ranks(values, dist, device="cpu"):
@@ -362,6 +368,12 @@ def precond_roofline(kt, ncell, precision, hbm_peak, hbm_kind, traffic=None):
         out.update(bound="alu", achieved=round(tfl, 4), peak=round(FP64_PEAK_TFLOPS, 4), unit="TFLOP/s (FP64)",
                    frac=round(tfl / FP64_PEAK_TFLOPS, 4),
                    peak_kind="FP64 rate from unit counts and clocks: 152 SMs x 2070 MHz x 4 flop/clk")
+        # the same time against the flops the kernels execute (fewer than the survey's count)
+        kfl = PRECOND_KERNEL_FLOPS_PER_CELL * ncell
+        out["kernel_count"] = {"flops_per_cell": PRECOND_KERNEL_FLOPS_PER_CELL, "flops": kfl,
+                               "achieved": round(kfl / t / 1e12, 4),
+                               "frac": round(kfl / t / 1e12 / FP64_PEAK_TFLOPS, 4),
+                               "traffic_frac": round(traffic / t / 1e9 / hbm_peak, 4) if traffic else None}
     else:
         out.update(bound="hbm", achieved=round(gbs, 1), peak=hbm_peak, unit="GB/s", frac=round(gbs / hbm_peak, 4),
                    peak_kind=hbm_kind)

@@ -442,14 +442,14 @@ size_t carve(pf_sim* s, char* base) {
     const size_t es = kind == 2 ? 2 : dts;
     const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
     s->cpr.ilu_cp.kind = kind;
-    // FP64 ILU(0): the black sweep reads the set-up's J_bj D_j^-1 by black
-    // slot, in the black copy's place (also without the copies)
-    const bool tform = s->opts.stage1 == PF_S1_ILU0 && !s->mixed;
-    s->cpr.ilu_cp.tform = tform ? 1 : 0;
+    // FP64 with the copies: the black copy holds the set-up's J_bj D_j^-1
+    // and the black sweep reads it (without the copies the extra array cost
+    // more in L2 residency than it saved: 100k cells, preconditioner apply
+    // 123.7 -> 130 us)
+    s->cpr.ilu_cp.tform = inv_by_slot ? 1 : 0;
     // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
     s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
-    for (int q = 0; q < 2; ++q)
-      s->cpr.ilu_cp.c[q] = (kind || (q == 1 && tform)) ? (void*)c.take<char>(54 * slots * es) : nullptr;
+    for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
     // with CPR after ILU(0): the black rows' pressure combination for stage 2
     // (18 values per black slot in the copy's type, or J's without a copy; 3
     // for the diagonal block)
@@ -1813,13 +1813,19 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     });
   }
   if (s->opts.precond == PF_PC_CPR) {
-    // the finest smoother pass is short (a few microseconds on small grids): turns over five rounds
-    static const int cand_rbgs[3] = {64, 128, 256};
-    t.rbgs = pick_interleaved(s, cand_rbgs, 3, 5, [&](int b) { cpr_time_rbgs0(s->cpr, s->mixed, b, st); });
-    s->cpr.block_rbgs0 = t.rbgs;
+    // the finest smoother's block size, timed as whole preconditioner
+    // applications (on small grids one smoother pass takes a few microseconds,
+    // about what it takes to enqueue it, so timing the pass alone measures the
+    // enqueueing), in turns over five rounds
     s->cpr.block_stage2 = t.stage2;
+    static const int cand_rbgs[3] = {64, 128, 256};
+    t.rbgs = pick_interleaved(s, cand_rbgs, 3, 5, [&](int b) {
+      s->cpr.block_rbgs0 = b;
+      precond_apply(s, s->b, s->dx, s->mixed ? s->Zf : nullptr);
+    });
+    s->cpr.block_rbgs0 = t.rbgs;
     // whole preconditioner applications: ILU(0) solve in two or three launches
-    // (FP64 has one form, through the set-up's products J_bj D_j^-1)
+    // (FP64 with the copies has one form, through the set-up's products J_bj D_j^-1)
     if (s->opts.stage1 == PF_S1_ILU0 && !s->cpr.ilu_cp.tform) {
       static const int cand_fused[2] = {1, 0};
       t.ilu_fused = pick_interleaved(s, cand_fused, 2, 5, [&](int f) {

@@ -987,34 +987,6 @@ void apply_t(CprData& c, const Grid& g, const Wells& w, const void* J, const voi
 
 }  // namespace
 
-void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st) {
-  CprLevel& L = c.lev[0];
-  const Dims d = dims_of(L);
-  const bool two = L.n >= kTwoSlotCells;  // as in the cycle's plain passes
-  const long long np = two ? (long long)((((L.nx + 1) / 2) + 1) / 2) * L.ny * L.nz
-                           : ((long long)(L.nx + 1) / 2) * L.ny * L.nz;
-  const int grid = grid_for(np, block);
-  if (mixed) {
-    const float *cp = (const float*)c.rb_cp[0], *A = (const float*)L.A, *di = (const float*)L.dinv;
-    const float* b = (const float*)L.b;
-    float* x = (float*)L.x;
-    const float* none = nullptr;
-    if (cp) launch(two ? k_rbgs_cp<float, false, 2> : k_rbgs_cp<float, false, 1>, grid, block, 0, st, d, cp, b, x,
-                   0, 0, none, Dims{}, TopOut{});
-    else launch(two ? k_rbgs<float, false, 2> : k_rbgs<float, false, 1>, grid, block, 0, st, d, A, di, b, x, 0, 0,
-                none, Dims{}, TopOut{});
-  } else {
-    const double *cp = (const double*)c.rb_cp[0], *A = (const double*)L.A, *di = (const double*)L.dinv;
-    const double* b = (const double*)L.b;
-    double* x = (double*)L.x;
-    const double* none = nullptr;
-    if (cp) launch(two ? k_rbgs_cp<double, false, 2> : k_rbgs_cp<double, false, 1>, grid, block, 0, st, d, cp, b,
-                   x, 0, 0, none, Dims{}, TopOut{});
-    else launch(two ? k_rbgs<double, false, 2> : k_rbgs<double, false, 1>, grid, block, 0, st, d, A, di, b, x, 0, 0,
-                none, Dims{}, TopOut{});
-  }
-}
-
 void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
                      const double* v, double* tmp, int block, cudaStream_t st) {
   // the mixed form reads the FP32 copy of its input; any float values serve for timing

@@ -49,10 +49,8 @@ struct CprData {
   int* coarse_status = nullptr; // device flag: 1 if a zero pivot was met
 };
 
-// One launch of the finest-level smoother colour / of the FP32 stage 2 with a
-// given block size (used by the launch-shape tuner; the values computed are
-// scratch).
-void cpr_time_rbgs0(CprData& c, bool mixed, int block, cudaStream_t st);
+// One launch of stage 2 with a given block size (used by the launch-shape
+// tuner; the values computed are scratch).
 void cpr_time_stage2(CprData& c, const Grid& g, const Wells& w, bool mixed, const void* J, const void* Bw,
                      const double* v, double* tmp, int block, cudaStream_t st);
 

@@ -226,11 +226,11 @@ struct IluCompact {
   // slots] in the preconditioner's type (the red diagonal sweep reads them
   // instead of the natural-order lines that carry both colours); null: none
   void* dr = nullptr;
-  // FP64: c[1] holds the products J_bj D_j^-1 of each black cell's six blocks
-  // with its red neighbours' inverses (formed by the set-up for the Schur
-  // update anyway; allocated with or without the copies), and the solve is
-  // two launches: the black sweep takes f_j of the red neighbours through
-  // them, so there is no diagonal red sweep
+  // FP64 with the copies: c[1] holds the products J_bj D_j^-1 of each black
+  // cell's six blocks with its red neighbours' inverses (formed by the set-up
+  // for the Schur update anyway) instead of J_bj, and the solve is two
+  // launches: the black sweep takes f_j of the red neighbours through them,
+  // so there is no diagonal red sweep
   int tform = 0;
 };
 // w_o, w_w: the CPR stage-2 weights (used when cp.p is set)

@@ -376,13 +376,15 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // black row's pressure combination w_o (oil row) + w_w (water row) of each of
 // its blocks for the CPR stage 2: pc [6 slots][3 columns][slots], pdg the
 // diagonal block's [3 columns][slots] (from J, before the Schur update).
-// With tform, cblack receives T = J_bj D_j^-1 (all nine entries; the oil
-// row's polymer column of T is not zero) in place of J_bj.
-template <typename DT, typename PT, typename CT>
+// With TF (the FP64 form), cblack receives T = J_bj D_j^-1 (all nine
+// entries; the oil row's polymer column of T is not zero) in place of J_bj,
+// and Dc is read and written; without it Dc is ignored (a compile-time
+// choice: the mixed form keeps its register count).
+template <typename DT, typename PT, typename CT, bool TF>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
                                                           PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
                                                           CT* __restrict__ pc, PT* __restrict__ pdg, PT w_o,
-                                                          PT w_w, PT* __restrict__ Dc, int tform) {
+                                                          PT w_w, PT* __restrict__ Dc) {
   PF_PDL_ENTRY();
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
@@ -406,8 +408,8 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
       // the red neighbour's colour slot (for its compact copies)
       const long long qc = nbr_slot(g, s, q, x);
-      const PT* Dj = Dc ? Dc + qc : Dinv + c;  // D_j^-1
-      const long long md = Dc ? nq : n;
+      const PT* Dj = TF && Dc ? Dc + qc : Dinv + c;  // D_j^-1
+      const long long md = TF && Dc ? nq : n;
       CT* bl = cblack ? cblack + (size_t)(s - 1) * 9 * nq + q : nullptr;
       CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
       const CT zc{};
@@ -417,14 +419,14 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       for (int r = 0; r < 3; ++r) {
         const DT b0r = J[((size_t)s * 9 + 3 * r) * n + i], b1r = J[((size_t)s * 9 + 3 * r + 1) * n + i];
         const PT b0 = (PT)b0r, b1 = (PT)b1r;
-        if (bl && !tform) {
+        if (bl && !TF) {
           bl[(size_t)(3 * r) * nq] = to_ct(b0r, zc);
           bl[(size_t)(3 * r + 1) * nq] = to_ct(b1r, zc);
         }
         DT b2r = 0;
         if (r != 0) {
           b2r = J[((size_t)s * 9 + 3 * r + 2) * n + i];
-          if (bl && !tform) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
+          if (bl && !TF) bl[(size_t)(3 * r + 2) * nq] = to_ct(b2r, zc);
         }
         // the pressure combination w_o (oil row) + w_w (water row) of this block
         if (pc && r == 0) { po0 = b0; po1 = b1; }
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
           }
         }
       }
-      if (bl && tform) {
+      if (TF && bl) {
 #pragma unroll
         for (int e = 0; e < 9; ++e) bl[(size_t)e * nq] = to_ct(T[e], zc);
       }
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
     }
     PT inv[9];
     inverse3(a, inv);
-    if (Dc) {
+    if (TF && Dc) {
 #pragma unroll
       for (int e = 0; e < 9; ++e) Dc[(size_t)(9 + e) * nq + q] = inv[e];
     } else {
@@ -630,16 +632,23 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
   // and the pressure combination stage 2 reads
   const int grid = grid_for(colour_slots_host(g), 256);
   const PT wo = (PT)w_o, ww = (PT)w_w;
+  if constexpr (std::is_same<PT, double>::value) {
+    if (cp.tform) {  // T = J_bj D_j^-1 into the black copy, the inverses per colour slot
+      launch(k_ilu_setup_black<DT, PT, DT, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
+             (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr);
+      return;
+    }
+  }
   if (cp.kind == 1)
-    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0], (DT*)cp.c[1],
-           (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr, cp.tform);
+    launch(k_ilu_setup_black<DT, PT, DT, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
+           (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr);
   else if (cp.kind == 2)
-    launch(k_ilu_setup_black<DT, PT, __nv_bfloat16>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
-           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr,
-           0);
+    launch(k_ilu_setup_black<DT, PT, __nv_bfloat16, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
+           (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww,
+           (PT*)nullptr);
   else
-    launch(k_ilu_setup_black<DT, PT, DT>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr,
-           cp.tform ? (DT*)cp.c[1] : (DT*)nullptr, (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr, cp.tform);
+    launch(k_ilu_setup_black<DT, PT, DT, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr,
+           (DT*)nullptr, (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr);
 }
 
 template <typename DT, typename PT, typename OT, typename VT>
@@ -649,15 +658,11 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
   const PT* Dc = (const PT*)cp.dr;  // the block inverses per colour slot (with the copies)
   const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
   if constexpr (std::is_same<DT, double>::value) {
-    if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep
+    if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep (FP64 with the copies)
       launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, (const DT*)cp.c[1], Dinv, Dc, Dwinv, f,
              y);
-      if (cp.kind == 1)
-        launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, (const DT*)cp.c[0], Dinv, Dc, Dwinv,
-               f, y);
-      else
-        launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv,
-               f, y);
+      launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, (const DT*)cp.c[0], Dinv, Dc, Dwinv, f,
+             y);
       return 2;
     }
   }

@@ -36,11 +36,10 @@ def test_footprint_grows_with_the_grid_and_shrinks_with_precision(B):
 # per colour slot: both colours' 6 off-diagonal blocks of 9 in the copy's type, and the finest
 # stencil's 6 slots + 1/diag of each colour in the preconditioner's type; the black rows'
 # stage-2 combination (18 values) moves from the preconditioner's type (without copies) to the
-# copy's.  In FP64 the black colour's 54 values per slot (the set-up's J_bj D_j^-1) are there
-# without the copies too, and the block inverses move from by cell (9 per cell) to per colour
-# slot (9 per slot and colour).
+# copy's.  In FP64 the block inverses move from by cell (9 per cell) to per colour slot (9 per
+# slot and colour).
 @pytest.mark.parametrize("precision,store,bytes_per_slot,bytes_per_cell", [
-    (0, 1, 54 * 8 + 2 * 7 * 8 + 2 * 9 * 8, -9 * 8),       # FP64
+    (0, 1, 2 * 54 * 8 + 2 * 7 * 8 + 2 * 9 * 8, -9 * 8),   # FP64
     (1, 1, 2 * 54 * 4 + 2 * 7 * 4, 0),                    # mixed, FP32 block copies
     (1, 2, 2 * 54 * 2 + 2 * 7 * 4 + 18 * (2 - 4), 0),     # mixed, BF16 block copies
 ])
