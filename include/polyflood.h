@@ -172,12 +172,12 @@ typedef struct pf_solver_opts {
                            made at each preconditioner set-up.  -1 (default): 2 in mixed and 1 in
                            FP64 precision from 1,000,000 cells on, else 0.  Any value but 0 also
                            gives the finest multigrid smoother per-colour copies of its stencil
-                           and 1/diag (in the preconditioner's precision).  In FP64 precision the
+                           and 1/diag (in the preconditioner's precision).  The black colour's copy
+                           holds J_bj D_j^-1 (the set-up's products with the red inverses) in place
+                           of J_bj, so the solve needs no diagonal red sweep; it then differs from
+                           the solve without the copies in rounding only.  In FP64 precision the
                            copies also keep the ILU(0) diagonal block inverses per colour slot, in
-                           place of the per-cell array, and the black colour's copy holds J_bj D_j^-1
-                           (the set-up's products with the red inverses) in place of J_bj, so the
-                           solve needs no diagonal red sweep; it then differs from the solve without
-                           the copies in rounding order only */
+                           place of the per-cell array */
   int krylov_lookahead; /* 1 (default): while Arnoldi step j runs, enqueue step j + 1 before the host
                            reads step j's Hessenberg column, unless the residual extrapolated from
                            the previous steps says step j may meet the tolerance; 0: enqueue each
@@ -340,8 +340,8 @@ typedef struct pf_tuning {
                        one thread block (default 512 in FP64, 4096 in FP32; the tuner keeps it) */
   int ilu_fused;    /* ILU(0) solve in two launches, the diagonal red sweep folded into the black
                        sweep (1), or three launches (0); the same arithmetic either way.  No
-                       effect in FP64 precision with the per-colour copies (ilu_store), whose
-                       solve is always two launches through the set-up's products J_bj D_j^-1 */
+                       effect with the per-colour copies (ilu_store), where the solve is always
+                       two launches through the set-up's products J_bj D_j^-1 */
   int cluster_cells;  /* CPR: larger levels of at most this many cells (<= 16384) run in one
                          thread-block cluster of up to 16 blocks with cluster barriers between
                          phases; 0: none.  The same arithmetic as the per-level kernels. */

@@ -442,11 +442,11 @@ size_t carve(pf_sim* s, char* base) {
     const size_t es = kind == 2 ? 2 : dts;
     const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
     s->cpr.ilu_cp.kind = kind;
-    // FP64 with the copies: the black copy holds the set-up's J_bj D_j^-1
-    // and the black sweep reads it (without the copies the extra array cost
-    // more in L2 residency than it saved: 100k cells, preconditioner apply
-    // 123.7 -> 130 us)
-    s->cpr.ilu_cp.tform = inv_by_slot ? 1 : 0;
+    // with the copies: the black copy holds the set-up's J_bj D_j^-1 and the
+    // black sweep reads it (without the copies an extra array of them cost
+    // more in L2 residency than it saved: 100k cells FP64, preconditioner
+    // apply 123.7 -> 130 us)
+    s->cpr.ilu_cp.tform = kind != 0 ? 1 : 0;
     // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
     s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
     for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
@@ -1825,7 +1825,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     });
     s->cpr.block_rbgs0 = t.rbgs;
     // whole preconditioner applications: ILU(0) solve in two or three launches
-    // (FP64 with the copies has one form, through the set-up's products J_bj D_j^-1)
+    // (with the copies there is one form, through the set-up's products J_bj D_j^-1)
     if (s->opts.stage1 == PF_S1_ILU0 && !s->cpr.ilu_cp.tform) {
       static const int cand_fused[2] = {1, 0};
       t.ilu_fused = pick_interleaved(s, cand_fused, 2, 5, [&](int f) {

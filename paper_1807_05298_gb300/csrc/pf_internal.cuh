@@ -226,7 +226,7 @@ struct IluCompact {
   // slots] in the preconditioner's type (the red diagonal sweep reads them
   // instead of the natural-order lines that carry both colours); null: none
   void* dr = nullptr;
-  // FP64 with the copies: c[1] holds the products J_bj D_j^-1 of each black
+  // with the copies: c[1] holds the products J_bj D_j^-1 of each black
   // cell's six blocks with its red neighbours' inverses (formed by the set-up
   // for the Schur update anyway) instead of J_bj, and the solve is two
   // launches: the black sweep takes f_j of the red neighbours through them,

@@ -376,16 +376,17 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // black row's pressure combination w_o (oil row) + w_w (water row) of each of
 // its blocks for the CPR stage 2: pc [6 slots][3 columns][slots], pdg the
 // diagonal block's [3 columns][slots] (from J, before the Schur update).
-// With TF (the FP64 form), cblack receives T = J_bj D_j^-1 (all nine
+// With TF (with the copies), cblack receives T = J_bj D_j^-1 (all nine
 // entries; the oil row's polymer column of T is not zero) in place of J_bj,
-// and Dc is read and written; without it Dc is ignored (a compile-time
-// choice: the mixed form keeps its register count).
+// and in FP64 Dc is read and written; otherwise Dc is ignored (compile-time
+// choices, so that each form keeps its own register count).
 template <typename DT, typename PT, typename CT, bool TF>
 __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
                                                           PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
                                                           CT* __restrict__ pc, PT* __restrict__ pdg, PT w_o,
                                                           PT w_w, PT* __restrict__ Dc) {
   PF_PDL_ENTRY();
+  constexpr bool DS = TF && std::is_same<PT, double>::value;  // the inverses per colour slot (FP64)
   const long long n = g.n, nq = colour_slots(g);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
        q += (long long)gridDim.x * blockDim.x) {
@@ -408,8 +409,8 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
       // the red neighbour's colour slot (for its compact copies)
       const long long qc = nbr_slot(g, s, q, x);
-      const PT* Dj = TF && Dc ? Dc + qc : Dinv + c;  // D_j^-1
-      const long long md = TF && Dc ? nq : n;
+      const PT* Dj = DS && Dc ? Dc + qc : Dinv + c;  // D_j^-1
+      const long long md = DS && Dc ? nq : n;
       CT* bl = cblack ? cblack + (size_t)(s - 1) * 9 * nq + q : nullptr;
       CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
       const CT zc{};
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __res
     }
     PT inv[9];
     inverse3(a, inv);
-    if (TF && Dc) {
+    if (DS && Dc) {
 #pragma unroll
       for (int e = 0; e < 9; ++e) Dc[(size_t)(9 + e) * nq + q] = inv[e];
     } else {
@@ -585,7 +586,8 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
       r1 = fnms3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), t0, t1, t2, r1);
       r2 = fnms3(as_pt(B[6 * m], pz), as_pt(B[7 * m], pz), as_pt(B[8 * m], pz), t0, t1, t2, r2);
     }
-    constexpr bool dslot = MODE == 0 || MODE == 3;  // the modes that run with the per-slot inverses
+    // the modes that run with the per-slot inverses (FP64)
+    constexpr bool dslot = (MODE == 0 || MODE == 3) && std::is_same<PT, double>::value;
     const PT* D = dslot && Dc ? Dc + (size_t)colour * 9 * nq + q : Dinv + i;
     const long long md = dslot && Dc ? nq : n;
     y[3 * i] = (OT)(D[0] * r0 + D[md] * r1 + D[2 * md] * r2);
@@ -632,12 +634,15 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
   // and the pressure combination stage 2 reads
   const int grid = grid_for(colour_slots_host(g), 256);
   const PT wo = (PT)w_o, ww = (PT)w_w;
-  if constexpr (std::is_same<PT, double>::value) {
-    if (cp.tform) {  // T = J_bj D_j^-1 into the black copy, the inverses per colour slot
+  if (cp.tform) {  // T = J_bj D_j^-1 into the black copy (FP64: also the inverses per colour slot)
+    if (cp.kind == 2)
+      launch(k_ilu_setup_black<DT, PT, __nv_bfloat16, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
+             (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww,
+             (PT*)cp.dr);
+    else
       launch(k_ilu_setup_black<DT, PT, DT, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
              (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr);
-      return;
-    }
+    return;
   }
   if (cp.kind == 1)
     launch(k_ilu_setup_black<DT, PT, DT, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
@@ -657,14 +662,17 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
   const long long nq = colour_slots_host(g);
   const PT* Dc = (const PT*)cp.dr;  // the block inverses per colour slot (with the copies)
   const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
-  if constexpr (std::is_same<DT, double>::value) {
-    if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep (FP64 with the copies)
-      launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, (const DT*)cp.c[1], Dinv, Dc, Dwinv, f,
-             y);
-      launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, (const DT*)cp.c[0], Dinv, Dc, Dwinv, f,
-             y);
-      return 2;
+  if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep (with the copies)
+    if (cp.kind == 2) {
+      const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
+      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
+    } else {
+      const DT *c0 = (const DT*)cp.c[0], *c1 = (const DT*)cp.c[1];
+      launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+      launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
     }
+    return 2;
   }
   if (!fused) launch(k_ilu_red_diag<PT, OT, VT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
   // the black sweep, then the red one (with the well rows)

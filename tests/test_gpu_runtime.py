@@ -329,12 +329,12 @@ def test_krylov_lookahead_gives_identical_results(B, precision):
 def test_per_colour_copies_give_identical_results(B, precision, shape):
     """ilu_store = 1: the ILU(0) sweeps, stage 2 and the finest multigrid
     smoother read per-colour copies of their blocks and stencil (grids above
-    the single-block size, so the finest level runs as separate passes).  In
-    mixed precision a 3-step run is bit-identical to reading the natural
-    layout.  In FP64 the black sweep then goes through the set-up's products
-    J_bj D_j^-1 (another rounding order of the same ILU(0) solve): the same
-    cuts, Newton and Krylov totals within one iteration and 5%, and states
-    equal far inside the oracle's 1e-6 tolerance."""
+    the single-block size, so the finest level runs as separate passes), and
+    the black sweep goes through the set-up's products J_bj D_j^-1 (another
+    rounding order of the same ILU(0) solve): against the natural layout a
+    3-step run has the same cuts, Newton and Krylov totals within one
+    iteration and 5%, and states equal far inside the oracle's 1e-6
+    tolerance."""
     nx, ny, nz = shape
     sc = G.scenario_c1(nx=nx, ny=ny, nz=nz, n_steps=3)
     outs = []
@@ -344,10 +344,6 @@ def test_per_colour_copies_give_identical_results(B, precision, shape):
         rep = B.run_schedule(sim, B.Schedule(sc["schedule"], 3))
         outs.append((sim.get_x(), (rep.newton_iters, rep.krylov_iters, rep.cuts)))
         sim.close()
-    if precision == 1:
-        assert outs[0][1] == outs[1][1]
-        assert np.array_equal(outs[0][0], outs[1][0])
-        return
     (x0, (n0, k0, c0)), (x1, (n1, k1, c1)) = outs
     assert c0 == c1 and abs(n0 - n1) <= 1
     assert abs(k0 - k1) <= max(2, 0.05 * k0)
