@@ -170,7 +170,8 @@ SPMV_TRAFFIC = {("c3s", "fp64"): 1000.17e6, ("c3s", "mixed"): 520.75e6,
 # kernels) from the ncu captures summarised in profiles/ (300x225x30; the
 # 600x450x100 figures scale its bytes per cell by the cells); None where no
 # capture of the current kernels exists.
-PRECOND_TRAFFIC = {("c3", "fp64"): 1091.9 * 27_000_000, ("c3s", "fp64"): 2211.2e6}
+PRECOND_TRAFFIC = {("c3", "fp64"): 1091.9 * 27_000_000, ("c3", "mixed"): 441.9 * 27_000_000,
+                   ("c3s", "fp64"): 2211.2e6, ("c3s", "mixed"): 894.8e6}
 
 
 def max_over_ranks(values, dist, device="cpu"):

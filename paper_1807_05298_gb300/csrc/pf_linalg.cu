@@ -376,12 +376,14 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // black row's pressure combination w_o (oil row) + w_w (water row) of each of
 // its blocks for the CPR stage 2: pc [6 slots][3 columns][slots], pdg the
 // diagonal block's [3 columns][slots] (from J, before the Schur update).
+// Two blocks of 256 per SM (128 registers; FP64 spills up to 48 bytes a thread):
+// at 27M cells FP64 0.9 ms per set-up faster than one block at 254 registers.
 // With TF (with the copies), cblack receives T = J_bj D_j^-1 (all nine
 // entries; the oil row's polymer column of T is not zero) in place of J_bj,
 // and in FP64 Dc is read and written; otherwise Dc is ignored (compile-time
 // choices, so that each form keeps its own register count).
 template <typename DT, typename PT, typename CT, bool TF>
-__global__ void __launch_bounds__(256) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
+__global__ void __launch_bounds__(256, 2) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
                                                           PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
                                                           CT* __restrict__ pc, PT* __restrict__ pdg, PT w_o,
                                                           PT w_w, PT* __restrict__ Dc) {
