@@ -399,9 +399,9 @@ size_t carve(pf_sim* s, char* base) {
   if (ilu_kind < 0) ilu_kind = s->g.n >= 1000000 ? (s->mixed ? 2 : 1) : 0;  // automatic: pays off on large grids
   if (s->opts.stage1 != PF_S1_ILU0) ilu_kind = 0;
   // the block inverses by cell; in FP64 with the copies they are kept per
-  // colour slot instead (measured at 27M cells: FP64 preconditioner apply
-  // 6.30 -> 6.07 ms; in mixed precision both the fused black sweep and the
-  // set-up ran slower reading them that way, so there they stay by cell)
+  // colour slot instead (27M cells: preconditioner apply 6.30 -> 6.07 ms; in
+  // mixed precision the same layout measured slower in both ILU(0) forms
+  // although it moved fewer bytes, so there they stay by cell)
   const bool inv_by_slot = ilu_kind != 0 && !s->mixed;
   s->Dinv = inv_by_slot ? nullptr : c.take<char>(9 * (size_t)n * dts);
   s->Dwinv = c.take<char>((size_t)std::max(1, s->nw) * dts);
@@ -442,11 +442,10 @@ size_t carve(pf_sim* s, char* base) {
     const size_t es = kind == 2 ? 2 : dts;
     const size_t slots = (size_t)((s->g.nx + 1) / 2) * s->g.ny * s->g.nz;
     s->cpr.ilu_cp.kind = kind;
-    // with the copies: the black copy holds the set-up's J_bj D_j^-1 and the
-    // black sweep reads it (without the copies an extra array of them cost
-    // more in L2 residency than it saved: 100k cells FP64, preconditioner
+    // with the copies the black copy holds the set-up's J_bj D_j^-1, which the
+    // black sweep reads (below 1M cells, without the copies, an array of them
+    // cost more in L2 residency than it saved: 100k cells FP64, preconditioner
     // apply 123.7 -> 130 us)
-    s->cpr.ilu_cp.tform = kind != 0 ? 1 : 0;
     // the finest multigrid smoother's per-colour stencil copies follow the same size rule (any first stage)
     s->cpr.rb_copy = s->opts.ilu_store < 0 ? s->g.n >= 1000000 : s->opts.ilu_store != 0;
     for (int q = 0; q < 2; ++q) s->cpr.ilu_cp.c[q] = kind ? (void*)c.take<char>(54 * slots * es) : nullptr;
@@ -1826,7 +1825,7 @@ pf_status pf_autotune(pf_sim* s, pf_tuning* out) {
     s->cpr.block_rbgs0 = t.rbgs;
     // whole preconditioner applications: ILU(0) solve in two or three launches
     // (with the copies there is one form, through the set-up's products J_bj D_j^-1)
-    if (s->opts.stage1 == PF_S1_ILU0 && !s->cpr.ilu_cp.tform) {
+    if (s->opts.stage1 == PF_S1_ILU0 && s->cpr.ilu_cp.kind == 0) {
       static const int cand_fused[2] = {1, 0};
       t.ilu_fused = pick_interleaved(s, cand_fused, 2, 5, [&](int f) {
         s->cpr.ilu_fused = f;

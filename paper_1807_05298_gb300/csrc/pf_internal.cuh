@@ -212,26 +212,26 @@ template <typename DT, typename PT>
 void launch_bjacobi_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, PT* Dinv,
                           PT* Dwinv, cudaStream_t st);
 // Compact per-colour copies of the off-diagonal blocks for the ILU(0) sweeps:
-// kind 0 none (the sweeps read J), 1 in the Jacobian's precision, 2 BF16.
+// kind 0 none (the sweeps read J and the inverses by cell), 1 in the
+// Jacobian's precision, 2 BF16.
 struct IluCompact {
   int kind = 0;
-  void* c[2] = {nullptr, nullptr};  // red, black: [6 slots][9 entries][colour slots]
+  // [6 slots][9 entries][colour slots] per colour: c[0] the red cells' blocks,
+  // c[1] the black cells' products J_bj D_j^-1 with their red neighbours'
+  // inverses (formed by the set-up for the Schur update anyway), through which
+  // the black sweep takes f_j of the red neighbours, so the solve is two
+  // launches with no diagonal red sweep
+  void* c[2] = {nullptr, nullptr};
   // the black rows' pressure combination w_o (oil row) + w_w (water row) of
   // every block, for the CPR stage 2 (null without CPR): off-diagonal blocks
   // [6 slots][3 columns][black slots] in the copy's type, the diagonal block
   // [3 columns][black slots] in the preconditioner's type
   void* p = nullptr;
   void* pd = nullptr;
-  // the red cells' block inverses per red colour slot, [9 entries][red
-  // slots] in the preconditioner's type (the red diagonal sweep reads them
-  // instead of the natural-order lines that carry both colours); null: none
+  // FP64 with the copies: both colours' block inverses per colour slot, [9
+  // entries][red slots] then [9 entries][black slots] (in place of the by-cell
+  // array, whose lines carry both colours); null otherwise
   void* dr = nullptr;
-  // with the copies: c[1] holds the products J_bj D_j^-1 of each black
-  // cell's six blocks with its red neighbours' inverses (formed by the set-up
-  // for the Schur update anyway) instead of J_bj, and the solve is two
-  // launches: the black sweep takes f_j of the red neighbours through them,
-  // so there is no diagonal red sweep
-  int tform = 0;
 };
 // w_o, w_w: the CPR stage-2 weights (used when cp.p is set)
 template <typename DT, typename PT>

@@ -380,8 +380,8 @@ __device__ __forceinline__ __nv_bfloat16 to_ct(double v, __nv_bfloat16) { return
 // at 27M cells FP64 0.9 ms per set-up faster than one block at 254 registers.
 // With TF (with the copies), cblack receives T = J_bj D_j^-1 (all nine
 // entries; the oil row's polymer column of T is not zero) in place of J_bj,
-// and in FP64 Dc is read and written; otherwise Dc is ignored (compile-time
-// choices, so that each form keeps its own register count).
+// and in FP64 the inverses go through Dc; otherwise Dc is ignored
+// (compile-time choices, so that each form keeps its own register count).
 template <typename DT, typename PT, typename CT, bool TF>
 __global__ void __launch_bounds__(256, 2) k_ilu_setup_black(Grid g, const DT* __restrict__ J, PT* __restrict__ Dinv,
                                                           PT guard, CT* __restrict__ cred, CT* __restrict__ cblack,
@@ -411,8 +411,8 @@ __global__ void __launch_bounds__(256, 2) k_ilu_setup_black(Grid g, const DT* __
       const int so = (s & 1) ? s + 1 : s - 1;  // the slot of row c that points back at i
       // the red neighbour's colour slot (for its compact copies)
       const long long qc = nbr_slot(g, s, q, x);
-      const PT* Dj = DS && Dc ? Dc + qc : Dinv + c;  // D_j^-1
-      const long long md = DS && Dc ? nq : n;
+      const PT* Dj = DS ? Dc + qc : Dinv + c;  // D_j^-1
+      const long long md = DS ? nq : n;
       CT* bl = cblack ? cblack + (size_t)(s - 1) * 9 * nq + q : nullptr;
       CT* rd = cred ? cred + (size_t)(so - 1) * 9 * nq + qc : nullptr;
       const CT zc{};
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256, 2) k_ilu_setup_black(Grid g, const DT* __
     }
     PT inv[9];
     inverse3(a, inv);
-    if (DS && Dc) {
+    if (DS) {
 #pragma unroll
       for (int e = 0; e < 9; ++e) Dc[(size_t)(9 + e) * nq + q] = inv[e];
     } else {
@@ -535,9 +535,9 @@ __device__ __forceinline__ double as_pt(__nv_bfloat16 v, double) { return (doubl
 // folded in (t_j = D_j^-1 f_j formed on the fly), 3 the black sweep through
 // the set-up's products T = J_bj D_j^-1 (J_bj t_j = T f_j; J is then the
 // by-slot array of T).  One instantiation per mode
-// keeps each launch's code (and registers) to its own path.  The diagonal
-// block inverses come from Dc (both colours per colour slot, red then black)
-// when it is set (modes 0 and 3, the FP64 solve), else from Dinv by cell.
+// keeps each launch's code (and registers) to its own path.  In FP64 with
+// COMPACT (modes 3 and 0) the diagonal block inverses come from Dc (both
+// colours per colour slot, red then black), else from Dinv by cell.
 template <typename BT, typename PT, typename OT, bool COMPACT, typename VT, int MODE>
 __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* __restrict__ J,
                                                    const PT* __restrict__ Dinv, const PT* __restrict__ Dc,
@@ -588,10 +588,10 @@ __global__ void __launch_bounds__(256, 4) k_ilu_sweep(Grid g, int nw, const BT* 
       r1 = fnms3(as_pt(B[3 * m], pz), as_pt(B[4 * m], pz), as_pt(B[5 * m], pz), t0, t1, t2, r1);
       r2 = fnms3(as_pt(B[6 * m], pz), as_pt(B[7 * m], pz), as_pt(B[8 * m], pz), t0, t1, t2, r2);
     }
-    // the modes that run with the per-slot inverses (FP64)
-    constexpr bool dslot = (MODE == 0 || MODE == 3) && std::is_same<PT, double>::value;
-    const PT* D = dslot && Dc ? Dc + (size_t)colour * 9 * nq + q : Dinv + i;
-    const long long md = dslot && Dc ? nq : n;
+    // FP64 with the copies: the inverses per colour slot
+    constexpr bool dslot = COMPACT && std::is_same<PT, double>::value;
+    const PT* D = dslot ? Dc + (size_t)colour * 9 * nq + q : Dinv + i;
+    const long long md = dslot ? nq : n;
     y[3 * i] = (OT)(D[0] * r0 + D[md] * r1 + D[2 * md] * r2);
     y[3 * i + 1] = (OT)(D[3 * md] * r0 + D[4 * md] * r1 + D[5 * md] * r2);
     y[3 * i + 2] = (OT)(D[6 * md] * r0 + D[7 * md] * r1 + D[8 * md] * r2);
@@ -636,24 +636,14 @@ void launch_ilu_setup(const Grid& g, const Wells& w, const DT* J, const DT* Dw, 
   // and the pressure combination stage 2 reads
   const int grid = grid_for(colour_slots_host(g), 256);
   const PT wo = (PT)w_o, ww = (PT)w_w;
-  if (cp.tform) {  // T = J_bj D_j^-1 into the black copy (FP64: also the inverses per colour slot)
-    if (cp.kind == 2)
-      launch(k_ilu_setup_black<DT, PT, __nv_bfloat16, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
-             (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww,
-             (PT*)cp.dr);
-    else
-      launch(k_ilu_setup_black<DT, PT, DT, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
-             (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr);
-    return;
-  }
-  if (cp.kind == 1)
-    launch(k_ilu_setup_black<DT, PT, DT, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
-           (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr);
-  else if (cp.kind == 2)
-    launch(k_ilu_setup_black<DT, PT, __nv_bfloat16, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
+  if (cp.kind == 2)  // the copies: T = J_bj D_j^-1 into the black copy (FP64: the inverses per colour slot)
+    launch(k_ilu_setup_black<DT, PT, __nv_bfloat16, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard,
            (__nv_bfloat16*)cp.c[0], (__nv_bfloat16*)cp.c[1], (__nv_bfloat16*)cp.p, (PT*)cp.pd, wo, ww,
-           (PT*)nullptr);
-  else
+           (PT*)cp.dr);
+  else if (cp.kind == 1)
+    launch(k_ilu_setup_black<DT, PT, DT, true>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)cp.c[0],
+           (DT*)cp.c[1], (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)cp.dr);
+  else  // without the copies: the inverses by cell
     launch(k_ilu_setup_black<DT, PT, DT, false>, grid, 256, 0, st, g, J, Dinv, (PT)guard, (DT*)nullptr,
            (DT*)nullptr, (DT*)cp.p, (PT*)cp.pd, wo, ww, (PT*)nullptr);
 }
@@ -664,35 +654,24 @@ int launch_ilu_apply(const Grid& g, int nw, const DT* J, const PT* Dinv, const P
   const long long nq = colour_slots_host(g);
   const PT* Dc = (const PT*)cp.dr;  // the block inverses per colour slot (with the copies)
   const int grid1 = grid_for(nq, 256), grid0 = grid_for(nq + nw, 256);
-  if (cp.tform) {  // black sweep through T = J_bj D_j^-1, then the red sweep (with the copies)
-    if (cp.kind == 2) {
-      const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
-      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
-      launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
-    } else {
-      const DT *c0 = (const DT*)cp.c[0], *c1 = (const DT*)cp.c[1];
-      launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
-      launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
-    }
+  if (cp.kind == 2) {  // the copies: black sweep through T = J_bj D_j^-1, then the red sweep
+    const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
+    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
     return 2;
   }
-  if (!fused) launch(k_ilu_red_diag<PT, OT, VT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
-  // the black sweep, then the red one (with the well rows)
   if (cp.kind == 1) {
     const DT *c0 = (const DT*)cp.c[0], *c1 = (const DT*)cp.c[1];
-    if (fused) launch(k_ilu_sweep<DT, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
-    else launch(k_ilu_sweep<DT, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
+    launch(k_ilu_sweep<DT, PT, OT, true, VT, 3>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
     launch(k_ilu_sweep<DT, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
-  } else if (cp.kind == 2) {
-    const __nv_bfloat16 *c0 = (const __nv_bfloat16*)cp.c[0], *c1 = (const __nv_bfloat16*)cp.c[1];
-    if (fused) launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 2>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
-    else launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 1>, grid1, 256, 0, st, g, nw, c1, Dinv, Dc, Dwinv, f, y);
-    launch(k_ilu_sweep<__nv_bfloat16, PT, OT, true, VT, 0>, grid0, 256, 0, st, g, nw, c0, Dinv, Dc, Dwinv, f, y);
-  } else {
-    if (fused) launch(k_ilu_sweep<DT, PT, OT, false, VT, 2>, grid1, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
-    else launch(k_ilu_sweep<DT, PT, OT, false, VT, 1>, grid1, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
-    launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, (const PT*)nullptr, Dwinv, f, y);
+    return 2;
   }
+  // without the copies, from J: the diagonal red sweep folded into the black one or on its own, then the red sweep
+  const PT* none = nullptr;
+  if (!fused) launch(k_ilu_red_diag<PT, OT, VT>, grid_for(nq, 256), 256, 0, st, g, Dinv, f, y);
+  if (fused) launch(k_ilu_sweep<DT, PT, OT, false, VT, 2>, grid1, 256, 0, st, g, nw, J, Dinv, none, Dwinv, f, y);
+  else launch(k_ilu_sweep<DT, PT, OT, false, VT, 1>, grid1, 256, 0, st, g, nw, J, Dinv, none, Dwinv, f, y);
+  launch(k_ilu_sweep<DT, PT, OT, false, VT, 0>, grid0, 256, 0, st, g, nw, J, Dinv, none, Dwinv, f, y);
   return fused ? 2 : 3;
 }
 
