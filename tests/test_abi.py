@@ -73,3 +73,15 @@ def test_invalid_options_rejected(B):
     with pytest.raises(B.PfError) as e:
         B.Simulator(_model(), krylov_lookahead=2)
     assert e.value.status == B.PF_EINVAL and "krylov_lookahead" in str(e.value)
+
+
+def test_tuning_calls_reject_null_arguments_without_gpu(B):
+    """pf_get_tuning, pf_set_tuning and pf_autotune refuse a NULL simulator
+    (and pf_get_tuning a NULL output) with PF_EINVAL before any CUDA call."""
+    import ctypes as C
+    L = B.lib()
+    t = B.pf_tuning()
+    assert L.pf_get_tuning(None, C.byref(t)) == B.PF_EINVAL
+    assert L.pf_set_tuning(None, C.byref(t)) == B.PF_EINVAL
+    assert L.pf_autotune(None, C.byref(t)) == B.PF_EINVAL
+    assert L.pf_get_tuning(None, None) == B.PF_EINVAL
